@@ -1,0 +1,212 @@
+/*
+ * C-ABI of the GB300 (sm_103a) library for V-filtration cubical persistence
+ * over F2 on float32 2D images and 3D volumes: the H0 pairs and the
+ * top-dimension pairs (H1 in 2D, H2 in 3D), after local pruning through the
+ * neighbourhood lookup table.  Method: arXiv 2606.04801, Sec. 2-4 and
+ * Appendix A (H0 by elder-rule union-find on vertices and edges, Sec. 4.1
+ * step 3 / Sec. 4.2 step 2; top dimension by union-find on the dual graph of
+ * top cells plus one outside vertex, Sec. 3.1 and Appendix A; pruning,
+ * Sec. 3.2; lookup table, Sec. 3.3).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Images are C-order float32: (H, W) in 2D, (D, H, W) in 3D.  Every axis
+ *    must be at least 2 long, every value finite.  -0.0 is read as +0.0.
+ *  - Pixels are ordered by (value, linear index) (first-order tie-break);
+ *    cells of one lower star by (dimension, doubled-grid index)
+ *    (second-order tie-break).
+ *  - A cell is named by its index in the doubled grid of its item: the cell
+ *    with doubled coordinates (Z, Y, X) (Z = 0 in 2D) has index
+ *    (Z*(2H-1) + Y)*(2W-1) + X; its dimension is the number of odd
+ *    coordinates.  A pixel is named by its linear index in its item.
+ *  - Limits per call: at most CP_MAX_ITEMS items; at most 2^27 pixels in
+ *    total over all items; every doubled grid below 2^31 cells.
+ *  - Memory: the caller owns every buffer and the stream.  Pointers marked
+ *    d_ are device pointers, h_ host pointers.  The library allocates no
+ *    device memory; it needs one caller-provided workspace whose size the
+ *    *_workspace_size functions return.  Nothing is printed, nothing aborts.
+ *  - Synchronisation: the work is enqueued on `stream`.  When h_out_count is
+ *    non-NULL the call waits for the stream once, to read the pair count and
+ *    the status word back; with h_out_count == NULL it returns right after
+ *    enqueueing, d_out_count (if non-NULL) receives the count on the device,
+ *    and cubical_persistence_status() reads the status later.
+ *  - Return value: CP_OK (0) or a negative CP_ERR_* code.
+ */
+#ifndef CUBICAL_PERSISTENCE_H
+#define CUBICAL_PERSISTENCE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CP_MAX_ITEMS 128
+
+enum {
+    CP_OK = 0,
+    CP_ERR_ARG = -1,       /* null pointer, axis < 2, too many pixels or items, bad sizes */
+    CP_ERR_NONFINITE = -2, /* NaN or +-inf in an input image */
+    CP_ERR_CAPACITY = -3,  /* an output or workspace capacity was too small; counts are still reported */
+    CP_ERR_CUDA = -4,      /* a CUDA runtime call failed */
+    CP_ERR_TIMEOUT = -5,   /* a bounded device-side wait gave up */
+    CP_ERR_INTERNAL = -6   /* an internal consistency check failed */
+};
+
+/*
+ * One persistence pair (32 bytes).
+ *  birth, death   : values copied from the input (-0.0 reported as +0.0);
+ *                   death = +inf for the essential H0 class.
+ *  birth_cell     : doubled-grid index of the positive cell (a vertex for
+ *                   H0, a facet for the top dimension).
+ *  death_cell     : doubled-grid index of the negative cell (an edge for H0,
+ *                   a top cell for the top dimension); -1 if essential.
+ *  birth_pixel,
+ *  death_pixel    : the pixel that gives the cell its value (its largest
+ *                   vertex under (value, index)); -1 if essential.
+ *  dim            : 0, or the top homology dimension (1 in 2D, 2 in 3D).
+ *  item           : index of the item in a batched call (0 otherwise).
+ * Only pairs with birth != death are reported (Sec. 2.3), sorted by
+ * (item, dim, birth_cell).
+ */
+typedef struct cp_pair {
+    float birth, death;
+    int32_t birth_cell, death_cell;
+    int32_t birth_pixel, death_pixel;
+    int32_t dim, item;
+} cp_pair;
+
+/* Per-call counters, filled by cubical_persistence_stats(). */
+typedef struct cp_stats {
+    int64_t n_pixels;
+    int64_t h0_survivors;     /* edges left for the H0 union-find after pruning */
+    int64_t top_survivors;    /* facets left for the dual union-find after pruning */
+    int64_t h0_roots;         /* local minima (roots of the H0 forest) */
+    int64_t top_roots;        /* top cells left as roots of the dual forest */
+    int64_t h0_rounds;        /* rounds of the H0 union-find */
+    int64_t top_rounds;       /* rounds of the dual union-find */
+    int64_t pairs;            /* reported pairs (nonzero persistence + essential) */
+    uint32_t status;          /* raw device status bits */
+    uint32_t pad;
+} cp_stats;
+
+/* ---------------------------------------------------------------- info */
+
+/* Library version (major*10000 + minor*100 + patch). */
+int cp_version(void);
+
+/* Human-readable name of a CP_* code; never NULL. */
+const char *cp_error_string(int code);
+
+/*
+ * Number of relevant neighbourhood configurations of the lookup table
+ * (Sec. 3.3): 47 for ndim = 2, 15,935 for ndim = 3; -1 for another ndim.
+ * Host only; needs no GPU.
+ */
+int cp_lut_num_classes(int ndim);
+
+/*
+ * Lookup-table entry of a raw lower-neighbour mask (host only, for tests).
+ * raw: bit n set when the neighbour at offset n precedes the vertex, with
+ * n = 9(dz+1)+3(dy+1)+(dx+1) in 3D (bit 13 ignored) and n = 3(dy+1)+(dx+1)
+ * in 2D (bit 4 ignored).  *relevant receives the collapsed mask, *entry the
+ * 64-bit entry (layout documented in the library source).  Returns CP_OK or
+ * CP_ERR_ARG.
+ */
+int cp_lut_lookup(int ndim, uint32_t raw, uint32_t *relevant, uint64_t *entry);
+
+/* ---------------------------------------------------------------- forward */
+
+/*
+ * Workspace bytes for one image (ndim 2 or 3, dims as for the image).
+ * max_survivors bounds the edges (and, separately, the facets and the roots)
+ * that survive pruning; 0 picks the default N/2 + 65536, which covers
+ * i.i.d. noise and smoother inputs.  Adversarial inputs (checkerboards) may
+ * need up to 2.5 N in 3D; a call that runs out returns CP_ERR_CAPACITY with
+ * the required counts in cubical_persistence_stats().  Returns 0 on bad
+ * arguments.
+ */
+size_t cubical_persistence_workspace_size(int ndim, const int64_t *dims, int64_t max_survivors);
+
+/*
+ * Persistence pairs of one 2D image (dims = {H, W}) (Sec. 4.1: lookup ->
+ * local pruning -> H0 union-find -> cross-pruning -> H1 dual union-find).
+ *  d_image     : device, H*W float32, read only.
+ *  d_out_pairs : device, capacity entries, written with the sorted pairs.
+ *  capacity    : entries available in d_out_pairs; H*W + (H-1)(W-1) + 1
+ *                always suffices.
+ *  h_out_count : host, optional: receives the number of pairs (may exceed
+ *                capacity: then CP_ERR_CAPACITY and the first `capacity`
+ *                pairs are not guaranteed).  Makes the call synchronous.
+ *  d_out_count : device, optional int64: receives the count on the device.
+ *  d_workspace : device, ws_bytes >= cubical_persistence_workspace_size().
+ *  stream      : a cudaStream_t (NULL = legacy default stream).
+ */
+int cubical_persistence_2d(const float *d_image, const int64_t dims[2], cp_pair *d_out_pairs, int64_t capacity,
+                           int64_t *h_out_count, int64_t *d_out_count, void *d_workspace, size_t ws_bytes,
+                           int64_t max_survivors, void *stream);
+
+/*
+ * Persistence pairs of one 3D volume (dims = {D, H, W}) (Sec. 4.2 steps 1-3:
+ * lookup -> H0 prune + union-find -> H2 prune + dual union-find).
+ * Arguments as for cubical_persistence_2d; capacity D*H*W +
+ * (D-1)(H-1)(W-1) + 1 always suffices.
+ */
+int cubical_persistence_3d(const float *d_image, const int64_t dims[3], cp_pair *d_out_pairs, int64_t capacity,
+                           int64_t *h_out_count, int64_t *d_out_count, void *d_workspace, size_t ws_bytes,
+                           int64_t max_survivors, void *stream);
+
+/*
+ * Batched form: n_items independent images and volumes of any sizes in one
+ * pass (one lookup pass, one sort and one union-find per dimension for the
+ * whole batch; unions never cross items).
+ *  h_images : host array of n_items device pointers.
+ *  ndims    : host array, 2 or 3 per item.
+ *  dims     : host array of 3*n_items extents: (D, H, W) per item, D ignored
+ *             (set to 1) for 2D items.
+ * Pairs carry their item index and item-local cells and pixels.  The other
+ * arguments are as for the single-image calls.
+ */
+size_t cubical_persistence_batched_workspace_size(int n_items, const int32_t *ndims, const int64_t *dims,
+                                                  int64_t max_survivors);
+int cubical_persistence_batched(int n_items, const float *const *h_images, const int32_t *ndims,
+                                const int64_t *dims, cp_pair *d_out_pairs, int64_t capacity, int64_t *h_out_count,
+                                int64_t *d_out_count, void *d_workspace, size_t ws_bytes, int64_t max_survivors,
+                                void *stream);
+
+/*
+ * Counters and status of the last call that used this workspace (waits for
+ * `stream`).  Returns the CP_* code the call would report.
+ */
+int cubical_persistence_stats(const void *d_workspace, cp_stats *h_stats, void *stream);
+
+/* ---------------------------------------------------------------- backward */
+
+/*
+ * Gradient of a loss L(birth, death) with respect to the image pixels.
+ * Each birth (death) value is a copy of one pixel, its birth_pixel
+ * (death_pixel), so dL/dx[p] is the sum of dL/dbirth over the pairs born at
+ * p plus the sum of dL/ddeath over the pairs that die at p.  Essential
+ * deaths (death_pixel = -1) contribute nothing.
+ *  d_pairs        : device, n_pairs pairs as returned by a forward call.
+ *  d_grad_birth,
+ *  d_grad_death   : device, n_pairs float32 each (dL/dbirth, dL/ddeath).
+ *  d_item_offsets : device, int64 per item: offset of the item's first pixel
+ *                   in d_grad_image (NULL for a single image).
+ *  d_grad_image   : device, n_pixels float32, overwritten (zeros where no
+ *                   pair lands).
+ *  d_workspace    : device, cubical_persistence_backward_workspace_size()
+ *                   bytes (double-precision accumulators).
+ * Sums are accumulated in double precision and rounded once to float32.
+ */
+size_t cubical_persistence_backward_workspace_size(int64_t n_pixels);
+int cubical_persistence_backward(const cp_pair *d_pairs, int64_t n_pairs, const float *d_grad_birth,
+                                 const float *d_grad_death, const int64_t *d_item_offsets, float *d_grad_image,
+                                 int64_t n_pixels, void *d_workspace, size_t ws_bytes, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CUBICAL_PERSISTENCE_H */

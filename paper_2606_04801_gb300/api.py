@@ -1,0 +1,216 @@
+"""PyTorch-facing API.  PyTorch supplies device memory and streams; every
+step of the computation runs in the library's CUDA kernels.
+
+    d = persistence(img)               # img: CUDA float32 (H, W) or (D, H, W)
+    d.birth, d.death, d.dim, ...       # views of the pairs on the device
+    d.numpy()                          # structured array (cp_pair layout)
+
+    ds = persistence_batched([img0, vol1, ...])   # pairs carry `item`
+
+    birth, death, dim = diagram(img)   # differentiable in img (autograd)
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+from typing import Optional, Sequence
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import CP_ERR_CAPACITY, CP_OK, CpError, CpStats, PAIR_DTYPE
+
+
+def _stream_ptr(device) -> int:
+    return int(torch.cuda.current_stream(device).cuda_stream)
+
+
+def _check_image(img: torch.Tensor):
+    if not isinstance(img, torch.Tensor) or not img.is_cuda:
+        raise TypeError("image must be a CUDA tensor")
+    if img.dtype != torch.float32:
+        raise TypeError("image must be float32")
+    if img.dim() not in (2, 3):
+        raise ValueError("image must be 2D (H, W) or 3D (D, H, W)")
+    if any(s < 2 for s in img.shape):
+        raise ValueError("every axis must be at least 2 long")
+
+
+@dataclass
+class Diagram:
+    """Persistence pairs on the device: raw is an int32 (P, 8) view of cp_pair records."""
+
+    raw: torch.Tensor
+    stats: Optional[dict] = None
+
+    def __len__(self):
+        return int(self.raw.shape[0])
+
+    @property
+    def birth(self):
+        return self.raw[:, 0].view(torch.float32)
+
+    @property
+    def death(self):
+        return self.raw[:, 1].view(torch.float32)
+
+    @property
+    def birth_cell(self):
+        return self.raw[:, 2]
+
+    @property
+    def death_cell(self):
+        return self.raw[:, 3]
+
+    @property
+    def birth_pixel(self):
+        return self.raw[:, 4]
+
+    @property
+    def death_pixel(self):
+        return self.raw[:, 5]
+
+    @property
+    def dim(self):
+        return self.raw[:, 6]
+
+    @property
+    def item(self):
+        return self.raw[:, 7]
+
+    def numpy(self) -> np.ndarray:
+        return self.raw.contiguous().cpu().numpy().view(PAIR_DTYPE).reshape(-1)
+
+
+def _stats(ws: torch.Tensor) -> dict:
+    st = CpStats()
+    _lib.load().cubical_persistence_stats(ctypes.c_void_p(ws.data_ptr()), ctypes.byref(st), ctypes.c_void_p(_stream_ptr(ws.device)))
+    return {k: int(getattr(st, k)) for k, _ in CpStats._fields_ if k != "pad"}
+
+
+def _grow(st: dict, ms: int, n_total: int) -> int:
+    need = max(st["h0_survivors"], st["top_survivors"], 2 * st["h0_roots"], 2 * st["top_roots"], ms)
+    return int(need * 1.25) + 65536
+
+
+def persistence(img: torch.Tensor, max_survivors: int = 0, with_stats: bool = False) -> Diagram:
+    """Exact H0 and top-dimension pairs of one image or volume (sorted by (dim, birth cell))."""
+    _check_image(img)
+    lib = _lib.load()
+    img = img.contiguous()
+    nd = img.dim()
+    dims = (ctypes.c_int64 * nd)(*img.shape)
+    n = img.numel()
+    fn = lib.cubical_persistence_2d if nd == 2 else lib.cubical_persistence_3d
+    ms = int(max_survivors)
+    for _ in range(4):
+        ws_bytes = lib.cubical_persistence_workspace_size(nd, dims, ms)
+        if ws_bytes == 0:
+            raise CpError(_lib.CP_ERR_ARG, "workspace size")
+        ws = torch.empty(ws_bytes, dtype=torch.uint8, device=img.device)
+        eff = ms if ms > 0 else n // 2 + 65536
+        cap = min(n + int(np.prod([s - 1 for s in img.shape])) + 1, eff + 4096)
+        out = torch.empty((cap, 8), dtype=torch.int32, device=img.device)
+        cnt = ctypes.c_int64(0)
+        rc = fn(
+            ctypes.c_void_p(img.data_ptr()), dims, ctypes.c_void_p(out.data_ptr()), cap, ctypes.byref(cnt), None,
+            ctypes.c_void_p(ws.data_ptr()), ws_bytes, ms, ctypes.c_void_p(_stream_ptr(img.device)),
+        )
+        if rc == CP_ERR_CAPACITY:
+            ms = _grow(_stats(ws), eff, n)
+            continue
+        if rc != CP_OK:
+            raise CpError(rc, "cubical_persistence")
+        return Diagram(out[: cnt.value], _stats(ws) if with_stats else None)
+    raise CpError(CP_ERR_CAPACITY, "cubical_persistence (after growing the workspace)")
+
+
+def persistence_batched(imgs: Sequence[torch.Tensor], max_survivors: int = 0, with_stats: bool = False) -> Diagram:
+    """Pairs of many images and volumes in one pass; each pair carries its item index."""
+    if not imgs:
+        raise ValueError("empty batch")
+    lib = _lib.load()
+    imgs = [im.contiguous() for im in imgs]
+    for im in imgs:
+        _check_image(im)
+    dev = imgs[0].device
+    k = len(imgs)
+    if k > _lib.CP_MAX_ITEMS:
+        raise ValueError(f"at most {_lib.CP_MAX_ITEMS} items per call")
+    ptrs = (ctypes.c_void_p * k)(*[im.data_ptr() for im in imgs])
+    ndims = (ctypes.c_int32 * k)(*[im.dim() for im in imgs])
+    flat = []
+    for im in imgs:
+        flat += ([1] + list(im.shape)) if im.dim() == 2 else list(im.shape)
+    dims = (ctypes.c_int64 * (3 * k))(*flat)
+    n = sum(im.numel() for im in imgs)
+    t = sum(int(np.prod([s - 1 for s in im.shape])) + 1 for im in imgs)
+    ms = int(max_survivors)
+    for _ in range(4):
+        ws_bytes = lib.cubical_persistence_batched_workspace_size(k, ndims, dims, ms)
+        if ws_bytes == 0:
+            raise CpError(_lib.CP_ERR_ARG, "batched workspace size")
+        ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
+        eff = ms if ms > 0 else n // 2 + 65536
+        cap = min(n + t, eff + 2 * k + 4096)
+        out = torch.empty((cap, 8), dtype=torch.int32, device=dev)
+        cnt = ctypes.c_int64(0)
+        rc = lib.cubical_persistence_batched(
+            k, ptrs, ndims, dims, ctypes.c_void_p(out.data_ptr()), cap, ctypes.byref(cnt), None,
+            ctypes.c_void_p(ws.data_ptr()), ws_bytes, ms, ctypes.c_void_p(_stream_ptr(dev)),
+        )
+        if rc == CP_ERR_CAPACITY:
+            ms = _grow(_stats(ws), eff, n)
+            continue
+        if rc != CP_OK:
+            raise CpError(rc, "cubical_persistence_batched")
+        return Diagram(out[: cnt.value], _stats(ws) if with_stats else None)
+    raise CpError(CP_ERR_CAPACITY, "cubical_persistence_batched (after growing the workspace)")
+
+
+def pairs_backward(raw: torch.Tensor, grad_birth: torch.Tensor, grad_death: torch.Tensor, n_pixels: int,
+                   item_offsets: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """dL/dimage (flat, float32) from dL/dbirth and dL/ddeath of each pair."""
+    lib = _lib.load()
+    dev = raw.device
+    gb = grad_birth.contiguous().to(torch.float32)
+    gd = grad_death.contiguous().to(torch.float32)
+    grad = torch.empty(n_pixels, dtype=torch.float32, device=dev)
+    ws_bytes = lib.cubical_persistence_backward_workspace_size(n_pixels)
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
+    offs = None if item_offsets is None else ctypes.c_void_p(item_offsets.data_ptr())
+    rc = lib.cubical_persistence_backward(
+        ctypes.c_void_p(raw.data_ptr()), raw.shape[0], ctypes.c_void_p(gb.data_ptr()), ctypes.c_void_p(gd.data_ptr()),
+        offs, ctypes.c_void_p(grad.data_ptr()), n_pixels, ctypes.c_void_p(ws.data_ptr()), ws_bytes,
+        ctypes.c_void_p(_stream_ptr(dev)),
+    )
+    if rc != CP_OK:
+        raise CpError(rc, "cubical_persistence_backward")
+    return grad
+
+
+class _DiagramFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, img, max_survivors):
+        d = persistence(img.detach(), max_survivors)
+        ctx.save_for_backward(d.raw)
+        ctx.shape = img.shape
+        ctx.mark_non_differentiable(d.raw)
+        return d.birth.clone(), d.death.clone(), d.raw
+
+    @staticmethod
+    def backward(ctx, gb, gd, _graw):
+        (raw,) = ctx.saved_tensors
+        n = int(np.prod(ctx.shape))
+        if gb is None:
+            gb = torch.zeros(raw.shape[0], dtype=torch.float32, device=raw.device)
+        if gd is None:
+            gd = torch.zeros(raw.shape[0], dtype=torch.float32, device=raw.device)
+        g = pairs_backward(raw, gb, gd, n)
+        return g.view(ctx.shape), None
+
+
+def diagram(img: torch.Tensor, max_survivors: int = 0):
+    """(birth, death, raw): birth and death are differentiable in img."""
+    return _DiagramFn.apply(img, max_survivors)

@@ -1,0 +1,427 @@
+// C-ABI entry points: argument checks, workspace layout, lookup-table set-up
+// and the enqueueing of the pipeline
+//   init -> K1 prune -> K2 sort (H0) -> K3 H0 union-find (+ 2D cross-pruning)
+//        -> K2 sort (dual) -> K3 dual union-find -> essential pairs
+//        -> K2 sort (pairs, canonical order) -> gather.
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "cp_common.cuh"
+#include "cp_kernels.h"
+#include "cp_lut.h"
+
+namespace cp {
+
+namespace {
+
+std::mutex g_mu;
+bool g_lut_built = false;
+std::vector<uint64_t> g_lut2d;
+Lut3D g_lut3d;
+int g_lut2d_classes = 0;
+uint64_t g_dev_ready = 0;  // bit d set once device d holds the tables
+
+bool build_host_luts() {
+    if (g_lut_built) return true;
+    build_lut2d(g_lut2d, &g_lut2d_classes);
+    if (!build_lut3d(g_lut3d)) return false;
+    g_lut_built = true;
+    return true;
+}
+
+int ensure_device_tables() {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!build_host_luts()) return CP_ERR_INTERNAL;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return CP_ERR_CUDA;
+    if (dev < 64 && (g_dev_ready >> dev) & 1u) return CP_OK;
+    if (upload_luts(g_lut2d.data(), g_lut3d.disp.data(), g_lut3d.entry.data()) != cudaSuccess) return CP_ERR_CUDA;
+    if (dev < 64) g_dev_ready |= 1ull << dev;
+    return CP_OK;
+}
+
+struct Plan {
+    ItemTable tab;
+    int64_t ntot = 0, ttot = 0;
+    uint32_t cap_s = 0, cap_r0 = 0, cap_rt = 0, cap_p = 0, cap_big = 0;
+    // byte offsets into the workspace
+    size_t o_ctr, o_uf0, o_uft, o_s0, o_st, o_salt, o_age0, o_res0, o_aget, o_rest;
+    size_t o_act0, o_act1, o_yn, o_on, o_yr, o_pairs, o_pvals, o_pvalt, o_hist, o_status;
+    size_t bytes = 0;
+};
+
+size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
+
+int make_plan(int n_items, const int32_t* ndims, const int64_t* dims, const float* const* imgs,
+              int64_t max_survivors, Plan& P) {
+    if (n_items <= 0 || n_items > kMaxItems || !ndims || !dims) return CP_ERR_ARG;
+    std::memset(&P.tab, 0, sizeof(P.tab));
+    P.tab.n = n_items;
+    // table order: 2D items first, then 3D items, each in the caller's order
+    std::vector<int> order;
+    for (int k = 0; k < 2; ++k)
+        for (int i = 0; i < n_items; ++i)
+            if (ndims[i] == (k == 0 ? 2 : 3)) order.push_back(i);
+    if (int(order.size()) != n_items) return CP_ERR_ARG;
+    int64_t voff = 0, toff = 0, edges = 0, facets = 0;
+    int32_t t2 = 0, t3 = 0;
+    for (int j = 0; j < n_items; ++j) {
+        int i = order[j];
+        Item& it = P.tab.it[j];
+        it.ndim = ndims[i];
+        it.D = it.ndim == 3 ? int32_t(dims[3 * i]) : 1;
+        it.H = int32_t(dims[3 * i + 1]);
+        it.W = int32_t(dims[3 * i + 2]);
+        int64_t D = it.ndim == 3 ? dims[3 * i] : 1, H = dims[3 * i + 1], W = dims[3 * i + 2];
+        if (H < 2 || W < 2 || (it.ndim == 3 && D < 2)) return CP_ERR_ARG;
+        if (H > (1 << 27) || W > (1 << 27) || D > (1 << 27)) return CP_ERR_ARG;
+        int64_t N = D * H * W;
+        int64_t G = (2 * D - 1) * (2 * H - 1) * (2 * W - 1);
+        if (N > (int64_t(1) << kVBits) || G >= (int64_t(1) << 31)) return CP_ERR_ARG;
+        it.img = imgs ? imgs[i] : nullptr;
+        if (imgs && !imgs[i]) return CP_ERR_ARG;
+        it.voff = voff;
+        it.toff = toff;
+        it.T = (it.ndim == 3 ? D - 1 : 1) * (H - 1) * (W - 1);
+        it.user = i;
+        voff += N;
+        toff += it.T + 1;
+        if (it.ndim == 2) {
+            it.tx = int32_t((W + prune_tile_x() - 1) / prune_tile_x());
+            it.ty = int32_t((H + prune_tile_y2d() - 1) / prune_tile_y2d());
+            it.tz = 1;
+            it.tile0 = t2;
+            t2 += it.tx * it.ty;
+            P.tab.n2d++;
+            edges += H * (W - 1) + (H - 1) * W;
+            facets += H * (W - 1) + (H - 1) * W;
+        } else {
+            it.tx = int32_t((W + prune_tile_x() - 1) / prune_tile_x());
+            it.ty = int32_t((H + prune_tile_y3d() - 1) / prune_tile_y3d());
+            it.tz = int32_t((D + prune_tile_z3d() - 1) / prune_tile_z3d());
+            it.tile0 = t3;
+            t3 += it.tx * it.ty * it.tz;
+            P.tab.n3d++;
+            edges += D * H * (W - 1) + D * (H - 1) * W + (D - 1) * H * W;
+            facets += D * (H - 1) * (W - 1) + (D - 1) * H * (W - 1) + (D - 1) * (H - 1) * W;
+        }
+        if (voff > (int64_t(1) << kVBits) || toff > (int64_t(1) << kVBits) + kMaxItems) return CP_ERR_ARG;
+    }
+    P.tab.tiles2d = t2;
+    P.tab.tiles3d = t3;
+    P.ntot = voff;
+    P.ttot = toff;
+    int64_t ms = max_survivors > 0 ? max_survivors : voff / 2 + 65536;
+    ms = std::min<int64_t>(ms, std::max(edges, facets) + 1);
+    ms = std::min<int64_t>(ms, int64_t(0x7FFFFFFF));
+    P.cap_s = uint32_t(ms);
+    P.cap_r0 = uint32_t(std::min<int64_t>(ms / 2 + n_items + 1024, voff + 1));
+    P.cap_rt = uint32_t(std::min<int64_t>(ms / 2 + n_items + 1024, toff + 1));
+    P.cap_p = P.cap_r0 + P.cap_rt;
+    P.cap_big = std::max(P.cap_s, P.cap_p);
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        size_t at = o;
+        o = align_up(o + bytes);
+        return at;
+    };
+    P.o_ctr = take(sizeof(Counters));
+    P.o_uf0 = take(sizeof(uint32_t) * size_t(P.ntot));
+    P.o_uft = take(sizeof(uint32_t) * size_t(P.ttot));
+    P.o_s0 = take(sizeof(uint64_t) * P.cap_big);
+    P.o_st = take(sizeof(uint64_t) * P.cap_s);
+    P.o_salt = take(sizeof(uint64_t) * P.cap_big);
+    P.o_age0 = take(sizeof(uint64_t) * P.cap_r0);
+    P.o_res0 = take(sizeof(uint64_t) * P.cap_r0);
+    P.o_aget = take(sizeof(uint64_t) * P.cap_rt);
+    P.o_rest = take(sizeof(uint64_t) * P.cap_rt);
+    P.o_act0 = take(sizeof(uint32_t) * P.cap_big);
+    P.o_act1 = take(sizeof(uint32_t) * P.cap_big);
+    P.o_yn = take(sizeof(uint32_t) * P.cap_s);
+    P.o_on = take(sizeof(uint32_t) * P.cap_s);
+    P.o_yr = take(sizeof(uint32_t) * P.cap_s);
+    P.o_pairs = take(sizeof(cp_pair) * P.cap_p);
+    P.o_pvals = P.o_act0;  // the active lists are dead once both union-finds are done
+    P.o_pvalt = P.o_act1;
+    P.o_hist = take(sizeof(uint32_t) * 8 * 256);
+    P.o_status = take(sizeof(uint64_t) * sort_status_words(P.cap_big));
+    P.bytes = o;
+    return CP_OK;
+}
+
+template <class T>
+T* at(void* ws, size_t off) {
+    return reinterpret_cast<T*>(static_cast<char*>(ws) + off);
+}
+
+int status_to_code(uint32_t st) {
+    if (st & kStNonfinite) return CP_ERR_NONFINITE;
+    if (st & kStTimeout) return CP_ERR_TIMEOUT;
+    if (st & kStCapacity) return CP_ERR_CAPACITY;
+    if (st & kStInternal) return CP_ERR_INTERNAL;
+    return CP_OK;
+}
+
+int run(const Plan& P, cp_pair* d_out, int64_t capacity, int64_t* h_out_count, int64_t* d_out_count, void* ws,
+        size_t ws_bytes, cudaStream_t s) {
+    if (!ws || ws_bytes < P.bytes || (!d_out && capacity > 0) || capacity < 0) return CP_ERR_ARG;
+    int rc = ensure_device_tables();
+    if (rc != CP_OK) return rc;
+    Counters* ctr = at<Counters>(ws, P.o_ctr);
+    uint32_t* uf0 = at<uint32_t>(ws, P.o_uf0);
+    uint32_t* uft = at<uint32_t>(ws, P.o_uft);
+    uint64_t* s0 = at<uint64_t>(ws, P.o_s0);
+    uint64_t* st = at<uint64_t>(ws, P.o_st);
+    uint64_t* salt = at<uint64_t>(ws, P.o_salt);
+    uint64_t* age0 = at<uint64_t>(ws, P.o_age0);
+    uint64_t* res0 = at<uint64_t>(ws, P.o_res0);
+    uint64_t* aget = at<uint64_t>(ws, P.o_aget);
+    uint64_t* rest = at<uint64_t>(ws, P.o_rest);
+    uint32_t* act0 = at<uint32_t>(ws, P.o_act0);
+    uint32_t* act1 = at<uint32_t>(ws, P.o_act1);
+    cp_pair* pairs = at<cp_pair>(ws, P.o_pairs);
+    uint32_t* hist = at<uint32_t>(ws, P.o_hist);
+    uint64_t* status = at<uint64_t>(ws, P.o_status);
+
+#define CP_TRY(x)                                  \
+    do {                                           \
+        if ((x) != cudaSuccess) return CP_ERR_CUDA; \
+    } while (0)
+    CP_TRY(cudaMemsetAsync(ctr, 0, sizeof(Counters), s));
+    CP_TRY(cudaMemsetAsync(status, 0, sizeof(uint64_t) * sort_status_words(P.cap_big), s));
+    CP_TRY(launch_init(P.tab, ctr, uft, aget, rest, s));
+
+    PruneOuts po;
+    po.uf0 = uf0;
+    po.uft = uft;
+    po.s0 = s0;
+    po.st = st;
+    po.age0 = age0;
+    po.res0 = res0;
+    po.aget = aget;
+    po.rest = rest;
+    po.cap_s = P.cap_s;
+    po.cap_r0 = P.cap_r0;
+    po.cap_rt = P.cap_rt;
+    po.ctr = ctr;
+    CP_TRY(launch_prune(P.tab, po, s));
+
+    SortBufs sb;
+    sb.keys = s0;
+    sb.keys_alt = salt;
+    sb.vals = nullptr;
+    sb.vals_alt = nullptr;
+    sb.d_count = &ctr->n_s0;
+    sb.cap = P.cap_s;
+    sb.hist = hist;
+    sb.status = status;
+    sb.tile_ctr = ctr->sort_tile;
+    sb.ctr = ctr;
+    CP_TRY(sort_keys(sb, 0, 8, 1, s));
+
+    UfParams up;
+    up.keys = s0;
+    up.d_nkeys = &ctr->n_s0;
+    up.cap_keys = P.cap_s;
+    up.uf = uf0;
+    up.age = age0;
+    up.res = res0;
+    up.act[0] = act0;
+    up.act[1] = act1;
+    up.ynode = at<uint32_t>(ws, P.o_yn);
+    up.onode = at<uint32_t>(ws, P.o_on);
+    up.yrid = at<uint32_t>(ws, P.o_yr);
+    up.pairs = pairs;
+    up.pair_cap = P.cap_p;
+    up.dual_keys = st;
+    up.d_ndual = &ctr->n_st;
+    up.dual_cap = P.cap_s;
+    up.ctr = ctr;
+    up.dual = 0;
+    CP_TRY(launch_uf(P.tab, up, s));
+
+    sb.keys = st;
+    sb.d_count = &ctr->n_st;
+    sb.tile_ctr = ctr->sort_tile + 8;
+    CP_TRY(sort_keys(sb, 0, 8, 9, s));
+
+    up.keys = st;
+    up.d_nkeys = &ctr->n_st;
+    up.uf = uft;
+    up.age = aget;
+    up.res = rest;
+    up.dual_keys = nullptr;
+    up.d_ndual = nullptr;
+    up.dual_cap = 0;
+    up.dual = 1;
+    CP_TRY(launch_uf(P.tab, up, s));
+
+    CP_TRY(launch_essential(P.tab, ctr, pairs, P.cap_p, s));
+    uint32_t* pvals = at<uint32_t>(ws, P.o_pvals);
+    uint32_t* pvalt = at<uint32_t>(ws, P.o_pvalt);
+    CP_TRY(launch_pair_keys(pairs, &ctr->n_pairs, P.cap_p, s0, pvals, s));
+    sb.keys = s0;
+    sb.keys_alt = salt;
+    sb.vals = pvals;
+    sb.vals_alt = pvalt;
+    sb.d_count = &ctr->n_pairs;
+    sb.cap = P.cap_p;
+    sb.tile_ctr = ctr->sort_tile + 16;
+    CP_TRY(sort_keys(sb, 0, 6, 17, s));
+    CP_TRY(launch_gather(pairs, pvals, &ctr->n_pairs, P.cap_p, d_out, capacity, d_out_count, ctr, s));
+#undef CP_TRY
+    if (h_out_count) {
+        Counters h;
+        if (cudaMemcpyAsync(&h, ctr, sizeof(Counters), cudaMemcpyDeviceToHost, s) != cudaSuccess) return CP_ERR_CUDA;
+        if (cudaStreamSynchronize(s) != cudaSuccess) return CP_ERR_CUDA;
+        *h_out_count = h.out_count;
+        return status_to_code(h.status);
+    }
+    return CP_OK;
+}
+
+int single(int ndim, const float* d_image, const int64_t* dims, cp_pair* d_out, int64_t capacity,
+           int64_t* h_out_count, int64_t* d_out_count, void* ws, size_t ws_bytes, int64_t max_survivors,
+           void* stream) {
+    if (!d_image || !dims) return CP_ERR_ARG;
+    int32_t nd = ndim;
+    int64_t d3[3] = {ndim == 3 ? dims[0] : 1, dims[ndim - 2], dims[ndim - 1]};
+    Plan P;
+    int rc = make_plan(1, &nd, d3, &d_image, max_survivors, P);
+    if (rc != CP_OK) return rc;
+    return run(P, d_out, capacity, h_out_count, d_out_count, ws, ws_bytes, static_cast<cudaStream_t>(stream));
+}
+
+}  // namespace
+
+int device_sm_count() {
+    static int cached[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 0 && dev < 64 && cached[dev]) return cached[dev];
+    int n = 0;
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 1;
+    if (dev >= 0 && dev < 64) cached[dev] = n;
+    return n;
+}
+
+}  // namespace cp
+
+using namespace cp;
+
+extern "C" {
+
+int cp_version(void) { return 100; }
+
+const char* cp_error_string(int code) {
+    switch (code) {
+        case CP_OK: return "ok";
+        case CP_ERR_ARG: return "invalid argument";
+        case CP_ERR_NONFINITE: return "non-finite value in the input";
+        case CP_ERR_CAPACITY: return "capacity exceeded";
+        case CP_ERR_CUDA: return "CUDA runtime error";
+        case CP_ERR_TIMEOUT: return "bounded device wait gave up";
+        case CP_ERR_INTERNAL: return "internal consistency check failed";
+        default: return "unknown error";
+    }
+}
+
+int cp_lut_num_classes(int ndim) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!build_host_luts()) return -1;
+    if (ndim == 2) return g_lut2d_classes;
+    if (ndim == 3) return g_lut3d.nclasses;
+    return -1;
+}
+
+int cp_lut_lookup(int ndim, uint32_t raw, uint32_t* relevant, uint64_t* entry) {
+    if (ndim != 2 && ndim != 3) return CP_ERR_ARG;
+    const Stencil& st = stencil(ndim);
+    raw &= ~(1u << st.center);
+    raw &= (1u << st.nbits) - 1u;
+    uint32_t rel = collapse(st, raw);
+    if (relevant) *relevant = rel;
+    if (entry) *entry = classify(st, rel);
+    return CP_OK;
+}
+
+size_t cubical_persistence_workspace_size(int ndim, const int64_t* dims, int64_t max_survivors) {
+    if ((ndim != 2 && ndim != 3) || !dims) return 0;
+    int32_t nd = ndim;
+    int64_t d3[3] = {ndim == 3 ? dims[0] : 1, dims[ndim - 2], dims[ndim - 1]};
+    Plan P;
+    if (make_plan(1, &nd, d3, nullptr, max_survivors, P) != CP_OK) return 0;
+    return P.bytes;
+}
+
+int cubical_persistence_2d(const float* d_image, const int64_t dims[2], cp_pair* d_out_pairs, int64_t capacity,
+                           int64_t* h_out_count, int64_t* d_out_count, void* d_workspace, size_t ws_bytes,
+                           int64_t max_survivors, void* stream) {
+    return single(2, d_image, dims, d_out_pairs, capacity, h_out_count, d_out_count, d_workspace, ws_bytes,
+                  max_survivors, stream);
+}
+
+int cubical_persistence_3d(const float* d_image, const int64_t dims[3], cp_pair* d_out_pairs, int64_t capacity,
+                           int64_t* h_out_count, int64_t* d_out_count, void* d_workspace, size_t ws_bytes,
+                           int64_t max_survivors, void* stream) {
+    return single(3, d_image, dims, d_out_pairs, capacity, h_out_count, d_out_count, d_workspace, ws_bytes,
+                  max_survivors, stream);
+}
+
+size_t cubical_persistence_batched_workspace_size(int n_items, const int32_t* ndims, const int64_t* dims,
+                                                  int64_t max_survivors) {
+    Plan P;
+    if (make_plan(n_items, ndims, dims, nullptr, max_survivors, P) != CP_OK) return 0;
+    return P.bytes;
+}
+
+int cubical_persistence_batched(int n_items, const float* const* h_images, const int32_t* ndims, const int64_t* dims,
+                                cp_pair* d_out_pairs, int64_t capacity, int64_t* h_out_count, int64_t* d_out_count,
+                                void* d_workspace, size_t ws_bytes, int64_t max_survivors, void* stream) {
+    if (!h_images) return CP_ERR_ARG;
+    Plan P;
+    int rc = make_plan(n_items, ndims, dims, h_images, max_survivors, P);
+    if (rc != CP_OK) return rc;
+    return run(P, d_out_pairs, capacity, h_out_count, d_out_count, d_workspace, ws_bytes,
+               static_cast<cudaStream_t>(stream));
+}
+
+int cubical_persistence_stats(const void* d_workspace, cp_stats* h_stats, void* stream) {
+    if (!d_workspace || !h_stats) return CP_ERR_ARG;
+    Counters h;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (cudaMemcpyAsync(&h, d_workspace, sizeof(Counters), cudaMemcpyDeviceToHost, s) != cudaSuccess) return CP_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return CP_ERR_CUDA;
+    std::memset(h_stats, 0, sizeof(*h_stats));
+    h_stats->h0_survivors = h.n_s0;
+    h_stats->top_survivors = h.n_st;
+    h_stats->h0_roots = h.n_r0;
+    h_stats->top_roots = h.n_rt;
+    h_stats->h0_rounds = h.rounds0;
+    h_stats->top_rounds = h.roundst;
+    h_stats->pairs = h.out_count;
+    h_stats->status = h.status;
+    return status_to_code(h.status);
+}
+
+size_t cubical_persistence_backward_workspace_size(int64_t n_pixels) {
+    if (n_pixels <= 0) return 0;
+    return align_up(sizeof(double) * size_t(n_pixels));
+}
+
+int cubical_persistence_backward(const cp_pair* d_pairs, int64_t n_pairs, const float* d_grad_birth,
+                                 const float* d_grad_death, const int64_t* d_item_offsets, float* d_grad_image,
+                                 int64_t n_pixels, void* d_workspace, size_t ws_bytes, void* stream) {
+    if (n_pairs < 0 || n_pixels <= 0 || !d_grad_image || !d_workspace) return CP_ERR_ARG;
+    if (n_pairs > 0 && (!d_pairs || !d_grad_birth || !d_grad_death)) return CP_ERR_ARG;
+    if (ws_bytes < cubical_persistence_backward_workspace_size(n_pixels)) return CP_ERR_ARG;
+    cudaError_t e = launch_backward(d_pairs, n_pairs, d_grad_birth, d_grad_death, d_item_offsets,
+                                    static_cast<double*>(d_workspace), d_grad_image, n_pixels,
+                                    static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? CP_OK : CP_ERR_CUDA;
+}
+
+}  // extern "C"

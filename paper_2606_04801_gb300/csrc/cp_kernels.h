@@ -1,0 +1,85 @@
+// Host-side interface between the C-ABI layer and the kernels.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "cp_common.cuh"
+
+namespace cp {
+
+// ---- K1 pruning
+struct PruneOuts {
+    uint32_t* uf0;   // H0 forest over global vertices
+    uint32_t* uft;   // dual forest over global top cells (+ one outside vertex per item)
+    uint64_t* s0;    // H0 survivor keys
+    uint64_t* st;    // dual survivor keys (complemented: ascending sort = descending order)
+    uint64_t* age0;  // age of each H0 root id
+    uint64_t* res0;  // reservation word of each H0 root id
+    uint64_t* aget;  // age of each dual root id
+    uint64_t* rest;  // reservation word of each dual root id
+    uint32_t cap_s, cap_r0, cap_rt;
+    Counters* ctr;
+};
+size_t prune_smem2d();
+size_t prune_smem3d();
+int prune_tile_x();
+int prune_tile_y2d();
+int prune_tile_y3d();
+int prune_tile_z3d();
+cudaError_t upload_luts(const uint64_t* lut2d, const uint16_t* disp3d, const uint64_t* entries3d);
+cudaError_t launch_prune(const ItemTable& tab, const PruneOuts& po, cudaStream_t s);
+
+// ---- K2 radix sort (LSD, 8-bit digits, decoupled look-back)
+struct SortBufs {
+    uint64_t* keys;       // in/out (result lands here: the pass count is even)
+    uint64_t* keys_alt;
+    uint32_t* vals;       // optional payload (nullptr = keys only)
+    uint32_t* vals_alt;
+    const uint32_t* d_count;  // number of keys, on the device
+    uint32_t cap;             // capacity of the key arrays
+    uint32_t* hist;           // 8 x 256 scratch
+    uint64_t* status;         // sort_status_words(cap) scratch, zeroed once per call
+    uint32_t* tile_ctr;       // one ticket counter per pass, zeroed once per call
+    Counters* ctr;
+};
+size_t sort_status_words(uint32_t cap);
+constexpr int kSortTile = 4096;
+// Sorts bytes [first_byte, first_byte + npasses) of each key, npasses even.
+cudaError_t sort_keys(const SortBufs& b, int first_byte, int npasses, uint32_t epoch, cudaStream_t s);
+
+// ---- K3 union-find (deterministic reservations)
+struct UfParams {
+    const uint64_t* keys;     // sorted survivor keys
+    const uint32_t* d_nkeys;
+    uint32_t cap_keys;
+    uint32_t* uf;
+    const uint64_t* age;
+    uint64_t* res;
+    uint32_t* act[2];
+    uint32_t* ynode;
+    uint32_t* onode;
+    uint32_t* yrid;
+    cp_pair* pairs;
+    uint32_t pair_cap;
+    uint64_t* dual_keys;      // H0 of 2D items: positive edges that the dual needs (cross-pruning)
+    uint32_t* d_ndual;
+    uint32_t dual_cap;
+    Counters* ctr;
+    int dual;                 // 0: H0 (ascending, larger age dies); 1: dual (smaller age dies)
+};
+cudaError_t launch_uf(const ItemTable& tab, const UfParams& p, cudaStream_t s);
+
+// ---- K4 emission, K5 backward
+cudaError_t launch_init(const ItemTable& tab, Counters* ctr, uint32_t* uft, uint64_t* aget, uint64_t* rest,
+                        cudaStream_t s);
+cudaError_t launch_essential(const ItemTable& tab, Counters* ctr, cp_pair* pairs, uint32_t pair_cap, cudaStream_t s);
+cudaError_t launch_pair_keys(const cp_pair* pairs, const uint32_t* d_n, uint32_t cap, uint64_t* keys, uint32_t* vals,
+                             cudaStream_t s);
+cudaError_t launch_gather(const cp_pair* pairs, const uint32_t* vals, const uint32_t* d_n, uint32_t cap,
+                          cp_pair* out, int64_t out_cap, int64_t* d_out_count, Counters* ctr, cudaStream_t s);
+cudaError_t launch_backward(const cp_pair* pairs, int64_t n, const float* gb, const float* gd, const int64_t* offs,
+                            double* acc, float* grad, int64_t n_pixels, cudaStream_t s);
+
+int device_sm_count();
+
+}  // namespace cp
