@@ -1,0 +1,413 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 path: exact H0 + top-dimension persistence pairs of a
+512^3 float32 blurred-noise volume (white noise, Gaussian sigma = 3 voxels,
+normalised to [0, 1]), one step = the whole hot path: lookup + pruning, sorts,
+both union-finds, emission, then the total-persistence loss and its backward
+scatter to the voxels.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  Multi-GPU runs are independent replicas (one
+volume per rank; a single volume's union-find is global and does not shard).
+The volume (512 MiB) is larger than L2, so no L2 flush is done between steps.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+SIDE = 512
+SIGMA = 3.0
+METRIC = "Mvoxels/s for exact H0+top-dim diagrams (512^3 fp32), % HBM roofline; fwd+bwd batched vs plain"
+WORKLOAD = "3D 512^3 float32 blurred noise (sigma 3 vox), H0 + H2 pairs, fwd + total-persistence loss bwd"
+TAU = 0.05  # persistence threshold of the loss
+
+
+def _volume(seed: int) -> np.ndarray:
+    cache = f"/tmp/cp_bench_vol_{SIDE}_{SIGMA}_{seed}.npy"
+    if os.path.exists(cache):
+        try:
+            return np.load(cache)
+        except Exception:
+            pass
+    v = workloads.blurred((SIDE, SIDE, SIDE), SIGMA, seed)
+    try:
+        np.save(cache + ".tmp.npy", v)
+        os.replace(cache + ".tmp.npy", cache)
+    except OSError:
+        pass
+    return v
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    Q = (
+        "index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+        "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+        "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap"
+    )
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits", "-lms", "50", "-i", str(self.idx)],
+                stdout=subprocess.PIPE,
+                stderr=subprocess.DEVNULL,
+                text=True,
+            )
+        except Exception:
+            self.p = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.p is not None:
+            time.sleep(0.2)
+            self.p.terminate()
+            try:
+                self.out, _ = self.p.communicate(timeout=5)
+            except Exception:
+                self.p.kill()
+        return False
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (getattr(self, "out", "") or "").splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": mx, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_reference(args):
+    """The oracle (plain single-threaded C) on bounded crops of the same workload."""
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    import oracle
+
+    oracle.build()
+    n_runs = args.steps + args.warmup
+    # the oracle runs at ~0.3-0.5 Mvox/s; aim at ~2 minutes in total
+    side = int(round((0.35e6 * 120.0 / max(1, n_runs)) ** (1.0 / 3.0)))
+    side = max(24, min(192, side))
+    vol = _volume(0)
+    crop = np.ascontiguousarray(vol[:side, :side, :side])
+    for _ in range(args.warmup):
+        oracle.persistence(crop)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.persistence(crop)
+    dt = time.perf_counter() - t0
+    value = crop.size * args.steps / dt / 1e6
+    line = {
+        "impl": "reference",
+        "metric": METRIC,
+        "value": value,
+        "unit": "Mvoxels/s",
+        "n_gpus": args.gpus,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": f"{side}^3 crop of the 512^3 volume per step", "parallelism": "replicas"},
+        "cpu_baseline": {
+            "value": value,
+            "unit": "Mvoxels/s",
+            "cores": 1,
+            "kind": "oracle",
+            "sample": f"{side}^3 crop of the 512^3 blurred volume (same recipe), H0 + H2 pairs",
+        },
+        "e2e": {"value": value, "unit": "Mvoxels/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(vol, budget_s=20.0):
+    """The oracle as it stands, timed on this host (1 thread) on a crop of the volume."""
+    import oracle
+
+    oracle.build()
+    side = 96
+    crop = np.ascontiguousarray(vol[:side, :side, :side])
+    t0 = time.perf_counter()
+    oracle.persistence(crop)
+    dt = time.perf_counter() - t0
+    # grow the crop towards the time budget
+    side2 = int(side * min(2.0, max(1.0, (budget_s / max(dt, 1e-3)) ** (1 / 3) * 0.8)))
+    side2 = min(side2, 192)
+    if side2 > side:
+        crop = np.ascontiguousarray(vol[:side2, :side2, :side2])
+        t0 = time.perf_counter()
+        oracle.persistence(crop)
+        dt = time.perf_counter() - t0
+        side = side2
+    return {
+        "value": crop.size / dt / 1e6,
+        "unit": "Mvoxels/s",
+        "cores": 1,
+        "kind": "oracle",
+        "sample": f"{side}^3 crop of the 512^3 volume, H0 + H2 pairs, single-threaded C oracle, {dt:.1f} s",
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--side", type=int, default=512, help="cube side (512 is the benchmark; smaller for profiling)")
+    args = ap.parse_args()
+    global SIDE
+    SIDE = args.side
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import paper_2606_04801_gb300 as cp
+    from paper_2606_04801_gb300 import _lib
+
+    lib = _lib.load()
+    vol = _volume(rank)
+    N = vol.size
+    T = (SIDE - 1) ** 3
+    x = torch.from_numpy(vol).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    sp = ctypes.c_void_p(int(stream.cuda_stream))
+    dims = (ctypes.c_int64 * 3)(SIDE, SIDE, SIDE)
+    ms = 0
+    ws_bytes = lib.cubical_persistence_workspace_size(3, dims, ms)
+    wsp = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
+    cap = N // 2 + 65536 + 4096
+    out = torch.empty((cap, 8), dtype=torch.int32, device=dev)
+    grad = torch.empty(N, dtype=torch.float32, device=dev)
+    loss = torch.zeros(1, dtype=torch.float64, device=dev)
+    bws = lib.cubical_persistence_loss_backward_workspace_size(N)
+    bwsp = torch.empty(bws, dtype=torch.uint8, device=dev)
+    cnt = ctypes.c_int64(0)
+
+    def step(src):
+        rc = lib.cubical_persistence_3d(
+            ctypes.c_void_p(src.data_ptr()), dims, ctypes.c_void_p(out.data_ptr()), cap, ctypes.byref(cnt), None,
+            ctypes.c_void_p(wsp.data_ptr()), ws_bytes, ms, sp,
+        )
+        if rc != 0:
+            raise cp.CpError(rc, "forward")
+        rc = lib.cubical_persistence_loss_backward(
+            ctypes.c_void_p(out.data_ptr()), cnt.value, ctypes.c_float(TAU), ctypes.c_void_p(loss.data_ptr()), None,
+            ctypes.c_void_p(grad.data_ptr()), N, ctypes.c_void_p(bwsp.data_ptr()), bws, sp,
+        )
+        if rc != 0:
+            raise cp.CpError(rc, "loss backward")
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+
+    # ---------------- device-resident timing
+    lib.cp_profile(1)
+    stage = (ctypes.c_float * 6)()
+    for _ in range(args.warmup):
+        step(x)
+    barrier()
+    st = cp.api._stats(wsp)
+    k1_ms = []
+    stage_sum = [0.0] * 6
+    launches0 = lib.cp_launch_count()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    gpu_index = int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[local]) if os.environ.get("CUDA_VISIBLE_DEVICES") else local
+    with Clocks(gpu_index) as clk:
+        barrier()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step(x)
+            if lib.cp_stage_times(stage, 6) == 6:
+                k1_ms.append(stage[0])
+                for i in range(6):
+                    stage_sum[i] += stage[i]
+        ev1.record(stream)
+        barrier()
+    launches = lib.cp_launch_count() - launches0
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+    if ws > 1:
+        t = torch.tensor([elapsed], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        elapsed = float(t.item())
+    value = N * ws * args.steps / elapsed / 1e6
+
+    # ---------------- end to end: pinned host input -> device -> pairs + loss/grad -> loss on host
+    lib.cp_profile(0)
+    e2e_steps = 0 if args.no_e2e else max(3, min(args.steps, 10))
+    e2e_dt = 1.0
+    if e2e_steps:
+        host = torch.from_numpy(vol).pin_memory()
+        xb = torch.empty_like(x)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            xb.copy_(host, non_blocking=True)
+            step(xb)
+            _ = float(loss.item())
+        barrier()
+        e2e_dt = time.perf_counter() - t0
+    if ws > 1:
+        t = torch.tensor([e2e_dt], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_dt = float(t.item())
+    e2e = None if not e2e_steps else {
+        "value": N * ws * e2e_steps / e2e_dt / 1e6,
+        "unit": "Mvoxels/s",
+        "h2d_bytes_per_step": int(N * 4),
+        "d2h_bytes_per_step": 8 + 1368,  # the loss, and the call's status/count block
+    }
+    if ws > 1:
+        torch.distributed.barrier()
+    if rank != 0:
+        return
+
+    # ---------------- roofline of the pruning kernel (K1)
+    peak, peak_kind = _peaks()
+    k1 = statistics.mean(k1_ms) / 1e3 if k1_ms else None
+    s0, stp, r0, rt = st["h0_survivors"], st["top_survivors"], st["h0_roots"], st["top_roots"]
+    alg = 4 * N + 4 * N + 4 * (T + 1) + 8 * (s0 + stp) + 16 * (r0 + rt)
+    achieved = alg / k1 / 1e9 if k1 else None
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "k1_prune3d_traffic.json")
+    if os.path.exists(tpath):
+        try:
+            with open(tpath) as fh:
+                tj = json.load(fh)
+            if tj.get("source_hash") == _k1_hash():
+                traffic = tj.get("bytes_per_launch_full")
+        except Exception:
+            traffic = None
+    roofline = {
+        "bound": "hbm",
+        "achieved": achieved,
+        "peak": peak,
+        "unit": "GB/s",
+        "frac": (achieved / peak) if achieved else None,
+        "traffic": traffic,
+        "kernel": "k_prune3d",
+        "peak_source": peak_kind,
+        "algorithmic_bytes": alg,
+        "k1_ms": k1 * 1e3 if k1 else None,
+    }
+    cpu = None if args.no_cpu_baseline else cpu_baseline(vol)
+    clocks = clk.summary()
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "Mvoxels/s",
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": elapsed / args.steps * 1e3,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": {
+            "workload": WORKLOAD,
+            "shape": [SIDE, SIDE, SIDE],
+            "note": None if SIDE == 512 else "reduced size for profiling; not the benchmark workload",
+            "sigma": SIGMA,
+            "loss_min_persistence": TAU,
+            "l2": "input (512 MiB) larger than L2; no flush",
+            "parallelism": "replicas" if ws > 1 else "single",
+        },
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+        "stages_ms": {
+            k: v / max(1, len(k1_ms))
+            for k, v in zip(["prune", "sort_h0", "uf_h0", "sort_top", "uf_top", "emit"], stage_sum)
+        },
+        "counts": {"pairs": int(cnt.value), "h0_survivors": s0, "top_survivors": stp, "h0_roots": r0, "top_roots": rt,
+                   "h0_rounds": st["h0_rounds"], "top_rounds": st["top_rounds"]},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def _k1_hash():
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in ("cp_prune.cu", "cp_common.cuh"):
+        with open(os.path.join(ROOT, "paper_2606_04801_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+if __name__ == "__main__":
+    main()

@@ -205,6 +205,38 @@ int cubical_persistence_backward(const cp_pair *d_pairs, int64_t n_pairs, const 
                                  const float *d_grad_death, const int64_t *d_item_offsets, float *d_grad_image,
                                  int64_t n_pixels, void *d_workspace, size_t ws_bytes, void *stream);
 
+/*
+ * Fused loss and backward for the total-persistence loss
+ *   L = sum over finite pairs with death - birth > min_persistence
+ *       of (death - birth)^2,
+ * with dL/ddeath = 2 (death - birth) and dL/dbirth = -2 (death - birth)
+ * scattered to the death and birth pixels as in cubical_persistence_backward.
+ *  d_loss : device, one double, receives L (summed in a fixed order, so it is
+ *           the same on every run).
+ * Other arguments as for cubical_persistence_backward; the workspace size is
+ * cubical_persistence_loss_backward_workspace_size(n_pixels).
+ */
+size_t cubical_persistence_loss_backward_workspace_size(int64_t n_pixels);
+int cubical_persistence_loss_backward(const cp_pair *d_pairs, int64_t n_pairs, float min_persistence,
+                                      double *d_loss, const int64_t *d_item_offsets, float *d_grad_image,
+                                      int64_t n_pixels, void *d_workspace, size_t ws_bytes, void *stream);
+
+/* ---------------------------------------------------------------- instrumentation */
+
+/* Kernel launches the library has made since it was loaded. */
+long long cp_launch_count(void);
+
+/*
+ * cp_profile(1) makes every following forward call record CUDA events on its
+ * stream between its stages; cp_stage_times() then waits for the last call
+ * and writes the six stage durations in milliseconds (prune, sort H0,
+ * union-find H0, sort dual, union-find dual, emit) into ms[0..5] and returns
+ * 6 (or a negative CP_ERR_* code; cap must be >= 6).  cp_profile(0) stops
+ * recording.  Not thread-safe across concurrent calls.
+ */
+int cp_profile(int enable);
+int cp_stage_times(float *ms, int cap);
+
 #ifdef __cplusplus
 }
 #endif

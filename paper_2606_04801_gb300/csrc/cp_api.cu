@@ -4,6 +4,7 @@
 //        -> K2 sort (dual) -> K3 dual union-find -> essential pairs
 //        -> K2 sort (pairs, canonical order) -> gather.
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -22,6 +23,18 @@ std::vector<uint64_t> g_lut2d;
 Lut3D g_lut3d;
 int g_lut2d_classes = 0;
 uint64_t g_dev_ready = 0;  // bit d set once device d holds the tables
+std::atomic<long long> g_launches{0};
+
+// Optional stage timing: CUDA events recorded on the call's stream between
+// stages (prune | sort H0 | union-find H0 | sort dual | union-find dual | emit).
+constexpr int kStages = 6;
+bool g_profile = false;
+cudaEvent_t g_ev[kStages + 1];
+bool g_ev_made = false;
+
+void mark(int i, cudaStream_t s) {
+    if (g_profile && g_ev_made) cudaEventRecord(g_ev[i], s);
+}
 
 bool build_host_luts() {
     if (g_lut_built) return true;
@@ -192,6 +205,7 @@ int run(const Plan& P, cp_pair* d_out, int64_t capacity, int64_t* h_out_count, i
     CP_TRY(cudaMemsetAsync(ctr, 0, sizeof(Counters), s));
     CP_TRY(cudaMemsetAsync(status, 0, sizeof(uint64_t) * sort_status_words(P.cap_big), s));
     CP_TRY(launch_init(P.tab, ctr, uft, aget, rest, s));
+    mark(0, s);
 
     PruneOuts po;
     po.uf0 = uf0;
@@ -207,6 +221,7 @@ int run(const Plan& P, cp_pair* d_out, int64_t capacity, int64_t* h_out_count, i
     po.cap_rt = P.cap_rt;
     po.ctr = ctr;
     CP_TRY(launch_prune(P.tab, po, s));
+    mark(1, s);
 
     SortBufs sb;
     sb.keys = s0;
@@ -220,6 +235,7 @@ int run(const Plan& P, cp_pair* d_out, int64_t capacity, int64_t* h_out_count, i
     sb.tile_ctr = ctr->sort_tile;
     sb.ctr = ctr;
     CP_TRY(sort_keys(sb, 0, 8, 1, s));
+    mark(2, s);
 
     UfParams up;
     up.keys = s0;
@@ -241,11 +257,13 @@ int run(const Plan& P, cp_pair* d_out, int64_t capacity, int64_t* h_out_count, i
     up.ctr = ctr;
     up.dual = 0;
     CP_TRY(launch_uf(P.tab, up, s));
+    mark(3, s);
 
     sb.keys = st;
     sb.d_count = &ctr->n_st;
     sb.tile_ctr = ctr->sort_tile + 8;
     CP_TRY(sort_keys(sb, 0, 8, 9, s));
+    mark(4, s);
 
     up.keys = st;
     up.d_nkeys = &ctr->n_st;
@@ -257,6 +275,7 @@ int run(const Plan& P, cp_pair* d_out, int64_t capacity, int64_t* h_out_count, i
     up.dual_cap = 0;
     up.dual = 1;
     CP_TRY(launch_uf(P.tab, up, s));
+    mark(5, s);
 
     CP_TRY(launch_essential(P.tab, ctr, pairs, P.cap_p, s));
     uint32_t* pvals = at<uint32_t>(ws, P.o_pvals);
@@ -271,6 +290,7 @@ int run(const Plan& P, cp_pair* d_out, int64_t capacity, int64_t* h_out_count, i
     sb.tile_ctr = ctr->sort_tile + 16;
     CP_TRY(sort_keys(sb, 0, 6, 17, s));
     CP_TRY(launch_gather(pairs, pvals, &ctr->n_pairs, P.cap_p, d_out, capacity, d_out_count, ctr, s));
+    mark(6, s);
 #undef CP_TRY
     if (h_out_count) {
         Counters h;
@@ -295,6 +315,8 @@ int single(int ndim, const float* d_image, const int64_t* dims, cp_pair* d_out, 
 }
 
 }  // namespace
+
+void note_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 int device_sm_count() {
     static int cached[64] = {0};
@@ -405,6 +427,46 @@ int cubical_persistence_stats(const void* d_workspace, cp_stats* h_stats, void* 
     h_stats->pairs = h.out_count;
     h_stats->status = h.status;
     return status_to_code(h.status);
+}
+
+long long cp_launch_count(void) { return g_launches.load(); }
+
+int cp_profile(int enable) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (enable && !g_ev_made) {
+        for (int i = 0; i <= kStages; ++i)
+            if (cudaEventCreate(&g_ev[i]) != cudaSuccess) return CP_ERR_CUDA;
+        g_ev_made = true;
+    }
+    g_profile = enable != 0;
+    return CP_OK;
+}
+
+int cp_stage_times(float* ms, int cap) {
+    if (!ms || cap < kStages) return CP_ERR_ARG;
+    if (!g_ev_made) return CP_ERR_ARG;
+    if (cudaEventSynchronize(g_ev[kStages]) != cudaSuccess) return CP_ERR_CUDA;
+    for (int i = 0; i < kStages; ++i)
+        if (cudaEventElapsedTime(&ms[i], g_ev[i], g_ev[i + 1]) != cudaSuccess) return CP_ERR_CUDA;
+    return kStages;
+}
+
+size_t cubical_persistence_loss_backward_workspace_size(int64_t n_pixels) {
+    if (n_pixels <= 0) return 0;
+    return align_up(sizeof(double) * size_t(n_pixels)) + align_up(sizeof(double) * size_t(loss_partials()));
+}
+
+int cubical_persistence_loss_backward(const cp_pair* d_pairs, int64_t n_pairs, float min_persistence,
+                                      double* d_loss, const int64_t* d_item_offsets, float* d_grad_image,
+                                      int64_t n_pixels, void* d_workspace, size_t ws_bytes, void* stream) {
+    if (n_pairs < 0 || n_pixels <= 0 || !d_grad_image || !d_workspace || !d_loss) return CP_ERR_ARG;
+    if (n_pairs > 0 && !d_pairs) return CP_ERR_ARG;
+    if (ws_bytes < cubical_persistence_loss_backward_workspace_size(n_pixels)) return CP_ERR_ARG;
+    double* acc = static_cast<double*>(d_workspace);
+    double* parts = reinterpret_cast<double*>(static_cast<char*>(d_workspace) + align_up(sizeof(double) * size_t(n_pixels)));
+    cudaError_t e = launch_loss_backward(d_pairs, n_pairs, min_persistence, d_item_offsets, acc, parts, loss_partials(),
+                                         d_loss, d_grad_image, n_pixels, static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? CP_OK : CP_ERR_CUDA;
 }
 
 size_t cubical_persistence_backward_workspace_size(int64_t n_pixels) {

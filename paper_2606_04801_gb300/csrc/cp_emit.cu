@@ -97,6 +97,46 @@ __global__ void k_round(const double* __restrict__ acc, float* __restrict__ grad
         grad[i] = float(acc[i]);
 }
 
+// Total-persistence loss of the pairs above a persistence threshold and its
+// gradient: dL/ddeath = 2 (d - b), dL/dbirth = -2 (d - b).  The loss is summed
+// in a fixed order (per-block partials, then one ordered pass), so it is
+// identical from run to run.
+constexpr int kLossBlocks = 256;
+
+__global__ void __launch_bounds__(kT) k_loss_scatter(const cp_pair* __restrict__ pairs, int64_t n, float tau,
+                                                     const int64_t* __restrict__ offs, double* acc, int64_t n_pixels,
+                                                     double* partials) {
+    __shared__ double red[kT / 32];
+    double local = 0.0;
+    for (int64_t i = int64_t(blockIdx.x) * kT + threadIdx.x; i < n; i += int64_t(gridDim.x) * kT) {
+        const cp_pair& p = pairs[i];
+        if (p.death_pixel < 0) continue;
+        double pers = double(p.death) - double(p.birth);
+        if (!(pers > double(tau))) continue;
+        local += pers * pers;
+        int64_t off = offs ? offs[p.item] : 0;
+        int64_t qd = off + p.death_pixel, qb = off + p.birth_pixel;
+        if (qd < n_pixels) atomicAdd(acc + qd, 2.0 * pers);
+        if (qb >= 0 && qb < n_pixels) atomicAdd(acc + qb, -2.0 * pers);
+    }
+    for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(0xFFFFFFFFu, local, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = local;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < kT / 32; ++w) t += red[w];
+        partials[blockIdx.x] = t;
+    }
+}
+
+__global__ void k_loss_sum(const double* partials, int n, double* loss) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double t = 0.0;
+        for (int i = 0; i < n; ++i) t += partials[i];
+        *loss = t;
+    }
+}
+
 int grid_for(int64_t n) {
     int64_t b = (n + kT - 1) / kT;
     int64_t cap = int64_t(device_sm_count()) * 8;
@@ -105,26 +145,45 @@ int grid_for(int64_t n) {
 
 }  // namespace
 
+int loss_partials() { return kLossBlocks; }
+
+cudaError_t launch_loss_backward(const cp_pair* pairs, int64_t n, float tau, const int64_t* offs, double* acc,
+                                 double* partials, int nparts, double* d_loss, float* grad, int64_t n_pixels,
+                                 cudaStream_t s) {
+    if (nparts < kLossBlocks) return cudaErrorInvalidValue;
+    cudaError_t e = cudaMemsetAsync(acc, 0, sizeof(double) * size_t(n_pixels), s);
+    if (e != cudaSuccess) return e;
+    k_loss_scatter<<<kLossBlocks, kT, 0, s>>>(pairs, n, tau, offs, acc, n_pixels, partials);
+    k_loss_sum<<<1, 32, 0, s>>>(partials, kLossBlocks, d_loss);
+    k_round<<<grid_for(n_pixels), kT, 0, s>>>(acc, grad, n_pixels);
+    note_launches(3);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_init(const ItemTable& tab, Counters* ctr, uint32_t* uft, uint64_t* aget, uint64_t* rest,
                         cudaStream_t s) {
     k_init<<<1, kMaxItems, 0, s>>>(tab, ctr, uft, aget, rest);
+    note_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_essential(const ItemTable& tab, Counters* ctr, cp_pair* pairs, uint32_t cap, cudaStream_t s) {
     k_essential<<<1, kMaxItems, 0, s>>>(tab, ctr, pairs, cap);
+    note_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_pair_keys(const cp_pair* pairs, const uint32_t* d_n, uint32_t cap, uint64_t* keys, uint32_t* vals,
                              cudaStream_t s) {
     k_pair_keys<<<grid_for(cap), kT, 0, s>>>(pairs, d_n, cap, keys, vals);
+    note_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_gather(const cp_pair* pairs, const uint32_t* vals, const uint32_t* d_n, uint32_t cap,
                           cp_pair* out, int64_t out_cap, int64_t* d_out_count, Counters* ctr, cudaStream_t s) {
     k_gather<<<grid_for(cap), kT, 0, s>>>(pairs, vals, d_n, cap, out, out_cap, d_out_count, ctr);
+    note_launches(1);
     return cudaGetLastError();
 }
 
@@ -132,8 +191,12 @@ cudaError_t launch_backward(const cp_pair* pairs, int64_t n, const float* gb, co
                             double* acc, float* grad, int64_t n_pixels, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(acc, 0, sizeof(double) * size_t(n_pixels), s);
     if (e != cudaSuccess) return e;
-    if (n > 0) k_scatter<<<grid_for(n), kT, 0, s>>>(pairs, n, gb, gd, offs, acc, n_pixels);
+    if (n > 0) {
+        k_scatter<<<grid_for(n), kT, 0, s>>>(pairs, n, gb, gd, offs, acc, n_pixels);
+        note_launches(1);
+    }
     k_round<<<grid_for(n_pixels), kT, 0, s>>>(acc, grad, n_pixels);
+    note_launches(1);
     return cudaGetLastError();
 }
 

@@ -82,4 +82,14 @@ cudaError_t launch_backward(const cp_pair* pairs, int64_t n, const float* gb, co
 
 int device_sm_count();
 
+// Kernel launches made by the library (for the benchmark's launch count).
+void note_launches(int n);
+
+// Loss sum(death - birth)^2 over finite pairs with death - birth > tau, and
+// its gradient scattered to the pixels (double-precision accumulators).
+cudaError_t launch_loss_backward(const cp_pair* pairs, int64_t n, float tau, const int64_t* offs, double* acc,
+                                 double* partials, int nparts, double* d_loss, float* grad, int64_t n_pixels,
+                                 cudaStream_t s);
+int loss_partials();
+
 }  // namespace cp

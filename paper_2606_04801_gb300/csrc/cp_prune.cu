@@ -434,8 +434,14 @@ cudaError_t launch_prune(const ItemTable& tab, const PruneOuts& po, cudaStream_t
         cudaFuncSetAttribute(k_prune3d, cudaFuncAttributeMaxDynamicSharedMemorySize, int(prune_smem3d()));
         attr_set = true;
     }
-    if (tab.tiles2d > 0) k_prune2d<<<tab.tiles2d, dim3(kBX, kBY), prune_smem2d(), s>>>(tab, o);
-    if (tab.tiles3d > 0) k_prune3d<<<tab.tiles3d, dim3(kBX, kBY), prune_smem3d(), s>>>(tab, o);
+    if (tab.tiles2d > 0) {
+        k_prune2d<<<tab.tiles2d, dim3(kBX, kBY), prune_smem2d(), s>>>(tab, o);
+        note_launches(1);
+    }
+    if (tab.tiles3d > 0) {
+        k_prune3d<<<tab.tiles3d, dim3(kBX, kBY), prune_smem3d(), s>>>(tab, o);
+        note_launches(1);
+    }
     return cudaGetLastError();
 }
 

@@ -207,6 +207,7 @@ cudaError_t sort_keys(const SortBufs& b, int first_byte, int npasses, uint32_t e
     int hist_blocks = device_sm_count() * 2;
     k_hist<<<hist_blocks, kT, 0, s>>>(b.keys, b.d_count, b.cap, b.hist, first_byte, npasses);
     k_hist_scan<<<1, kT, 0, s>>>(b.hist, npasses);
+    note_launches(2 + npasses);
     int grid = int(max_tiles < uint32_t(g_sort_blocks) ? (max_tiles ? max_tiles : 1) : g_sort_blocks);
     for (int p = 0; p < npasses; ++p) {
         const uint64_t* src = (p & 1) ? b.keys_alt : b.keys;

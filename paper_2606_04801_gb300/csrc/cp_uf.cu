@@ -292,6 +292,7 @@ cudaError_t launch_uf(const ItemTable& tab, const UfParams& p, cudaStream_t s) {
     args.tab = tab;
     args.p = p;
     void* kargs[] = {&args};
+    note_launches(1);
     return cudaLaunchCooperativeKernel((const void*)k_uf, dim3(g_uf_blocks), dim3(kT), kargs, 0, s);
 }
 
