@@ -221,6 +221,32 @@ int cubical_persistence_loss_backward(const cp_pair *d_pairs, int64_t n_pairs, f
                                       double *d_loss, const int64_t *d_item_offsets, float *d_grad_image,
                                       int64_t n_pixels, void *d_workspace, size_t ws_bytes, void *stream);
 
+/*
+ * Backward scatter that allocates nothing (the paper has no counterpart: it
+ * is a convenience of this library).  For callers that cannot allocate
+ * device memory, such as code running while a stream is captured into a
+ * CUDA graph, or code inside another framework's hooks without access to
+ * its allocator, this computes exactly what cubical_persistence_backward
+ * computes, but keeps its double-precision accumulators in a fixed array
+ * inside the library's device image instead of a caller-provided workspace.
+ *  - The array holds cubical_persistence_backward_noalloc_max_pixels()
+ *    (= 4,194,304) doubles, 32 MiB; every GPU that loads the library keeps it
+ *    until the process exits.  n_pixels above that maximum returns
+ *    CP_ERR_CAPACITY without touching the GPU.
+ *  - The first call on a device looks the array's device address up
+ *    (cudaGetSymbolAddress, with that device current); make that first call
+ *    before any stream capture on that device.
+ *  - Every call shares the one array: each call clears the part it uses
+ *    before accumulating, so consecutive calls are independent, but calls
+ *    whose work overlaps on the GPU (unordered streams) race on it.
+ *  - It calls no allocating function.  Other arguments as for
+ *    cubical_persistence_backward.
+ */
+int64_t cubical_persistence_backward_noalloc_max_pixels(void);
+int cubical_persistence_backward_noalloc(const cp_pair *d_pairs, int64_t n_pairs, const float *d_grad_birth,
+                                         const float *d_grad_death, const int64_t *d_item_offsets,
+                                         float *d_grad_image, int64_t n_pixels, void *stream);
+
 /* ---------------------------------------------------------------- instrumentation */
 
 /* Kernel launches the library has made since it was loaded. */

@@ -76,6 +76,8 @@ _SIGS = {
         ctypes.c_int,
         [_P, _I64, ctypes.c_float, _P, _P, _P, _I64, _P, ctypes.c_size_t, _P],
     ),
+    "cubical_persistence_backward_noalloc_max_pixels": (ctypes.c_int64, []),
+    "cubical_persistence_backward_noalloc": (ctypes.c_int, [_P, _I64, _P, _P, _P, _P, _I64, _P]),
     "cp_launch_count": (ctypes.c_longlong, []),
     "cp_profile": (ctypes.c_int, [ctypes.c_int]),
     "cp_stage_times": (ctypes.c_int, [_P, ctypes.c_int]),

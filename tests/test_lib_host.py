@@ -32,7 +32,7 @@ def lib():
 
 def test_exports_every_declared_symbol(lib):
     hdr = open(os.path.join(ROOT, "include", "cubical_persistence.h")).read()
-    declared = set(re.findall(r"^\s*(?:int|size_t|long long|const char \*)\s*\**\s*(\w+)\s*\(", hdr, re.M))
+    declared = set(re.findall(r"^\s*(?:int|int64_t|size_t|long long|const char \*)\s*\**\s*(\w+)\s*\(", hdr, re.M))
     assert declared, "no declarations parsed"
     for name in declared:
         assert hasattr(lib, name), name
