@@ -34,6 +34,7 @@ SIGMA = 3.0
 METRIC = "Mvoxels/s for exact H0+top-dim diagrams (512^3 fp32), % HBM roofline; fwd+bwd batched vs plain"
 WORKLOAD = "3D 512^3 float32 blurred noise (sigma 3 vox), H0 + H2 pairs, fwd + total-persistence loss bwd"
 TAU = 0.05  # persistence threshold of the loss
+COUNTERS_BYTES = 4056  # status/count block the forward call copies back (sizeof the library's counters)
 
 
 def _volume(seed: int) -> np.ndarray:
@@ -325,7 +326,7 @@ def main():
         "value": N * ws * e2e_steps / e2e_dt / 1e6,
         "unit": "Mvoxels/s",
         "h2d_bytes_per_step": int(N * 4),
-        "d2h_bytes_per_step": 8 + 1368,  # the loss, and the call's status/count block
+        "d2h_bytes_per_step": 8 + COUNTERS_BYTES,  # the loss, and the call's status/count block
     }
     if ws > 1:
         torch.distributed.barrier()
@@ -360,6 +361,14 @@ def main():
         "algorithmic_bytes": alg,
         "k1_ms": k1 * 1e3 if k1 else None,
     }
+    trace = {}
+    for dual, name in ((0, "h0"), (1, "top")):
+        act = (ctypes.c_uint32 * 48)()
+        us = (ctypes.c_double * 48)()
+        usa = (ctypes.c_double * 48)()
+        hops = (ctypes.c_uint64 * 48)()
+        k = lib.cubical_persistence_uf_trace2(ctypes.c_void_p(wsp.data_ptr()), dual, act, us, usa, hops, 48, sp)
+        trace[name] = [[int(act[i]), round(us[i], 1), round(usa[i], 1), int(hops[i])] for i in range(max(0, k))]
     cpu = None if args.no_cpu_baseline else cpu_baseline(vol)
     clocks = clk.summary()
     line = {
@@ -393,6 +402,7 @@ def main():
             k: v / max(1, len(k1_ms))
             for k, v in zip(["prune", "sort_h0", "uf_h0", "sort_top", "uf_top", "emit"], stage_sum)
         },
+        "uf_trace": trace,
         "counts": {"pairs": int(cnt.value), "h0_survivors": s0, "top_survivors": stp, "h0_roots": r0, "top_roots": rt,
                    "h0_rounds": st["h0_rounds"], "top_rounds": st["top_rounds"]},
     }

@@ -249,6 +249,20 @@ int cubical_persistence_backward_noalloc(const cp_pair *d_pairs, int64_t n_pairs
 
 /* ---------------------------------------------------------------- instrumentation */
 
+/*
+ * Union-find trace of the last forward call that used this workspace (waits
+ * for `stream`): for round i (up to min(cap, 48) rounds, plus the final
+ * empty one), h_active[i] = survivors still unresolved at its start and
+ * h_us[i] = microseconds since the start of round 0.  dual = 0 for H0, 1 for
+ * the top dimension.  Returns the number of entries or a CP_ERR_* code.
+ */
+int cubical_persistence_uf_trace(const void *d_workspace, int dual, uint32_t *h_active, double *h_us, int cap,
+                                 void *stream);
+/* As above, plus (if non-NULL) the end of each round's find phase in
+ * microseconds since the start of round 0, and the parent hops walked in it. */
+int cubical_persistence_uf_trace2(const void *d_workspace, int dual, uint32_t *h_active, double *h_us,
+                                  double *h_us_phase_a, uint64_t *h_hops, int cap, void *stream);
+
 /* Kernel launches the library has made since it was loaded. */
 long long cp_launch_count(void);
 

@@ -78,6 +78,8 @@ _SIGS = {
     ),
     "cubical_persistence_backward_noalloc_max_pixels": (ctypes.c_int64, []),
     "cubical_persistence_backward_noalloc": (ctypes.c_int, [_P, _I64, _P, _P, _P, _P, _I64, _P]),
+    "cubical_persistence_uf_trace": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, ctypes.c_int, _P]),
+    "cubical_persistence_uf_trace2": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P, _P, ctypes.c_int, _P]),
     "cp_launch_count": (ctypes.c_longlong, []),
     "cp_profile": (ctypes.c_int, [ctypes.c_int]),
     "cp_stage_times": (ctypes.c_int, [_P, ctypes.c_int]),

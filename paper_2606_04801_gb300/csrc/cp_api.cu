@@ -61,7 +61,7 @@ struct Plan {
     uint32_t cap_s = 0, cap_r0 = 0, cap_rt = 0, cap_p = 0, cap_big = 0;
     // byte offsets into the workspace
     size_t o_ctr, o_uf0, o_uft, o_s0, o_st, o_salt, o_age0, o_res0, o_aget, o_rest;
-    size_t o_act0, o_act1, o_yn, o_on, o_yr, o_pairs, o_pvals, o_pvalt, o_hist, o_status;
+    size_t o_act0, o_act1, o_yn, o_on, o_yr, o_na0, o_na1, o_nb0, o_nb1, o_pairs, o_pvals, o_pvalt, o_hist, o_status;
     size_t bytes = 0;
 };
 
@@ -155,6 +155,10 @@ int make_plan(int n_items, const int32_t* ndims, const int64_t* dims, const floa
     P.o_yn = take(sizeof(uint32_t) * P.cap_s);
     P.o_on = take(sizeof(uint32_t) * P.cap_s);
     P.o_yr = take(sizeof(uint32_t) * P.cap_s);
+    P.o_na0 = take(sizeof(uint32_t) * P.cap_s);
+    P.o_na1 = take(sizeof(uint32_t) * P.cap_s);
+    P.o_nb0 = take(sizeof(uint32_t) * P.cap_s);
+    P.o_nb1 = take(sizeof(uint32_t) * P.cap_s);
     P.o_pairs = take(sizeof(cp_pair) * P.cap_p);
     P.o_pvals = P.o_act0;  // the active lists are dead once both union-finds are done
     P.o_pvalt = P.o_act1;
@@ -246,12 +250,16 @@ int run(const Plan& P, cp_pair* d_out, int64_t capacity, int64_t* h_out_count, i
     up.res = res0;
     up.act[0] = act0;
     up.act[1] = act1;
+    up.na[0] = at<uint32_t>(ws, P.o_na0);
+    up.na[1] = at<uint32_t>(ws, P.o_na1);
+    up.nb[0] = at<uint32_t>(ws, P.o_nb0);
+    up.nb[1] = at<uint32_t>(ws, P.o_nb1);
     up.ynode = at<uint32_t>(ws, P.o_yn);
     up.onode = at<uint32_t>(ws, P.o_on);
     up.yrid = at<uint32_t>(ws, P.o_yr);
     up.pairs = pairs;
     up.pair_cap = P.cap_p;
-    up.dual_keys = st;
+    up.dual_keys = P.tab.n2d > 0 ? st : nullptr;  // cross-pruning feeds the dual list of 2D items only
     up.d_ndual = &ctr->n_st;
     up.dual_cap = P.cap_s;
     up.ctr = ctr;
@@ -430,6 +438,31 @@ int cubical_persistence_stats(const void* d_workspace, cp_stats* h_stats, void* 
 }
 
 long long cp_launch_count(void) { return g_launches.load(); }
+
+int cubical_persistence_uf_trace(const void* d_workspace, int dual, uint32_t* h_active, double* h_us, int cap,
+                                 void* stream) {
+    return cubical_persistence_uf_trace2(d_workspace, dual, h_active, h_us, nullptr, nullptr, cap, stream);
+}
+
+int cubical_persistence_uf_trace2(const void* d_workspace, int dual, uint32_t* h_active, double* h_us,
+                                  double* h_us_phase_a, uint64_t* h_hops, int cap, void* stream) {
+    if (!d_workspace || !h_active || !h_us || cap <= 0 || (dual != 0 && dual != 1)) return CP_ERR_ARG;
+    Counters h;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (cudaMemcpyAsync(&h, d_workspace, sizeof(Counters), cudaMemcpyDeviceToHost, s) != cudaSuccess) return CP_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return CP_ERR_CUDA;
+    uint32_t rounds = dual ? h.roundst : h.rounds0;
+    int n = int(std::min<uint32_t>(rounds + 1, uint32_t(kTraceRounds)));
+    n = std::min(n, cap);
+    for (int i = 0; i < n; ++i) {
+        h_active[i] = h.trace_active[dual][i];
+        h_us[i] = double(h.trace_t[dual][i] - h.trace_t[dual][0]) * 1e-3;
+        if (h_us_phase_a)
+            h_us_phase_a[i] = h.trace_ta[dual][i] ? double(h.trace_ta[dual][i] - h.trace_t[dual][0]) * 1e-3 : 0.0;
+        if (h_hops) h_hops[i] = h.trace_hops[dual][i];
+    }
+    return n;
+}
 
 int cp_profile(int enable) {
     std::lock_guard<std::mutex> lk(g_mu);

@@ -58,7 +58,14 @@ struct Counters {
     uint32_t pad[7];
     unsigned long long gmin[kMaxItems];  // (ord bits << 32 | local vertex) of each item's minimum
     int64_t out_count;
+    // union-find trace: active survivors and device time at the start of each
+    // of the first kTraceRounds rounds (H0, dual)
+    uint32_t trace_active[2][48];
+    unsigned long long trace_t[2][48];
+    unsigned long long trace_ta[2][48];   // end of phase A
+    unsigned long long trace_hops[2][48]; // parent hops walked in phase A
 };
+constexpr int kTraceRounds = 48;
 
 // ---------------------------------------------------------------- order keys
 // Order-preserving bits of a finite float: a < b as floats <=> ord(a) < ord(b)

@@ -92,11 +92,6 @@ __global__ void k_scatter(const cp_pair* __restrict__ pairs, int64_t n, const fl
     }
 }
 
-__global__ void k_round(const double* __restrict__ acc, float* __restrict__ grad, int64_t n) {
-    for (int64_t i = int64_t(blockIdx.x) * kT + threadIdx.x; i < n; i += int64_t(gridDim.x) * kT)
-        grad[i] = float(acc[i]);
-}
-
 // Total-persistence loss of the pairs above a persistence threshold and its
 // gradient: dL/ddeath = 2 (d - b), dL/dbirth = -2 (d - b).  The loss is summed
 // in a fixed order (per-block partials, then one ordered pass), so it is
@@ -137,6 +132,31 @@ __global__ void k_loss_sum(const double* partials, int n, double* loss) {
     }
 }
 
+// Sparse accumulation: only the birth and death pixels of the pairs carry
+// gradient, so the accumulators of those pixels alone are cleared, filled and
+// rounded; the output is zeroed as a whole first.
+__global__ void k_touch_clear(const cp_pair* __restrict__ pairs, int64_t n, const int64_t* __restrict__ offs,
+                              double* acc, int64_t n_pixels) {
+    for (int64_t i = int64_t(blockIdx.x) * kT + threadIdx.x; i < n; i += int64_t(gridDim.x) * kT) {
+        const cp_pair& p = pairs[i];
+        int64_t off = offs ? offs[p.item] : 0;
+        int64_t qb = off + p.birth_pixel, qd = off + p.death_pixel;
+        if (p.birth_pixel >= 0 && qb < n_pixels) acc[qb] = 0.0;
+        if (p.death_pixel >= 0 && qd < n_pixels) acc[qd] = 0.0;
+    }
+}
+
+__global__ void k_touch_round(const cp_pair* __restrict__ pairs, int64_t n, const int64_t* __restrict__ offs,
+                              const double* __restrict__ acc, float* __restrict__ grad, int64_t n_pixels) {
+    for (int64_t i = int64_t(blockIdx.x) * kT + threadIdx.x; i < n; i += int64_t(gridDim.x) * kT) {
+        const cp_pair& p = pairs[i];
+        int64_t off = offs ? offs[p.item] : 0;
+        int64_t qb = off + p.birth_pixel, qd = off + p.death_pixel;
+        if (p.birth_pixel >= 0 && qb < n_pixels) grad[qb] = float(acc[qb]);
+        if (p.death_pixel >= 0 && qd < n_pixels) grad[qd] = float(acc[qd]);
+    }
+}
+
 int grid_for(int64_t n) {
     int64_t b = (n + kT - 1) / kT;
     int64_t cap = int64_t(device_sm_count()) * 8;
@@ -151,12 +171,13 @@ cudaError_t launch_loss_backward(const cp_pair* pairs, int64_t n, float tau, con
                                  double* partials, int nparts, double* d_loss, float* grad, int64_t n_pixels,
                                  cudaStream_t s) {
     if (nparts < kLossBlocks) return cudaErrorInvalidValue;
-    cudaError_t e = cudaMemsetAsync(acc, 0, sizeof(double) * size_t(n_pixels), s);
+    cudaError_t e = cudaMemsetAsync(grad, 0, sizeof(float) * size_t(n_pixels), s);
     if (e != cudaSuccess) return e;
+    k_touch_clear<<<grid_for(n), kT, 0, s>>>(pairs, n, offs, acc, n_pixels);
     k_loss_scatter<<<kLossBlocks, kT, 0, s>>>(pairs, n, tau, offs, acc, n_pixels, partials);
     k_loss_sum<<<1, 32, 0, s>>>(partials, kLossBlocks, d_loss);
-    k_round<<<grid_for(n_pixels), kT, 0, s>>>(acc, grad, n_pixels);
-    note_launches(3);
+    k_touch_round<<<grid_for(n), kT, 0, s>>>(pairs, n, offs, acc, grad, n_pixels);
+    note_launches(4);
     return cudaGetLastError();
 }
 
@@ -189,14 +210,14 @@ cudaError_t launch_gather(const cp_pair* pairs, const uint32_t* vals, const uint
 
 cudaError_t launch_backward(const cp_pair* pairs, int64_t n, const float* gb, const float* gd, const int64_t* offs,
                             double* acc, float* grad, int64_t n_pixels, cudaStream_t s) {
-    cudaError_t e = cudaMemsetAsync(acc, 0, sizeof(double) * size_t(n_pixels), s);
+    cudaError_t e = cudaMemsetAsync(grad, 0, sizeof(float) * size_t(n_pixels), s);
     if (e != cudaSuccess) return e;
     if (n > 0) {
+        k_touch_clear<<<grid_for(n), kT, 0, s>>>(pairs, n, offs, acc, n_pixels);
         k_scatter<<<grid_for(n), kT, 0, s>>>(pairs, n, gb, gd, offs, acc, n_pixels);
-        note_launches(1);
+        k_touch_round<<<grid_for(n), kT, 0, s>>>(pairs, n, offs, acc, grad, n_pixels);
+        note_launches(3);
     }
-    k_round<<<grid_for(n_pixels), kT, 0, s>>>(acc, grad, n_pixels);
-    note_launches(1);
     return cudaGetLastError();
 }
 

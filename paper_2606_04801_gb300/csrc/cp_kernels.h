@@ -55,7 +55,9 @@ struct UfParams {
     uint32_t* uf;
     const uint64_t* age;
     uint64_t* res;
-    uint32_t* act[2];
+    uint32_t* act[2];         // survivor index of each active slot (ping-pong)
+    uint32_t* na[2];          // current root of the first endpoint of each active slot
+    uint32_t* nb[2];          // current root of the second endpoint
     uint32_t* ynode;
     uint32_t* onode;
     uint32_t* yrid;

@@ -191,8 +191,13 @@ uint64_t classify(const Stencil& st, uint32_t rel) {
         else unite(ra, rb);
     }
     uint64_t e = uint64_t(direct) | (uint64_t(h0_surv) << 3);
-    for (int t = 0; t < 8; ++t) e |= uint64_t(dual_code[t]) << (9 + 4 * t);
+    uint32_t in_mask = 0;
+    for (int t = 0; t < 8; ++t) {
+        e |= uint64_t(dual_code[t]) << (9 + 4 * t);
+        if (dual_code[t] != 15) in_mask |= 1u << t;
+    }
     e |= uint64_t(dual_surv) << 41;
+    e |= uint64_t(in_mask) << 53;
     return e;
 }
 

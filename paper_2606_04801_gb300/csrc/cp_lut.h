@@ -23,6 +23,7 @@
 //                            locally, 8 = survives locally (dual root),
 //                            15 = not in L(v)
 //   bits 41..52  dual_surv : facet slots of L(v) left for the dual union-find
+//   bits 53..60  in_l      : top-cell slots that belong to L(v) (dual code != 15)
 // 2D uses the same fields with 4 face slots, 4 facet slots (the same edges)
 // and 4 top-cell slots.
 //
@@ -41,6 +42,7 @@ inline int lut_direct(uint64_t e) { return int(e & 7u); }
 inline uint32_t lut_h0_surv(uint64_t e) { return uint32_t((e >> 3) & 0x3Fu); }
 inline uint32_t lut_dual(uint64_t e, int t) { return uint32_t((e >> (9 + 4 * t)) & 0xFu); }
 inline uint32_t lut_dual_surv(uint64_t e) { return uint32_t((e >> 41) & 0xFFFu); }
+inline uint32_t lut_in_l(uint64_t e) { return uint32_t((e >> 53) & 0xFFu); }
 
 // Offsets and slot tables for one dimension.
 struct Stencil {

@@ -20,8 +20,10 @@
 
 namespace cp {
 
-__constant__ uint64_t c_lut2d[256];
-__constant__ uint16_t c_disp3d[1 << 12];
+// Lookup tables in global memory, read through the read-only cache (lanes of
+// a warp look up different entries, which constant memory would serialise).
+__device__ uint64_t g_lut2d[256];
+__device__ uint16_t g_disp3d[1 << 12];
 __device__ uint64_t g_entries3d[1 << 14];  // perfect-hash slots of the 3D table (128 KB)
 
 // slot -> stencil bit tables
@@ -274,7 +276,7 @@ __device__ __forceinline__ uint32_t collapse3(uint32_t raw) {
 
 __device__ __forceinline__ uint64_t lookup3(uint32_t rel) {
     uint32_t b = (rel * 0x9E3779B1u) >> (32 - 12);
-    uint32_t d = c_disp3d[b];
+    uint32_t d = __ldg(g_disp3d + b);
     uint32_t s = ((rel ^ (d * 0x27D4EB2Fu)) * 0x85EBCA77u) >> (32 - 14);
     return __ldg(g_entries3d + s);
 }
@@ -295,6 +297,8 @@ __global__ void __launch_bounds__(kThreads) k_prune2d(ItemTable tab, Outs o) {
     const Item& it = tab.it[ii];
     const int lt = t - it.tile0;
     const int x0 = (lt % it.tx) * kBX, y0 = (lt / it.tx) * kT2Y;
+    __shared__ uint64_t lut[256];
+    lut[tid] = g_lut2d[tid];
     if (tid == 0) {
         sg.n_s0 = sg.n_st = sg.n_r0 = sg.n_rt = 0;
         sg.gmin = ~0ull;
@@ -327,7 +331,7 @@ __global__ void __launch_bounds__(kThreads) k_prune2d(ItemTable tab, Outs o) {
             raw |= (c[SW] < cv) ? 64u : 0u;
             raw |= (c[SW + 1] < cv) ? 128u : 0u;
         }
-        uint64_t e = c_lut2d[raw];
+        uint64_t e = lut[raw];
         uint32_t vg = uint32_t(it.voff + int64_t(y) * it.W + x);
         emit_vertex<2>(sg, o, it, valid, 0, y, x, vg, ord_bits(cv), e, my_min);
         __syncthreads();
@@ -337,79 +341,380 @@ __global__ void __launch_bounds__(kThreads) k_prune2d(ItemTable tab, Outs o) {
 }
 
 // ---------------------------------------------------------------- 3D
-// Tile: 32 x 8 x kT3Z vertices (x, y, z), CTA 32 x 8, one z column per thread.
-constexpr int kT3Z = 8;
+// A CTA of 8 warps owns a patch of 32 x 8 vertices (x, y) and marches
+// through a chunk of kZC planes in z.  Each plane of the patch plus a
+// one-vertex halo (34 x 10 floats) is loaded once per CTA into a 4-slot
+// shared-memory ring, one step ahead of its use (the global loads of plane
+// z+2 are issued before the work on plane z and stored after it), with one
+// barrier per step.  Each thread keeps the 3x3 neighbourhoods of planes z-1
+// and z in registers and reads the 3x3 of plane z+1 from the ring.
+// Survivors and roots are staged per warp and flushed with one atomic per
+// buffer when a buffer would overflow and at the end of the kernel.
+constexpr int kW3 = 8;          // warps per CTA (one row of the patch each)
+constexpr int kZC = 64;         // planes per task
+constexpr int kCapW0 = 32 * 5;   // staged H0 keys per warp: one step's maximum
+constexpr int kCapWT = 32 * 7;   // staged dual keys per warp: one step's maximum
+constexpr int kCapWR = 32;       // staged roots per warp and kind
+constexpr int kRW = 34, kRH = kW3 + 2, kRP = kRW * kRH;  // ring plane: 34 x 10
 
-__global__ void __launch_bounds__(kThreads) k_prune3d(ItemTable tab, Outs o) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    Stage& sg = *reinterpret_cast<Stage*>(smem_raw);
-    float* tile = reinterpret_cast<float*>(smem_raw + sizeof(Stage));  // (kT3Z+2) x 10 x 34
-    const int tid = threadIdx.y * kBX + threadIdx.x;
-    const int t = blockIdx.x;
-    const int ii = tile_item(tab, tab.n2d, tab.n - 1, t);
-    const Item& it = tab.it[ii];
-    const int lt = t - it.tile0;
-    const int x0 = (lt % it.tx) * kBX;
-    const int y0 = ((lt / it.tx) % it.ty) * kBY;
-    const int z0 = (lt / (it.tx * it.ty)) * kT3Z;
-    if (tid == 0) {
-        sg.n_s0 = sg.n_st = sg.n_r0 = sg.n_rt = 0;
-        sg.gmin = ~0ull;
+struct WarpStage {
+    uint64_t s0[kCapW0];
+    uint64_t st[kCapWT];
+    uint64_t r0age[kCapWR];
+    uint64_t rtage[kCapWR];
+    uint32_t r0node[kCapWR];
+    uint32_t rtnode[kCapWR];
+};
+
+struct Smem3 {
+    float ring[4][kRP];
+    WarpStage ws[kW3];
+};
+
+struct WarpCounts {
+    uint32_t s0, st, r0, rt;
+};
+
+__device__ __forceinline__ void warp_flush(WarpStage& ws, WarpCounts& c, const Outs& o) {
+    __syncwarp();
+    const unsigned lane = lane_id();
+    uint32_t b0 = 0, bt = 0, br0 = 0, brt = 0;
+    if (lane == 0) {
+        if (c.s0) b0 = atomicAdd(&o.ctr->n_s0, c.s0);
+        if (c.st) bt = atomicAdd(&o.ctr->n_st, c.st);
+        if (c.r0) br0 = atomicAdd(&o.ctr->n_r0, c.r0);
+        if (c.rt) brt = atomicAdd(&o.ctr->n_rt, c.rt);
+        bool over = (c.s0 && b0 + c.s0 > o.cap_s) || (c.st && bt + c.st > o.cap_s) ||
+                    (c.r0 && br0 + c.r0 > o.cap_r0) || (c.rt && brt + c.rt > o.cap_rt);
+        if (over) set_status(o.ctr, kStCapacity);
     }
-    constexpr int SW = kBX + 2, SH = kBY + 2, SP = SW * SH;
-    for (int i = tid; i < (kT3Z + 2) * SP; i += kThreads) {
-        int lz = i / SP, rem = i % SP, ly = rem / SW, lx = rem % SW;
-        int gz = z0 + lz - 1, gy = y0 + ly - 1, gx = x0 + lx - 1;
-        float v = __int_as_float(0x7F800000);
-        if (gz >= 0 && gz < it.D && gy >= 0 && gy < it.H && gx >= 0 && gx < it.W)
-            v = load_finite(it.img + (int64_t(gz) * it.H + gy) * it.W + gx, o.ctr);
-        tile[i] = v;
-    }
-    __syncthreads();
-    unsigned long long my_min = ~0ull;
-    const int lx = threadIdx.x, ly = threadIdx.y;
-    const int x = x0 + lx, y = y0 + ly;
-    for (int lz = 0; lz < kT3Z; ++lz) {
-        // keep room in the stage buffers for one more plane of vertices
-        if (sg.n_s0 > uint32_t(kCapS - 5 * kThreads) || sg.n_st > uint32_t(kCapS - 7 * kThreads) ||
-            sg.n_r0 > uint32_t(kCapR - kThreads) || sg.n_rt > uint32_t(kCapR - kThreads))
-            flush(sg, o);
-        int z = z0 + lz;
-        bool valid = z < it.D && y < it.H && x < it.W;
-        const float* c = tile + ((lz + 1) * SH + (ly + 1)) * SW + (lx + 1);
-        float cv = c[0];
-        uint32_t raw = 0;
-        if (valid) {
-#pragma unroll
-            for (int n = 0; n < 27; ++n) {
-                if (n == 13) continue;
-                const int dz = n / 9 - 1, dy = (n / 3) % 3 - 1, dx = n % 3 - 1;
-                float nv = c[(dz * SH + dy) * SW + dx];
-                bool lower = n < 13 ? (nv <= cv) : (nv < cv);
-                raw |= lower ? (1u << n) : 0u;
-            }
+    b0 = __shfl_sync(0xFFFFFFFFu, b0, 0);
+    bt = __shfl_sync(0xFFFFFFFFu, bt, 0);
+    br0 = __shfl_sync(0xFFFFFFFFu, br0, 0);
+    brt = __shfl_sync(0xFFFFFFFFu, brt, 0);
+    for (uint32_t i = lane; i < c.s0; i += 32)
+        if (b0 + i < o.cap_s) o.s0[b0 + i] = ws.s0[i];
+    for (uint32_t i = lane; i < c.st; i += 32)
+        if (bt + i < o.cap_s) o.st[bt + i] = ws.st[i];
+    for (uint32_t i = lane; i < c.r0; i += 32) {
+        uint32_t g = br0 + i;
+        if (g < o.cap_r0) {
+            o.age0[g] = ws.r0age[i];
+            o.res0[g] = 0;
+            o.uf0[ws.r0node[i]] = kTag | g;
+        } else {
+            o.uf0[ws.r0node[i]] = kTag;  // out of capacity: keep the forest well formed (result flagged invalid)
         }
-        uint64_t e = lookup3(collapse3(raw));
-        uint32_t vg = uint32_t(it.voff + (int64_t(z) * it.H + y) * it.W + x);
-        emit_vertex<3>(sg, o, it, valid, z, y, x, vg, ord_bits(cv), e, my_min);
-        __syncthreads();
     }
-    flush(sg, o);
-    finish_min(sg, o, ii, my_min);
+    for (uint32_t i = lane; i < c.rt; i += 32) {
+        uint32_t g = brt + i;
+        if (g < o.cap_rt) {
+            o.aget[g] = ws.rtage[i];
+            o.rest[g] = 0;
+            o.uft[ws.rtnode[i]] = kTag | g;
+        } else {
+            o.uft[ws.rtnode[i]] = kTag;
+        }
+    }
+    c.s0 = c.st = c.r0 = c.rt = 0;
+    __syncwarp();
+}
+
+// lower-than bit: all ones when the neighbour precedes the centre
+__device__ __forceinline__ uint32_t set_le(float a, float b) {
+    uint32_t r;
+    asm("set.le.u32.f32 %0, %1, %2;" : "=r"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ uint32_t set_lt(float a, float b) {
+    uint32_t r;
+    asm("set.lt.u32.f32 %0, %1, %2;" : "=r"(r) : "f"(a), "f"(b));
+    return r;
+}
+
+struct Nbr {
+    float v[3][3];  // [row y-1, y, y+1][col x-1, x, x+1] of one plane
+};
+
+__device__ __forceinline__ void read_nbr(const float* plane, int ly, int lx, Nbr& P) {
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) P.v[r][c] = plane[(ly + r) * kRW + (lx + c)];
+}
+
+// raw mask: bit n = 9a + 3b + c set when the neighbour at plane a, row b,
+// column c precedes the centre (ties: earlier linear index first)
+__device__ __forceinline__ uint32_t mask26(const Nbr& A, const Nbr& B, const Nbr& C) {
+    const float cv = B.v[1][1];
+    uint32_t raw = 0;
+#pragma unroll
+    for (int n = 26; n >= 0; --n) {
+        if (n == 13) continue;
+        const int a = n / 9, b = (n / 3) % 3, c = n % 3;
+        const Nbr& P = a == 0 ? A : (a == 1 ? B : C);
+        const uint32_t t = n < 13 ? set_le(P.v[b][c], cv) : set_lt(P.v[b][c], cv);
+        raw = (raw << 1) - t;  // append one bit (t is 0 or all ones)
+        if (n == 14) raw <<= 1;  // leave bit 13 (the centre) clear
+    }
+    return raw;
+}
+
+// Plane loader: each thread owns up to two ring positions of the next plane.
+// Out-of-image positions read +inf (they never precede anything).  A
+// non-finite pixel fails the call and reads as the largest finite float, so
+// the order stays total and every structure written stays well formed.
+struct PlaneLoad {
+    float v0, v1;
+    bool bad;
+};
+
+// The (at most two) ring positions a thread loads, fixed for a task: offset
+// of the pixel within a plane and whether it lies inside the image.
+struct RingPos {
+    uint32_t off0, off1;
+    bool in0, in1;
+};
+
+__device__ __forceinline__ void ring_positions(const Item& it, int x0, int y0, RingPos& rp) {
+    const int tid = threadIdx.x;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const int i = tid + k * (kW3 * 32);
+        const int ly = i / kRW, lx = i - ly * kRW;
+        const int gy = y0 + ly - 1, gx = x0 + lx - 1;
+        const bool in = i < kRP && unsigned(gy) < unsigned(it.H) && unsigned(gx) < unsigned(it.W);
+        const uint32_t off = in ? uint32_t(gy) * uint32_t(it.W) + uint32_t(gx) : 0u;
+        if (k == 0) {
+            rp.off0 = off;
+            rp.in0 = in;
+        } else {
+            rp.off1 = off;
+            rp.in1 = in;
+        }
+    }
+}
+
+__device__ __forceinline__ void issue_plane(const Item& it, int z, const RingPos& rp, uint32_t HW, PlaneLoad& pl) {
+    const float inf = __int_as_float(0x7F800000), fmax = 3.40282347e38f;
+    const bool zin = unsigned(z) < unsigned(it.D);
+    const float* base = it.img + uint32_t(z) * HW;
+    float v0 = inf, v1 = inf;
+    if (zin && rp.in0) v0 = __ldg(base + rp.off0);
+    if (zin && rp.in1) v1 = __ldg(base + rp.off1);
+    const bool b0 = zin && rp.in0 && !(fabsf(v0) <= fmax);
+    const bool b1 = zin && rp.in1 && !(fabsf(v1) <= fmax);
+    pl.v0 = b0 ? fmax : v0;
+    pl.v1 = b1 ? fmax : v1;
+    pl.bad = b0 || b1;
+}
+
+__device__ __forceinline__ void store_plane(float* plane, const PlaneLoad& pl, Counters* ctr) {
+    const int tid = threadIdx.x;
+    plane[tid] = pl.v0;
+    if (tid + kW3 * 32 < kRP) plane[tid + kW3 * 32] = pl.v1;
+    if (pl.bad) set_status(ctr, kStNonfinite);
+}
+
+struct Col {
+    int item, x, y, x0, y0, W, H, D;
+    uint32_t voff, toff, T, HW, HW1, W1;
+    bool xy_valid;
+    uint32_t bxy;  // boundary bits (2: y==0, 3: y==H-1, 4: x==0, 5: x==W-1)
+};
+
+// H0 forest links: a vertex may point to any vertex of its own descent chain
+// (every link of the chain formed earlier in the filtration), so when the
+// first edge of L(v) goes to the z-1 neighbour -- processed by this thread one
+// step before -- v links directly to where that neighbour links (`far`),
+// collapsing descents along z within a task.
+__device__ __forceinline__ void vertex3d(const Col& cc, const Outs& o, int z, const Nbr& A, const Nbr& B,
+                                         const Nbr& C, WarpStage& ws, WarpCounts& cnt,
+                                         unsigned long long& my_min, uint32_t& far, bool chain) {
+    const bool valid = cc.xy_valid;
+    const uint32_t raw = mask26(A, B, C);
+    const uint64_t e = valid ? lookup3(collapse3(raw)) : 0ull;
+    const uint32_t ord = ord_bits(B.v[1][1]);
+    const uint32_t vl = (uint32_t(z) * uint32_t(cc.H) + uint32_t(cc.y)) * uint32_t(cc.W) + uint32_t(cc.x);
+    const uint32_t vg = cc.voff + vl;
+    const int direct = int(e & 7u);
+    const bool root0 = valid && direct == 7;
+    if (valid && !root0) {
+        // face slots: (-1,0,0) (0,-1,0) (0,0,-1) (0,0,1) (0,1,0) (1,0,0)
+        const uint32_t mag = (direct == 0 || direct == 5) ? cc.HW : ((direct == 1 || direct == 4) ? uint32_t(cc.W) : 1u);
+        const uint32_t u = direct < 3 ? vg - mag : vg + mag;
+        far = (direct == 0 && chain) ? far : u;
+        o.uf0[vg] = far;
+    } else {
+        far = vg;
+    }
+    int rt_node = -1;
+    uint64_t rt_age = 0;
+    uint32_t in_l = uint32_t(e >> 53) & 0xFFu;
+    if (in_l) {
+        const uint32_t B6 = cc.bxy | (z == 0 ? 1u : 0u) | (z == cc.D - 1 ? 2u : 0u);
+        const uint32_t cbase = cc.toff + (uint32_t(z) * uint32_t(cc.H - 1) + uint32_t(cc.y)) * cc.W1 + uint32_t(cc.x);
+        const uint32_t OUT = cc.toff + cc.T;
+        do {
+            const int t = __ffs(in_l) - 1;
+            in_l &= in_l - 1;
+            const uint32_t code = uint32_t(e >> (9 + 4 * t)) & 15u;
+            const uint32_t self = cbase - (((t & 4) ? 0u : cc.HW1) + ((t & 2) ? 0u : cc.W1) + ((t & 1) ? 0u : 1u));
+            if (code == 8u) {
+                rt_node = int(self);
+                rt_age = make_key(ord, vg, uint32_t(18 * ((t >> 2) & 1) + 6 * ((t >> 1) & 1) + 2 * (t & 1)));
+            } else {
+                const uint32_t c = code;
+                const uint32_t sel = (1u << ((c >> 2) & 1u)) | (4u << ((c >> 1) & 1u)) | (16u << (c & 1u));
+                const uint32_t tgt = cbase - (((c & 4u) ? 0u : cc.HW1) + ((c & 2u) ? 0u : cc.W1) + ((c & 1u) ? 0u : 1u));
+                o.uft[self] = (B6 & sel) ? OUT : tgt;
+            }
+        } while (in_l);
+    }
+    if (root0) {
+        unsigned long long k = (unsigned long long)(uint64_t(ord) << 32 | vl);
+        my_min = k < my_min ? k : my_min;
+    }
+    const uint32_t h0s = valid ? uint32_t((e >> 3) & 0x3Fu) : 0u;
+    const uint32_t ds = valid ? uint32_t((e >> 41) & 0xFFFu) : 0u;
+    const bool any = (h0s | ds) != 0u || root0 || rt_node >= 0;
+    if (!__any_sync(0xFFFFFFFFu, any)) return;
+    // ---- stage survivors and roots (rare in smooth fields)
+    const uint32_t packed = __popc(h0s) | (__popc(ds) << 8) | ((root0 ? 1u : 0u) << 16) | ((rt_node >= 0 ? 1u : 0u) << 24);
+    uint32_t incl = packed;
+    const unsigned lane = lane_id();
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        uint32_t t = __shfl_up_sync(0xFFFFFFFFu, incl, d);
+        if (lane >= unsigned(d)) incl += t;
+    }
+    const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+    const uint32_t excl = incl - packed;
+    if (cnt.s0 + (total & 255u) > uint32_t(kCapW0) || cnt.st + ((total >> 8) & 255u) > uint32_t(kCapWT) ||
+        cnt.r0 + ((total >> 16) & 255u) > uint32_t(kCapWR) || cnt.rt + (total >> 24) > uint32_t(kCapWR))
+        warp_flush(ws, cnt, o);
+    uint32_t p0 = cnt.s0 + (excl & 255u), pt = cnt.st + ((excl >> 8) & 255u);
+    uint32_t m = h0s;
+    while (m) {
+        const int s = __ffs(m) - 1;
+        m &= m - 1;
+        const uint32_t n = s == 0 ? 4u : (s == 1 ? 10u : (s == 2 ? 12u : (s == 3 ? 14u : (s == 4 ? 16u : 22u))));
+        ws.s0[p0++] = make_key(ord, vg, n);
+    }
+    m = ds;
+    while (m) {
+        const int f = __ffs(m) - 1;
+        m &= m - 1;
+        // facet slots 0..11 -> stencil bits 1,3,5,7,9,11,15,17,19,21,23,25
+        const uint32_t n = f < 6 ? uint32_t(2 * f + 1) : uint32_t(2 * f + 3);
+        ws.st[pt++] = ~make_key(ord, vg, n);
+    }
+    if (root0) {
+        const uint32_t p = cnt.r0 + ((excl >> 16) & 255u);
+        ws.r0node[p] = vg;
+        ws.r0age[p] = make_key(ord, vg, 0);
+    }
+    if (rt_node >= 0) {
+        const uint32_t p = cnt.rt + (excl >> 24);
+        ws.rtnode[p] = uint32_t(rt_node);
+        ws.rtage[p] = rt_age;
+    }
+    cnt.s0 += total & 255u;
+    cnt.st += (total >> 8) & 255u;
+    cnt.r0 += (total >> 16) & 255u;
+    cnt.rt += total >> 24;
+    __syncwarp();
+}
+
+__global__ void __launch_bounds__(kW3 * 32, 4) k_prune3d(ItemTable tab, Outs o) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Smem3& sm = *reinterpret_cast<Smem3*>(smem_raw);
+    const int warp = threadIdx.x >> 5;
+    const int lane = int(lane_id());
+    WarpStage& ws = sm.ws[warp];
+    WarpCounts cnt = {0, 0, 0, 0};
+    for (int task = blockIdx.x; task < tab.tiles3d; task += gridDim.x) {
+        const int ii = tile_item(tab, tab.n2d, tab.n - 1, task);
+        const Item& it = tab.it[ii];
+        const int lt = task - it.tile0;
+        // task order: x segment fastest, then y segment, then z chunk, so the
+        // CTAs running together cover a compact region and share halos in L2
+        const int xs = lt % it.tx;
+        const int rest = lt / it.tx;
+        const int ys = rest % it.ty;
+        const int zc = rest / it.ty;
+        Col cc;
+        cc.item = ii;
+        cc.W = it.W;
+        cc.H = it.H;
+        cc.D = it.D;
+        cc.x0 = xs * 32;
+        cc.y0 = ys * kW3;
+        cc.x = cc.x0 + lane;
+        cc.y = cc.y0 + warp;
+        cc.xy_valid = cc.x < it.W && cc.y < it.H;
+        cc.bxy = (cc.y == 0 ? 4u : 0u) | (cc.y == it.H - 1 ? 8u : 0u) | (cc.x == 0 ? 16u : 0u) |
+                 (cc.x == it.W - 1 ? 32u : 0u);
+        cc.voff = uint32_t(it.voff);
+        cc.toff = uint32_t(it.toff);
+        cc.T = uint32_t(it.T);
+        cc.HW = uint32_t(it.H) * uint32_t(it.W);
+        cc.W1 = uint32_t(it.W - 1);
+        cc.HW1 = uint32_t(it.H - 1) * uint32_t(it.W - 1);
+        RingPos rp;
+        ring_positions(it, cc.x0, cc.y0, rp);
+        const int z0 = zc * kZC, z1 = min(it.D, z0 + kZC);
+        unsigned long long my_min = ~0ull;
+        uint32_t far = 0;
+        PlaneLoad pl;
+        __syncthreads();  // the ring may still be read by the previous task
+        issue_plane(it, z0 - 1, rp, cc.HW, pl);
+        store_plane(sm.ring[(z0 + 3) & 3], pl, o.ctr);
+        issue_plane(it, z0, rp, cc.HW, pl);
+        store_plane(sm.ring[z0 & 3], pl, o.ctr);
+        issue_plane(it, z0 + 1, rp, cc.HW, pl);
+        store_plane(sm.ring[(z0 + 1) & 3], pl, o.ctr);
+        __syncthreads();
+        Nbr A, B, C;
+        read_nbr(sm.ring[(z0 + 3) & 3], warp, lane, A);
+        read_nbr(sm.ring[z0 & 3], warp, lane, B);
+        // one step: prefetch plane z+2, read plane z+1 into `nxt`, process z
+#define CP_STEP(Pm, P0, Pp)                                          \
+    {                                                                \
+        issue_plane(it, z + 2, rp, cc.HW, pl);                       \
+        read_nbr(sm.ring[(z + 1) & 3], warp, lane, Pp);              \
+        vertex3d(cc, o, z, Pm, P0, Pp, ws, cnt, my_min, far, z > z0); \
+        store_plane(sm.ring[(z + 2) & 3], pl, o.ctr);                \
+        __syncthreads();                                             \
+        ++z;                                                         \
+    }
+        int z = z0;
+        for (; z + 3 <= z1;) {
+            CP_STEP(A, B, C)
+            CP_STEP(B, C, A)
+            CP_STEP(C, A, B)
+        }
+        if (z < z1) CP_STEP(A, B, C)
+        if (z < z1) CP_STEP(B, C, A)
+#undef CP_STEP
+        unsigned long long w = warp_min_u64(my_min);
+        if (lane == 0 && w != ~0ull) atomicMin(&o.ctr->gmin[ii], w);
+    }
+    if (__any_sync(0xFFFFFFFFu, (cnt.s0 | cnt.st | cnt.r0 | cnt.rt) != 0)) warp_flush(ws, cnt, o);
 }
 
 // ---------------------------------------------------------------- host side
 size_t prune_smem2d() { return sizeof(Stage) + sizeof(float) * (kT2Y + 2) * (kBX + 2); }
-size_t prune_smem3d() { return sizeof(Stage) + sizeof(float) * (kT3Z + 2) * (kBY + 2) * (kBX + 2); }
+size_t prune_smem3d() { return sizeof(Smem3); }
 int prune_tile_x() { return kBX; }
 int prune_tile_y2d() { return kT2Y; }
-int prune_tile_y3d() { return kBY; }
-int prune_tile_z3d() { return kT3Z; }
+int prune_tile_y3d() { return kW3; }
+int prune_tile_z3d() { return kZC; }
 
 cudaError_t upload_luts(const uint64_t* lut2d, const uint16_t* disp3d, const uint64_t* entries3d) {
-    cudaError_t e = cudaMemcpyToSymbol(c_lut2d, lut2d, sizeof(uint64_t) * 256);
+    cudaError_t e = cudaMemcpyToSymbol(g_lut2d, lut2d, sizeof(uint64_t) * 256);
     if (e != cudaSuccess) return e;
-    e = cudaMemcpyToSymbol(c_disp3d, disp3d, sizeof(uint16_t) * (1 << 12));
+    e = cudaMemcpyToSymbol(g_disp3d, disp3d, sizeof(uint16_t) * (1 << 12));
     if (e != cudaSuccess) return e;
     return cudaMemcpyToSymbol(g_entries3d, entries3d, sizeof(uint64_t) * (1 << 14));
 }
@@ -429,9 +734,13 @@ cudaError_t launch_prune(const ItemTable& tab, const PruneOuts& po, cudaStream_t
     o.cap_rt = po.cap_rt;
     o.ctr = po.ctr;
     static bool attr_set = false;
+    static int blocks3d = 0;
     if (!attr_set) {
         cudaFuncSetAttribute(k_prune2d, cudaFuncAttributeMaxDynamicSharedMemorySize, int(prune_smem2d()));
         cudaFuncSetAttribute(k_prune3d, cudaFuncAttributeMaxDynamicSharedMemorySize, int(prune_smem3d()));
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_prune3d, kW3 * 32, prune_smem3d());
+        blocks3d = device_sm_count() * (per_sm > 0 ? per_sm : 1);
         attr_set = true;
     }
     if (tab.tiles2d > 0) {
@@ -439,7 +748,8 @@ cudaError_t launch_prune(const ItemTable& tab, const PruneOuts& po, cudaStream_t
         note_launches(1);
     }
     if (tab.tiles3d > 0) {
-        k_prune3d<<<tab.tiles3d, dim3(kBX, kBY), prune_smem3d(), s>>>(tab, o);
+        int grid = tab.tiles3d < blocks3d ? tab.tiles3d : blocks3d;
+        k_prune3d<<<grid, kW3 * 32, prune_smem3d(), s>>>(tab, o);
         note_launches(1);
     }
     return cudaGetLastError();

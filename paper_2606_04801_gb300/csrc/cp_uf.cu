@@ -27,7 +27,7 @@
 namespace cp {
 namespace {
 
-constexpr int kT = 256;
+constexpr int kT = 1024;  // one large CTA per SM keeps grid barriers cheap
 constexpr uint32_t kInvalid = 0xFFFFFFFFu;
 
 struct UfKernelArgs {
@@ -35,20 +35,28 @@ struct UfKernelArgs {
     UfParams p;
 };
 
-__device__ __forceinline__ uint32_t find_root(uint32_t* uf, uint32_t x, uint32_t& rid) {
-    uint32_t px = __ldcg(uf + x);
-    while (!(px & kTag)) {
-        uint32_t gp = __ldcg(uf + px);
-        if (gp & kTag) {
-            rid = gp & ~kTag;
-            return px;
+// Roots of a and b, walking both paths in lockstep (two independent loads in
+// flight per thread).  The walks only read: the active survivors carry their
+// roots from round to round, so nothing needs compressing, and random partial
+// writes into the large forest array would cost read-modify-write traffic.
+__device__ __forceinline__ void find_two(const uint32_t* uf, uint32_t a, uint32_t b, uint32_t& rida, uint32_t& ridb,
+                                         uint32_t& ra, uint32_t& rb, uint32_t& hops) {
+    uint32_t pa = __ldcg(uf + a), pb = __ldcg(uf + b);
+    while (!(pa & kTag) || !(pb & kTag)) {
+        ++hops;
+        if (!(pa & kTag)) {
+            a = pa;
+            pa = __ldcg(uf + a);
         }
-        __stcg(uf + x, gp);  // path halving: x now points to its grandparent
-        x = gp;
-        px = __ldcg(uf + x);
+        if (!(pb & kTag)) {
+            b = pb;
+            pb = __ldcg(uf + b);
+        }
     }
-    rid = px & ~kTag;
-    return x;
+    ra = a;
+    rb = b;
+    rida = pa & ~kTag;
+    ridb = pb & ~kTag;
 }
 
 __device__ __forceinline__ void reserve(uint64_t* res, uint32_t rid, uint64_t stamp) {
@@ -74,7 +82,7 @@ __device__ void grid_barrier(Counters* ctr, uint32_t nblocks) {
                     set_status(ctr, kStTimeout);
                     break;
                 }
-                __nanosleep(64);
+                __nanosleep(20);
             }
         }
         __threadfence();
@@ -182,31 +190,43 @@ __global__ void __launch_bounds__(kT) k_uf(UfKernelArgs args) {
     int cur = 0;
     uint32_t round = 1;
     for (;; ++round) {
+        if (gtid == 0 && round <= uint32_t(kTraceRounds)) {
+            ctr->trace_active[p.dual][round - 1] = n;
+            ctr->trace_t[p.dual][round - 1] = global_timer_ns();
+        }
         if (n == 0) break;
         if (gtid == 0) ctr->act_count[round % 3] = 0;
         // ---- phase A: find roots, resolve positives, reserve
+        uint32_t hops = 0;
         for (uint32_t j0 = blockIdx.x * kT; j0 < n; j0 += gstride) {
             uint32_t j = j0 + threadIdx.x;
             bool active = j < n;
-            uint32_t i = 0;
             bool cross = false;
             uint64_t ckey = 0;
             if (active) {
-                i = round == 1 ? j : __ldcg(p.act[cur] + j);
-                uint64_t key = p.keys[i];
-                if (p.dual) key = ~key;
-                uint32_t a, b;
-                int item;
-                endpoints(tab, key, p.dual, a, b, item);
-                uint32_t ra_id, rb_id;
-                uint32_t ra = find_root(p.uf, a, ra_id);
-                uint32_t rb = find_root(p.uf, b, rb_id);
+                uint32_t i, a, b;
+                int item = 0;
+                if (round == 1) {
+                    i = j;
+                    uint64_t key = p.keys[i];
+                    if (p.dual) key = ~key;
+                    endpoints(tab, key, p.dual, a, b, item);
+                } else {
+                    i = __ldcg(p.act[cur] + j);
+                    a = __ldcg(p.na[cur] + j);
+                    b = __ldcg(p.nb[cur] + j);
+                }
+                uint32_t ra, ra_id, rb, rb_id;
+                find_two(p.uf, a, b, ra_id, rb_id, ra, rb, hops);
                 if (ra == rb) {
                     __stcg(p.ynode + j, kInvalid);
                     // 2D cross-pruning: a positive edge of H0 is a merging facet of the dual
-                    if (!p.dual && tab.it[item].ndim == 2 && (key & 1u)) {
-                        cross = true;
-                        ckey = ~(key & ~1ull);
+                    if (!p.dual && p.dual_keys) {
+                        uint64_t key = p.keys[i];
+                        if (tab.it[item_of_vertex(tab, key_vertex(key))].ndim == 2 && (key & 1u)) {
+                            cross = true;
+                            ckey = ~(key & ~1ull);
+                        }
                     }
                 } else {
                     uint64_t aa = p.age[ra_id], ab = p.age[rb_id];
@@ -221,6 +241,7 @@ __global__ void __launch_bounds__(kT) k_uf(UfKernelArgs args) {
                     __stcg(p.onode + j, o);
                     __stcg(p.yrid + j, yr);
                 }
+                (void)item;
             }
             uint32_t pos = warp_append(p.d_ndual, cross);
             if (cross) {
@@ -228,7 +249,13 @@ __global__ void __launch_bounds__(kT) k_uf(UfKernelArgs args) {
                 else set_status(ctr, kStCapacity);
             }
         }
+        if (round <= uint32_t(kTraceRounds)) {
+            uint32_t h = hops;
+            for (int o = 16; o > 0; o >>= 1) h += __shfl_xor_sync(0xFFFFFFFFu, h, o);
+            if (lane_id() == 0 && h) atomicAdd(&ctr->trace_hops[p.dual][round - 1], (unsigned long long)h);
+        }
         grid_barrier(ctr, nblocks);
+        if (gtid == 0 && round <= uint32_t(kTraceRounds)) ctr->trace_ta[p.dual][round - 1] = global_timer_ns();
         // ---- phase B: commit the survivors that hold the reservation of their dying root
         uint32_t* next = p.act[cur ^ 1];
         for (uint32_t j0 = blockIdx.x * kT; j0 < n; j0 += gstride) {
@@ -255,7 +282,11 @@ __global__ void __launch_bounds__(kT) k_uf(UfKernelArgs args) {
                 }
             }
             uint32_t pos = warp_append(&ctr->act_count[round % 3], keep);
-            if (keep) next[pos] = i;
+            if (keep) {
+                next[pos] = i;
+                p.na[cur ^ 1][pos] = __ldcg(p.ynode + j);
+                p.nb[cur ^ 1][pos] = __ldcg(p.onode + j);
+            }
             uint32_t pp = warp_append(&ctr->n_pairs, emit);
             if (emit) {
                 if (pp < p.pair_cap) p.pairs[pp] = pr;
