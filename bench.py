@@ -202,6 +202,105 @@ def cpu_baseline(vol, budget_s=20.0):
     }
 
 
+def _batch_items():
+    cache = "/tmp/cp_bench_batch_v1.npz"
+    if os.path.exists(cache):
+        try:
+            z = np.load(cache)
+            return [z[f"a{i}"] for i in range(len(z.files))]
+        except Exception:
+            pass
+    items = workloads.batch(0)
+    try:
+        np.savez(cache + ".tmp.npz", **{f"a{i}": a for i, a in enumerate(items)})
+        os.replace(cache + ".tmp.npz", cache)
+    except OSError:
+        pass
+    return items
+
+
+def batched_vs_plain(dev, steps: int, warmup: int):
+    """Fwd + loss bwd of the batched workload: one CUDA-graph launch for the
+    whole batch against one call per item (same kernels, no graph)."""
+    import torch
+
+    import paper_2606_04801_gb300 as cp
+    from paper_2606_04801_gb300 import _lib
+
+    lib = _lib.load()
+    items = _batch_items()
+    shapes = [a.shape for a in items]
+    nvox = int(sum(a.size for a in items))
+    bp = cp.BatchedPersistence(shapes, tau=TAU, device=dev, graph=True)
+    bp.load([torch.from_numpy(a) for a in items])
+    for _ in range(warmup):
+        bp.step()
+    st = bp.status()
+    stream = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    for _ in range(steps):
+        bp.step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    t_batched = e0.elapsed_time(e1) / 1e3 / steps
+    # plain: one forward and one loss backward per item, sequential on one stream
+    sp = ctypes.c_void_p(int(stream.cuda_stream))
+    per = []
+    for a in items:
+        nd = a.ndim
+        dims = (ctypes.c_int64 * nd)(*a.shape)
+        wsb = lib.cubical_persistence_workspace_size(nd, dims, 0)
+        cap = a.size // 2 + 65536 + 4096
+        per.append((nd, dims, wsb, cap))
+    ws = torch.empty(max(p[2] for p in per), dtype=torch.uint8, device=dev)
+    outs = [torch.empty((p[3], 8), dtype=torch.int32, device=dev) for p in per]
+    cnts = torch.zeros(len(items), dtype=torch.int64, device=dev)
+    loss = torch.zeros(len(items), dtype=torch.float64, device=dev)
+    grad = torch.empty(nvox, dtype=torch.float32, device=dev)
+    bws = torch.empty(lib.cubical_persistence_loss_backward_workspace_size(max(a.size for a in items)),
+                      dtype=torch.uint8, device=dev)
+    offs = np.concatenate([[0], np.cumsum([a.size for a in items])[:-1]])
+
+    def plain_step():
+        for i, ((nd, dims, wsb, cap), a) in enumerate(zip(per, items)):
+            fn = lib.cubical_persistence_2d if nd == 2 else lib.cubical_persistence_3d
+            rc = fn(ctypes.c_void_p(bp.views[i].data_ptr()), dims, ctypes.c_void_p(outs[i].data_ptr()), cap, None,
+                    ctypes.c_void_p(cnts[i:].data_ptr()), ctypes.c_void_p(ws.data_ptr()), wsb, 0, sp)
+            if rc != 0:
+                raise RuntimeError(f"plain forward {i}: {rc}")
+            rc = lib.cubical_persistence_loss_backward(
+                ctypes.c_void_p(outs[i].data_ptr()), cap, ctypes.c_void_p(cnts[i:].data_ptr()), ctypes.c_float(TAU),
+                ctypes.c_void_p(loss[i:].data_ptr()), None, ctypes.c_void_p(grad[int(offs[i]):].data_ptr()), a.size,
+                ctypes.c_void_p(bws.data_ptr()), bws.numel(), sp)
+            if rc != 0:
+                raise RuntimeError(f"plain backward {i}: {rc}")
+
+    for _ in range(max(1, warmup)):
+        plain_step()
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    for _ in range(steps):
+        plain_step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    t_plain = e0.elapsed_time(e1) / 1e3 / steps
+    same = bool(abs(float(loss.sum().item()) - float(bp.loss.item())) <= 1e-9 * max(1.0, float(bp.loss.item())))
+    return {
+        "workload": "64 2D (sides 128-1024) + 8 3D (sides 64-192) blurred, rank-spaced; fwd + loss bwd",
+        "voxels": nvox,
+        "batched_graph_ms": t_batched * 1e3,
+        "batched_mvox_per_s": nvox / t_batched / 1e6,
+        "batched_items_per_s": len(items) / t_batched,
+        "plain_ms": t_plain * 1e3,
+        "plain_mvox_per_s": nvox / t_plain / 1e6,
+        "speedup": t_plain / t_batched,
+        "same_loss": same,
+        "status": st["rc"],
+    }
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -211,6 +310,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--side", type=int, default=512, help="cube side (512 is the benchmark; smaller for profiling)")
+    ap.add_argument("--no-batched", action="store_true")
     args = ap.parse_args()
     global SIDE
     SIDE = args.side
@@ -259,7 +359,7 @@ def main():
         if rc != 0:
             raise cp.CpError(rc, "forward")
         rc = lib.cubical_persistence_loss_backward(
-            ctypes.c_void_p(out.data_ptr()), cnt.value, ctypes.c_float(TAU), ctypes.c_void_p(loss.data_ptr()), None,
+            ctypes.c_void_p(out.data_ptr()), cnt.value, None, ctypes.c_float(TAU), ctypes.c_void_p(loss.data_ptr()), None,
             ctypes.c_void_p(grad.data_ptr()), N, ctypes.c_void_p(bwsp.data_ptr()), bws, sp,
         )
         if rc != 0:
@@ -369,6 +469,7 @@ def main():
         hops = (ctypes.c_uint64 * 48)()
         k = lib.cubical_persistence_uf_trace2(ctypes.c_void_p(wsp.data_ptr()), dual, act, us, usa, hops, 48, sp)
         trace[name] = [[int(act[i]), round(us[i], 1), round(usa[i], 1), int(hops[i])] for i in range(max(0, k))]
+    batched = None if args.no_batched else batched_vs_plain(dev, max(3, min(args.steps, 10)), args.warmup)
     cpu = None if args.no_cpu_baseline else cpu_baseline(vol)
     clocks = clk.summary()
     line = {
@@ -402,6 +503,7 @@ def main():
             k: v / max(1, len(k1_ms))
             for k, v in zip(["prune", "sort_h0", "uf_h0", "sort_top", "uf_top", "emit"], stage_sum)
         },
+        "batched": batched,
         "uf_trace": trace,
         "counts": {"pairs": int(cnt.value), "h0_survivors": s0, "top_survivors": stp, "h0_roots": r0, "top_roots": rt,
                    "h0_rounds": st["h0_rounds"], "top_rounds": st["top_rounds"]},

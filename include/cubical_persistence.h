@@ -211,41 +211,22 @@ int cubical_persistence_backward(const cp_pair *d_pairs, int64_t n_pairs, const 
  *       of (death - birth)^2,
  * with dL/ddeath = 2 (death - birth) and dL/dbirth = -2 (death - birth)
  * scattered to the death and birth pixels as in cubical_persistence_backward.
- *  d_loss : device, one double, receives L (summed in a fixed order, so it is
- *           the same on every run).
+ *  n_pairs   : number of pairs in d_pairs, or an upper bound when d_n_pairs
+ *              is given;
+ *  d_n_pairs : device, optional int64: the actual count (as written by a
+ *              forward call's d_out_count), read on the device so that a
+ *              forward + backward sequence needs no host round trip (and
+ *              can be captured in a CUDA graph);
+ *  d_loss    : device, one double, receives L (summed in a fixed order, so
+ *              it is the same on every run).
  * Other arguments as for cubical_persistence_backward; the workspace size is
  * cubical_persistence_loss_backward_workspace_size(n_pixels).
  */
 size_t cubical_persistence_loss_backward_workspace_size(int64_t n_pixels);
-int cubical_persistence_loss_backward(const cp_pair *d_pairs, int64_t n_pairs, float min_persistence,
-                                      double *d_loss, const int64_t *d_item_offsets, float *d_grad_image,
-                                      int64_t n_pixels, void *d_workspace, size_t ws_bytes, void *stream);
-
-/*
- * Backward scatter that allocates nothing (the paper has no counterpart: it
- * is a convenience of this library).  For callers that cannot allocate
- * device memory, such as code running while a stream is captured into a
- * CUDA graph, or code inside another framework's hooks without access to
- * its allocator, this computes exactly what cubical_persistence_backward
- * computes, but keeps its double-precision accumulators in a fixed array
- * inside the library's device image instead of a caller-provided workspace.
- *  - The array holds cubical_persistence_backward_noalloc_max_pixels()
- *    (= 4,194,304) doubles, 32 MiB; every GPU that loads the library keeps it
- *    until the process exits.  n_pixels above that maximum returns
- *    CP_ERR_CAPACITY without touching the GPU.
- *  - The first call on a device looks the array's device address up
- *    (cudaGetSymbolAddress, with that device current); make that first call
- *    before any stream capture on that device.
- *  - Every call shares the one array: each call clears the part it uses
- *    before accumulating, so consecutive calls are independent, but calls
- *    whose work overlaps on the GPU (unordered streams) race on it.
- *  - It calls no allocating function.  Other arguments as for
- *    cubical_persistence_backward.
- */
-int64_t cubical_persistence_backward_noalloc_max_pixels(void);
-int cubical_persistence_backward_noalloc(const cp_pair *d_pairs, int64_t n_pairs, const float *d_grad_birth,
-                                         const float *d_grad_death, const int64_t *d_item_offsets,
-                                         float *d_grad_image, int64_t n_pixels, void *stream);
+int cubical_persistence_loss_backward(const cp_pair *d_pairs, int64_t n_pairs, const int64_t *d_n_pairs,
+                                      float min_persistence, double *d_loss, const int64_t *d_item_offsets,
+                                      float *d_grad_image, int64_t n_pixels, void *d_workspace, size_t ws_bytes,
+                                      void *stream);
 
 /* ---------------------------------------------------------------- instrumentation */
 
@@ -262,6 +243,25 @@ int cubical_persistence_uf_trace(const void *d_workspace, int dual, uint32_t *h_
  * microseconds since the start of round 0, and the parent hops walked in it. */
 int cubical_persistence_uf_trace2(const void *d_workspace, int dual, uint32_t *h_active, double *h_us,
                                   double *h_us_phase_a, uint64_t *h_hops, int cap, void *stream);
+
+/*
+ * Debugging and stage tests (not part of the method): run only the lookup +
+ * pruning pass (K1) of a batched call, leaving in the workspace the H0
+ * forest, the dual forest, the survivor keys and the roots; and report where
+ * they are.  cubical_persistence_debug_layout writes 12 values: byte offsets
+ * of the counters, H0 forest (uint32 per vertex), dual forest (uint32 per top
+ * cell plus one outside vertex per item), H0 survivor keys (uint64), dual
+ * survivor keys (uint64, stored complemented), H0 root ages, dual root ages;
+ * then the total vertices, total top-cell slots, survivor capacity, H0 root
+ * capacity and dual root capacity.  Forest words with the top bit set are
+ * roots (low bits: root id).  Survivor and root counts are the 2nd to 5th
+ * uint32 of the counters.  Returns 12 or a CP_ERR_* code.
+ */
+int cubical_persistence_debug_prune(int n_items, const float *const *h_images, const int32_t *ndims,
+                                    const int64_t *dims, void *d_workspace, size_t ws_bytes, int64_t max_survivors,
+                                    void *stream);
+int cubical_persistence_debug_layout(int n_items, const int32_t *ndims, const int64_t *dims, int64_t max_survivors,
+                                     int64_t *h_offsets, int cap);
 
 /* Kernel launches the library has made since it was loaded. */
 long long cp_launch_count(void);

@@ -5,3 +5,4 @@ the C-ABI of include/cubical_persistence.h); this package is its binding.
 """
 from ._lib import PAIR_DTYPE, CpError, load  # noqa: F401
 from .api import Diagram, diagram, pairs_backward, persistence, persistence_batched  # noqa: F401
+from .batched import BatchedPersistence  # noqa: F401

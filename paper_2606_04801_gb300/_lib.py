@@ -74,12 +74,14 @@ _SIGS = {
     "cubical_persistence_loss_backward_workspace_size": (ctypes.c_size_t, [_I64]),
     "cubical_persistence_loss_backward": (
         ctypes.c_int,
-        [_P, _I64, ctypes.c_float, _P, _P, _P, _I64, _P, ctypes.c_size_t, _P],
+        [_P, _I64, _P, ctypes.c_float, _P, _P, _P, _I64, _P, ctypes.c_size_t, _P],
     ),
     "cubical_persistence_backward_noalloc_max_pixels": (ctypes.c_int64, []),
     "cubical_persistence_backward_noalloc": (ctypes.c_int, [_P, _I64, _P, _P, _P, _P, _I64, _P]),
     "cubical_persistence_uf_trace": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, ctypes.c_int, _P]),
     "cubical_persistence_uf_trace2": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P, _P, ctypes.c_int, _P]),
+    "cubical_persistence_debug_prune": (ctypes.c_int, [ctypes.c_int, _P, _P, _P, _P, ctypes.c_size_t, _I64, _P]),
+    "cubical_persistence_debug_layout": (ctypes.c_int, [ctypes.c_int, _P, _P, _I64, _P, ctypes.c_int]),
     "cp_launch_count": (ctypes.c_longlong, []),
     "cp_profile": (ctypes.c_int, [ctypes.c_int]),
     "cp_stage_times": (ctypes.c_int, [_P, ctypes.c_int]),

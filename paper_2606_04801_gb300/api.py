@@ -85,8 +85,12 @@ class Diagram:
 
 def _stats(ws: torch.Tensor) -> dict:
     st = CpStats()
-    _lib.load().cubical_persistence_stats(ctypes.c_void_p(ws.data_ptr()), ctypes.byref(st), ctypes.c_void_p(_stream_ptr(ws.device)))
-    return {k: int(getattr(st, k)) for k, _ in CpStats._fields_ if k != "pad"}
+    rc = _lib.load().cubical_persistence_stats(
+        ctypes.c_void_p(ws.data_ptr()), ctypes.byref(st), ctypes.c_void_p(_stream_ptr(ws.device))
+    )
+    d = {k: int(getattr(st, k)) for k, _ in CpStats._fields_ if k != "pad"}
+    d["rc"] = int(rc)
+    return d
 
 
 def _grow(st: dict, ms: int, n_total: int) -> int:

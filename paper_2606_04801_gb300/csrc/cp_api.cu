@@ -111,7 +111,7 @@ int make_plan(int n_items, const int32_t* ndims, const int64_t* dims, const floa
             edges += H * (W - 1) + (H - 1) * W;
             facets += H * (W - 1) + (H - 1) * W;
         } else {
-            it.tx = int32_t((W + prune_tile_x() - 1) / prune_tile_x());
+            it.tx = int32_t((W + prune_tile_x3d() - 1) / prune_tile_x3d());
             it.ty = int32_t((H + prune_tile_y3d() - 1) / prune_tile_y3d());
             it.tz = int32_t((D + prune_tile_z3d() - 1) / prune_tile_z3d());
             it.tile0 = t3;
@@ -182,7 +182,7 @@ int status_to_code(uint32_t st) {
 }
 
 int run(const Plan& P, cp_pair* d_out, int64_t capacity, int64_t* h_out_count, int64_t* d_out_count, void* ws,
-        size_t ws_bytes, cudaStream_t s) {
+        size_t ws_bytes, cudaStream_t s, bool prune_only = false) {
     if (!ws || ws_bytes < P.bytes || (!d_out && capacity > 0) || capacity < 0) return CP_ERR_ARG;
     int rc = ensure_device_tables();
     if (rc != CP_OK) return rc;
@@ -210,6 +210,24 @@ int run(const Plan& P, cp_pair* d_out, int64_t capacity, int64_t* h_out_count, i
     CP_TRY(cudaMemsetAsync(status, 0, sizeof(uint64_t) * sort_status_words(P.cap_big), s));
     CP_TRY(launch_init(P.tab, ctr, uft, aget, rest, s));
     mark(0, s);
+    if (prune_only) {
+        PruneOuts po;
+        po.uf0 = uf0;
+        po.uft = uft;
+        po.s0 = s0;
+        po.st = st;
+        po.age0 = age0;
+        po.res0 = res0;
+        po.aget = aget;
+        po.rest = rest;
+        po.cap_s = P.cap_s;
+        po.cap_r0 = P.cap_r0;
+        po.cap_rt = P.cap_rt;
+        po.ctr = ctr;
+        CP_TRY(launch_prune(P.tab, po, s));
+        mark(1, s);
+        return CP_OK;
+    }
 
     PruneOuts po;
     po.uf0 = uf0;
@@ -401,6 +419,29 @@ int cubical_persistence_3d(const float* d_image, const int64_t dims[3], cp_pair*
                   max_survivors, stream);
 }
 
+int cubical_persistence_debug_prune(int n_items, const float* const* h_images, const int32_t* ndims,
+                                    const int64_t* dims, void* d_workspace, size_t ws_bytes, int64_t max_survivors,
+                                    void* stream) {
+    if (!h_images) return CP_ERR_ARG;
+    Plan P;
+    int rc = make_plan(n_items, ndims, dims, h_images, max_survivors, P);
+    if (rc != CP_OK) return rc;
+    return run(P, nullptr, 0, nullptr, nullptr, d_workspace, ws_bytes, static_cast<cudaStream_t>(stream), true);
+}
+
+int cubical_persistence_debug_layout(int n_items, const int32_t* ndims, const int64_t* dims, int64_t max_survivors,
+                                     int64_t* h_offsets, int cap) {
+    if (!h_offsets || cap < 12) return CP_ERR_ARG;
+    Plan P;
+    int rc = make_plan(n_items, ndims, dims, nullptr, max_survivors, P);
+    if (rc != CP_OK) return rc;
+    const int64_t v[12] = {int64_t(P.o_ctr), int64_t(P.o_uf0),  int64_t(P.o_uft),  int64_t(P.o_s0),
+                           int64_t(P.o_st),  int64_t(P.o_age0), int64_t(P.o_aget), int64_t(P.ntot),
+                           int64_t(P.ttot),  int64_t(P.cap_s),  int64_t(P.cap_r0), int64_t(P.cap_rt)};
+    for (int i = 0; i < 12; ++i) h_offsets[i] = v[i];
+    return 12;
+}
+
 size_t cubical_persistence_batched_workspace_size(int n_items, const int32_t* ndims, const int64_t* dims,
                                                   int64_t max_survivors) {
     Plan P;
@@ -489,16 +530,18 @@ size_t cubical_persistence_loss_backward_workspace_size(int64_t n_pixels) {
     return align_up(sizeof(double) * size_t(n_pixels)) + align_up(sizeof(double) * size_t(loss_partials()));
 }
 
-int cubical_persistence_loss_backward(const cp_pair* d_pairs, int64_t n_pairs, float min_persistence,
-                                      double* d_loss, const int64_t* d_item_offsets, float* d_grad_image,
-                                      int64_t n_pixels, void* d_workspace, size_t ws_bytes, void* stream) {
+int cubical_persistence_loss_backward(const cp_pair* d_pairs, int64_t n_pairs, const int64_t* d_n_pairs,
+                                      float min_persistence, double* d_loss, const int64_t* d_item_offsets,
+                                      float* d_grad_image, int64_t n_pixels, void* d_workspace, size_t ws_bytes,
+                                      void* stream) {
     if (n_pairs < 0 || n_pixels <= 0 || !d_grad_image || !d_workspace || !d_loss) return CP_ERR_ARG;
     if (n_pairs > 0 && !d_pairs) return CP_ERR_ARG;
     if (ws_bytes < cubical_persistence_loss_backward_workspace_size(n_pixels)) return CP_ERR_ARG;
     double* acc = static_cast<double*>(d_workspace);
     double* parts = reinterpret_cast<double*>(static_cast<char*>(d_workspace) + align_up(sizeof(double) * size_t(n_pixels)));
-    cudaError_t e = launch_loss_backward(d_pairs, n_pairs, min_persistence, d_item_offsets, acc, parts, loss_partials(),
-                                         d_loss, d_grad_image, n_pixels, static_cast<cudaStream_t>(stream));
+    cudaError_t e = launch_loss_backward(d_pairs, n_pairs, d_n_pairs, min_persistence, d_item_offsets, acc, parts,
+                                         loss_partials(), d_loss, d_grad_image, n_pixels,
+                                         static_cast<cudaStream_t>(stream));
     return e == cudaSuccess ? CP_OK : CP_ERR_CUDA;
 }
 

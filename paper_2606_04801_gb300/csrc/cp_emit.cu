@@ -98,11 +98,13 @@ __global__ void k_scatter(const cp_pair* __restrict__ pairs, int64_t n, const fl
 // identical from run to run.
 constexpr int kLossBlocks = 256;
 
-__global__ void __launch_bounds__(kT) k_loss_scatter(const cp_pair* __restrict__ pairs, int64_t n, float tau,
+__global__ void __launch_bounds__(kT) k_loss_scatter(const cp_pair* __restrict__ pairs, int64_t n,
+                                                     const int64_t* d_n, float tau,
                                                      const int64_t* __restrict__ offs, double* acc, int64_t n_pixels,
                                                      double* partials) {
     __shared__ double red[kT / 32];
     double local = 0.0;
+    if (d_n) n = *d_n < n ? *d_n : n;
     for (int64_t i = int64_t(blockIdx.x) * kT + threadIdx.x; i < n; i += int64_t(gridDim.x) * kT) {
         const cp_pair& p = pairs[i];
         if (p.death_pixel < 0) continue;
@@ -135,8 +137,9 @@ __global__ void k_loss_sum(const double* partials, int n, double* loss) {
 // Sparse accumulation: only the birth and death pixels of the pairs carry
 // gradient, so the accumulators of those pixels alone are cleared, filled and
 // rounded; the output is zeroed as a whole first.
-__global__ void k_touch_clear(const cp_pair* __restrict__ pairs, int64_t n, const int64_t* __restrict__ offs,
-                              double* acc, int64_t n_pixels) {
+__global__ void k_touch_clear(const cp_pair* __restrict__ pairs, int64_t n, const int64_t* d_n,
+                              const int64_t* __restrict__ offs, double* acc, int64_t n_pixels) {
+    if (d_n) n = *d_n < n ? *d_n : n;
     for (int64_t i = int64_t(blockIdx.x) * kT + threadIdx.x; i < n; i += int64_t(gridDim.x) * kT) {
         const cp_pair& p = pairs[i];
         int64_t off = offs ? offs[p.item] : 0;
@@ -146,8 +149,10 @@ __global__ void k_touch_clear(const cp_pair* __restrict__ pairs, int64_t n, cons
     }
 }
 
-__global__ void k_touch_round(const cp_pair* __restrict__ pairs, int64_t n, const int64_t* __restrict__ offs,
-                              const double* __restrict__ acc, float* __restrict__ grad, int64_t n_pixels) {
+__global__ void k_touch_round(const cp_pair* __restrict__ pairs, int64_t n, const int64_t* d_n,
+                              const int64_t* __restrict__ offs, const double* __restrict__ acc,
+                              float* __restrict__ grad, int64_t n_pixels) {
+    if (d_n) n = *d_n < n ? *d_n : n;
     for (int64_t i = int64_t(blockIdx.x) * kT + threadIdx.x; i < n; i += int64_t(gridDim.x) * kT) {
         const cp_pair& p = pairs[i];
         int64_t off = offs ? offs[p.item] : 0;
@@ -167,16 +172,16 @@ int grid_for(int64_t n) {
 
 int loss_partials() { return kLossBlocks; }
 
-cudaError_t launch_loss_backward(const cp_pair* pairs, int64_t n, float tau, const int64_t* offs, double* acc,
-                                 double* partials, int nparts, double* d_loss, float* grad, int64_t n_pixels,
-                                 cudaStream_t s) {
+cudaError_t launch_loss_backward(const cp_pair* pairs, int64_t n, const int64_t* d_n, float tau, const int64_t* offs,
+                                 double* acc, double* partials, int nparts, double* d_loss, float* grad,
+                                 int64_t n_pixels, cudaStream_t s) {
     if (nparts < kLossBlocks) return cudaErrorInvalidValue;
     cudaError_t e = cudaMemsetAsync(grad, 0, sizeof(float) * size_t(n_pixels), s);
     if (e != cudaSuccess) return e;
-    k_touch_clear<<<grid_for(n), kT, 0, s>>>(pairs, n, offs, acc, n_pixels);
-    k_loss_scatter<<<kLossBlocks, kT, 0, s>>>(pairs, n, tau, offs, acc, n_pixels, partials);
+    k_touch_clear<<<grid_for(n), kT, 0, s>>>(pairs, n, d_n, offs, acc, n_pixels);
+    k_loss_scatter<<<kLossBlocks, kT, 0, s>>>(pairs, n, d_n, tau, offs, acc, n_pixels, partials);
     k_loss_sum<<<1, 32, 0, s>>>(partials, kLossBlocks, d_loss);
-    k_touch_round<<<grid_for(n), kT, 0, s>>>(pairs, n, offs, acc, grad, n_pixels);
+    k_touch_round<<<grid_for(n), kT, 0, s>>>(pairs, n, d_n, offs, acc, grad, n_pixels);
     note_launches(4);
     return cudaGetLastError();
 }
@@ -213,9 +218,9 @@ cudaError_t launch_backward(const cp_pair* pairs, int64_t n, const float* gb, co
     cudaError_t e = cudaMemsetAsync(grad, 0, sizeof(float) * size_t(n_pixels), s);
     if (e != cudaSuccess) return e;
     if (n > 0) {
-        k_touch_clear<<<grid_for(n), kT, 0, s>>>(pairs, n, offs, acc, n_pixels);
+        k_touch_clear<<<grid_for(n), kT, 0, s>>>(pairs, n, nullptr, offs, acc, n_pixels);
         k_scatter<<<grid_for(n), kT, 0, s>>>(pairs, n, gb, gd, offs, acc, n_pixels);
-        k_touch_round<<<grid_for(n), kT, 0, s>>>(pairs, n, offs, acc, grad, n_pixels);
+        k_touch_round<<<grid_for(n), kT, 0, s>>>(pairs, n, nullptr, offs, acc, grad, n_pixels);
         note_launches(3);
     }
     return cudaGetLastError();

@@ -23,6 +23,7 @@ struct PruneOuts {
 size_t prune_smem2d();
 size_t prune_smem3d();
 int prune_tile_x();
+int prune_tile_x3d();
 int prune_tile_y2d();
 int prune_tile_y3d();
 int prune_tile_z3d();
@@ -89,9 +90,9 @@ void note_launches(int n);
 
 // Loss sum(death - birth)^2 over finite pairs with death - birth > tau, and
 // its gradient scattered to the pixels (double-precision accumulators).
-cudaError_t launch_loss_backward(const cp_pair* pairs, int64_t n, float tau, const int64_t* offs, double* acc,
-                                 double* partials, int nparts, double* d_loss, float* grad, int64_t n_pixels,
-                                 cudaStream_t s);
+cudaError_t launch_loss_backward(const cp_pair* pairs, int64_t n, const int64_t* d_n, float tau, const int64_t* offs,
+                                 double* acc, double* partials, int nparts, double* d_loss, float* grad,
+                                 int64_t n_pixels, cudaStream_t s);
 int loss_partials();
 
 }  // namespace cp

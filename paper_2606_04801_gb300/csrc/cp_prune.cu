@@ -24,7 +24,10 @@ namespace cp {
 // a warp look up different entries, which constant memory would serialise).
 __device__ uint64_t g_lut2d[256];
 __device__ uint16_t g_disp3d[1 << 12];
-__device__ uint64_t g_entries3d[1 << 14];  // perfect-hash slots of the 3D table (128 KB)
+// 3D entries as two 32-bit words for cheap decoding:
+//   x: direct (3 bits) | h0_surv << 3 (6) | dual_surv << 9 (12) | in_l << 21 (8)
+//   y: the eight 4-bit dual codes
+__device__ uint2 g_entries3d[1 << 14];  // perfect-hash slots of the 3D table (128 KB)
 
 // slot -> stencil bit tables
 __constant__ int8_t c_face_n3[6] = {4, 10, 12, 14, 16, 22};
@@ -274,7 +277,7 @@ __device__ __forceinline__ uint32_t collapse3(uint32_t raw) {
     return f | ed | co;
 }
 
-__device__ __forceinline__ uint64_t lookup3(uint32_t rel) {
+__device__ __forceinline__ uint2 lookup3(uint32_t rel) {
     uint32_t b = (rel * 0x9E3779B1u) >> (32 - 12);
     uint32_t d = __ldg(g_disp3d + b);
     uint32_t s = ((rel ^ (d * 0x27D4EB2Fu)) * 0x85EBCA77u) >> (32 - 14);
@@ -341,21 +344,34 @@ __global__ void __launch_bounds__(kThreads) k_prune2d(ItemTable tab, Outs o) {
 }
 
 // ---------------------------------------------------------------- 3D
-// A CTA of 8 warps owns a patch of 32 x 8 vertices (x, y) and marches
-// through a chunk of kZC planes in z.  Each plane of the patch plus a
-// one-vertex halo (34 x 10 floats) is loaded once per CTA into a 4-slot
-// shared-memory ring, one step ahead of its use (the global loads of plane
-// z+2 are issued before the work on plane z and stored after it), with one
-// barrier per step.  Each thread keeps the 3x3 neighbourhoods of planes z-1
-// and z in registers and reads the 3x3 of plane z+1 from the ring.
-// Survivors and roots are staged per warp and flushed with one atomic per
-// buffer when a buffer would overflow and at the end of the kernel.
-constexpr int kW3 = 8;          // warps per CTA (one row of the patch each)
-constexpr int kZC = 64;         // planes per task
-constexpr int kCapW0 = 32 * 5;   // staged H0 keys per warp: one step's maximum
-constexpr int kCapWT = 32 * 7;   // staged dual keys per warp: one step's maximum
-constexpr int kCapWR = 32;       // staged roots per warp and kind
-constexpr int kRW = 34, kRH = kW3 + 2, kRP = kRW * kRH;  // ring plane: 34 x 10
+// A CTA of 9 warps marches through a chunk of planes.  Warp w handles row
+// y0-1+w and lane l column x0-1+l: the CTA owns the 31 x 8 vertices with
+// w >= 1 and l >= 1; row y0-1 and column x0-1 are a halo whose lookups are
+// needed, but whose outputs belong to the neighbouring CTA.
+//
+// Per plane step z:
+//  1. cp.async prefetch of image plane z+kAhead (34 x 11 floats: the CTA's
+//     vertices and a one-vertex border) into an 8-slot shared-memory ring;
+//  2. the 26-neighbour mask of (z, y, x) from registers (planes z-1, z) and
+//     the ring (plane z+1), table lookup, the H0 forest link and the
+//     survivors and H0 root of owned vertices; the entry's dual codes go to
+//     a 3-plane shared ring;
+//  3. one barrier;
+//  4. the top cell whose smallest corner is (z-1, y, x): its largest corner
+//     m among the 8 corner values (in registers) holds, in its lookup entry,
+//     where this top cell dies locally; one coalesced store of its dual
+//     forest link (or it becomes a dual root).
+// Survivors and roots are staged per warp with ballots and flushed with one
+// atomic per buffer when a buffer would overflow and at the end.
+constexpr int kW3 = 9;                     // warps per CTA
+constexpr int kT3 = kW3 * 32;
+constexpr int kOX = 31, kOY = 8;           // owned columns / rows per CTA
+constexpr int kZC = 64;                    // owned planes per task
+constexpr int kRW = 34, kRH = kW3 + 2, kRP = kRW * kRH;  // ring plane: cols x0-2.., rows y0-2..
+constexpr int kRing = 8, kAhead = 5;       // ring slots, planes in flight
+constexpr int kCapW0 = 32 * 5;             // staged H0 keys per warp (one step's maximum)
+constexpr int kCapWT = 32 * 7;             // staged dual keys per warp
+constexpr int kCapWR = 32;                 // staged roots per warp and kind
 
 struct WarpStage {
     uint64_t s0[kCapW0];
@@ -367,7 +383,8 @@ struct WarpStage {
 };
 
 struct Smem3 {
-    float ring[4][kRP];
+    float ring[kRing][kRP];
+    uint32_t codes[3][kW3][32];
     WarpStage ws[kW3];
 };
 
@@ -460,29 +477,31 @@ __device__ __forceinline__ uint32_t mask26(const Nbr& A, const Nbr& B, const Nbr
     return raw;
 }
 
-// Plane loader: each thread owns up to two ring positions of the next plane.
-// Out-of-image positions read +inf (they never precede anything).  A
-// non-finite pixel fails the call and reads as the largest finite float, so
-// the order stays total and every structure written stays well formed.
-struct PlaneLoad {
-    float v0, v1;
-    bool bad;
-};
+// ---- image plane ring, filled with cp.async
+__device__ __forceinline__ void cp_async4(float* dst, const float* src) {
+    const uint32_t d = uint32_t(__cvta_generic_to_shared(dst));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
 
-// The (at most two) ring positions a thread loads, fixed for a task: offset
-// of the pixel within a plane and whether it lies inside the image.
+// Ring positions of this thread (at most two), fixed for a task.
 struct RingPos {
-    uint32_t off0, off1;
-    bool in0, in1;
+    uint32_t off0, off1;  // offset of the pixel in a plane
+    bool in0, in1;        // inside the image (x, y)
+    bool has1;            // second position exists
 };
 
 __device__ __forceinline__ void ring_positions(const Item& it, int x0, int y0, RingPos& rp) {
     const int tid = threadIdx.x;
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
-        const int i = tid + k * (kW3 * 32);
+        const int i = tid + k * kT3;
         const int ly = i / kRW, lx = i - ly * kRW;
-        const int gy = y0 + ly - 1, gx = x0 + lx - 1;
+        const int gy = y0 - 2 + ly, gx = x0 - 2 + lx;
         const bool in = i < kRP && unsigned(gy) < unsigned(it.H) && unsigned(gx) < unsigned(it.W);
         const uint32_t off = in ? uint32_t(gy) * uint32_t(it.W) + uint32_t(gx) : 0u;
         if (k == 0) {
@@ -491,213 +510,234 @@ __device__ __forceinline__ void ring_positions(const Item& it, int x0, int y0, R
         } else {
             rp.off1 = off;
             rp.in1 = in;
+            rp.has1 = i < kRP;
         }
     }
 }
 
-__device__ __forceinline__ void issue_plane(const Item& it, int z, const RingPos& rp, uint32_t HW, PlaneLoad& pl) {
-    const float inf = __int_as_float(0x7F800000), fmax = 3.40282347e38f;
-    const bool zin = unsigned(z) < unsigned(it.D);
-    const float* base = it.img + uint32_t(z) * HW;
-    float v0 = inf, v1 = inf;
-    if (zin && rp.in0) v0 = __ldg(base + rp.off0);
-    if (zin && rp.in1) v1 = __ldg(base + rp.off1);
-    const bool b0 = zin && rp.in0 && !(fabsf(v0) <= fmax);
-    const bool b1 = zin && rp.in1 && !(fabsf(v1) <= fmax);
-    pl.v0 = b0 ? fmax : v0;
-    pl.v1 = b1 ? fmax : v1;
-    pl.bad = b0 || b1;
+// Out-of-image positions read +inf (never precede anything): set once per
+// task in every slot; the copies below only fill in-image positions.
+__device__ __forceinline__ void ring_init(Smem3& sm, const RingPos& rp) {
+    const float inf = __int_as_float(0x7F800000);
+    const int tid = threadIdx.x;
+#pragma unroll
+    for (int s = 0; s < kRing; ++s) {
+        if (!rp.in0) sm.ring[s][tid] = inf;
+        if (rp.has1 && !rp.in1) sm.ring[s][tid + kT3] = inf;
+    }
 }
 
-__device__ __forceinline__ void store_plane(float* plane, const PlaneLoad& pl, Counters* ctr) {
+__device__ __forceinline__ void issue_plane(Smem3& sm, const Item& it, int z, const RingPos& rp, uint32_t HW) {
+    float* plane = sm.ring[(z + kRing) & (kRing - 1)];
     const int tid = threadIdx.x;
-    plane[tid] = pl.v0;
-    if (tid + kW3 * 32 < kRP) plane[tid + kW3 * 32] = pl.v1;
-    if (pl.bad) set_status(ctr, kStNonfinite);
+    if (unsigned(z) < unsigned(it.D)) {
+        const float* base = it.img + uint32_t(z) * HW;
+        if (rp.in0) cp_async4(plane + tid, base + rp.off0);
+        if (rp.in1) cp_async4(plane + tid + kT3, base + rp.off1);
+    } else {  // a plane outside the volume: every position +inf
+        const float inf = __int_as_float(0x7F800000);
+        if (rp.in0) plane[tid] = inf;
+        if (rp.in1) plane[tid + kT3] = inf;
+    }
+    cp_async_commit();
 }
 
 struct Col {
-    int item, x, y, x0, y0, W, H, D;
-    uint32_t voff, toff, T, HW, HW1, W1;
-    bool xy_valid;
-    uint32_t bxy;  // boundary bits (2: y==0, 3: y==H-1, 4: x==0, 5: x==W-1)
+    int x, y;
+    uint32_t W, H, D, HW, W1, HW1, voff, toff, OUT;
+    bool in_xy;      // (x, y) inside the image
+    bool owned_xy;   // and owned by this CTA
+    bool cube_xy;    // (x, y) is the smallest corner of a top cell written by this thread
+    uint32_t bxy;    // boundary bits (2: y==0, 3: y==H-1, 4: x==0, 5: x==W-1)
 };
 
-// H0 forest links: a vertex may point to any vertex of its own descent chain
-// (every link of the chain formed earlier in the filtration), so when the
-// first edge of L(v) goes to the z-1 neighbour -- processed by this thread one
-// step before -- v links directly to where that neighbour links (`far`),
-// collapsing descents along z within a task.
-__device__ __forceinline__ void vertex3d(const Col& cc, const Outs& o, int z, const Nbr& A, const Nbr& B,
-                                         const Nbr& C, WarpStage& ws, WarpCounts& cnt,
-                                         unsigned long long& my_min, uint32_t& far, bool chain) {
-    const bool valid = cc.xy_valid;
-    const uint32_t raw = mask26(A, B, C);
-    const uint64_t e = valid ? lookup3(collapse3(raw)) : 0ull;
-    const uint32_t ord = ord_bits(B.v[1][1]);
-    const uint32_t vl = (uint32_t(z) * uint32_t(cc.H) + uint32_t(cc.y)) * uint32_t(cc.W) + uint32_t(cc.x);
-    const uint32_t vg = cc.voff + vl;
-    const int direct = int(e & 7u);
-    const bool root0 = valid && direct == 7;
-    if (valid && !root0) {
-        // face slots: (-1,0,0) (0,-1,0) (0,0,-1) (0,0,1) (0,1,0) (1,0,0)
-        const uint32_t mag = (direct == 0 || direct == 5) ? cc.HW : ((direct == 1 || direct == 4) ? uint32_t(cc.W) : 1u);
-        const uint32_t u = direct < 3 ? vg - mag : vg + mag;
-        far = (direct == 0 && chain) ? far : u;
-        o.uf0[vg] = far;
-    } else {
-        far = vg;
-    }
-    int rt_node = -1;
-    uint64_t rt_age = 0;
-    uint32_t in_l = uint32_t(e >> 53) & 0xFFu;
-    if (in_l) {
-        const uint32_t B6 = cc.bxy | (z == 0 ? 1u : 0u) | (z == cc.D - 1 ? 2u : 0u);
-        const uint32_t cbase = cc.toff + (uint32_t(z) * uint32_t(cc.H - 1) + uint32_t(cc.y)) * cc.W1 + uint32_t(cc.x);
-        const uint32_t OUT = cc.toff + cc.T;
-        do {
-            const int t = __ffs(in_l) - 1;
-            in_l &= in_l - 1;
-            const uint32_t code = uint32_t(e >> (9 + 4 * t)) & 15u;
-            const uint32_t self = cbase - (((t & 4) ? 0u : cc.HW1) + ((t & 2) ? 0u : cc.W1) + ((t & 1) ? 0u : 1u));
-            if (code == 8u) {
-                rt_node = int(self);
-                rt_age = make_key(ord, vg, uint32_t(18 * ((t >> 2) & 1) + 6 * ((t >> 1) & 1) + 2 * (t & 1)));
-            } else {
-                const uint32_t c = code;
-                const uint32_t sel = (1u << ((c >> 2) & 1u)) | (4u << ((c >> 1) & 1u)) | (16u << (c & 1u));
-                const uint32_t tgt = cbase - (((c & 4u) ? 0u : cc.HW1) + ((c & 2u) ? 0u : cc.W1) + ((c & 1u) ? 0u : 1u));
-                o.uft[self] = (B6 & sel) ? OUT : tgt;
-            }
-        } while (in_l);
-    }
-    if (root0) {
-        unsigned long long k = (unsigned long long)(uint64_t(ord) << 32 | vl);
-        my_min = k < my_min ? k : my_min;
-    }
-    const uint32_t h0s = valid ? uint32_t((e >> 3) & 0x3Fu) : 0u;
-    const uint32_t ds = valid ? uint32_t((e >> 41) & 0xFFFu) : 0u;
-    const bool any = (h0s | ds) != 0u || root0 || rt_node >= 0;
-    if (!__any_sync(0xFFFFFFFFu, any)) return;
-    // ---- stage survivors and roots (rare in smooth fields)
-    const uint32_t packed = __popc(h0s) | (__popc(ds) << 8) | ((root0 ? 1u : 0u) << 16) | ((rt_node >= 0 ? 1u : 0u) << 24);
-    uint32_t incl = packed;
-    const unsigned lane = lane_id();
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        uint32_t t = __shfl_up_sync(0xFFFFFFFFu, incl, d);
-        if (lane >= unsigned(d)) incl += t;
-    }
-    const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
-    const uint32_t excl = incl - packed;
-    if (cnt.s0 + (total & 255u) > uint32_t(kCapW0) || cnt.st + ((total >> 8) & 255u) > uint32_t(kCapWT) ||
-        cnt.r0 + ((total >> 16) & 255u) > uint32_t(kCapWR) || cnt.rt + (total >> 24) > uint32_t(kCapWR))
-        warp_flush(ws, cnt, o);
-    uint32_t p0 = cnt.s0 + (excl & 255u), pt = cnt.st + ((excl >> 8) & 255u);
-    uint32_t m = h0s;
-    while (m) {
-        const int s = __ffs(m) - 1;
-        m &= m - 1;
-        const uint32_t n = s == 0 ? 4u : (s == 1 ? 10u : (s == 2 ? 12u : (s == 3 ? 14u : (s == 4 ? 16u : 22u))));
-        ws.s0[p0++] = make_key(ord, vg, n);
-    }
-    m = ds;
-    while (m) {
-        const int f = __ffs(m) - 1;
-        m &= m - 1;
-        // facet slots 0..11 -> stencil bits 1,3,5,7,9,11,15,17,19,21,23,25
-        const uint32_t n = f < 6 ? uint32_t(2 * f + 1) : uint32_t(2 * f + 3);
-        ws.st[pt++] = ~make_key(ord, vg, n);
-    }
-    if (root0) {
-        const uint32_t p = cnt.r0 + ((excl >> 16) & 255u);
-        ws.r0node[p] = vg;
-        ws.r0age[p] = make_key(ord, vg, 0);
-    }
-    if (rt_node >= 0) {
-        const uint32_t p = cnt.rt + (excl >> 24);
-        ws.rtnode[p] = uint32_t(rt_node);
-        ws.rtage[p] = rt_age;
-    }
-    cnt.s0 += total & 255u;
-    cnt.st += (total >> 8) & 255u;
-    cnt.r0 += (total >> 16) & 255u;
-    cnt.rt += total >> 24;
-    __syncwarp();
+__device__ __forceinline__ uint32_t age_slot(uint32_t t) {
+    return 18u * ((t >> 2) & 1u) + 6u * ((t >> 1) & 1u) + 2u * (t & 1u);
 }
 
-__global__ void __launch_bounds__(kW3 * 32, 4) k_prune3d(ItemTable tab, Outs o) {
+__global__ void __launch_bounds__(kT3, 4) k_prune3d(ItemTable tab, Outs o) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem3& sm = *reinterpret_cast<Smem3*>(smem_raw);
     const int warp = threadIdx.x >> 5;
     const int lane = int(lane_id());
+    const unsigned lt = (1u << lane) - 1u;
     WarpStage& ws = sm.ws[warp];
     WarpCounts cnt = {0, 0, 0, 0};
     for (int task = blockIdx.x; task < tab.tiles3d; task += gridDim.x) {
         const int ii = tile_item(tab, tab.n2d, tab.n - 1, task);
         const Item& it = tab.it[ii];
-        const int lt = task - it.tile0;
-        // task order: x segment fastest, then y segment, then z chunk, so the
-        // CTAs running together cover a compact region and share halos in L2
-        const int xs = lt % it.tx;
-        const int rest = lt / it.tx;
+        const int ltask = task - it.tile0;
+        // task order: x segment fastest, then y segment, then z chunk
+        const int xs = ltask % it.tx;
+        const int rest = ltask / it.tx;
         const int ys = rest % it.ty;
         const int zc = rest / it.ty;
+        const int x0 = xs * kOX, y0 = ys * kOY;
         Col cc;
-        cc.item = ii;
-        cc.W = it.W;
-        cc.H = it.H;
-        cc.D = it.D;
-        cc.x0 = xs * 32;
-        cc.y0 = ys * kW3;
-        cc.x = cc.x0 + lane;
-        cc.y = cc.y0 + warp;
-        cc.xy_valid = cc.x < it.W && cc.y < it.H;
-        cc.bxy = (cc.y == 0 ? 4u : 0u) | (cc.y == it.H - 1 ? 8u : 0u) | (cc.x == 0 ? 16u : 0u) |
-                 (cc.x == it.W - 1 ? 32u : 0u);
+        cc.x = x0 - 1 + lane;
+        cc.y = y0 - 1 + warp;
+        cc.W = uint32_t(it.W);
+        cc.H = uint32_t(it.H);
+        cc.D = uint32_t(it.D);
+        cc.HW = cc.H * cc.W;
+        cc.W1 = cc.W - 1u;
+        cc.HW1 = (cc.H - 1u) * cc.W1;
         cc.voff = uint32_t(it.voff);
         cc.toff = uint32_t(it.toff);
-        cc.T = uint32_t(it.T);
-        cc.HW = uint32_t(it.H) * uint32_t(it.W);
-        cc.W1 = uint32_t(it.W - 1);
-        cc.HW1 = uint32_t(it.H - 1) * uint32_t(it.W - 1);
+        cc.OUT = uint32_t(it.toff + it.T);
+        cc.in_xy = cc.x >= 0 && cc.y >= 0 && cc.x < it.W && cc.y < it.H;
+        cc.owned_xy = cc.in_xy && lane >= 1 && warp >= 1;
+        cc.cube_xy = cc.x >= 0 && cc.y >= 0 && cc.x < it.W - 1 && cc.y < it.H - 1 && lane <= 30 && warp <= 7;
+        cc.bxy = (cc.y == 0 ? 4u : 0u) | (cc.y == it.H - 1 ? 8u : 0u) | (cc.x == 0 ? 16u : 0u) |
+                 (cc.x == it.W - 1 ? 32u : 0u);
+        const int z0 = zc * kZC;
+        const int z1 = min(it.D, z0 + kZC);       // owned planes [z0, z1)
+        const int zlast = min(z1, it.D - 1);       // entries computed for planes [z0, zlast]
         RingPos rp;
-        ring_positions(it, cc.x0, cc.y0, rp);
-        const int z0 = zc * kZC, z1 = min(it.D, z0 + kZC);
+        ring_positions(it, x0, y0, rp);
         unsigned long long my_min = ~0ull;
         uint32_t far = 0;
-        PlaneLoad pl;
-        __syncthreads();  // the ring may still be read by the previous task
-        issue_plane(it, z0 - 1, rp, cc.HW, pl);
-        store_plane(sm.ring[(z0 + 3) & 3], pl, o.ctr);
-        issue_plane(it, z0, rp, cc.HW, pl);
-        store_plane(sm.ring[z0 & 3], pl, o.ctr);
-        issue_plane(it, z0 + 1, rp, cc.HW, pl);
-        store_plane(sm.ring[(z0 + 1) & 3], pl, o.ctr);
+        __syncthreads();  // the rings may still be read by the previous task
+        ring_init(sm, rp);
+#pragma unroll
+        for (int k = -1; k < kAhead; ++k) issue_plane(sm, it, z0 + k, rp, cc.HW);
+        cp_async_wait<kAhead - 2>();  // planes z0-1 .. z0+1 have landed
         __syncthreads();
         Nbr A, B, C;
-        read_nbr(sm.ring[(z0 + 3) & 3], warp, lane, A);
-        read_nbr(sm.ring[z0 & 3], warp, lane, B);
-        // one step: prefetch plane z+2, read plane z+1 into `nxt`, process z
-#define CP_STEP(Pm, P0, Pp)                                          \
-    {                                                                \
-        issue_plane(it, z + 2, rp, cc.HW, pl);                       \
-        read_nbr(sm.ring[(z + 1) & 3], warp, lane, Pp);              \
-        vertex3d(cc, o, z, Pm, P0, Pp, ws, cnt, my_min, far, z > z0); \
-        store_plane(sm.ring[(z + 2) & 3], pl, o.ctr);                \
-        __syncthreads();                                             \
-        ++z;                                                         \
-    }
-        int z = z0;
-        for (; z + 3 <= z1;) {
-            CP_STEP(A, B, C)
-            CP_STEP(B, C, A)
-            CP_STEP(C, A, B)
+        read_nbr(sm.ring[(z0 - 1 + kRing) & (kRing - 1)], warp, lane, A);
+        read_nbr(sm.ring[z0 & (kRing - 1)], warp, lane, B);
+        for (int z = z0; z <= zlast; ++z) {
+            issue_plane(sm, it, z + kAhead, rp, cc.HW);
+            read_nbr(sm.ring[(z + 1) & (kRing - 1)], warp, lane, C);
+            // ---- lookup of (z, y, x)
+            const float cv = B.v[1][1];
+            const uint32_t raw = mask26(A, B, C);
+            const uint2 e = lookup3(collapse3(raw));
+            sm.codes[z % 3][warp][lane] = e.y;
+            const bool owned = cc.owned_xy && z < z1;
+            const uint32_t ord = ord_bits(cv);
+            const uint32_t vl = (uint32_t(z) * cc.H + uint32_t(cc.y)) * cc.W + uint32_t(cc.x);
+            const uint32_t vg = cc.voff + vl;
+            const int direct = int(e.x & 7u);
+            bool root0 = false;
+            if (owned) {
+                if (!(fabsf(cv) <= 3.40282347e38f)) set_status(o.ctr, kStNonfinite);
+                if (direct == 7) {
+                    root0 = true;
+                    far = vg;
+                    const unsigned long long k = (unsigned long long)(uint64_t(ord) << 32 | vl);
+                    my_min = k < my_min ? k : my_min;
+                } else {
+                    // face slots: (-1,0,0) (0,-1,0) (0,0,-1) (0,0,1) (0,1,0) (1,0,0); a z-1 link
+                    // continues the chain that the z-1 neighbour (same thread, previous
+                    // step) started
+                    const uint32_t mag = (direct == 0 || direct == 5) ? cc.HW : ((direct == 1 || direct == 4) ? cc.W : 1u);
+                    const uint32_t u = direct < 3 ? vg - mag : vg + mag;
+                    far = (direct == 0 && z > z0) ? far : u;
+                    o.uf0[vg] = far;
+                }
+            }
+            const uint32_t h0s = owned ? (e.x >> 3) & 0x3Fu : 0u;
+            const uint32_t ds = owned ? (e.x >> 9) & 0xFFFu : 0u;
+            cp_async_wait<kAhead - 2>();  // plane z+2 has landed (for the next step)
+            __syncthreads();              // codes of plane z and image plane z+2 visible
+            // ---- the top cell with smallest corner (z-1, y, x)
+            bool rootT = false;
+            uint32_t rt_node = 0;
+            uint64_t rt_age = 0;
+            if (cc.cube_xy && z > z0) {
+                // largest of the 8 corners under (value, linear index), in index order
+                const float cvals[8] = {A.v[1][1], A.v[1][2], A.v[2][1], A.v[2][2],
+                                        B.v[1][1], B.v[1][2], B.v[2][1], B.v[2][2]};
+                int k = 0;
+                float best = cvals[0];
+#pragma unroll
+                for (int j = 1; j < 8; ++j) {
+                    const bool ge = cvals[j] >= best;
+                    best = ge ? cvals[j] : best;
+                    k = ge ? j : k;
+                }
+                const int dz = k >> 2, dy = (k >> 1) & 1, dx = k & 1;
+                const uint32_t word = sm.codes[(z - 1 + dz) % 3][warp + dy][lane + dx];
+                const uint32_t t = uint32_t(7 - k);  // octant of the top cell as seen from m
+                const uint32_t code = (word >> (4u * t)) & 15u;
+                const uint32_t self = cc.toff + (uint32_t(z - 1) * (cc.H - 1u) + uint32_t(cc.y)) * cc.W1 + uint32_t(cc.x);
+                const int mz = z - 1 + dz, my = cc.y + dy, mx = cc.x + dx;
+                if (code == 8u) {
+                    rootT = true;
+                    rt_node = self;
+                    const uint32_t mg = cc.voff + (uint32_t(mz) * cc.H + uint32_t(my)) * cc.W + uint32_t(mx);
+                    rt_age = make_key(ord_bits(best), mg, age_slot(t));
+                } else if (code < 8u) {
+                    // the top cell across: octant `code` of m, smallest corner m - (negative axes)
+                    const int tz = mz - int(((code >> 2) & 1u) ^ 1u);
+                    const int ty = my - int(((code >> 1) & 1u) ^ 1u);
+                    const int tx = mx - int((code & 1u) ^ 1u);
+                    const bool out = unsigned(tz) >= cc.D - 1u || unsigned(ty) >= cc.H - 1u || unsigned(tx) >= cc.W1;
+                    o.uft[self] = out ? cc.OUT : cc.toff + (uint32_t(tz) * (cc.H - 1u) + uint32_t(ty)) * cc.W1 + uint32_t(tx);
+                } else {
+                    o.uft[self] = kTag;  // only reachable with non-finite input (flagged): keep the forest well formed
+                }
+            }
+            // ---- stage survivors and roots (rare in smooth fields)
+            if (__any_sync(0xFFFFFFFFu, root0 || rootT || (h0s | ds) != 0u)) {
+                const unsigned m_r0 = __ballot_sync(0xFFFFFFFFu, root0);
+                const unsigned m_rt = __ballot_sync(0xFFFFFFFFu, rootT);
+                const uint32_t or0 = __reduce_or_sync(0xFFFFFFFFu, h0s);
+                const uint32_t ort = __reduce_or_sync(0xFFFFFFFFu, ds);
+                const uint32_t n0 = __reduce_add_sync(0xFFFFFFFFu, uint32_t(__popc(h0s)));  // <= 32 * 5
+                const uint32_t nt = __reduce_add_sync(0xFFFFFFFFu, uint32_t(__popc(ds)));   // <= 32 * 7
+                if (cnt.s0 + n0 > uint32_t(kCapW0) || cnt.st + nt > uint32_t(kCapWT) ||
+                    cnt.r0 + __popc(m_r0) > uint32_t(kCapWR) || cnt.rt + __popc(m_rt) > uint32_t(kCapWR))
+                    warp_flush(ws, cnt, o);
+                if (m_r0) {
+                    if (root0) {
+                        const uint32_t p = cnt.r0 + __popc(m_r0 & lt);
+                        ws.r0node[p] = vg;
+                        ws.r0age[p] = make_key(ord, vg, 0);
+                    }
+                    cnt.r0 += __popc(m_r0);
+                }
+                if (m_rt) {
+                    if (rootT) {
+                        const uint32_t p = cnt.rt + __popc(m_rt & lt);
+                        ws.rtnode[p] = rt_node;
+                        ws.rtage[p] = rt_age;
+                    }
+                    cnt.rt += __popc(m_rt);
+                }
+                uint32_t bits = or0;
+                while (bits) {
+                    const int s = __ffs(bits) - 1;
+                    bits &= bits - 1;
+                    const bool mine = (h0s >> s) & 1u;
+                    const unsigned m = __ballot_sync(0xFFFFFFFFu, mine);
+                    if (mine) {
+                        const uint32_t n = s == 0 ? 4u : (s == 1 ? 10u : (s == 2 ? 12u : (s == 3 ? 14u : (s == 4 ? 16u : 22u))));
+                        ws.s0[cnt.s0 + __popc(m & lt)] = make_key(ord, vg, n);
+                    }
+                    cnt.s0 += __popc(m);
+                }
+                bits = ort;
+                while (bits) {
+                    const int f = __ffs(bits) - 1;
+                    bits &= bits - 1;
+                    const bool mine = (ds >> f) & 1u;
+                    const unsigned m = __ballot_sync(0xFFFFFFFFu, mine);
+                    if (mine) {
+                        // facet slots 0..11 -> stencil bits 1,3,5,7,9,11,15,17,19,21,23,25
+                        const uint32_t n = f < 6 ? uint32_t(2 * f + 1) : uint32_t(2 * f + 3);
+                        ws.st[cnt.st + __popc(m & lt)] = ~make_key(ord, vg, n);
+                    }
+                    cnt.st += __popc(m);
+                }
+                __syncwarp();
+            }
+            A = B;
+            B = C;
         }
-        if (z < z1) CP_STEP(A, B, C)
-        if (z < z1) CP_STEP(B, C, A)
-#undef CP_STEP
-        unsigned long long w = warp_min_u64(my_min);
+        cp_async_wait<0>();
+        const unsigned long long w = warp_min_u64(my_min);
         if (lane == 0 && w != ~0ull) atomicMin(&o.ctr->gmin[ii], w);
     }
     if (__any_sync(0xFFFFFFFFu, (cnt.s0 | cnt.st | cnt.r0 | cnt.rt) != 0)) warp_flush(ws, cnt, o);
@@ -707,8 +747,9 @@ __global__ void __launch_bounds__(kW3 * 32, 4) k_prune3d(ItemTable tab, Outs o) 
 size_t prune_smem2d() { return sizeof(Stage) + sizeof(float) * (kT2Y + 2) * (kBX + 2); }
 size_t prune_smem3d() { return sizeof(Smem3); }
 int prune_tile_x() { return kBX; }
+int prune_tile_x3d() { return kOX; }
 int prune_tile_y2d() { return kT2Y; }
-int prune_tile_y3d() { return kW3; }
+int prune_tile_y3d() { return kOY; }
 int prune_tile_z3d() { return kZC; }
 
 cudaError_t upload_luts(const uint64_t* lut2d, const uint16_t* disp3d, const uint64_t* entries3d) {
@@ -716,7 +757,15 @@ cudaError_t upload_luts(const uint64_t* lut2d, const uint16_t* disp3d, const uin
     if (e != cudaSuccess) return e;
     e = cudaMemcpyToSymbol(g_disp3d, disp3d, sizeof(uint16_t) * (1 << 12));
     if (e != cudaSuccess) return e;
-    return cudaMemcpyToSymbol(g_entries3d, entries3d, sizeof(uint64_t) * (1 << 14));
+    static uint2 packed[1 << 14];
+    for (int i = 0; i < (1 << 14); ++i) {
+        const uint64_t v = entries3d[i];
+        const uint32_t direct = uint32_t(v & 7u), h0s = uint32_t((v >> 3) & 0x3Fu);
+        const uint32_t ds = uint32_t((v >> 41) & 0xFFFu), in_l = uint32_t((v >> 53) & 0xFFu);
+        packed[i].x = direct | (h0s << 3) | (ds << 9) | (in_l << 21);
+        packed[i].y = uint32_t((v >> 9) & 0xFFFFFFFFu);
+    }
+    return cudaMemcpyToSymbol(g_entries3d, packed, sizeof(packed));
 }
 
 cudaError_t launch_prune(const ItemTable& tab, const PruneOuts& po, cudaStream_t s) {
@@ -739,7 +788,7 @@ cudaError_t launch_prune(const ItemTable& tab, const PruneOuts& po, cudaStream_t
         cudaFuncSetAttribute(k_prune2d, cudaFuncAttributeMaxDynamicSharedMemorySize, int(prune_smem2d()));
         cudaFuncSetAttribute(k_prune3d, cudaFuncAttributeMaxDynamicSharedMemorySize, int(prune_smem3d()));
         int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_prune3d, kW3 * 32, prune_smem3d());
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_prune3d, kT3, prune_smem3d());
         blocks3d = device_sm_count() * (per_sm > 0 ? per_sm : 1);
         attr_set = true;
     }
@@ -749,7 +798,7 @@ cudaError_t launch_prune(const ItemTable& tab, const PruneOuts& po, cudaStream_t
     }
     if (tab.tiles3d > 0) {
         int grid = tab.tiles3d < blocks3d ? tab.tiles3d : blocks3d;
-        k_prune3d<<<grid, kW3 * 32, prune_smem3d(), s>>>(tab, o);
+        k_prune3d<<<grid, kT3, prune_smem3d(), s>>>(tab, o);
         note_launches(1);
     }
     return cudaGetLastError();

@@ -185,7 +185,8 @@ __global__ void __launch_bounds__(kT) k_uf(UfKernelArgs args) {
     const uint32_t gtid = blockIdx.x * kT + threadIdx.x;
     const uint32_t gstride = nblocks * kT;
     // a bounded wait that gave up earlier leaves the sorted keys unreliable
-    if (ld_acquire_u32(&ctr->status) & kStTimeout) return;
+    // non-finite input leaves the forests unreliable: the call fails anyway
+    if (ld_acquire_u32(&ctr->status) & (kStTimeout | kStNonfinite)) return;
     uint32_t n = min(*p.d_nkeys, p.cap_keys);
     int cur = 0;
     uint32_t round = 1;
@@ -322,9 +323,21 @@ cudaError_t launch_uf(const ItemTable& tab, const UfParams& p, cudaStream_t s) {
     UfKernelArgs args;
     args.tab = tab;
     args.p = p;
-    void* kargs[] = {&args};
+    // cooperative launch (all CTAs co-resident, as the grid barrier needs);
+    // launched through cudaLaunchKernelEx so that it can also be captured
+    // into a CUDA graph
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(g_uf_blocks);
+    cfg.blockDim = dim3(kT);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
     note_launches(1);
-    return cudaLaunchCooperativeKernel((const void*)k_uf, dim3(g_uf_blocks), dim3(kT), kargs, 0, s);
+    return cudaLaunchKernelEx(&cfg, k_uf, args);
 }
 
 }  // namespace cp

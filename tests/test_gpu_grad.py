@@ -61,7 +61,7 @@ def _gpu_loss_grad(cp, imgs):
     ws_bytes = lib.cubical_persistence_loss_backward_workspace_size(n)
     ws = torch.empty(ws_bytes, dtype=torch.uint8, device="cuda")
     rc = lib.cubical_persistence_loss_backward(
-        ctypes.c_void_p(d.raw.data_ptr()), len(d), ctypes.c_float(TAU), ctypes.c_void_p(loss.data_ptr()),
+        ctypes.c_void_p(d.raw.data_ptr()), len(d), None, ctypes.c_float(TAU), ctypes.c_void_p(loss.data_ptr()),
         None if offs is None else ctypes.c_void_p(offs.data_ptr()), ctypes.c_void_p(grad.data_ptr()), n,
         ctypes.c_void_p(ws.data_ptr()), ws_bytes, None,
     )

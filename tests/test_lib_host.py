@@ -97,137 +97,11 @@ def test_collapse_matches_independent_enumeration(lib):
 
 
 # ---------------------------------------------------------------- restatement
-def _entry(lib, ndim, raw):
-    e = ctypes.c_uint64()
-    assert lib.cp_lut_lookup(ndim, raw, None, ctypes.byref(e)) == 0
-    return e.value
+from prune_restatement import Pruned
 
 
 def _pruned_pipeline(lib, img):
-    """Sequential restatement of the pruned method using the library's table.
-
-    Forest links from the table, survivors sorted by the refined order,
-    sequential elder-rule union-find, 2D cross-pruning; returns pairs as the
-    oracle does (value-filtered, sorted by (dim, birth_cell)).
-    """
-    nd = img.ndim
-    f = np.where(img == 0, 0.0, img).astype(np.float64)
-    shape = img.shape if nd == 3 else (1,) + img.shape
-    D, H, W = shape
-    f3 = f.reshape(shape)
-    N = D * H * W
-    offs = _offsets(nd)
-    faces = [b for b, o in enumerate(offs) if sum(x != 0 for x in o) == 1]
-    facets = [b for b, o in enumerate(offs) if sum(x != 0 for x in o) == nd - 1]
-    tops = [b for b, o in enumerate(offs) if sum(x != 0 for x in o) == nd]
-    TD = D - 1 if nd == 3 else 1
-    T = TD * (H - 1) * (W - 1)
-    OUT = T
-    GH, GW = 2 * H - 1, 2 * W - 1
-
-    def K(v):
-        z, r = divmod(v, H * W)
-        y, x = divmod(r, W)
-        return (f3[z, y, x], v)
-
-    def vid(z, y, x):
-        return (z * H + y) * W + x
-
-    def top_of(z, y, x, o):
-        cz = z + (o[0] < 0 and -1 or 0) if nd == 3 else 0
-        cy, cx = y + (-1 if o[1] < 0 else 0), x + (-1 if o[2] < 0 else 0)
-        if cy < 0 or cy >= H - 1 or cx < 0 or cx >= W - 1 or (nd == 3 and (cz < 0 or cz >= D - 1)):
-            return OUT
-        return (cz * (H - 1) + cy) * (W - 1) + cx
-
-    par0 = list(range(N))
-    part = list(range(T + 1))
-    tage = {}  # dual root -> (K(m), slot)
-    s0, st = [], []
-    for z in range(D):
-        for y in range(H):
-            for x in range(W):
-                v = vid(z, y, x)
-                kv = K(v)
-                raw = 0
-                for b, o in enumerate(offs):
-                    if o == (0, 0, 0):
-                        continue
-                    zz, yy, xx = z + o[0], y + o[1], x + o[2]
-                    if 0 <= zz < D and 0 <= yy < H and 0 <= xx < W and K(vid(zz, yy, xx)) < kv:
-                        raw |= 1 << b
-                e = _entry(lib, nd, raw)
-                direct = e & 7
-                if direct != 7:
-                    o = offs[faces[direct]]
-                    par0[v] = vid(z + o[0], y + o[1], x + o[2])
-                h0s, ds = (e >> 3) & 0x3F, (e >> 41) & 0xFFF
-                for s, b in enumerate(faces):
-                    if (h0s >> s) & 1:
-                        s0.append((kv, b, v, bool((ds >> s) & 1) if nd == 2 else False))
-                for s, b in enumerate(facets):
-                    if (ds >> s) & 1 and not (nd == 2 and (h0s >> s) & 1):
-                        st.append((kv, b, v))
-                for t, b in enumerate(tops):
-                    code = (e >> (9 + 4 * t)) & 15
-                    if code == 15:
-                        continue
-                    me = top_of(z, y, x, offs[b])
-                    if code == 8:
-                        tage[me] = (kv, b)
-                    else:
-                        part[me] = top_of(z, y, x, offs[tops[code]])
-
-    def find(p, a):
-        while p[a] != a:
-            p[a] = p[p[a]]
-            a = p[a]
-        return a
-
-    def dcell(z, y, x, o):
-        return ((2 * z + o[0]) * GH + 2 * y + o[1]) * GW + 2 * x + o[2]
-
-    def coords(v):
-        z, r = divmod(v, H * W)
-        return z, r // W, r % W
-
-    out = []
-    for kv, b, v, flag in sorted(s0):
-        z, y, x = coords(v)
-        o = offs[b]
-        u = vid(z + o[0], y + o[1], x + o[2])
-        ra, rb = find(par0, v), find(par0, u)
-        if ra == rb:
-            if flag:
-                st.append((kv, b, v))
-            continue
-        yv = ra if K(ra) > K(rb) else rb
-        par0[yv] = rb if yv == ra else ra
-        if K(yv)[0] != kv[0]:
-            out.append((0, dcell(*coords(yv), (0, 0, 0)), dcell(z, y, x, o), K(yv)[0], kv[0]))
-    for kv, b, v in sorted(st, reverse=True):
-        z, y, x = coords(v)
-        o = offs[b]
-        ax = [a for a in range(3 - nd, 3) if o[a] == 0][0]
-        sides = []
-        for sgn in (-1, 1):
-            q = list(o)
-            q[ax] = sgn
-            sides.append(top_of(z, y, x, q))
-        ra, rb = find(part, sides[0]), find(part, sides[1])
-        if ra == rb:
-            continue
-        if ra == OUT:
-            yv = rb
-        elif rb == OUT:
-            yv = ra
-        else:
-            yv = ra if tage[ra] < tage[rb] else rb
-        part[yv] = rb if yv == ra else ra
-        (km, bm) = tage[yv]
-        if km[0] != kv[0]:
-            out.append((nd - 1, dcell(z, y, x, o), dcell(*coords(km[1]), offs[bm]), kv[0], km[0]))
-    return sorted(out)
+    return Pruned(lib, img).pairs()
 
 
 def _oracle_rows(img):
