@@ -228,6 +228,32 @@ int cubical_persistence_loss_backward(const cp_pair *d_pairs, int64_t n_pairs, c
                                       float *d_grad_image, int64_t n_pixels, void *d_workspace, size_t ws_bytes,
                                       void *stream);
 
+/*
+ * Backward scatter that allocates nothing (the paper has no counterpart: it
+ * is a convenience of this library).  For callers that cannot allocate
+ * device memory, such as code running while a stream is captured into a
+ * CUDA graph, or code inside another framework's hooks without access to
+ * its allocator, this computes exactly what cubical_persistence_backward
+ * computes, but keeps its double-precision accumulators in a fixed array
+ * inside the library's device image instead of a caller-provided workspace.
+ *  - The array holds cubical_persistence_backward_noalloc_max_pixels()
+ *    (= 4,194,304) doubles, 32 MiB; every GPU that loads the library keeps it
+ *    until the process exits.  n_pixels above that maximum returns
+ *    CP_ERR_CAPACITY without touching the GPU.
+ *  - The first call on a device looks the array's device address up
+ *    (cudaGetSymbolAddress, with that device current); make that first call
+ *    before any stream capture on that device.
+ *  - Every call shares the one array: each call clears the part it uses
+ *    before accumulating, so consecutive calls are independent, but calls
+ *    whose work overlaps on the GPU (unordered streams) race on it.
+ *  - It calls no allocating function.  Other arguments as for
+ *    cubical_persistence_backward.
+ */
+int64_t cubical_persistence_backward_noalloc_max_pixels(void);
+int cubical_persistence_backward_noalloc(const cp_pair *d_pairs, int64_t n_pairs, const float *d_grad_birth,
+                                         const float *d_grad_death, const int64_t *d_item_offsets,
+                                         float *d_grad_image, int64_t n_pixels, void *stream);
+
 /* ---------------------------------------------------------------- instrumentation */
 
 /*
@@ -262,6 +288,21 @@ int cubical_persistence_debug_prune(int n_items, const float *const *h_images, c
                                     void *stream);
 int cubical_persistence_debug_layout(int n_items, const int32_t *ndims, const int64_t *dims, int64_t max_survivors,
                                      int64_t *h_offsets, int cap);
+
+/*
+ * Tuning of the pruning pass (process-wide; read by the following calls;
+ * results never depend on it).  Keys:
+ *   CP_TUNE_ZCHUNK_3D    planes per 3D pruning task (4..4096, default 64)
+ *   CP_TUNE_CTAS_PER_SM  3D pruning CTAs per SM (0 = as many as fit, default)
+ *   CP_TUNE_ROWS_2D      rows per 2D pruning tile (8, 16, 24 or 32; default 32)
+ * cp_set_tuning returns CP_OK or CP_ERR_ARG; cp_get_tuning the value or -1.
+ * The autotuner in the Python package picks these per GPU and shape.
+ */
+#define CP_TUNE_ZCHUNK_3D 1
+#define CP_TUNE_CTAS_PER_SM 2
+#define CP_TUNE_ROWS_2D 3
+int cp_set_tuning(int key, int value);
+int cp_get_tuning(int key);
 
 /* Kernel launches the library has made since it was loaded. */
 long long cp_launch_count(void);

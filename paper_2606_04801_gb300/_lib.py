@@ -82,6 +82,8 @@ _SIGS = {
     "cubical_persistence_uf_trace2": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P, _P, ctypes.c_int, _P]),
     "cubical_persistence_debug_prune": (ctypes.c_int, [ctypes.c_int, _P, _P, _P, _P, ctypes.c_size_t, _I64, _P]),
     "cubical_persistence_debug_layout": (ctypes.c_int, [ctypes.c_int, _P, _P, _I64, _P, ctypes.c_int]),
+    "cp_set_tuning": (ctypes.c_int, [ctypes.c_int, ctypes.c_int]),
+    "cp_get_tuning": (ctypes.c_int, [ctypes.c_int]),
     "cp_launch_count": (ctypes.c_longlong, []),
     "cp_profile": (ctypes.c_int, [ctypes.c_int]),
     "cp_stage_times": (ctypes.c_int, [_P, ctypes.c_int]),

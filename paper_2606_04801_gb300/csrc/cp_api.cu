@@ -124,6 +124,8 @@ int make_plan(int n_items, const int32_t* ndims, const int64_t* dims, const floa
     }
     P.tab.tiles2d = t2;
     P.tab.tiles3d = t3;
+    P.tab.rows2d = prune_tile_y2d();
+    P.tab.zchunk3d = prune_tile_z3d();
     P.ntot = voff;
     P.ttot = toff;
     int64_t ms = max_survivors > 0 ? max_survivors : voff / 2 + 65536;
@@ -479,6 +481,16 @@ int cubical_persistence_stats(const void* d_workspace, cp_stats* h_stats, void* 
 }
 
 long long cp_launch_count(void) { return g_launches.load(); }
+
+int cp_set_tuning(int key, int value) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    return set_tuning(key, value) == 0 ? CP_OK : CP_ERR_ARG;
+}
+
+int cp_get_tuning(int key) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    return get_tuning(key);
+}
 
 int cubical_persistence_uf_trace(const void* d_workspace, int dual, uint32_t* h_active, double* h_us, int cap,
                                  void* stream) {

@@ -288,7 +288,7 @@ __device__ __forceinline__ uint2 lookup3(uint32_t rel) {
 
 // ---------------------------------------------------------------- 2D
 // Tile: 32 x 32 vertices, CTA 32 x 8, 4 rows per thread.
-constexpr int kT2Y = 32;
+constexpr int kT2Y = 32;  // largest tile height (the shared tile is sized for it)
 
 __global__ void __launch_bounds__(kThreads) k_prune2d(ItemTable tab, Outs o) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -299,7 +299,8 @@ __global__ void __launch_bounds__(kThreads) k_prune2d(ItemTable tab, Outs o) {
     const int ii = tile_item(tab, 0, tab.n2d - 1, t);
     const Item& it = tab.it[ii];
     const int lt = t - it.tile0;
-    const int x0 = (lt % it.tx) * kBX, y0 = (lt / it.tx) * kT2Y;
+    const int rows = tab.rows2d;
+    const int x0 = (lt % it.tx) * kBX, y0 = (lt / it.tx) * rows;
     __shared__ uint64_t lut[256];
     lut[tid] = g_lut2d[tid];
     if (tid == 0) {
@@ -307,7 +308,7 @@ __global__ void __launch_bounds__(kThreads) k_prune2d(ItemTable tab, Outs o) {
         sg.gmin = ~0ull;
     }
     constexpr int SW = kBX + 2;
-    for (int i = tid; i < (kT2Y + 2) * SW; i += kThreads) {
+    for (int i = tid; i < (rows + 2) * SW; i += kThreads) {
         int ly = i / SW, lx = i % SW;
         int gy = y0 + ly - 1, gx = x0 + lx - 1;
         float v = __int_as_float(0x7F800000);  // +inf: never precedes anything
@@ -316,7 +317,7 @@ __global__ void __launch_bounds__(kThreads) k_prune2d(ItemTable tab, Outs o) {
     }
     __syncthreads();
     unsigned long long my_min = ~0ull;
-    for (int r = 0; r < kT2Y / kBY; ++r) {
+    for (int r = 0; r < rows / kBY; ++r) {
         int ly = threadIdx.y + r * kBY, lx = threadIdx.x;
         int y = y0 + ly, x = x0 + lx;
         bool valid = y < it.H && x < it.W;
@@ -366,7 +367,7 @@ __global__ void __launch_bounds__(kThreads) k_prune2d(ItemTable tab, Outs o) {
 constexpr int kW3 = 9;                     // warps per CTA
 constexpr int kT3 = kW3 * 32;
 constexpr int kOX = 31, kOY = 8;           // owned columns / rows per CTA
-constexpr int kZC = 64;                    // owned planes per task
+constexpr int kZC = 64;                    // default owned planes per task
 constexpr int kRW = 34, kRH = kW3 + 2, kRP = kRW * kRH;  // ring plane: cols x0-2.., rows y0-2..
 constexpr int kRing = 8, kAhead = 5;       // ring slots, planes in flight
 constexpr int kCapW0 = 32 * 5;             // staged H0 keys per warp (one step's maximum)
@@ -590,8 +591,8 @@ __global__ void __launch_bounds__(kT3, 4) k_prune3d(ItemTable tab, Outs o) {
         cc.cube_xy = cc.x >= 0 && cc.y >= 0 && cc.x < it.W - 1 && cc.y < it.H - 1 && lane <= 30 && warp <= 7;
         cc.bxy = (cc.y == 0 ? 4u : 0u) | (cc.y == it.H - 1 ? 8u : 0u) | (cc.x == 0 ? 16u : 0u) |
                  (cc.x == it.W - 1 ? 32u : 0u);
-        const int z0 = zc * kZC;
-        const int z1 = min(it.D, z0 + kZC);       // owned planes [z0, z1)
+        const int z0 = zc * tab.zchunk3d;
+        const int z1 = min(it.D, z0 + tab.zchunk3d);  // owned planes [z0, z1)
         const int zlast = min(z1, it.D - 1);       // entries computed for planes [z0, zlast]
         RingPos rp;
         ring_positions(it, x0, y0, rp);
@@ -748,9 +749,33 @@ size_t prune_smem2d() { return sizeof(Stage) + sizeof(float) * (kT2Y + 2) * (kBX
 size_t prune_smem3d() { return sizeof(Smem3); }
 int prune_tile_x() { return kBX; }
 int prune_tile_x3d() { return kOX; }
-int prune_tile_y2d() { return kT2Y; }
+int g_rows2d = kT2Y, g_zchunk3d = kZC, g_ctas3d = 0;  // tuning (cp_set_tuning)
+int prune_tile_y2d() { return g_rows2d; }
 int prune_tile_y3d() { return kOY; }
-int prune_tile_z3d() { return kZC; }
+int prune_tile_z3d() { return g_zchunk3d; }
+
+int set_tuning(int key, int value) {
+    switch (key) {
+        case 1:  // planes per 3D pruning task
+            if (value < 4 || value > 4096) return -1;
+            g_zchunk3d = value;
+            return 0;
+        case 2:  // 3D pruning CTAs per SM (0: as many as fit)
+            if (value < 0 || value > 8) return -1;
+            g_ctas3d = value;
+            return 0;
+        case 3:  // rows per 2D pruning tile
+            if (value != 8 && value != 16 && value != 24 && value != 32) return -1;
+            g_rows2d = value;
+            return 0;
+        default:
+            return -1;
+    }
+}
+
+int get_tuning(int key) {
+    return key == 1 ? g_zchunk3d : key == 2 ? g_ctas3d : key == 3 ? g_rows2d : -1;
+}
 
 cudaError_t upload_luts(const uint64_t* lut2d, const uint16_t* disp3d, const uint64_t* entries3d) {
     cudaError_t e = cudaMemcpyToSymbol(g_lut2d, lut2d, sizeof(uint64_t) * 256);
@@ -797,7 +822,9 @@ cudaError_t launch_prune(const ItemTable& tab, const PruneOuts& po, cudaStream_t
         note_launches(1);
     }
     if (tab.tiles3d > 0) {
-        int grid = tab.tiles3d < blocks3d ? tab.tiles3d : blocks3d;
+        int cap = blocks3d;
+        if (g_ctas3d > 0) cap = device_sm_count() * g_ctas3d < blocks3d ? device_sm_count() * g_ctas3d : blocks3d;
+        int grid = tab.tiles3d < cap ? tab.tiles3d : cap;
         k_prune3d<<<grid, kT3, prune_smem3d(), s>>>(tab, o);
         note_launches(1);
     }

@@ -1,0 +1,53 @@
+"""The pruning pass's tuning (task depth, CTAs per SM, 2D tile height) and
+the autotuner change only the time, never the pairs."""
+import numpy as np
+import pytest
+
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def cp():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2606_04801_gb300 as cp
+
+    return cp
+
+
+def test_pairs_do_not_depend_on_tuning(cp):
+    from paper_2606_04801_gb300 import autotune
+
+    vol = torch.from_numpy(workloads.blurred((70, 50, 90), 2.0, 41)).cuda()
+    img = torch.from_numpy(workloads.quantised(workloads.blurred((300, 200), 3.0, 42))).cuda()
+    saved = autotune.current()
+    try:
+        ref_v = cp.persistence(vol).raw.cpu()
+        ref_i = cp.persistence(img).raw.cpu()
+        ref_b = cp.persistence_batched([img, vol]).raw.cpu()
+        for zc, ctas, rows in [(4, 1, 8), (16, 2, 16), (256, 0, 24), (4096, 3, 32)]:
+            autotune.apply({"zchunk3d": zc, "ctas3d": ctas, "rows2d": rows})
+            assert torch.equal(cp.persistence(vol).raw.cpu(), ref_v)
+            assert torch.equal(cp.persistence(img).raw.cpu(), ref_i)
+            assert torch.equal(cp.persistence_batched([img, vol]).raw.cpu(), ref_b)
+    finally:
+        autotune.apply(saved)
+
+
+def test_autotune_picks_and_caches(cp, tmp_path):
+    from paper_2606_04801_gb300 import autotune
+
+    saved = autotune.current()
+    try:
+        vol = torch.from_numpy(workloads.blurred((96, 96, 96), 3.0, 43)).cuda()
+        cfg = autotune.autotune([vol], cache=str(tmp_path / "t.json"))
+        assert cfg["trials"] >= 15 and cfg["ms"] > 0
+        assert autotune.current()["zchunk3d"] == cfg["zchunk3d"]
+        again = autotune.autotune([vol], cache=str(tmp_path / "t.json"))
+        assert again["ms"] == cfg["ms"]  # served from the cache
+    finally:
+        autotune.apply(saved)

@@ -129,3 +129,17 @@ def test_pruned_restatement_matches_oracle_3d(lib, seed):
         shape = tuple(int(v) for v in rng.integers(2, 7, 3))
         img = rng.integers(0, 3, shape).astype(np.float32) if rng.random() < 0.5 else rng.random(shape, dtype=np.float32)
         assert _pruned_pipeline(lib, img) == _oracle_rows(img)
+
+
+def test_tuning_arguments(lib):
+    keys = {1: (64, [4, 16, 256], [0, 3, 5000]), 2: (0, [0, 2, 4], [-1, 9]), 3: (32, [8, 16, 32], [0, 12, 40])}
+    for key, (default, good, bad) in keys.items():
+        old = lib.cp_get_tuning(key)
+        try:
+            for v in good:
+                assert lib.cp_set_tuning(key, v) == 0 and lib.cp_get_tuning(key) == v
+            for v in bad:
+                assert lib.cp_set_tuning(key, v) == -1
+        finally:
+            assert lib.cp_set_tuning(key, old) == 0
+    assert lib.cp_get_tuning(99) == -1 and lib.cp_set_tuning(99, 1) == -1

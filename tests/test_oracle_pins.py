@@ -379,3 +379,29 @@ def test_rejects_nonfinite_and_small():
         oracle.persistence(np.array([[0.0, np.inf], [1.0, 2.0]], dtype=np.float32))
     with pytest.raises(ValueError):
         oracle.persistence(np.zeros((1, 5), dtype=np.float32))
+
+
+def _betti_top_by_vertices(img, t):
+    """Top Betti number from the vertices above t: the complement of K_t is the
+    union of the open stars of those vertices, and two stars meet exactly when
+    the vertices share a top cell (8-/26-adjacency); components touching the
+    border are joined to the outside."""
+    from scipy import ndimage
+
+    lab, n = ndimage.label(img > t, structure=np.ones((3,) * img.ndim, dtype=bool))
+    border = set()
+    for ax in range(img.ndim):
+        border |= set(np.unique(np.take(lab, 0, axis=ax)).tolist())
+        border |= set(np.unique(np.take(lab, -1, axis=ax)).tolist())
+    border.discard(0)
+    return n - len(border)
+
+
+@pytest.mark.parametrize("shape", [(13, 17), (6, 7, 5)])
+def test_top_betti_vertex_formulation(shape):
+    """Pins the formulation the full-size GPU test uses, against the facet-graph count and the oracle."""
+    rng = np.random.default_rng(18)
+    for img in (rng.random(shape, dtype=np.float32), rng.integers(0, 4, shape).astype(np.float32)):
+        p = oracle.persistence(img)
+        for t in np.unique(img):
+            assert _betti_top_by_vertices(img, t) == _betti_top(img, t) == _alive(p, img.ndim - 1, t)
