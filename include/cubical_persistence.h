@@ -290,6 +290,16 @@ int cubical_persistence_debug_layout(int n_items, const int32_t *ndims, const in
                                      int64_t *h_offsets, int cap);
 
 /*
+ * Failure-path test: a kernel waits, through the same bounded-wait routine
+ * the grid barrier uses, on a workspace word that nothing sets, and gives up
+ * after limit_us microseconds (1 .. 2,000,000).  Needs a workspace of at
+ * least 4 KiB.  Returns CP_ERR_TIMEOUT when the wait gave up as designed
+ * (the CUDA context stays usable), another code otherwise.  Waits for
+ * `stream`.
+ */
+int cubical_persistence_debug_wait_timeout(void *d_workspace, size_t ws_bytes, int64_t limit_us, void *stream);
+
+/*
  * Tuning of the pruning pass (process-wide; read by the following calls;
  * results never depend on it).  Keys:
  *   CP_TUNE_ZCHUNK_3D    planes per 3D pruning task (4..4096, default 64)

@@ -82,6 +82,7 @@ _SIGS = {
     "cubical_persistence_uf_trace2": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P, _P, ctypes.c_int, _P]),
     "cubical_persistence_debug_prune": (ctypes.c_int, [ctypes.c_int, _P, _P, _P, _P, ctypes.c_size_t, _I64, _P]),
     "cubical_persistence_debug_layout": (ctypes.c_int, [ctypes.c_int, _P, _P, _I64, _P, ctypes.c_int]),
+    "cubical_persistence_debug_wait_timeout": (ctypes.c_int, [_P, ctypes.c_size_t, _I64, _P]),
     "cp_set_tuning": (ctypes.c_int, [ctypes.c_int, ctypes.c_int]),
     "cp_get_tuning": (ctypes.c_int, [ctypes.c_int]),
     "cp_launch_count": (ctypes.c_longlong, []),

@@ -482,6 +482,19 @@ int cubical_persistence_stats(const void* d_workspace, cp_stats* h_stats, void* 
 
 long long cp_launch_count(void) { return g_launches.load(); }
 
+int cubical_persistence_debug_wait_timeout(void* d_workspace, size_t ws_bytes, int64_t limit_us, void* stream) {
+    if (!d_workspace || ws_bytes < sizeof(Counters) + 256 || limit_us <= 0 || limit_us > 2000000) return CP_ERR_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Counters* ctr = static_cast<Counters*>(d_workspace);
+    const uint32_t* flag = reinterpret_cast<const uint32_t*>(static_cast<char*>(d_workspace) + align_up(sizeof(Counters)));
+    if (cudaMemsetAsync(d_workspace, 0, align_up(sizeof(Counters)) + 4, s) != cudaSuccess) return CP_ERR_CUDA;
+    if (launch_wait_test(ctr, flag, uint64_t(limit_us) * 1000u, s) != cudaSuccess) return CP_ERR_CUDA;
+    Counters h;
+    if (cudaMemcpyAsync(&h, ctr, sizeof(Counters), cudaMemcpyDeviceToHost, s) != cudaSuccess) return CP_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return CP_ERR_CUDA;
+    return status_to_code(h.status);
+}
+
 int cp_set_tuning(int key, int value) {
     std::lock_guard<std::mutex> lk(g_mu);
     return set_tuning(key, value) == 0 ? CP_OK : CP_ERR_ARG;

@@ -180,6 +180,21 @@ __device__ __forceinline__ void st_release_u64(uint64_t* p, uint64_t v) {
 constexpr uint64_t kWaitLimitNs = 2000000000ull;
 
 __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
+
+// Waits until *p != v, for at most limit_ns of wall time.  Returns false
+// (and sets kStTimeout) when it gave up; the caller then carries on, its
+// result flagged invalid, so every thread terminates.
+__device__ __forceinline__ bool bounded_wait_ne(const uint32_t* p, uint32_t v, Counters* ctr, uint64_t limit_ns) {
+    const uint64_t t0 = global_timer_ns();
+    while (ld_acquire_u32(p) == v) {
+        if (global_timer_ns() - t0 > limit_ns) {
+            set_status(ctr, kStTimeout);
+            return false;
+        }
+        __nanosleep(20);
+    }
+    return true;
+}
 #endif
 
 }  // namespace cp

@@ -168,7 +168,18 @@ int grid_for(int64_t n) {
     return int(b < 1 ? 1 : (b > cap ? cap : b));
 }
 
+// Test of the bounded-wait path: waits on a word that nothing sets.
+__global__ void k_wait_flag(Counters* ctr, const uint32_t* flag, uint64_t limit_ns) {
+    if (threadIdx.x == 0) bounded_wait_ne(flag, 0u, ctr, limit_ns);
+}
+
 }  // namespace
+
+cudaError_t launch_wait_test(Counters* ctr, const uint32_t* flag, uint64_t limit_ns, cudaStream_t s) {
+    k_wait_flag<<<1, 32, 0, s>>>(ctr, flag, limit_ns);
+    note_launches(1);
+    return cudaGetLastError();
+}
 
 int loss_partials() { return kLossBlocks; }
 

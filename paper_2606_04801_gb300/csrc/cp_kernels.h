@@ -96,5 +96,6 @@ cudaError_t launch_loss_backward(const cp_pair* pairs, int64_t n, const int64_t*
                                  double* acc, double* partials, int nparts, double* d_loss, float* grad,
                                  int64_t n_pixels, cudaStream_t s);
 int loss_partials();
+cudaError_t launch_wait_test(Counters* ctr, const uint32_t* flag, uint64_t limit_ns, cudaStream_t s);
 
 }  // namespace cp

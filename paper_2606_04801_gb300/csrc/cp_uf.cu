@@ -76,14 +76,7 @@ __device__ void grid_barrier(Counters* ctr, uint32_t nblocks) {
             __threadfence();
             atomicAdd(&ctr->bar_gen, 1u);
         } else {
-            uint64_t t0 = global_timer_ns();
-            while (ld_acquire_u32(&ctr->bar_gen) == gen) {
-                if (global_timer_ns() - t0 > kWaitLimitNs) {
-                    set_status(ctr, kStTimeout);
-                    break;
-                }
-                __nanosleep(20);
-            }
+            bounded_wait_ne(&ctr->bar_gen, gen, ctr, kWaitLimitNs);
         }
         __threadfence();
     }
