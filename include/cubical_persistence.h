@@ -304,7 +304,7 @@ int cubical_persistence_debug_wait_timeout(void *d_workspace, size_t ws_bytes, i
  * results never depend on it).  Keys:
  *   CP_TUNE_ZCHUNK_3D    planes per 3D pruning task (4..4096, default 64)
  *   CP_TUNE_CTAS_PER_SM  3D pruning CTAs per SM (0 = as many as fit, default)
- *   CP_TUNE_ROWS_2D      rows per 2D pruning tile (8, 16, 24 or 32; default 32)
+ *   CP_TUNE_ROWS_2D      rows per 2D pruning task (4 .. 4096; default 64)
  * cp_set_tuning returns CP_OK or CP_ERR_ARG; cp_get_tuning the value or -1.
  * The autotuner in the Python package picks these per GPU and shape.
  */

@@ -1,7 +1,7 @@
 """Autotuner for the pruning pass (K1).
 
 Picks the 3D task depth (planes per task), the number of 3D pruning CTAs per
-SM and the 2D tile height by timing the lookup + pruning pass alone
+SM and the rows per 2D task by timing the lookup + pruning pass alone
 (cubical_persistence_debug_prune) on the given inputs, and caches the winner
 per GPU and shape bucket in a JSON file (default
 ~/.cache/cp_gb300/autotune.json, or $CP_AUTOTUNE_CACHE).  The pairs never
@@ -25,7 +25,7 @@ from . import _lib
 ZCHUNK_3D, CTAS_PER_SM, ROWS_2D = 1, 2, 3
 CAND_ZCHUNK = (16, 32, 64, 128, 256)
 CAND_CTAS = (0, 2, 3)
-CAND_ROWS = (8, 16, 32)
+CAND_ROWS = (16, 32, 64, 128)
 
 
 def _cache_path() -> str:

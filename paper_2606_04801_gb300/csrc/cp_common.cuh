@@ -38,7 +38,7 @@ struct ItemTable {
     int32_t n;
     int32_t n2d, n3d;         // items 0..n2d-1 are 2D, n2d..n-1 are 3D
     int32_t tiles2d, tiles3d; // total pruning tiles of each kind
-    int32_t rows2d;           // vertex rows per 2D pruning tile (a multiple of 8, at most 32)
+    int32_t rows2d;           // vertex rows per 2D pruning task (4 .. 4096)
     int32_t zchunk3d;         // planes per 3D pruning task
     int32_t pad;
     Item it[kMaxItems];

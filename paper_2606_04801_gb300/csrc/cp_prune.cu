@@ -1,19 +1,22 @@
 // K1: fused lookup + local pruning (Sec. 3.2, Sec. 3.3, Sec. 4.1 steps 1-2,
 // Sec. 4.2 steps 1-3 before the union-finds).
 //
-// One CTA per tile of vertices.  The tile and a one-vertex halo are staged
-// in shared memory (out-of-image halo = +inf, so such neighbours never
-// precede the centre and no bounds test is needed).  Per vertex v:
+// Warps march through the image row by row (2D) or plane by plane (3D) with
+// the neighbourhood of the current vertex in registers and the rows / planes
+// ahead prefetched into shared memory with cp.async (out-of-image positions
+// read +inf, so such neighbours never precede the centre).  Per vertex v:
 //   1. 8/26-bit mask of the neighbours that precede v (value, then index);
 //   2. collapse to the relevant mask and look it up (2D: direct 256-entry
 //      table; 3D: perfect hash of the 15,935 relevant masks);
-//   3. write the H0 forest parent of v (first edge of L(v)) or register v as
-//      an H0 root (local minimum);
-//   4. write the dual forest parent of every top cell of L(v) (the top cell
-//      across the facet where it dies locally, or the outside vertex) or
-//      register it as a dual root;
+//   3. write the H0 forest parent of v (first edge of L(v), chained through
+//      the previous step's vertex when that edge points back along the
+//      marching axis) or register v as an H0 root (local minimum);
+//   4. for the top cell whose smallest corner is one step behind v, find its
+//      largest corner m (the vertex whose lower star holds it) and write its
+//      dual forest parent from m's entry: the top cell across the facet where
+//      it dies locally, the outside vertex, or register it as a dual root;
 //   5. emit the surviving edges and facets as 64-bit order keys.
-// Survivors and roots are staged per CTA in shared memory and appended to
+// Survivors and roots are staged per warp with ballots and appended to the
 // global arrays with one atomic per buffer per flush.
 #include "cp_common.cuh"
 #include "cp_kernels.h"
@@ -22,38 +25,14 @@ namespace cp {
 
 // Lookup tables in global memory, read through the read-only cache (lanes of
 // a warp look up different entries, which constant memory would serialise).
-__device__ uint64_t g_lut2d[256];
+__device__ uint2 g_lut2d[256];  // same two-word entry layout as the 3D table
 __device__ uint16_t g_disp3d[1 << 12];
 // 3D entries as two 32-bit words for cheap decoding:
 //   x: direct (3 bits) | h0_surv << 3 (6) | dual_surv << 9 (12) | in_l << 21 (8)
 //   y: the eight 4-bit dual codes
 __device__ uint2 g_entries3d[1 << 14];  // perfect-hash slots of the 3D table (128 KB)
 
-// slot -> stencil bit tables
-__constant__ int8_t c_face_n3[6] = {4, 10, 12, 14, 16, 22};
-__constant__ int8_t c_facet_n3[12] = {1, 3, 5, 7, 9, 11, 15, 17, 19, 21, 23, 25};
-__constant__ int8_t c_top_n3[8] = {0, 2, 6, 8, 18, 20, 24, 26};
-__constant__ int8_t c_face_n2[4] = {1, 3, 5, 7};
-__constant__ int8_t c_top_n2[4] = {0, 2, 6, 8};
-
 namespace {
-
-constexpr int kBX = 32, kBY = 8;          // CTA shape
-constexpr int kThreads = kBX * kBY;
-constexpr int kCapS = 4096;               // staged survivor keys per kind
-constexpr int kCapR = 1024;               // staged roots per kind
-
-struct Stage {
-    uint64_t s0[kCapS];
-    uint64_t st[kCapS];
-    uint64_t r0age[kCapR];
-    uint64_t rtage[kCapR];
-    uint32_t r0node[kCapR];
-    uint32_t rtnode[kCapR];
-    uint32_t n_s0, n_st, n_r0, n_rt;
-    uint32_t base_s0, base_st, base_r0, base_rt;
-    unsigned long long gmin;
-};
 
 struct Outs {
     uint32_t* uf0;
@@ -68,83 +47,6 @@ struct Outs {
     Counters* ctr;
 };
 
-// warp-aggregated reservation of `k` slots in a shared-memory buffer
-__device__ __forceinline__ uint32_t stage_reserve(uint32_t* counter, uint32_t k) {
-    unsigned lane = lane_id();
-    uint32_t incl = k;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        uint32_t t = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-        if (lane >= unsigned(o)) incl += t;
-    }
-    uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
-    uint32_t base = 0;
-    if (lane == 31 && total) base = atomicAdd(counter, total);
-    base = __shfl_sync(0xFFFFFFFFu, base, 31);
-    return base + incl - k;
-}
-
-__device__ void flush(Stage& sg, const Outs& o) {
-    __syncthreads();
-    if (threadIdx.x == 0 && threadIdx.y == 0) {
-        sg.base_s0 = sg.n_s0 ? atomicAdd(&o.ctr->n_s0, sg.n_s0) : 0;
-        sg.base_st = sg.n_st ? atomicAdd(&o.ctr->n_st, sg.n_st) : 0;
-        sg.base_r0 = sg.n_r0 ? atomicAdd(&o.ctr->n_r0, sg.n_r0) : 0;
-        sg.base_rt = sg.n_rt ? atomicAdd(&o.ctr->n_rt, sg.n_rt) : 0;
-    }
-    __syncthreads();
-    const int tid = threadIdx.y * kBX + threadIdx.x;
-    for (uint32_t i = tid; i < sg.n_s0; i += kThreads) {
-        uint32_t g = sg.base_s0 + i;
-        if (g < o.cap_s) o.s0[g] = sg.s0[i];
-    }
-    for (uint32_t i = tid; i < sg.n_st; i += kThreads) {
-        uint32_t g = sg.base_st + i;
-        if (g < o.cap_s) o.st[g] = sg.st[i];
-    }
-    for (uint32_t i = tid; i < sg.n_r0; i += kThreads) {
-        uint32_t g = sg.base_r0 + i;
-        if (g < o.cap_r0) {
-            o.age0[g] = sg.r0age[i];
-            o.res0[g] = 0;
-            o.uf0[sg.r0node[i]] = kTag | g;
-        } else {
-            o.uf0[sg.r0node[i]] = kTag;  // out of capacity: keep the forest well formed (result flagged invalid)
-        }
-    }
-    for (uint32_t i = tid; i < sg.n_rt; i += kThreads) {
-        uint32_t g = sg.base_rt + i;
-        if (g < o.cap_rt) {
-            o.aget[g] = sg.rtage[i];
-            o.rest[g] = 0;
-            o.uft[sg.rtnode[i]] = kTag | g;
-        } else {
-            o.uft[sg.rtnode[i]] = kTag;
-        }
-    }
-    if (tid == 0) {
-        bool over = (sg.n_s0 && sg.base_s0 + sg.n_s0 > o.cap_s) || (sg.n_st && sg.base_st + sg.n_st > o.cap_s) ||
-                    (sg.n_r0 && sg.base_r0 + sg.n_r0 > o.cap_r0) || (sg.n_rt && sg.base_rt + sg.n_rt > o.cap_rt);
-        if (over) set_status(o.ctr, kStCapacity);
-    }
-    __syncthreads();
-    if (tid == 0) sg.n_s0 = sg.n_st = sg.n_r0 = sg.n_rt = 0;
-    __syncthreads();
-}
-
-// A non-finite pixel flags the call as failed and is read as the largest
-// finite float, so the order stays total and every cell still lies in exactly
-// one lower star (the forests stay well formed even though the result is
-// discarded).  The +inf halo stays above every pixel.
-__device__ __forceinline__ float load_finite(const float* p, Counters* ctr) {
-    float v = __ldg(p);
-    if (!isfinite(v)) {
-        set_status(ctr, kStNonfinite);
-        v = 3.40282347e38f;
-    }
-    return v;
-}
-
 __device__ __forceinline__ unsigned long long warp_min_u64(unsigned long long v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -152,94 +54,6 @@ __device__ __forceinline__ unsigned long long warp_min_u64(unsigned long long v)
         v = t < v ? t : v;
     }
     return v;
-}
-
-// Emit everything one vertex contributes, given its lookup entry.
-// (z, y, x): local coordinates; vg: global vertex id; valid: vertex exists.
-template <int NDIM>
-__device__ __forceinline__ void emit_vertex(Stage& sg, const Outs& o, const Item& it, bool valid, int z, int y,
-                                            int x, uint32_t vg, uint32_t ord, uint64_t e,
-                                            unsigned long long& my_min) {
-    // ---- H0 forest parent / root
-    int direct = valid ? int(e & 7u) : 0;
-    bool root0 = valid && direct == 7;
-    if (valid && !root0) {
-        int n = NDIM == 3 ? c_face_n3[direct] : c_face_n2[direct];
-        int dz, dy, dx;
-        stencil_off(NDIM, n, dz, dy, dx);
-        o.uf0[vg] = uint32_t(int64_t(vg) + (int64_t(dz) * it.H + dy) * it.W + dx);
-    }
-    if (root0) {
-        unsigned long long k = (unsigned long long)(uint64_t(ord) << 32 | uint32_t(vg - it.voff));
-        my_min = k < my_min ? k : my_min;
-    }
-    uint32_t h0s = valid ? uint32_t((e >> 3) & 0x3Fu) : 0u;
-    uint32_t ds = valid ? uint32_t((e >> 41) & 0xFFFu) : 0u;
-    // ---- dual forest parents / dual root
-    int rt_node = -1;
-    uint64_t rt_age = 0;
-    if (valid) {
-        const int ntops = NDIM == 3 ? 8 : 4;
-#pragma unroll
-        for (int t = 0; t < ntops; ++t) {
-            uint32_t code = uint32_t(e >> (9 + 4 * t)) & 15u;
-            if (code == 15u) continue;
-            int n = NDIM == 3 ? c_top_n3[t] : c_top_n2[t];
-            int dz, dy, dx;
-            stencil_off(NDIM, n, dz, dy, dx);
-            uint32_t self = top_of_octant(it, z, y, x, dz, dy, dx);
-            if (code == 8u) {
-                rt_node = int(self);
-                rt_age = make_key(ord, vg, NDIM == 3 ? uint32_t(n) : uint32_t(n) << 1);
-            } else {
-                int n2 = NDIM == 3 ? c_top_n3[code] : c_top_n2[code];
-                int ez, ey, ex;
-                stencil_off(NDIM, n2, ez, ey, ex);
-                o.uft[self] = top_of_octant(it, z, y, x, ez, ey, ex);
-            }
-        }
-    }
-    // ---- stage survivors and roots
-    uint32_t k0 = __popc(h0s);
-    uint32_t kt = NDIM == 3 ? __popc(ds) : __popc(ds & ~h0s);
-    uint32_t p0 = stage_reserve(&sg.n_s0, k0);
-    uint32_t pt = stage_reserve(&sg.n_st, kt);
-    uint32_t pr0 = stage_reserve(&sg.n_r0, root0 ? 1u : 0u);
-    uint32_t prt = stage_reserve(&sg.n_rt, rt_node >= 0 ? 1u : 0u);
-    const int nf = NDIM == 3 ? 6 : 4;
-    for (int s = 0; s < nf; ++s) {
-        if (!((h0s >> s) & 1u)) continue;
-        int n = NDIM == 3 ? c_face_n3[s] : c_face_n2[s];
-        uint32_t low = NDIM == 3 ? uint32_t(n) : (uint32_t(n) << 1) | ((ds >> s) & 1u);
-        sg.s0[p0++] = make_key(ord, vg, low);
-    }
-    if (NDIM == 3) {
-        for (int f = 0; f < 12; ++f) {
-            if (!((ds >> f) & 1u)) continue;
-            sg.st[pt++] = ~make_key(ord, vg, uint32_t(c_facet_n3[f]));
-        }
-    } else {
-        uint32_t m = ds & ~h0s;
-        for (int f = 0; f < 4; ++f) {
-            if (!((m >> f) & 1u)) continue;
-            sg.st[pt++] = ~make_key(ord, vg, uint32_t(c_face_n2[f]) << 1);
-        }
-    }
-    if (root0) {
-        sg.r0node[pr0] = vg;
-        sg.r0age[pr0] = make_key(ord, vg, 0);
-    }
-    if (rt_node >= 0) {
-        sg.rtnode[prt] = uint32_t(rt_node);
-        sg.rtage[prt] = rt_age;
-    }
-}
-
-__device__ __forceinline__ void finish_min(Stage& sg, const Outs& o, int item, unsigned long long my_min) {
-    unsigned long long w = warp_min_u64(my_min);
-    if (lane_id() == 0 && w != ~0ull) atomicMin(&sg.gmin, w);
-    __syncthreads();
-    if (threadIdx.x == 0 && threadIdx.y == 0 && sg.gmin != ~0ull) atomicMin(&o.ctr->gmin[item], sg.gmin);
 }
 
 __device__ __forceinline__ int tile_item(const ItemTable& t, int first, int last, int tile) {
@@ -285,64 +99,6 @@ __device__ __forceinline__ uint2 lookup3(uint32_t rel) {
 }
 
 }  // namespace
-
-// ---------------------------------------------------------------- 2D
-// Tile: 32 x 32 vertices, CTA 32 x 8, 4 rows per thread.
-constexpr int kT2Y = 32;  // largest tile height (the shared tile is sized for it)
-
-__global__ void __launch_bounds__(kThreads) k_prune2d(ItemTable tab, Outs o) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    Stage& sg = *reinterpret_cast<Stage*>(smem_raw);
-    float* tile = reinterpret_cast<float*>(smem_raw + sizeof(Stage));  // (kT2Y+2) x (32+2)
-    const int tid = threadIdx.y * kBX + threadIdx.x;
-    const int t = blockIdx.x;
-    const int ii = tile_item(tab, 0, tab.n2d - 1, t);
-    const Item& it = tab.it[ii];
-    const int lt = t - it.tile0;
-    const int rows = tab.rows2d;
-    const int x0 = (lt % it.tx) * kBX, y0 = (lt / it.tx) * rows;
-    __shared__ uint64_t lut[256];
-    lut[tid] = g_lut2d[tid];
-    if (tid == 0) {
-        sg.n_s0 = sg.n_st = sg.n_r0 = sg.n_rt = 0;
-        sg.gmin = ~0ull;
-    }
-    constexpr int SW = kBX + 2;
-    for (int i = tid; i < (rows + 2) * SW; i += kThreads) {
-        int ly = i / SW, lx = i % SW;
-        int gy = y0 + ly - 1, gx = x0 + lx - 1;
-        float v = __int_as_float(0x7F800000);  // +inf: never precedes anything
-        if (gy >= 0 && gy < it.H && gx >= 0 && gx < it.W) v = load_finite(it.img + int64_t(gy) * it.W + gx, o.ctr);
-        tile[i] = v;
-    }
-    __syncthreads();
-    unsigned long long my_min = ~0ull;
-    for (int r = 0; r < rows / kBY; ++r) {
-        int ly = threadIdx.y + r * kBY, lx = threadIdx.x;
-        int y = y0 + ly, x = x0 + lx;
-        bool valid = y < it.H && x < it.W;
-        const float* c = tile + (ly + 1) * SW + (lx + 1);
-        float cv = c[0];
-        uint32_t raw = 0;
-        if (valid) {
-            // bits 0..3: offsets before v in linear order (ties precede); 4..7 after
-            raw |= (c[-SW - 1] <= cv) ? 1u : 0u;
-            raw |= (c[-SW] <= cv) ? 2u : 0u;
-            raw |= (c[-SW + 1] <= cv) ? 4u : 0u;
-            raw |= (c[-1] <= cv) ? 8u : 0u;
-            raw |= (c[1] < cv) ? 16u : 0u;
-            raw |= (c[SW - 1] < cv) ? 32u : 0u;
-            raw |= (c[SW] < cv) ? 64u : 0u;
-            raw |= (c[SW + 1] < cv) ? 128u : 0u;
-        }
-        uint64_t e = lut[raw];
-        uint32_t vg = uint32_t(it.voff + int64_t(y) * it.W + x);
-        emit_vertex<2>(sg, o, it, valid, 0, y, x, vg, ord_bits(cv), e, my_min);
-        __syncthreads();
-    }
-    flush(sg, o);
-    finish_min(sg, o, ii, my_min);
-}
 
 // ---------------------------------------------------------------- 3D
 // A CTA of 9 warps marches through a chunk of planes.  Warp w handles row
@@ -393,7 +149,8 @@ struct WarpCounts {
     uint32_t s0, st, r0, rt;
 };
 
-__device__ __forceinline__ void warp_flush(WarpStage& ws, WarpCounts& c, const Outs& o) {
+template <class WS>
+__device__ __forceinline__ void warp_flush(WS& ws, WarpCounts& c, const Outs& o) {
     __syncwarp();
     const unsigned lane = lane_id();
     uint32_t b0 = 0, bt = 0, br0 = 0, brt = 0;
@@ -744,12 +501,270 @@ __global__ void __launch_bounds__(kT3, 4) k_prune3d(ItemTable tab, Outs o) {
     if (__any_sync(0xFFFFFFFFu, (cnt.s0 | cnt.st | cnt.r0 | cnt.rt) != 0)) warp_flush(ws, cnt, o);
 }
 
+// ---------------------------------------------------------------- 2D
+// Each warp marches down a strip of one image on its own (no block
+// barriers): lane l handles column x0-1+l; lanes 1..31 own their columns (31
+// per strip), lane 0 is a halo whose lookup codes the top cells of column
+// x0-1 need.  The task owns rows [y0, y1) and computes lookups for rows
+// [y0, min(y1, H-1)].
+//
+// Per row step y:
+//  1. cp.async prefetch of row y+kAhead2 (columns x0-2 .. x0+31) into the
+//     warp's 8-row shared-memory ring; out-of-image positions read +inf;
+//  2. the 8-neighbour mask of (y, x) from registers (rows y-1, y) and the
+//     ring (row y+1), direct table lookup, the H0 forest link (an up link
+//     continues the chain of (y-1, x), the same lane's previous step) and
+//     the survivors and H0 root of owned vertices;
+//  3. the top cell whose smallest corner is (y-1, x): its largest corner m
+//     among the 4 corner values holds, in its entry, where the top cell dies
+//     locally; the codes of rows y-1 and y of column x+1 come by shuffle, so
+//     each lane stores one coalesced dual forest link (or a dual root).
+constexpr int kW2 = 8;                   // warps per CTA (independent tasks)
+constexpr int kOX2 = 31;                 // owned columns per strip
+constexpr int kRW2 = 34;                 // ring row: columns x0-2 .. x0+31
+constexpr int kRing2 = 8, kAhead2 = 5;   // ring rows, rows in flight
+constexpr int kCap2 = 32 * 4;            // staged keys per warp and kind (one step's maximum)
+
+struct WarpStage2 {
+    uint64_t s0[kCap2];
+    uint64_t st[kCap2];
+    uint64_t r0age[kCapWR];
+    uint64_t rtage[kCapWR];
+    uint32_t r0node[kCapWR];
+    uint32_t rtnode[kCapWR];
+};
+
+struct Smem2 {
+    uint2 lut[256];
+    float ring[kW2][kRing2][kRW2];
+    WarpStage2 ws[kW2];
+};
+
+struct Row {
+    float l, c, r;  // columns x-1, x, x+1
+};
+
+__device__ __forceinline__ void read_row(const float* slot, int lane, Row& R) {
+    R.l = slot[lane];
+    R.c = slot[lane + 1];
+    R.r = slot[lane + 2];
+}
+
+struct RowPos {
+    const float* img;
+    uint32_t W, H;
+    int gx0, gx1;     // image columns copied by this lane
+    int idx1;         // ring position of the second column
+    bool in0, in1;    // inside the image
+};
+
+__device__ __forceinline__ void issue_row(float (*ring)[kRW2], const RowPos& p, int lane, int y) {
+    float* slot = ring[(y + kRing2) & (kRing2 - 1)];
+    if (unsigned(y) < p.H) {
+        const float* base = p.img + uint32_t(y) * p.W;
+        if (p.in0) cp_async4(slot + lane + 1, base + p.gx0);
+        if (p.in1) cp_async4(slot + p.idx1, base + p.gx1);
+    } else {  // a row outside the image: every position +inf
+        const float inf = __int_as_float(0x7F800000);
+        if (p.in0) slot[lane + 1] = inf;
+        if (p.in1) slot[p.idx1] = inf;
+    }
+    cp_async_commit();
+}
+
+__global__ void __launch_bounds__(kW2 * 32) k_prune2d(ItemTable tab, Outs o) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Smem2& sm = *reinterpret_cast<Smem2*>(smem_raw);
+    const int warp = threadIdx.x >> 5;
+    const int lane = int(lane_id());
+    const unsigned lt = (1u << lane) - 1u;
+    for (int i = threadIdx.x; i < 256; i += kW2 * 32) sm.lut[i] = g_lut2d[i];
+    __syncthreads();
+    WarpStage2& ws = sm.ws[warp];
+    float(*ring)[kRW2] = sm.ring[warp];
+    WarpCounts cnt = {0, 0, 0, 0};
+    const float inf = __int_as_float(0x7F800000);
+    for (int task = blockIdx.x * kW2 + warp; task < tab.tiles2d; task += gridDim.x * kW2) {
+        const int ii = tile_item(tab, 0, tab.n2d - 1, task);
+        const Item& it = tab.it[ii];
+        const int ltask = task - it.tile0;
+        const int x0 = (ltask % it.tx) * kOX2, y0 = (ltask / it.tx) * tab.rows2d;
+        const int y1 = min(it.H, y0 + tab.rows2d);  // owned rows [y0, y1)
+        const int ylast = min(y1, it.H - 1);        // lookups for rows [y0, ylast]
+        const int x = x0 - 1 + lane;
+        const uint32_t W = uint32_t(it.W), H = uint32_t(it.H), W1 = W - 1u;
+        const uint32_t voff = uint32_t(it.voff), toff = uint32_t(it.toff), OUT = uint32_t(it.toff + it.T);
+        const bool owned_x = lane >= 1 && x < it.W;
+        const bool cube_x = lane <= 30 && x >= 0 && x < it.W - 1;
+        RowPos rp;
+        rp.img = it.img;
+        rp.W = W;
+        rp.H = H;
+        rp.gx0 = x;
+        rp.in0 = unsigned(x) < W;
+        rp.gx1 = lane == 0 ? x0 - 2 : x0 + 31;
+        rp.idx1 = lane == 0 ? 0 : kRW2 - 1;
+        rp.in1 = (lane == 0 || lane == 31) && unsigned(rp.gx1) < W;
+        const bool has1 = lane == 0 || lane == 31;
+        __syncwarp();  // the ring may still be read by the previous task
+#pragma unroll
+        for (int s = 0; s < kRing2; ++s) {
+            if (!rp.in0) ring[s][lane + 1] = inf;
+            if (has1 && !rp.in1) ring[s][rp.idx1] = inf;
+        }
+#pragma unroll
+        for (int k = -1; k < kAhead2; ++k) issue_row(ring, rp, lane, y0 + k);
+        cp_async_wait<kAhead2 - 2>();  // rows y0-1 .. y0+1 have landed
+        __syncwarp();
+        Row A, B, C;
+        read_row(ring[(y0 - 1 + kRing2) & (kRing2 - 1)], lane, A);
+        read_row(ring[y0 & (kRing2 - 1)], lane, B);
+        unsigned long long my_min = ~0ull;
+        uint32_t far = 0, cprev = 0;
+        for (int y = y0; y <= ylast; ++y) {
+            issue_row(ring, rp, lane, y + kAhead2);
+            read_row(ring[(y + 1) & (kRing2 - 1)], lane, C);
+            // ---- lookup of (y, x): bit i of the mask is stencil offset n = i (i < 4) or
+            // i + 1 (i >= 4); offsets before the centre in linear order precede on ties
+            const float cv = B.c;
+            uint32_t raw = 0;
+            raw = (raw << 1) - set_lt(C.r, cv);
+            raw = (raw << 1) - set_lt(C.c, cv);
+            raw = (raw << 1) - set_lt(C.l, cv);
+            raw = (raw << 1) - set_lt(B.r, cv);
+            raw = (raw << 1) - set_le(B.l, cv);
+            raw = (raw << 1) - set_le(A.r, cv);
+            raw = (raw << 1) - set_le(A.c, cv);
+            raw = (raw << 1) - set_le(A.l, cv);
+            const uint2 e = sm.lut[raw];
+            const bool owned = owned_x && y < y1;
+            const uint32_t ord = ord_bits(cv);
+            const uint32_t vl = uint32_t(y) * W + uint32_t(x);
+            const uint32_t vg = voff + vl;
+            const uint32_t direct = e.x & 7u;
+            bool root0 = false;
+            if (owned) {
+                if (!(fabsf(cv) <= 3.40282347e38f)) set_status(o.ctr, kStNonfinite);
+                if (direct == 7u) {
+                    root0 = true;
+                    far = vg;
+                    const unsigned long long k = (unsigned long long)(uint64_t(ord) << 32 | vl);
+                    my_min = k < my_min ? k : my_min;
+                } else {
+                    // face slots: up, left, right, down
+                    const uint32_t mag = (direct == 0u || direct == 3u) ? W : 1u;
+                    const uint32_t u = direct < 2u ? vg - mag : vg + mag;
+                    far = (direct == 0u && y > y0) ? far : u;
+                    o.uf0[vg] = far;
+                }
+            }
+            const uint32_t h0s = owned ? (e.x >> 3) & 0xFu : 0u;
+            const uint32_t ds = owned ? (e.x >> 9) & 0xFu : 0u;
+            const uint32_t dn = ds & ~h0s;  // dual survivors that are not also H0 survivors
+            // ---- the top cell with smallest corner (y-1, x)
+            const uint32_t cprev_r = __shfl_down_sync(0xFFFFFFFFu, cprev, 1);
+            const uint32_t ccur_r = __shfl_down_sync(0xFFFFFFFFu, e.y, 1);
+            bool rootT = false;
+            uint32_t rt_node = 0;
+            uint64_t rt_age = 0;
+            if (cube_x && y > y0) {
+                // largest of the 4 corners under (value, linear index), in index order
+                const float cvals[4] = {A.c, A.r, B.c, B.r};
+                int k = 0;
+                float best = cvals[0];
+#pragma unroll
+                for (int j = 1; j < 4; ++j) {
+                    const bool ge = cvals[j] >= best;
+                    best = ge ? cvals[j] : best;
+                    k = ge ? j : k;
+                }
+                const uint32_t word = k == 0 ? cprev : (k == 1 ? cprev_r : (k == 2 ? e.y : ccur_r));
+                const uint32_t t = uint32_t(3 - k);  // quadrant of the top cell as seen from m
+                const uint32_t code = (word >> (4u * t)) & 15u;
+                const uint32_t self = toff + uint32_t(y - 1) * W1 + uint32_t(x);
+                const int my = y - 1 + (k >> 1), mx = x + (k & 1);
+                if (code == 8u) {
+                    rootT = true;
+                    rt_node = self;
+                    const uint32_t mg = voff + uint32_t(my) * W + uint32_t(mx);
+                    rt_age = make_key(ord_bits(best), mg, (6u * (t >> 1) + 2u * (t & 1u)) << 1);
+                } else if (code < 4u) {
+                    // the top cell across: quadrant `code` of m, smallest corner m - (negative axes)
+                    const int ty = my - int(((code >> 1) & 1u) ^ 1u);
+                    const int tx = mx - int((code & 1u) ^ 1u);
+                    const bool out = unsigned(ty) >= H - 1u || unsigned(tx) >= W1;
+                    o.uft[self] = out ? OUT : toff + uint32_t(ty) * W1 + uint32_t(tx);
+                } else {
+                    o.uft[self] = kTag;  // only reachable with non-finite input (flagged): keep the forest well formed
+                }
+            }
+            cprev = e.y;
+            // ---- stage survivors and roots
+            if (__any_sync(0xFFFFFFFFu, root0 || rootT || (h0s | dn) != 0u)) {
+                const unsigned m_r0 = __ballot_sync(0xFFFFFFFFu, root0);
+                const unsigned m_rt = __ballot_sync(0xFFFFFFFFu, rootT);
+                const uint32_t or0 = __reduce_or_sync(0xFFFFFFFFu, h0s);
+                const uint32_t ort = __reduce_or_sync(0xFFFFFFFFu, dn);
+                const uint32_t n0 = __reduce_add_sync(0xFFFFFFFFu, uint32_t(__popc(h0s)));  // <= 32 * 4
+                const uint32_t nt = __reduce_add_sync(0xFFFFFFFFu, uint32_t(__popc(dn)));   // <= 32 * 4
+                if (cnt.s0 + n0 > uint32_t(kCap2) || cnt.st + nt > uint32_t(kCap2) ||
+                    cnt.r0 + __popc(m_r0) > uint32_t(kCapWR) || cnt.rt + __popc(m_rt) > uint32_t(kCapWR))
+                    warp_flush(ws, cnt, o);
+                if (m_r0) {
+                    if (root0) {
+                        const uint32_t p = cnt.r0 + __popc(m_r0 & lt);
+                        ws.r0node[p] = vg;
+                        ws.r0age[p] = make_key(ord, vg, 0);
+                    }
+                    cnt.r0 += __popc(m_r0);
+                }
+                if (m_rt) {
+                    if (rootT) {
+                        const uint32_t p = cnt.rt + __popc(m_rt & lt);
+                        ws.rtnode[p] = rt_node;
+                        ws.rtage[p] = rt_age;
+                    }
+                    cnt.rt += __popc(m_rt);
+                }
+                uint32_t bits = or0;
+                while (bits) {
+                    const int s = __ffs(bits) - 1;
+                    bits &= bits - 1;
+                    const bool mine = (h0s >> s) & 1u;
+                    const unsigned m = __ballot_sync(0xFFFFFFFFu, mine);
+                    if (mine)  // face slot s is stencil offset 2s+1; low bit: also a dual survivor
+                        ws.s0[cnt.s0 + __popc(m & lt)] = make_key(ord, vg, (uint32_t(2 * s + 1) << 1) | ((ds >> s) & 1u));
+                    cnt.s0 += __popc(m);
+                }
+                bits = ort;
+                while (bits) {
+                    const int f = __ffs(bits) - 1;
+                    bits &= bits - 1;
+                    const bool mine = (dn >> f) & 1u;
+                    const unsigned m = __ballot_sync(0xFFFFFFFFu, mine);
+                    if (mine) ws.st[cnt.st + __popc(m & lt)] = ~make_key(ord, vg, uint32_t(2 * f + 1) << 1);
+                    cnt.st += __popc(m);
+                }
+                __syncwarp();
+            }
+            cp_async_wait<kAhead2 - 2>();  // row y+2 has landed (for the next step)
+            __syncwarp();
+            A = B;
+            B = C;
+        }
+        cp_async_wait<0>();
+        const unsigned long long w = warp_min_u64(my_min);
+        if (lane == 0 && w != ~0ull) atomicMin(&o.ctr->gmin[ii], w);
+    }
+    if (__any_sync(0xFFFFFFFFu, (cnt.s0 | cnt.st | cnt.r0 | cnt.rt) != 0)) warp_flush(ws, cnt, o);
+}
+
 // ---------------------------------------------------------------- host side
-size_t prune_smem2d() { return sizeof(Stage) + sizeof(float) * (kT2Y + 2) * (kBX + 2); }
+size_t prune_smem2d() { return sizeof(Smem2); }
 size_t prune_smem3d() { return sizeof(Smem3); }
-int prune_tile_x() { return kBX; }
+int prune_tile_x() { return kOX2; }
 int prune_tile_x3d() { return kOX; }
-int g_rows2d = kT2Y, g_zchunk3d = kZC, g_ctas3d = 0;  // tuning (cp_set_tuning)
+int g_rows2d = 64, g_zchunk3d = kZC, g_ctas3d = 0;  // tuning (cp_set_tuning)
 int prune_tile_y2d() { return g_rows2d; }
 int prune_tile_y3d() { return kOY; }
 int prune_tile_z3d() { return g_zchunk3d; }
@@ -764,8 +779,8 @@ int set_tuning(int key, int value) {
             if (value < 0 || value > 8) return -1;
             g_ctas3d = value;
             return 0;
-        case 3:  // rows per 2D pruning tile
-            if (value != 8 && value != 16 && value != 24 && value != 32) return -1;
+        case 3:  // rows per 2D pruning task
+            if (value < 4 || value > 4096) return -1;
             g_rows2d = value;
             return 0;
         default:
@@ -777,19 +792,27 @@ int get_tuning(int key) {
     return key == 1 ? g_zchunk3d : key == 2 ? g_ctas3d : key == 3 ? g_rows2d : -1;
 }
 
+// Table entry as two 32-bit words:
+//   x: direct (3 bits) | h0_surv << 3 (6) | dual_surv << 9 (12) | in_l << 21 (8)
+//   y: the eight 4-bit dual codes
+static uint2 pack_entry(uint64_t v) {
+    const uint32_t direct = uint32_t(v & 7u), h0s = uint32_t((v >> 3) & 0x3Fu);
+    const uint32_t ds = uint32_t((v >> 41) & 0xFFFu), in_l = uint32_t((v >> 53) & 0xFFu);
+    uint2 r;
+    r.x = direct | (h0s << 3) | (ds << 9) | (in_l << 21);
+    r.y = uint32_t((v >> 9) & 0xFFFFFFFFu);
+    return r;
+}
+
 cudaError_t upload_luts(const uint64_t* lut2d, const uint16_t* disp3d, const uint64_t* entries3d) {
-    cudaError_t e = cudaMemcpyToSymbol(g_lut2d, lut2d, sizeof(uint64_t) * 256);
+    uint2 p2[256];
+    for (int i = 0; i < 256; ++i) p2[i] = pack_entry(lut2d[i]);
+    cudaError_t e = cudaMemcpyToSymbol(g_lut2d, p2, sizeof(p2));
     if (e != cudaSuccess) return e;
     e = cudaMemcpyToSymbol(g_disp3d, disp3d, sizeof(uint16_t) * (1 << 12));
     if (e != cudaSuccess) return e;
     static uint2 packed[1 << 14];
-    for (int i = 0; i < (1 << 14); ++i) {
-        const uint64_t v = entries3d[i];
-        const uint32_t direct = uint32_t(v & 7u), h0s = uint32_t((v >> 3) & 0x3Fu);
-        const uint32_t ds = uint32_t((v >> 41) & 0xFFFu), in_l = uint32_t((v >> 53) & 0xFFu);
-        packed[i].x = direct | (h0s << 3) | (ds << 9) | (in_l << 21);
-        packed[i].y = uint32_t((v >> 9) & 0xFFFFFFFFu);
-    }
+    for (int i = 0; i < (1 << 14); ++i) packed[i] = pack_entry(entries3d[i]);
     return cudaMemcpyToSymbol(g_entries3d, packed, sizeof(packed));
 }
 
@@ -808,17 +831,21 @@ cudaError_t launch_prune(const ItemTable& tab, const PruneOuts& po, cudaStream_t
     o.cap_rt = po.cap_rt;
     o.ctr = po.ctr;
     static bool attr_set = false;
-    static int blocks3d = 0;
+    static int blocks3d = 0, blocks2d = 0;
     if (!attr_set) {
         cudaFuncSetAttribute(k_prune2d, cudaFuncAttributeMaxDynamicSharedMemorySize, int(prune_smem2d()));
         cudaFuncSetAttribute(k_prune3d, cudaFuncAttributeMaxDynamicSharedMemorySize, int(prune_smem3d()));
         int per_sm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_prune3d, kT3, prune_smem3d());
         blocks3d = device_sm_count() * (per_sm > 0 ? per_sm : 1);
+        int per_sm2 = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, k_prune2d, kW2 * 32, prune_smem2d());
+        blocks2d = device_sm_count() * (per_sm2 > 0 ? per_sm2 : 1);
         attr_set = true;
     }
     if (tab.tiles2d > 0) {
-        k_prune2d<<<tab.tiles2d, dim3(kBX, kBY), prune_smem2d(), s>>>(tab, o);
+        const int need2 = (tab.tiles2d + kW2 - 1) / kW2;
+        k_prune2d<<<need2 < blocks2d ? need2 : blocks2d, kW2 * 32, prune_smem2d(), s>>>(tab, o);
         note_launches(1);
     }
     if (tab.tiles3d > 0) {

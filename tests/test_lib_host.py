@@ -132,7 +132,7 @@ def test_pruned_restatement_matches_oracle_3d(lib, seed):
 
 
 def test_tuning_arguments(lib):
-    keys = {1: (64, [4, 16, 256], [0, 3, 5000]), 2: (0, [0, 2, 4], [-1, 9]), 3: (32, [8, 16, 32], [0, 12, 40])}
+    keys = {1: (64, [4, 16, 256], [0, 3, 5000]), 2: (0, [0, 2, 4], [-1, 9]), 3: (64, [4, 37, 4096], [0, 3, 4097])}
     for key, (default, good, bad) in keys.items():
         old = lib.cp_get_tuning(key)
         try:
