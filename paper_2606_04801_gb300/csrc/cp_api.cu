@@ -31,6 +31,7 @@ constexpr int kStages = 6;
 bool g_profile = false;
 cudaEvent_t g_ev[kStages + 1];
 bool g_ev_made = false;
+bool g_ev_joint = false;  // the last profiled call ran both union-finds in one launch
 
 void mark(int i, cudaStream_t s) {
     if (g_profile && g_ev_made) cudaEventRecord(g_ev[i], s);
@@ -61,7 +62,7 @@ struct Plan {
     uint32_t cap_s = 0, cap_r0 = 0, cap_rt = 0, cap_p = 0, cap_big = 0;
     // byte offsets into the workspace
     size_t o_ctr, o_uf0, o_uft, o_s0, o_st, o_salt, o_age0, o_res0, o_aget, o_rest;
-    size_t o_act0, o_act1, o_yn, o_on, o_yr, o_na0, o_na1, o_nb0, o_nb1, o_pairs, o_pvals, o_pvalt, o_hist, o_status;
+    size_t o_act0, o_act1, o_yn, o_on, o_na0, o_na1, o_nb0, o_nb1, o_pairs, o_pvals, o_pvalt, o_hist, o_status;
     size_t bytes = 0;
 };
 
@@ -156,7 +157,6 @@ int make_plan(int n_items, const int32_t* ndims, const int64_t* dims, const floa
     P.o_act1 = take(sizeof(uint32_t) * P.cap_big);
     P.o_yn = take(sizeof(uint32_t) * P.cap_s);
     P.o_on = take(sizeof(uint32_t) * P.cap_s);
-    P.o_yr = take(sizeof(uint32_t) * P.cap_s);
     P.o_na0 = take(sizeof(uint32_t) * P.cap_s);
     P.o_na1 = take(sizeof(uint32_t) * P.cap_s);
     P.o_nb0 = take(sizeof(uint32_t) * P.cap_s);
@@ -247,63 +247,108 @@ int run(const Plan& P, cp_pair* d_out, int64_t capacity, int64_t* h_out_count, i
     CP_TRY(launch_prune(P.tab, po, s));
     mark(1, s);
 
+    // First-round root walks over the unsorted survivors (tile order), then the
+    // sort carrying each survivor's position, then the first active list.
+    // Scratch while a list is being prepared: na1 / nb1 hold the endpoints'
+    // root ids and act1 / ynode the sort payload (none of these is live yet).
+    uint32_t* na0 = at<uint32_t>(ws, P.o_na0);
+    uint32_t* na1 = at<uint32_t>(ws, P.o_na1);
+    uint32_t* nb0 = at<uint32_t>(ws, P.o_nb0);
+    uint32_t* nb1 = at<uint32_t>(ws, P.o_nb1);
+    uint32_t* ynode = at<uint32_t>(ws, P.o_yn);
+    RootArgs ra;
+    ra.tab = P.tab;
+    ra.cap = P.cap_s;
+    ra.ra = na1;
+    ra.rb = nb1;
+    ra.pos = act1;
+    ra.sorted_pos = act1;  // an even number of passes leaves the payload in place
+    ra.scratch_cap = P.cap_s;
+    ra.act = act0;
+    ra.na = na0;
+    ra.nb = nb0;
+    ra.ctr = ctr;
     SortBufs sb;
-    sb.keys = s0;
     sb.keys_alt = salt;
-    sb.vals = nullptr;
-    sb.vals_alt = nullptr;
-    sb.d_count = &ctr->n_s0;
+    sb.vals = act1;
+    sb.vals_alt = ynode;
     sb.cap = P.cap_s;
     sb.hist = hist;
     sb.status = status;
-    sb.tile_ctr = ctr->sort_tile;
     sb.ctr = ctr;
-    CP_TRY(sort_keys(sb, 0, 8, 1, s));
+    auto prepare = [&](int dual, const uint32_t* d_n_before) -> cudaError_t {
+        ra.keys = dual ? st : s0;
+        ra.d_n = dual ? &ctr->n_st : &ctr->n_s0;
+        ra.uf = dual ? uft : uf0;
+        ra.dual = dual;
+        ra.d_n_before = d_n_before;
+        cudaError_t e = launch_roots(ra, s);
+        if (e != cudaSuccess) return e;
+        sb.keys = dual ? st : s0;
+        sb.d_count = ra.d_n;
+        sb.tile_ctr = ctr->sort_tile + (dual ? 8 : 0);
+        e = sort_keys(sb, 0, 8, dual ? 9 : 1, s);
+        if (e != cudaSuccess) return e;
+        return launch_place_roots(ra, s);
+    };
+    CP_TRY(prepare(0, nullptr));
     mark(2, s);
 
-    UfParams up;
-    up.keys = s0;
-    up.d_nkeys = &ctr->n_s0;
-    up.cap_keys = P.cap_s;
-    up.uf = uf0;
-    up.age = age0;
-    up.res = res0;
-    up.act[0] = act0;
-    up.act[1] = act1;
-    up.na[0] = at<uint32_t>(ws, P.o_na0);
-    up.na[1] = at<uint32_t>(ws, P.o_na1);
-    up.nb[0] = at<uint32_t>(ws, P.o_nb0);
-    up.nb[1] = at<uint32_t>(ws, P.o_nb1);
-    up.ynode = at<uint32_t>(ws, P.o_yn);
-    up.onode = at<uint32_t>(ws, P.o_on);
-    up.yrid = at<uint32_t>(ws, P.o_yr);
-    up.pairs = pairs;
-    up.pair_cap = P.cap_p;
-    up.dual_keys = P.tab.n2d > 0 ? st : nullptr;  // cross-pruning feeds the dual list of 2D items only
-    up.d_ndual = &ctr->n_st;
-    up.dual_cap = P.cap_s;
-    up.ctr = ctr;
-    up.dual = 0;
-    CP_TRY(launch_uf(P.tab, up, s));
-    mark(3, s);
+    UfParams up[2];
+    up[0].keys = s0;
+    up[0].d_nkeys = &ctr->n_s0;
+    up[0].cap_keys = P.cap_s;
+    up[0].uf = uf0;
+    up[0].age = age0;
+    up[0].res = res0;
+    up[0].act[0] = act0;
+    up[0].act[1] = act1;
+    up[0].na[0] = na0;
+    up[0].na[1] = na1;
+    up[0].nb[0] = nb0;
+    up[0].nb[1] = nb1;
+    up[0].ynode = ynode;
+    up[0].onode = at<uint32_t>(ws, P.o_on);
+    up[0].scratch_cap = P.cap_s;
+    up[0].log = salt;  // the sort's spare buffer is free from here to the pair sort
+    up[0].pairs = pairs;
+    up[0].pair_cap = P.cap_p;
+    up[0].dual_keys = P.tab.n2d > 0 ? st : nullptr;  // cross-pruning feeds the dual list of 2D items only
+    up[0].d_ndual = &ctr->n_st;
+    up[0].dual_cap = P.cap_s;
+    up[0].ctr = ctr;
+    up[0].dual = 0;
+    up[1] = up[0];
+    up[1].keys = st;
+    up[1].d_nkeys = &ctr->n_st;
+    up[1].uf = uft;
+    up[1].age = aget;
+    up[1].res = rest;
+    up[1].dual_keys = nullptr;
+    up[1].d_ndual = nullptr;
+    up[1].dual_cap = 0;
+    up[1].dual = 1;
 
-    sb.keys = st;
-    sb.d_count = &ctr->n_st;
-    sb.tile_ctr = ctr->sort_tile + 8;
-    CP_TRY(sort_keys(sb, 0, 8, 9, s));
-    mark(4, s);
-
-    up.keys = st;
-    up.d_nkeys = &ctr->n_st;
-    up.uf = uft;
-    up.age = aget;
-    up.res = rest;
-    up.dual_keys = nullptr;
-    up.d_ndual = nullptr;
-    up.dual_cap = 0;
-    up.dual = 1;
-    CP_TRY(launch_uf(P.tab, up, s));
-    mark(5, s);
+    if (P.tab.n2d > 0) {
+        // the H0 union-find appends positive edges of 2D items to the dual list
+        // (cross-pruning): the dual list is prepared after it
+        g_ev_joint = false;
+        CP_TRY(launch_uf(P.tab, &up[0], 1, s));
+        mark(3, s);
+        CP_TRY(prepare(1, nullptr));
+        mark(4, s);
+        CP_TRY(launch_uf(P.tab, &up[1], 1, s));
+        mark(5, s);
+    } else {
+        // volumes only: the two lists are independent; both union-finds share
+        // one launch and its rounds (the dual list after the H0 list)
+        CP_TRY(prepare(1, &ctr->n_s0));
+        mark(3, s);
+        g_ev_joint = true;
+        CP_TRY(launch_uf(P.tab, up, 2, s));
+        mark(4, s);
+        mark(5, s);
+    }
 
     CP_TRY(launch_essential(P.tab, ctr, pairs, P.cap_p, s));
     uint32_t* pvals = at<uint32_t>(ws, P.o_pvals);
@@ -545,8 +590,12 @@ int cp_stage_times(float* ms, int cap) {
     if (!ms || cap < kStages) return CP_ERR_ARG;
     if (!g_ev_made) return CP_ERR_ARG;
     if (cudaEventSynchronize(g_ev[kStages]) != cudaSuccess) return CP_ERR_CUDA;
+    // event intervals of (prune, sort H0, union-find H0, sort dual, union-find dual, emit)
+    static const int seq[kStages] = {0, 1, 2, 3, 4, 5};
+    static const int joint[kStages] = {0, 1, 3, 2, 4, 5};  // events: sort H0 | sort dual | both | - | emit
+    const int* order = g_ev_joint ? joint : seq;
     for (int i = 0; i < kStages; ++i)
-        if (cudaEventElapsedTime(&ms[i], g_ev[i], g_ev[i + 1]) != cudaSuccess) return CP_ERR_CUDA;
+        if (cudaEventElapsedTime(&ms[i], g_ev[order[i]], g_ev[order[i] + 1]) != cudaSuccess) return CP_ERR_CUDA;
     return kStages;
 }
 

@@ -55,9 +55,10 @@ struct Counters {
     uint32_t n_pairs;         // pairs appended by the union-finds
     uint32_t rounds0, roundst;
     uint32_t bar_count, bar_gen;
-    uint32_t act_count[3];
+    uint32_t act_count[2][3]; // active survivors of the next round (H0 / dual list), rotating
     uint32_t sort_tile[64];   // tile tickets of the sort passes of one call
-    uint32_t pad[7];
+    uint32_t find_ctr;        // work counter of the first union-find round's root walks
+    uint32_t pad[3];
     unsigned long long gmin[kMaxItems];  // (ord bits << 32 | local vertex) of each item's minimum
     int64_t out_count;
     // union-find trace: active survivors and device time at the start of each
@@ -168,6 +169,12 @@ __device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {
 __device__ __forceinline__ uint64_t ld_acquire_u64(const uint64_t* p) {
     uint64_t v;
     asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+// Relaxed (unordered) load at GPU scope: several can be in flight at once.
+__device__ __forceinline__ uint64_t ld_relaxed_u64(const uint64_t* p) {
+    uint64_t v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p));
     return v;
 }
 __device__ __forceinline__ void st_release_u64(uint64_t* p, uint64_t v) {

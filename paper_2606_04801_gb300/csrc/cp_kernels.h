@@ -59,11 +59,12 @@ struct UfParams {
     const uint64_t* age;
     uint64_t* res;
     uint32_t* act[2];         // survivor index of each active slot (ping-pong)
-    uint32_t* na[2];          // current root of the first endpoint of each active slot
-    uint32_t* nb[2];          // current root of the second endpoint
-    uint32_t* ynode;
+    uint32_t* na[2];          // a root id of the first endpoint's class, per active slot
+    uint32_t* nb[2];          // a root id of the second endpoint's class
+    uint32_t* ynode;          // young / old root id between the phases (slots past the registers)
     uint32_t* onode;
-    uint32_t* yrid;
+    uint32_t scratch_cap;     // entries of act / na / nb / ynode / onode and of log
+    uint64_t* log;            // per survivor: young root << 32 | its age id, or ~0 (no commit)
     cp_pair* pairs;
     uint32_t pair_cap;
     uint64_t* dual_keys;      // H0 of 2D items: positive edges that the dual needs (cross-pruning)
@@ -72,7 +73,34 @@ struct UfParams {
     Counters* ctr;
     int dual;                 // 0: H0 (ascending, larger age dies); 1: dual (smaller age dies)
 };
-cudaError_t launch_uf(const ItemTable& tab, const UfParams& p, cudaStream_t s);
+// First-round root walks, before the sort (k_roots: ra / rb / pos per unsorted
+// survivor), and the first active list from the sorted positions
+// (k_place_roots).
+struct RootArgs {
+    ItemTable tab;
+    const uint64_t* keys;        // unsorted survivor keys (k_roots)
+    const uint32_t* d_n;
+    uint32_t cap;
+    const uint32_t* uf;
+    int dual;
+    uint32_t* ra;                // root id of each survivor's endpoints, by unsorted position
+    uint32_t* rb;
+    uint32_t* pos;               // sort payload: the unsorted position
+    const uint32_t* sorted_pos;  // k_place_roots: the payload after the sort
+    const uint32_t* d_n_before;  // dual list after the H0 list: the H0 count (else nullptr)
+    uint32_t scratch_cap;
+    uint32_t* act;               // first active list (ping-pong buffer 0)
+    uint32_t* na;
+    uint32_t* nb;
+    Counters* ctr;
+};
+cudaError_t launch_roots(const RootArgs& r, cudaStream_t s);
+cudaError_t launch_place_roots(const RootArgs& r, cudaStream_t s);
+
+// One problem, or two (H0 and dual of a call without 2D items) carried through
+// the same rounds.  Two problems share the scratch lists (the pointers of p[0])
+// side by side when both fit, else they run one after the other.
+cudaError_t launch_uf(const ItemTable& tab, const UfParams* p, int nprob, cudaStream_t s);
 
 // ---- K4 emission, K5 backward
 cudaError_t launch_init(const ItemTable& tab, Counters* ctr, uint32_t* uft, uint64_t* aget, uint64_t* rest,

@@ -345,7 +345,7 @@ __global__ void __launch_bounds__(kT3, 4) k_prune3d(ItemTable tab, Outs o) {
         cc.OUT = uint32_t(it.toff + it.T);
         cc.in_xy = cc.x >= 0 && cc.y >= 0 && cc.x < it.W && cc.y < it.H;
         cc.owned_xy = cc.in_xy && lane >= 1 && warp >= 1;
-        cc.cube_xy = cc.x >= 0 && cc.y >= 0 && cc.x < it.W - 1 && cc.y < it.H - 1 && lane <= 30 && warp <= 7;
+        cc.cube_xy = cc.x >= 0 && cc.y >= 0 && cc.x < it.W - 1 && cc.y < it.H - 1 && lane <= 30 && warp <= kW3 - 2;
         cc.bxy = (cc.y == 0 ? 4u : 0u) | (cc.y == it.H - 1 ? 8u : 0u) | (cc.x == 0 ? 16u : 0u) |
                  (cc.x == it.W - 1 ? 32u : 0u);
         const int z0 = zc * tab.zchunk3d;
@@ -354,7 +354,7 @@ __global__ void __launch_bounds__(kT3, 4) k_prune3d(ItemTable tab, Outs o) {
         RingPos rp;
         ring_positions(it, x0, y0, rp);
         unsigned long long my_min = ~0ull;
-        uint32_t far = 0;
+        uint32_t far = 0, far_t = 0;  // last H0 link / dual link written by this thread
         __syncthreads();  // the rings may still be read by the previous task
         ring_init(sm, rp);
 #pragma unroll
@@ -364,14 +364,17 @@ __global__ void __launch_bounds__(kT3, 4) k_prune3d(ItemTable tab, Outs o) {
         Nbr A, B, C;
         read_nbr(sm.ring[(z0 - 1 + kRing) & (kRing - 1)], warp, lane, A);
         read_nbr(sm.ring[z0 & (kRing - 1)], warp, lane, B);
-        for (int z = z0; z <= zlast; ++z) {
+        // One plane step: P (plane z-1) and Q (plane z) in registers, R gets plane
+        // z+1.  The loop below rotates the three register planes and the three
+        // codes slots (cs: plane z, ps: plane z-1), so nothing is copied.
+        auto step = [&](const Nbr& A, const Nbr& B, Nbr& C, const int z, const int cs, const int ps) {
             issue_plane(sm, it, z + kAhead, rp, cc.HW);
             read_nbr(sm.ring[(z + 1) & (kRing - 1)], warp, lane, C);
             // ---- lookup of (z, y, x)
             const float cv = B.v[1][1];
             const uint32_t raw = mask26(A, B, C);
             const uint2 e = lookup3(collapse3(raw));
-            sm.codes[z % 3][warp][lane] = e.y;
+            sm.codes[cs][warp][lane] = e.y;
             const bool owned = cc.owned_xy && z < z1;
             const uint32_t ord = ord_bits(cv);
             const uint32_t vl = (uint32_t(z) * cc.H + uint32_t(cc.y)) * cc.W + uint32_t(cc.x);
@@ -416,7 +419,7 @@ __global__ void __launch_bounds__(kT3, 4) k_prune3d(ItemTable tab, Outs o) {
                     k = ge ? j : k;
                 }
                 const int dz = k >> 2, dy = (k >> 1) & 1, dx = k & 1;
-                const uint32_t word = sm.codes[(z - 1 + dz) % 3][warp + dy][lane + dx];
+                const uint32_t word = sm.codes[dz ? cs : ps][warp + dy][lane + dx];
                 const uint32_t t = uint32_t(7 - k);  // octant of the top cell as seen from m
                 const uint32_t code = (word >> (4u * t)) & 15u;
                 const uint32_t self = cc.toff + (uint32_t(z - 1) * (cc.H - 1u) + uint32_t(cc.y)) * cc.W1 + uint32_t(cc.x);
@@ -424,6 +427,7 @@ __global__ void __launch_bounds__(kT3, 4) k_prune3d(ItemTable tab, Outs o) {
                 if (code == 8u) {
                     rootT = true;
                     rt_node = self;
+                    far_t = self;
                     const uint32_t mg = cc.voff + (uint32_t(mz) * cc.H + uint32_t(my)) * cc.W + uint32_t(mx);
                     rt_age = make_key(ord_bits(best), mg, age_slot(t));
                 } else if (code < 8u) {
@@ -432,8 +436,14 @@ __global__ void __launch_bounds__(kT3, 4) k_prune3d(ItemTable tab, Outs o) {
                     const int ty = my - int(((code >> 1) & 1u) ^ 1u);
                     const int tx = mx - int((code & 1u) ^ 1u);
                     const bool out = unsigned(tz) >= cc.D - 1u || unsigned(ty) >= cc.H - 1u || unsigned(tx) >= cc.W1;
-                    o.uft[self] = out ? cc.OUT : cc.toff + (uint32_t(tz) * (cc.H - 1u) + uint32_t(ty)) * cc.W1 + uint32_t(tx);
+                    // a link to (z-2, y, x) continues the chain that this thread wrote for that
+                    // top cell in the previous step
+                    const bool chain = tz == z - 2 && ty == cc.y && tx == cc.x && z - 1 > z0;
+                    far_t = chain ? far_t
+                                  : (out ? cc.OUT : cc.toff + (uint32_t(tz) * (cc.H - 1u) + uint32_t(ty)) * cc.W1 + uint32_t(tx));
+                    o.uft[self] = far_t;
                 } else {
+                    far_t = kTag;
                     o.uft[self] = kTag;  // only reachable with non-finite input (flagged): keep the forest well formed
                 }
             }
@@ -491,8 +501,14 @@ __global__ void __launch_bounds__(kT3, 4) k_prune3d(ItemTable tab, Outs o) {
                 }
                 __syncwarp();
             }
-            A = B;
-            B = C;
+        };
+        for (int z = z0;;) {
+            step(A, B, C, z, 0, 2);
+            if (++z > zlast) break;
+            step(B, C, A, z, 1, 0);
+            if (++z > zlast) break;
+            step(C, A, B, z, 2, 1);
+            if (++z > zlast) break;
         }
         cp_async_wait<0>();
         const unsigned long long w = warp_min_u64(my_min);
@@ -620,7 +636,7 @@ __global__ void __launch_bounds__(kW2 * 32) k_prune2d(ItemTable tab, Outs o) {
         read_row(ring[(y0 - 1 + kRing2) & (kRing2 - 1)], lane, A);
         read_row(ring[y0 & (kRing2 - 1)], lane, B);
         unsigned long long my_min = ~0ull;
-        uint32_t far = 0, cprev = 0;
+        uint32_t far = 0, far_t = 0, cprev = 0;  // last H0 link / dual link written by this lane
         for (int y = y0; y <= ylast; ++y) {
             issue_row(ring, rp, lane, y + kAhead2);
             read_row(ring[(y + 1) & (kRing2 - 1)], lane, C);
@@ -686,6 +702,7 @@ __global__ void __launch_bounds__(kW2 * 32) k_prune2d(ItemTable tab, Outs o) {
                 if (code == 8u) {
                     rootT = true;
                     rt_node = self;
+                    far_t = self;
                     const uint32_t mg = voff + uint32_t(my) * W + uint32_t(mx);
                     rt_age = make_key(ord_bits(best), mg, (6u * (t >> 1) + 2u * (t & 1u)) << 1);
                 } else if (code < 4u) {
@@ -693,8 +710,13 @@ __global__ void __launch_bounds__(kW2 * 32) k_prune2d(ItemTable tab, Outs o) {
                     const int ty = my - int(((code >> 1) & 1u) ^ 1u);
                     const int tx = mx - int((code & 1u) ^ 1u);
                     const bool out = unsigned(ty) >= H - 1u || unsigned(tx) >= W1;
-                    o.uft[self] = out ? OUT : toff + uint32_t(ty) * W1 + uint32_t(tx);
+                    // a link to (y-2, x) continues the chain that this lane wrote for that top
+                    // cell in the previous step
+                    const bool chain = ty == y - 2 && tx == x && y - 1 > y0;
+                    far_t = chain ? far_t : (out ? OUT : toff + uint32_t(ty) * W1 + uint32_t(tx));
+                    o.uft[self] = far_t;
                 } else {
+                    far_t = kTag;
                     o.uft[self] = kTag;  // only reachable with non-finite input (flagged): keep the forest well formed
                 }
             }

@@ -21,6 +21,7 @@ constexpr int kT = 256;                 // threads per CTA
 constexpr int kWarps = kT / 32;
 constexpr int kKPT = kSortTile / kT;    // keys per thread (16)
 constexpr uint32_t kFlagAgg = 1u, kFlagIncl = 2u;
+constexpr int kLook = 16;               // look-back window: predecessor tiles read together
 
 __global__ void __launch_bounds__(kT) k_hist(const uint64_t* __restrict__ keys, const uint32_t* d_count, uint32_t cap,
                                              uint32_t* __restrict__ hist, int first_byte, int npasses) {
@@ -39,21 +40,29 @@ __global__ void __launch_bounds__(kT) k_hist(const uint64_t* __restrict__ keys, 
     }
 }
 
-// exclusive scan of each pass's 256 digit counts (in place)
+// exclusive scan of each pass's 256 digit counts (in place): warp p scans
+// pass p, 8 digits per lane, with shuffles (no block barriers)
 __global__ void __launch_bounds__(kT) k_hist_scan(uint32_t* hist, int npasses) {
-    __shared__ uint32_t s[256];
-    for (int p = 0; p < npasses; ++p) {
-        uint32_t v = hist[p * 256 + threadIdx.x];
-        s[threadIdx.x] = v;
-        __syncthreads();
-        for (int o = 1; o < 256; o <<= 1) {
-            uint32_t t = threadIdx.x >= unsigned(o) ? s[threadIdx.x - o] : 0u;
-            __syncthreads();
-            s[threadIdx.x] += t;
-            __syncthreads();
-        }
-        hist[p * 256 + threadIdx.x] = s[threadIdx.x] - v;
-        __syncthreads();
+    const int p = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (p >= npasses) return;
+    uint32_t* h = hist + p * 256 + lane * 8;
+    uint32_t v[8], sum = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        v[k] = h[k];
+        sum += v[k];
+    }
+    uint32_t incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    uint32_t run = incl - sum;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        h[k] = run;
+        run += v[k];
     }
 }
 
@@ -127,24 +136,40 @@ __global__ void __launch_bounds__(kT) k_onesweep(const uint64_t* __restrict__ sr
         // publish this tile's aggregate, then look back
         uint64_t* my = status + size_t(tile) * 256 + d;
         st_release_u64(my, pack_status(epoch, kFlagAgg, cnt));
+        // Look back over windows of kLook predecessors whose status words are
+        // read together (relaxed loads: the counts are in the words themselves,
+        // nothing else is read through them), summing aggregates until an
+        // inclusive prefix: a round trip per window, not per tile.
         uint32_t prefix = 0;
         bool timed_out = false;
         uint64_t t0 = 0;
-        for (int64_t j = int64_t(tile) - 1; j >= 0; --j) {
-            const uint64_t* ps = status + size_t(j) * 256 + d;
-            uint64_t s = ld_acquire_u64(ps);
-            while (uint32_t(s >> 34) != epoch || ((s >> 32) & 3u) == 0u) {
-                if (t0 == 0) t0 = global_timer_ns();
-                else if (global_timer_ns() - t0 > kWaitLimitNs) {
-                    timed_out = true;
-                    break;
+        for (int64_t j = int64_t(tile) - 1; j >= 0 && !timed_out; j -= kLook) {
+            uint64_t w[kLook];
+#pragma unroll
+            for (int k = 0; k < kLook; ++k)
+                w[k] = j - k >= 0 ? ld_relaxed_u64(status + size_t(j - k) * 256 + d) : 0ull;
+            bool done = false;
+#pragma unroll
+            for (int k = 0; k < kLook; ++k) {
+                if (!done && !timed_out && j - k >= 0) {
+                    uint64_t v = w[k];
+                    // a predecessor that has not published yet (this epoch): wait for it
+                    while (uint32_t(v >> 34) != epoch || ((v >> 32) & 3u) == 0u) {
+                        if (t0 == 0) t0 = global_timer_ns();
+                        else if (global_timer_ns() - t0 > kWaitLimitNs) {
+                            timed_out = true;
+                            break;
+                        }
+                        __nanosleep(32);
+                        v = ld_relaxed_u64(status + size_t(j - k) * 256 + d);
+                    }
+                    if (!timed_out) {
+                        prefix += uint32_t(v);
+                        done = ((v >> 32) & 3u) == kFlagIncl;
+                    }
                 }
-                __nanosleep(32);
-                s = ld_acquire_u64(ps);
             }
-            if (timed_out) break;
-            prefix += uint32_t(s);
-            if (((s >> 32) & 3u) == kFlagIncl) break;
+            if (done) break;
         }
         if (timed_out) set_status(ctr, kStTimeout);
         st_release_u64(my, pack_status(epoch, kFlagIncl, prefix + cnt));

@@ -19,8 +19,15 @@
 //
 // The H0 forest and the dual forest written by the pruning pass are the
 // initial parent arrays; roots carry a tag and a root id, which indexes the
-// age and reservation arrays.  The union-find runs as one persistent
-// cooperative kernel with a grid barrier between phases.
+// age and reservation arrays.  The first round's root walks (the long ones,
+// through the large forests) run in their own launch and hand over root ids;
+// from then on the union-find lives in root-id space: a root that dies gets
+// the dead mark and its parent's root id in its reservation word, so the
+// finds of later rounds read only the compact per-root arrays (which stay in
+// L2).  The rounds run as one persistent cooperative kernel with a grid
+// barrier between phases.  A commit only marks the root and notes its id in
+// a per-survivor log; the pairs are written from the log in one parallel pass
+// after the last round.
 #include "cp_common.cuh"
 #include "cp_kernels.h"
 
@@ -32,16 +39,19 @@ constexpr uint32_t kInvalid = 0xFFFFFFFFu;
 
 struct UfKernelArgs {
     ItemTable tab;
-    UfParams p;
+    UfParams p[2];
+    int nprob;
 };
 
 // Roots of a and b, walking both paths in lockstep (two independent loads in
 // flight per thread).  The walks only read: the active survivors carry their
 // roots from round to round, so nothing needs compressing, and random partial
 // writes into the large forest array would cost read-modify-write traffic.
-__device__ __forceinline__ void find_two(const uint32_t* uf, uint32_t a, uint32_t b, uint32_t& rida, uint32_t& ridb,
-                                         uint32_t& ra, uint32_t& rb, uint32_t& hops) {
-    uint32_t pa = __ldcg(uf + a), pb = __ldcg(uf + b);
+// Paths end at roots (the forests are acyclic); the wall-clock bound only
+// guards against a corrupted forest (the walk then stops and reports false).
+__device__ __forceinline__ bool walk(const uint32_t* uf, uint32_t& a, uint32_t& pa, uint32_t& b, uint32_t& pb,
+                                     uint32_t& hops) {
+    uint64_t t0 = 0;
     while (!(pa & kTag) || !(pb & kTag)) {
         ++hops;
         if (!(pa & kTag)) {
@@ -52,16 +62,50 @@ __device__ __forceinline__ void find_two(const uint32_t* uf, uint32_t a, uint32_
             b = pb;
             pb = __ldcg(uf + b);
         }
+        if ((hops & 1023u) == 0) {
+            const uint64_t now = global_timer_ns();
+            if (t0 == 0) t0 = now;
+            else if (now - t0 > kWaitLimitNs) return false;
+        }
     }
+    return true;
+}
+
+__device__ __forceinline__ bool find_two(const uint32_t* uf, uint32_t a, uint32_t b, uint32_t& rida, uint32_t& ridb,
+                                         uint32_t& ra, uint32_t& rb, uint32_t& hops) {
+    uint32_t pa = __ldcg(uf + a), pb = __ldcg(uf + b);
+    const bool ok = walk(uf, a, pa, b, pb, hops);
     ra = a;
     rb = b;
     rida = pa & ~kTag;
     ridb = pb & ~kTag;
+    return ok;
 }
 
+// Reservation word of a root that has died: the dead mark in the high half
+// (above every stamp, whose high half is the round) and the parent root id.
+constexpr uint64_t kDead = 0xFFFFFFFF00000000ull;
+
+// Current root id of a class given a root id it once had.
+__device__ __forceinline__ bool find_rid(const uint64_t* res, uint32_t& rid, uint32_t& hops) {
+    uint64_t w = __ldcg(res + rid);
+    uint64_t t0 = 0;
+    while ((w & kDead) == kDead) {
+        rid = uint32_t(w);
+        w = __ldcg(res + rid);
+        if ((++hops & 1023u) == 0) {
+            const uint64_t now = global_timer_ns();
+            if (t0 == 0) t0 = now;
+            else if (now - t0 > kWaitLimitNs) return false;
+        }
+    }
+    return true;
+}
+
+// The result is not needed: the atomic goes out as a reduction, and the
+// thread does not wait for it (the grid barrier orders it before the checks).
 __device__ __forceinline__ void reserve(uint64_t* res, uint32_t rid, uint64_t stamp) {
-    uint64_t cur = __ldcg(res + rid);
-    if (cur < stamp) atomicMax(reinterpret_cast<unsigned long long*>(res + rid), (unsigned long long)stamp);
+    atomicMax(reinterpret_cast<unsigned long long*>(res + rid), (unsigned long long)stamp);
 }
 
 // Grid-wide barrier for a cooperative launch (all CTAs co-resident).
@@ -109,8 +153,9 @@ __device__ __forceinline__ void endpoints(const ItemTable& tab, uint64_t k, int 
         b = uint32_t(int64_t(vg) + (int64_t(dz) * it.H + dy) * it.W + dx);
         return;
     }
-    int64_t local = int64_t(vg) - it.voff;
-    int x = int(local % it.W), y = int((local / it.W) % it.H), z = int(local / (int64_t(it.W) * it.H));
+    const uint32_t local = vg - uint32_t(it.voff), W = uint32_t(it.W), H = uint32_t(it.H);
+    const uint32_t row = local / W;
+    const int x = int(local - row * W), y = int(row % H), z = int(row / H);
     // the facet's zero coordinate (on one of the item's axes) picks the side
     int sz0 = dz, sy0 = dy, sx0 = dx, sz1 = dz, sy1 = dy, sx1 = dx;
     if (it.ndim == 3 && dz == 0) {
@@ -127,10 +172,14 @@ __device__ __forceinline__ void endpoints(const ItemTable& tab, uint64_t k, int 
     b = top_of_octant(it, z, y, x, sz1, sy1, sx1);
 }
 
+// The pair of a committed survivor with key `key`, whose dying class has root
+// id yrid (the root's age key names the root vertex, or for the dual the
+// vertex whose lower star holds the dying top cell).
 __device__ __forceinline__ void emit_pair(const UfParams& p, const ItemTable& tab, uint64_t key, int item,
-                                          uint32_t young, uint32_t yrid, bool* emitted, cp_pair& out) {
+                                          uint32_t yrid, bool* emitted, cp_pair& out) {
     const Item& it = tab.it[item];
     uint64_t age = p.age[yrid];
+    const uint32_t young = key_vertex(age);
     uint32_t vg = key_vertex(key);
     int n = int(key_n(key, it.ndim));
     int dz, dy, dx;
@@ -170,143 +219,459 @@ __device__ __forceinline__ void emit_pair(const UfParams& p, const ItemTable& ta
     *emitted = out.birth != out.death;  // zero persistence: omitted (Sec. 2.3)
 }
 
-__global__ void __launch_bounds__(kT) k_uf(UfKernelArgs args) {
-    const ItemTable& tab = args.tab;
-    const UfParams& p = args.p;
-    Counters* ctr = p.ctr;
-    const uint32_t nblocks = gridDim.x;
-    const uint32_t gtid = blockIdx.x * kT + threadIdx.x;
-    const uint32_t gstride = nblocks * kT;
-    // a bounded wait that gave up earlier leaves the sorted keys unreliable
-    // non-finite input leaves the forests unreliable: the call fails anyway
+__device__ __forceinline__ bool side_by_side(const UfKernelArgs& args, uint32_t n0, uint32_t n1) {
+    return uint64_t(n0) + n1 <= args.p[0].scratch_cap;
+}
+
+constexpr int kR = 4;  // active items per thread whose phase-A results stay in registers
+
+// 2D cross-pruning: a positive edge of H0 whose key carries the dual flag is
+// a merging facet of the dual graph (only the H0 problem of a call with 2D
+// items has that list, and it runs alone).
+__device__ __forceinline__ void cross_prune(const ItemTable& tab, const UfParams& p, uint32_t i) {
+    if (p.dual || !p.dual_keys) return;
+    const uint64_t key = p.keys[i];
+    if (tab.it[item_of_vertex(tab, key_vertex(key))].ndim == 2 && (key & 1u)) {
+        const uint32_t pos = atomicAdd(p.d_ndual, 1u);
+        if (pos < p.dual_cap) p.dual_keys[pos] = ~(key & ~1ull);
+        else set_status(p.ctr, kStCapacity);
+    }
+}
+
+// The first round's root walks, the long ones (later rounds start from root
+// ids carried over).  They run before the sort, over the survivors in the
+// order the pruning pass wrote them -- tile by tile, so neighbouring
+// survivors walk through the same parts of the forest and share its sectors
+// in L2 -- and the sort carries each survivor's position as its payload.  A
+// separate, non-cooperative launch: warps take 32 survivors at a time from a
+// counter, so a warp held up by a long path delays no other warp.
+constexpr int kFT = 256;
+__global__ void __launch_bounds__(kFT) k_roots(const __grid_constant__ RootArgs r) {
+    Counters* ctr = r.ctr;
     if (ld_acquire_u32(&ctr->status) & (kStTimeout | kStNonfinite)) return;
-    uint32_t n = min(*p.d_nkeys, p.cap_keys);
+    const uint32_t n = min(*r.d_n, r.cap);
+    const unsigned lane = lane_id();
+    uint32_t hops = 0;
+    for (;;) {
+        uint32_t base = 0;
+        if (lane == 0) base = atomicAdd(&ctr->find_ctr, 32u);
+        base = __shfl_sync(0xFFFFFFFFu, base, 0);
+        if (base >= n) break;
+        const uint32_t i = base + lane;
+        if (i >= n) continue;
+        uint64_t key = r.keys[i];
+        if (r.dual) key = ~key;
+        uint32_t a, b, va, vb, ra, rb;
+        int item;
+        endpoints(r.tab, key, r.dual, a, b, item);
+        if (!find_two(r.uf, a, b, ra, rb, va, vb, hops)) {
+            set_status(ctr, kStTimeout);
+            rb = ra;
+        }
+        __stcg(r.ra + i, ra);
+        __stcg(r.rb + i, rb);
+        __stcg(r.pos + i, i);
+    }
+    for (int o = 16; o > 0; o >>= 1) hops += __shfl_xor_sync(0xFFFFFFFFu, hops, o);
+    if (lane == 0 && hops) atomicAdd(&ctr->trace_hops[r.dual][0], (unsigned long long)hops);
+}
+
+// The first active list of a problem from the sorted positions: slot off + j
+// gets sorted survivor j and the root ids of its endpoints.  The dual list of
+// a call without 2D items sits after the H0 list (off = the H0 count) when
+// both fit the scratch; otherwise the union-find walks it itself.
+__global__ void __launch_bounds__(kFT) k_place_roots(const __grid_constant__ RootArgs r) {
+    // k_roots skipped the walks (the payload was never written): nothing to place
+    if (ld_acquire_u32(&r.ctr->status) & (kStTimeout | kStNonfinite)) return;
+    const uint32_t n = min(*r.d_n, r.cap);
+    uint32_t off = 0;
+    if (r.d_n_before) {
+        off = min(*r.d_n_before, r.cap);
+        if (uint64_t(off) + n > r.scratch_cap) return;
+    }
+    for (uint32_t j = blockIdx.x * kFT + threadIdx.x; j < n; j += gridDim.x * kFT) {
+        uint32_t i = __ldcg(r.sorted_pos + j);
+        if (i >= n) {  // never: the payload is a permutation of 0 .. n-1
+            set_status(r.ctr, kStInternal);
+            i = 0;
+        }
+        __stcg(r.act + off + j, j);
+        __stcg(r.na + off + j, __ldcg(r.ra + i));
+        __stcg(r.nb + off + j, __ldcg(r.rb + i));
+    }
+}
+
+// Root ids of the two endpoints of a survivor that starts here (the first
+// round of a problem whose walks did not run before the sort): a walk
+// through the forest.
+__device__ __forceinline__ void fresh_roots(const UfKernelArgs& args, const UfParams& p, uint32_t i, uint32_t& ra,
+                                            uint32_t& rb, uint32_t& hops) {
+    uint64_t key = p.keys[i];
+    if (p.dual) key = ~key;
+    uint32_t a, b, va, vb;
+    int item;
+    endpoints(args.tab, key, p.dual, a, b, item);
+    if (!find_two(p.uf, a, b, ra, rb, va, vb, hops)) {
+        set_status(p.ctr, kStTimeout);
+        rb = ra;
+    }
+}
+
+// Phase A of one active item whose results go through memory (the items of a
+// thread beyond the first kR).
+__device__ __forceinline__ void phase_a_mem(const UfKernelArgs& args, int q, uint32_t jj, uint32_t slot, bool fresh,
+                                            int cur, uint32_t round, uint32_t& hops) {
+    const UfParams& p = args.p[q];
+    uint32_t i, a, b;
+    if (round == 1) __stcg(p.log + slot, ~0ull);  // no commit yet
+    if (fresh) {
+        i = jj;
+        fresh_roots(args, p, i, a, b, hops);
+    } else {
+        i = __ldcg(p.act[cur] + slot);
+        a = __ldcg(p.na[cur] + slot);
+        b = __ldcg(p.nb[cur] + slot);
+    }
+    if (!find_rid(p.res, a, hops) || !find_rid(p.res, b, hops)) {
+        set_status(p.ctr, kStTimeout);
+        b = a;
+    }
+    if (a == b) {
+        __stcg(p.ynode + slot, kInvalid);
+        cross_prune(args.tab, p, i);
+        return;
+    }
+    const uint64_t aa = p.age[a], ab = p.age[b];
+    const bool a_young = p.dual ? (aa < ab) : (aa > ab);
+    const uint64_t stamp = (uint64_t(round) << 32) | (0xFFFFFFFFu - i);
+    if (aa != ~0ull) reserve(p.res, a, stamp);  // the outside vertex never dies
+    if (ab != ~0ull) reserve(p.res, b, stamp);
+    __stcg(p.ynode + slot, a_young ? a : b);
+    __stcg(p.onode + slot, a_young ? b : a);
+}
+
+// The rounds of one or two problems (H0 and the dual of a call without 2D
+// items, whose lists do not depend on each other) in lockstep: one round
+// covers the active survivors of both, so the grid barriers and the memory
+// latency of a round are paid once for the two.  Problem q's entries of the
+// shared scratch lists and of the commit log start at 0 and base1.  The
+// first kR items of each thread keep their phase-A results in registers, and
+// their loads are issued together.
+__device__ void uf_rounds(const UfKernelArgs& args, uint32_t n0, uint32_t n1, uint32_t base1, unsigned live,
+                          unsigned prefound) {
+    const ItemTable& tab = args.tab;
+    Counters* ctr = args.p[0].ctr;
+    const uint32_t nblocks = gridDim.x;
+    const uint32_t gstride = nblocks * kT;
+    const uint32_t gtid = blockIdx.x * kT + threadIdx.x;
+    const unsigned lane = lane_id();
+    const uint32_t ninit[2] = {n0, n1};
+    uint32_t n[2] = {n0, n1};
+    uint32_t rounds[2] = {0u, 0u};
     int cur = 0;
     uint32_t round = 1;
     for (;; ++round) {
         if (gtid == 0 && round <= uint32_t(kTraceRounds)) {
-            ctr->trace_active[p.dual][round - 1] = n;
-            ctr->trace_t[p.dual][round - 1] = global_timer_ns();
+            const uint64_t now = global_timer_ns();
+            for (int q = 0; q < 2; ++q) {
+                if (!((live >> q) & 1u)) continue;
+                const int d = args.p[q].dual;
+                ctr->trace_active[d][round - 1] = n[q];
+                ctr->trace_t[d][round - 1] = now;
+            }
         }
-        if (n == 0) break;
-        if (gtid == 0) ctr->act_count[round % 3] = 0;
+        if (n[0] + n[1] == 0) break;
+        if (n[0]) rounds[0] = round;
+        if (n[1]) rounds[1] = round;
+        if (gtid == 0) ctr->act_count[0][round % 3] = ctr->act_count[1][round % 3] = 0;
+        const uint32_t ntot = n[0] + n[1];
+        uint32_t hops0 = 0, hops1 = 0;
         // ---- phase A: find roots, resolve positives, reserve
-        uint32_t hops = 0;
-        for (uint32_t j0 = blockIdx.x * kT; j0 < n; j0 += gstride) {
-            uint32_t j = j0 + threadIdx.x;
-            bool active = j < n;
-            bool cross = false;
-            uint64_t ckey = 0;
-            if (active) {
-                uint32_t i, a, b;
-                int item = 0;
-                if (round == 1) {
-                    i = j;
-                    uint64_t key = p.keys[i];
-                    if (p.dual) key = ~key;
-                    endpoints(tab, key, p.dual, a, b, item);
-                } else {
-                    i = __ldcg(p.act[cur] + j);
-                    a = __ldcg(p.na[cur] + j);
-                    b = __ldcg(p.nb[cur] + j);
-                }
-                uint32_t ra, ra_id, rb, rb_id;
-                find_two(p.uf, a, b, ra_id, rb_id, ra, rb, hops);
-                if (ra == rb) {
-                    __stcg(p.ynode + j, kInvalid);
-                    // 2D cross-pruning: a positive edge of H0 is a merging facet of the dual
-                    if (!p.dual && p.dual_keys) {
-                        uint64_t key = p.keys[i];
-                        if (tab.it[item_of_vertex(tab, key_vertex(key))].ndim == 2 && (key & 1u)) {
-                            cross = true;
-                            ckey = ~(key & ~1ull);
-                        }
+        uint32_t ri[kR], ry[kR], ro[kR];  // survivor index, young and old root ids
+        unsigned pend = 0, isq1 = 0;  // bit k: item k waits for its check / belongs to problem 1
+        {
+            uint32_t a[kR], b[kR];
+            uint64_t wa[kR], wb[kR];
+            unsigned has = 0;
+#pragma unroll
+            for (int k = 0; k < kR; ++k) {
+                const uint32_t j = gtid + uint32_t(k) * gstride;
+                ri[k] = ry[k] = ro[k] = 0;
+                a[k] = b[k] = 0;
+                if (j < ntot) {
+                    const int q = j >= n[0] ? 1 : 0;
+                    const UfParams& p = args.p[q];
+                    const uint32_t jj = j - (q ? n[0] : 0u);
+                    const uint32_t slot = (q ? base1 : 0u) + jj;
+                    has |= 1u << k;
+                    if (q) isq1 |= 1u << k;
+                    if (round == 1) __stcg(p.log + slot, ~0ull);  // no commit yet
+                    if (round == 1 && !((prefound >> q) & 1u)) {
+                        ri[k] = jj;
+                        uint32_t h = 0;
+                        fresh_roots(args, p, jj, a[k], b[k], h);
+                        if (q) hops1 += h;
+                        else hops0 += h;
+                    } else {
+                        ri[k] = __ldcg(p.act[cur] + slot);
+                        a[k] = __ldcg(p.na[cur] + slot);
+                        b[k] = __ldcg(p.nb[cur] + slot);
                     }
-                } else {
-                    uint64_t aa = p.age[ra_id], ab = p.age[rb_id];
-                    // H0: the root with the larger key (later vertex) dies; dual: the smaller key dies
-                    bool a_young = p.dual ? (aa < ab) : (aa > ab);
-                    uint32_t y = a_young ? ra : rb, o = a_young ? rb : ra;
-                    uint32_t yr = a_young ? ra_id : rb_id;
-                    uint64_t stamp = (uint64_t(round) << 32) | (0xFFFFFFFFu - i);
-                    if (aa != ~0ull) reserve(p.res, ra_id, stamp);  // the outside vertex never dies
-                    if (ab != ~0ull) reserve(p.res, rb_id, stamp);
-                    __stcg(p.ynode + j, y);
-                    __stcg(p.onode + j, o);
-                    __stcg(p.yrid + j, yr);
                 }
-                (void)item;
             }
-            uint32_t pos = warp_append(p.d_ndual, cross);
-            if (cross) {
-                if (pos < p.dual_cap) p.dual_keys[pos] = ckey;
-                else set_status(ctr, kStCapacity);
+            // reservation words of the carried roots (loads of the kR items in flight together)
+#pragma unroll
+            for (int k = 0; k < kR; ++k) {
+                const uint64_t* res = ((isq1 >> k) & 1u) ? args.p[1].res : args.p[0].res;
+                const bool h = (has >> k) & 1u;
+                wa[k] = h ? __ldcg(res + a[k]) : 0ull;
+                wb[k] = h ? __ldcg(res + b[k]) : 0ull;
             }
+#pragma unroll
+            for (int k = 0; k < kR; ++k) {
+                if ((wa[k] & kDead) != kDead && (wb[k] & kDead) != kDead) continue;  // both still roots
+                // a carried root has died: follow the dead marks to the current roots
+                const int q = (isq1 >> k) & 1u;
+                const uint64_t* res = args.p[q].res;
+                uint32_t h = 0;
+                if ((wa[k] & kDead) == kDead) {
+                    a[k] = uint32_t(wa[k]);
+                    if (!find_rid(res, a[k], h)) set_status(ctr, kStTimeout);
+                    ++h;
+                }
+                if ((wb[k] & kDead) == kDead) {
+                    b[k] = uint32_t(wb[k]);
+                    if (!find_rid(res, b[k], h)) set_status(ctr, kStTimeout);
+                    ++h;
+                }
+                if (q) hops1 += h;
+                else hops0 += h;
+            }
+            uint64_t aa[kR], ab[kR];
+#pragma unroll
+            for (int k = 0; k < kR; ++k) {
+                aa[k] = ab[k] = 0;
+                if (((has >> k) & 1u) && a[k] != b[k]) {
+                    const uint64_t* age = ((isq1 >> k) & 1u) ? args.p[1].age : args.p[0].age;
+                    aa[k] = age[a[k]];
+                    ab[k] = age[b[k]];
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < kR; ++k) {
+                if (!((has >> k) & 1u)) continue;
+                const int q = (isq1 >> k) & 1u;
+                const UfParams& p = args.p[q];
+                if (a[k] == b[k]) {
+                    cross_prune(tab, p, ri[k]);
+                    continue;
+                }
+                // H0: the root with the larger key (later vertex) dies; dual: the smaller key dies
+                const bool a_young = p.dual ? (aa[k] < ab[k]) : (aa[k] > ab[k]);
+                const uint64_t stamp = (uint64_t(round) << 32) | (0xFFFFFFFFu - ri[k]);
+                if (aa[k] != ~0ull) reserve(p.res, a[k], stamp);  // the outside vertex never dies
+                if (ab[k] != ~0ull) reserve(p.res, b[k], stamp);
+                ry[k] = a_young ? a[k] : b[k];
+                ro[k] = a_young ? b[k] : a[k];
+                pend |= 1u << k;
+            }
+        }
+        // items beyond kR per thread: state through memory
+        for (uint32_t j0 = blockIdx.x * kT + kR * gstride; j0 < ntot; j0 += gstride) {
+            const uint32_t j = j0 + threadIdx.x;
+            if (j >= ntot) continue;
+            const int q = j >= n[0] ? 1 : 0;
+            const uint32_t jj = j - (q ? n[0] : 0u);
+            uint32_t h = 0;
+            phase_a_mem(args, q, jj, (q ? base1 : 0u) + jj, round == 1 && !((prefound >> q) & 1u), cur, round, h);
+            if (q) hops1 += h;
+            else hops0 += h;
         }
         if (round <= uint32_t(kTraceRounds)) {
-            uint32_t h = hops;
-            for (int o = 16; o > 0; o >>= 1) h += __shfl_xor_sync(0xFFFFFFFFu, h, o);
-            if (lane_id() == 0 && h) atomicAdd(&ctr->trace_hops[p.dual][round - 1], (unsigned long long)h);
+            for (int q = 0; q < 2; ++q) {
+                uint32_t h = q ? hops1 : hops0;
+                for (int o = 16; o > 0; o >>= 1) h += __shfl_xor_sync(0xFFFFFFFFu, h, o);
+                if (lane == 0 && h) atomicAdd(&ctr->trace_hops[args.p[q].dual][round - 1], (unsigned long long)h);
+            }
         }
         grid_barrier(ctr, nblocks);
-        if (gtid == 0 && round <= uint32_t(kTraceRounds)) ctr->trace_ta[p.dual][round - 1] = global_timer_ns();
+        if (gtid == 0 && round <= uint32_t(kTraceRounds))
+            for (int q = 0; q < 2; ++q)
+                if ((live >> q) & 1u) ctr->trace_ta[args.p[q].dual][round - 1] = global_timer_ns();
         // ---- phase B: commit the survivors that hold the reservation of their dying root
-        uint32_t* next = p.act[cur ^ 1];
-        for (uint32_t j0 = blockIdx.x * kT; j0 < n; j0 += gstride) {
-            uint32_t j = j0 + threadIdx.x;
-            bool keep = false, emit = false;
-            uint32_t i = 0;
-            cp_pair pr;
-            if (j < n) {
-                uint32_t y = __ldcg(p.ynode + j);
+        {
+            uint64_t rv[kR];
+#pragma unroll
+            for (int k = 0; k < kR; ++k) {
+                const uint64_t* res = ((isq1 >> k) & 1u) ? args.p[1].res : args.p[0].res;
+                rv[k] = ((pend >> k) & 1u) ? __ldcg(res + ry[k]) : 0ull;
+            }
+            unsigned keep = 0;
+#pragma unroll
+            for (int k = 0; k < kR; ++k) {
+                if (!((pend >> k) & 1u)) continue;
+                const int q = (isq1 >> k) & 1u;
+                const UfParams& p = args.p[q];
+                const uint64_t stamp = (uint64_t(round) << 32) | (0xFFFFFFFFu - ri[k]);
+                if (rv[k] == stamp) {
+                    __stcg(p.res + ry[k], kDead | ro[k]);  // the young class joins the old one
+                    __stcg(p.log + (q ? base1 : 0u) + ri[k], uint64_t(ry[k]));
+                } else {
+                    keep |= 1u << k;
+                }
+            }
+            // one atomic per warp and problem for the next round's slots
+            uint32_t c0 = __popc(keep & ~isq1), c1 = __popc(keep & isq1);
+            uint32_t s0 = c0, s1 = c1;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t t0 = __shfl_up_sync(0xFFFFFFFFu, s0, o), t1 = __shfl_up_sync(0xFFFFFFFFu, s1, o);
+                if (lane >= unsigned(o)) {
+                    s0 += t0;
+                    s1 += t1;
+                }
+            }
+            uint32_t b0 = 0, b1 = 0;
+            if (lane == 31) {
+                if (s0) b0 = atomicAdd(&ctr->act_count[0][round % 3], s0);
+                if (s1) b1 = atomicAdd(&ctr->act_count[1][round % 3], s1);
+            }
+            b0 = __shfl_sync(0xFFFFFFFFu, b0, 31) + s0 - c0;
+            b1 = __shfl_sync(0xFFFFFFFFu, b1, 31) + s1 - c1;
+#pragma unroll
+            for (int k = 0; k < kR; ++k) {
+                if (!((keep >> k) & 1u)) continue;
+                const int q = (isq1 >> k) & 1u;
+                const UfParams& p = args.p[q];
+                const uint32_t at = q ? base1 + b1++ : b0++;
+                p.act[cur ^ 1][at] = ri[k];
+                p.na[cur ^ 1][at] = ry[k];
+                p.nb[cur ^ 1][at] = ro[k];
+            }
+        }
+        for (uint32_t j0 = blockIdx.x * kT + kR * gstride; j0 < ntot; j0 += gstride) {
+            const uint32_t j = j0 + threadIdx.x;
+            const int q = j >= n[0] ? 1 : 0;
+            const UfParams& p = args.p[q];
+            const uint32_t jj = j - (q ? n[0] : 0u);
+            const uint32_t slot = (q ? base1 : 0u) + jj;
+            bool keep = false;
+            uint32_t i = 0, y = 0;
+            if (j < ntot) {
+                y = __ldcg(p.ynode + slot);
                 if (y != kInvalid) {
-                    i = round == 1 ? j : __ldcg(p.act[cur] + j);
-                    uint32_t yr = __ldcg(p.yrid + j);
-                    uint64_t stamp = (uint64_t(round) << 32) | (0xFFFFFFFFu - i);
-                    if (__ldcg(p.res + yr) == stamp) {
-                        __stcg(p.uf + y, __ldcg(p.onode + j));
-                        uint64_t key = p.keys[i];
-                        if (p.dual) key = ~key;
-                        uint32_t vg = key_vertex(key);
-                        int item = item_of_vertex(tab, vg);
-                        emit_pair(p, tab, key, item, y, yr, &emit, pr);
+                    i = (round == 1 && !((prefound >> q) & 1u)) ? jj : __ldcg(p.act[cur] + slot);
+                    const uint64_t stamp = (uint64_t(round) << 32) | (0xFFFFFFFFu - i);
+                    if (__ldcg(p.res + y) == stamp) {
+                        __stcg(p.res + y, kDead | __ldcg(p.onode + slot));
+                        __stcg(p.log + (q ? base1 : 0u) + i, uint64_t(y));
                     } else {
                         keep = true;
                     }
                 }
             }
-            uint32_t pos = warp_append(&ctr->act_count[round % 3], keep);
+            const uint32_t pos0 = warp_append(&ctr->act_count[0][round % 3], keep && q == 0);
+            const uint32_t pos1 = warp_append(&ctr->act_count[1][round % 3], keep && q == 1);
             if (keep) {
-                next[pos] = i;
-                p.na[cur ^ 1][pos] = __ldcg(p.ynode + j);
-                p.nb[cur ^ 1][pos] = __ldcg(p.onode + j);
-            }
-            uint32_t pp = warp_append(&ctr->n_pairs, emit);
-            if (emit) {
-                if (pp < p.pair_cap) p.pairs[pp] = pr;
-                else set_status(ctr, kStCapacity);
+                const uint32_t at = (q ? base1 + pos1 : pos0);
+                p.act[cur ^ 1][at] = i;
+                p.na[cur ^ 1][at] = y;
+                p.nb[cur ^ 1][at] = __ldcg(p.onode + slot);
             }
         }
         grid_barrier(ctr, nblocks);
-        n = ld_acquire_u32(&ctr->act_count[round % 3]);
+        // one thread reads the next round's counts and the status for the CTA,
+        // so that every thread of the CTA takes the same path even after a
+        // bounded wait has given up
+        __shared__ uint32_t sh_n[2], sh_stop;
+        if (threadIdx.x == 0) {
+            sh_n[0] = ld_acquire_u32(&ctr->act_count[0][round % 3]);
+            sh_n[1] = ld_acquire_u32(&ctr->act_count[1][round % 3]);
+            sh_stop = ld_acquire_u32(&ctr->status) & kStTimeout;
+        }
+        __syncthreads();
+        n[0] = sh_n[0];
+        n[1] = sh_n[1];
+        const bool stop = sh_stop != 0;
+        __syncthreads();  // sh_* are rewritten in the next round
         cur ^= 1;
-        if (ld_acquire_u32(&ctr->status) & kStTimeout) break;
+        if (stop) break;
         if (round > 0x7FFFFFF0u) {
             if (gtid == 0) set_status(ctr, kStInternal);
             break;
         }
     }
-    if (gtid == 0) {
-        if (p.dual) ctr->roundst = round - 1;
-        else ctr->rounds0 = round - 1;
+    if (gtid == 0)
+        for (int q = 0; q < 2; ++q) {
+            if (!((live >> q) & 1u)) continue;
+            if (args.p[q].dual) ctr->roundst = rounds[q];
+            else ctr->rounds0 = rounds[q];
+        }
+    // ---- the pairs, from the commit log (the last round's commits are ordered
+    // before this by its final grid barrier)
+    for (int q = 0; q < 2; ++q) {
+        if (!((live >> q) & 1u)) continue;
+        const UfParams& p = args.p[q];
+        const uint64_t* log = p.log + (q ? base1 : 0u);
+        for (uint32_t i0 = blockIdx.x * kT; i0 < ninit[q]; i0 += gstride) {
+            const uint32_t i = i0 + threadIdx.x;
+            bool emit = false;
+            cp_pair pr;
+            if (i < ninit[q]) {
+                const uint64_t e = __ldcg(log + i);
+                if (e != ~0ull) {
+                    uint64_t key = p.keys[i];
+                    if (p.dual) key = ~key;
+                    const int item = item_of_vertex(tab, key_vertex(key));
+                    emit_pair(p, tab, key, item, uint32_t(e), &emit, pr);
+                }
+            }
+            const uint32_t pp = warp_append(&ctr->n_pairs, emit);
+            if (emit) {
+                if (pp < p.pair_cap) p.pairs[pp] = pr;
+                else set_status(ctr, kStCapacity);
+            }
+        }
     }
 }
 
-int g_uf_blocks = 0;
+__global__ void __launch_bounds__(kT) k_uf(const __grid_constant__ UfKernelArgs args) {
+    Counters* ctr = args.p[0].ctr;
+    // a bounded wait that gave up earlier leaves the sorted keys unreliable;
+    // non-finite input leaves the forests unreliable: the call fails anyway
+    if (ld_acquire_u32(&ctr->status) & (kStTimeout | kStNonfinite)) return;
+    const uint32_t n0 = min(*args.p[0].d_nkeys, args.p[0].cap_keys);
+    // k_roots / k_place_roots have walked the first round's paths of problem
+    // 0, and of problem 1 when the two lists sit side by side
+    if (args.nprob == 1) {
+        uf_rounds(args, n0, 0u, 0u, 1u, 1u);
+        return;
+    }
+    const uint32_t n1 = min(*args.p[1].d_nkeys, args.p[1].cap_keys);
+    if (side_by_side(args, n0, n1)) {
+        uf_rounds(args, n0, n1, n0, 3u, 3u);
+    } else {  // one after the other, each with the whole scratch and log
+        uf_rounds(args, n0, 0u, 0u, 1u, 1u);
+        grid_barrier(ctr, gridDim.x);  // problem 0's log is read before problem 1 rewrites it
+        uf_rounds(args, 0u, n1, 0u, 2u, 0u);
+    }
+}
+
+int g_uf_blocks = 0, g_find_blocks = 0;
+
+int find_blocks() {
+    if (g_find_blocks == 0) {
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_roots, kFT, 0);
+        g_find_blocks = device_sm_count() * (per_sm > 0 ? per_sm : 1);
+    }
+    return g_find_blocks;
+}
 
 }  // namespace
 
-cudaError_t launch_uf(const ItemTable& tab, const UfParams& p, cudaStream_t s) {
+cudaError_t launch_uf(const ItemTable& tab, const UfParams* p, int nprob, cudaStream_t s) {
+    if (nprob < 1 || nprob > 2) return cudaErrorInvalidValue;
     if (g_uf_blocks == 0) {
         int per_sm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_uf, kT, 0);
@@ -315,7 +680,9 @@ cudaError_t launch_uf(const ItemTable& tab, const UfParams& p, cudaStream_t s) {
     }
     UfKernelArgs args;
     args.tab = tab;
-    args.p = p;
+    args.p[0] = p[0];
+    args.p[1] = p[nprob - 1];
+    args.nprob = nprob;
     // cooperative launch (all CTAs co-resident, as the grid barrier needs);
     // launched through cudaLaunchKernelEx so that it can also be captured
     // into a CUDA graph
@@ -331,6 +698,20 @@ cudaError_t launch_uf(const ItemTable& tab, const UfParams& p, cudaStream_t s) {
     cfg.numAttrs = 1;
     note_launches(1);
     return cudaLaunchKernelEx(&cfg, k_uf, args);
+}
+
+cudaError_t launch_roots(const RootArgs& r, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(&r.ctr->find_ctr, 0, sizeof(uint32_t), s);
+    if (e != cudaSuccess) return e;
+    k_roots<<<find_blocks(), kFT, 0, s>>>(r);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_place_roots(const RootArgs& r, cudaStream_t s) {
+    k_place_roots<<<device_sm_count() * 4, kFT, 0, s>>>(r);
+    note_launches(1);
+    return cudaGetLastError();
 }
 
 }  // namespace cp

@@ -149,6 +149,22 @@ def test_capacity_growth(cp):
     _check(cp, vol, "3d small capacity", max_survivors=64)
 
 
+def test_joint_union_find_one_after_the_other(cp):
+    """Volumes run both union-finds in one launch with their active lists side by
+    side; when the two lists do not fit the scratch together, the launch runs
+    them one after the other.  Both must give the oracle's pairs."""
+    vol = workloads.blurred((40, 44, 48), 1.5, 17)
+    want = oracle.persistence(vol)
+    d = cp.persistence(torch.from_numpy(vol).cuda(), with_stats=True)
+    _assert_same(d.numpy(), want, "joint, side by side")
+    st = d.stats
+    ms = max(st["h0_survivors"], st["top_survivors"], 2 * st["h0_roots"], 2 * st["top_roots"]) + 16
+    assert st["h0_survivors"] + st["top_survivors"] > ms  # the lists do not fit side by side
+    d2 = cp.persistence(torch.from_numpy(vol).cuda(), max_survivors=ms, with_stats=True)
+    _assert_same(d2.numpy(), want, "joint, one after the other")
+    assert d2.stats["h0_rounds"] == st["h0_rounds"] and d2.stats["top_rounds"] == st["top_rounds"]
+
+
 def test_errors_through_c_abi(cp):
     lib = cp.load()
     img = torch.zeros((8, 8), device="cuda")
