@@ -246,6 +246,9 @@ __device__ __forceinline__ void cross_prune(const ItemTable& tab, const UfParams
 // separate, non-cooperative launch: warps take 32 survivors at a time from a
 // counter, so a warp held up by a long path delays no other warp.
 constexpr int kFT = 256;
+constexpr int kRootsPerLane = 1;  // survivors per lane (more paths in lockstep measured slower: the walks are
+                                  // bound by random DRAM accesses, and lockstep waste grows)
+
 __global__ void __launch_bounds__(kFT) k_roots(const __grid_constant__ RootArgs r) {
     Counters* ctr = r.ctr;
     if (ld_acquire_u32(&ctr->status) & (kStTimeout | kStNonfinite)) return;
@@ -254,23 +257,60 @@ __global__ void __launch_bounds__(kFT) k_roots(const __grid_constant__ RootArgs 
     uint32_t hops = 0;
     for (;;) {
         uint32_t base = 0;
-        if (lane == 0) base = atomicAdd(&ctr->find_ctr, 32u);
+        if (lane == 0) base = atomicAdd(&ctr->find_ctr, 32u * kRootsPerLane);
         base = __shfl_sync(0xFFFFFFFFu, base, 0);
         if (base >= n) break;
-        const uint32_t i = base + lane;
-        if (i >= n) continue;
-        uint64_t key = r.keys[i];
-        if (r.dual) key = ~key;
-        uint32_t a, b, va, vb, ra, rb;
-        int item;
-        endpoints(r.tab, key, r.dual, a, b, item);
-        if (!find_two(r.uf, a, b, ra, rb, va, vb, hops)) {
-            set_status(ctr, kStTimeout);
-            rb = ra;
+        // the endpoints of this lane's survivors and their first parents (all loads in flight together)
+        uint32_t node[2 * kRootsPerLane], par[2 * kRootsPerLane];
+#pragma unroll
+        for (int s = 0; s < kRootsPerLane; ++s) {
+            const uint32_t i = base + 32u * s + lane;
+            node[2 * s] = node[2 * s + 1] = 0;
+            if (i < n) {
+                uint64_t key = r.keys[i];
+                if (r.dual) key = ~key;
+                int item;
+                endpoints(r.tab, key, r.dual, node[2 * s], node[2 * s + 1], item);
+            }
         }
-        __stcg(r.ra + i, ra);
-        __stcg(r.rb + i, rb);
-        __stcg(r.pos + i, i);
+#pragma unroll
+        for (int k = 0; k < 2 * kRootsPerLane; ++k)
+            par[k] = base + 32u * (k >> 1) + lane < n ? __ldcg(r.uf + node[k]) : kTag;
+        // walk all paths one hop per step until every one has reached its root
+        uint64_t t0 = 0;
+        uint32_t steps = 0;
+        for (;;) {
+            bool more = false;
+#pragma unroll
+            for (int k = 0; k < 2 * kRootsPerLane; ++k) {
+                if (!(par[k] & kTag)) {
+                    node[k] = par[k];
+                    par[k] = __ldcg(r.uf + node[k]);
+                    more = true;
+                }
+            }
+            if (!more) break;
+            ++hops;
+            if ((++steps & 1023u) == 0) {
+                const uint64_t now = global_timer_ns();
+                if (t0 == 0) t0 = now;
+                else if (now - t0 > kWaitLimitNs) {  // only a corrupted forest gets here
+                    set_status(ctr, kStTimeout);
+#pragma unroll
+                    for (int k = 0; k < 2 * kRootsPerLane; ++k) par[k] = kTag;
+                    break;
+                }
+            }
+        }
+#pragma unroll
+        for (int s = 0; s < kRootsPerLane; ++s) {
+            const uint32_t i = base + 32u * s + lane;
+            if (i < n) {
+                __stcg(r.ra + i, par[2 * s] & ~kTag);
+                __stcg(r.rb + i, par[2 * s + 1] & ~kTag);
+                __stcg(r.pos + i, i);
+            }
+        }
     }
     for (int o = 16; o > 0; o >>= 1) hops += __shfl_xor_sync(0xFFFFFFFFu, hops, o);
     if (lane == 0 && hops) atomicAdd(&ctr->trace_hops[r.dual][0], (unsigned long long)hops);
