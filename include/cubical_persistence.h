@@ -322,10 +322,11 @@ long long cp_launch_count(void);
  * stream between its stages; cp_stage_times() then waits for the last call
  * and writes the six stage durations in milliseconds (prune, sort H0,
  * union-find H0, sort dual, union-find dual, emit) into ms[0..5] and returns
- * 6 (or a negative CP_ERR_* code; cap must be >= 6).  In a call with volumes
- * only, both union-finds run in one launch: ms[2] holds their joint time and
- * ms[4] is 0.  cp_profile(0) stops recording.  Not thread-safe across
- * concurrent calls.
+ * 6 (or a negative CP_ERR_* code; cap must be >= 6).  Each sort stage
+ * includes the first-round root walks of its list.  In a call with volumes
+ * only, both lists are walked and sorted together and both union-finds run in
+ * one launch: ms[1] and ms[2] hold those joint times and ms[3], ms[4] are 0.
+ * cp_profile(0) stops recording.  Not thread-safe across concurrent calls.
  */
 int cp_profile(int enable);
 int cp_stage_times(float *ms, int cap);

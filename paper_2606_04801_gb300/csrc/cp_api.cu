@@ -63,6 +63,7 @@ struct Plan {
     // byte offsets into the workspace
     size_t o_ctr, o_uf0, o_uft, o_s0, o_st, o_salt, o_age0, o_res0, o_aget, o_rest;
     size_t o_act0, o_act1, o_yn, o_on, o_na0, o_na1, o_nb0, o_nb1, o_pairs, o_pvals, o_pvalt, o_hist, o_status;
+    size_t o_hist2, o_status2;
     size_t bytes = 0;
 };
 
@@ -161,11 +162,15 @@ int make_plan(int n_items, const int32_t* ndims, const int64_t* dims, const floa
     P.o_na1 = take(sizeof(uint32_t) * P.cap_s);
     P.o_nb0 = take(sizeof(uint32_t) * P.cap_s);
     P.o_nb1 = take(sizeof(uint32_t) * P.cap_s);
-    P.o_pairs = take(sizeof(cp_pair) * P.cap_p);
+    // the pairs buffer also holds the dual list's sort scratch (key ping-pong,
+    // endpoint root ids, payload) while both survivor lists are sorted together
+    P.o_pairs = take(std::max(sizeof(cp_pair) * size_t(P.cap_p), size_t(8 + 4 + 4 + 4) * P.cap_s + 1024));
     P.o_pvals = P.o_act0;  // the active lists are dead once both union-finds are done
     P.o_pvalt = P.o_act1;
     P.o_hist = take(sizeof(uint32_t) * 8 * 256);
     P.o_status = take(sizeof(uint64_t) * sort_status_words(P.cap_big));
+    P.o_hist2 = take(sizeof(uint32_t) * 8 * 256);
+    P.o_status2 = take(sizeof(uint64_t) * sort_status_words(P.cap_s));
     P.bytes = o;
     return CP_OK;
 }
@@ -209,7 +214,6 @@ int run(const Plan& P, cp_pair* d_out, int64_t capacity, int64_t* h_out_count, i
         if ((x) != cudaSuccess) return CP_ERR_CUDA; \
     } while (0)
     CP_TRY(cudaMemsetAsync(ctr, 0, sizeof(Counters), s));
-    CP_TRY(cudaMemsetAsync(status, 0, sizeof(uint64_t) * sort_status_words(P.cap_big), s));
     CP_TRY(launch_init(P.tab, ctr, uft, aget, rest, s));
     mark(0, s);
     if (prune_only) {
@@ -291,7 +295,48 @@ int run(const Plan& P, cp_pair* d_out, int64_t capacity, int64_t* h_out_count, i
         if (e != cudaSuccess) return e;
         return launch_place_roots(ra, s);
     };
-    CP_TRY(prepare(0, nullptr));
+    const bool joint = P.tab.n2d == 0;  // volumes only: the two lists are independent
+    if (joint) {
+        // both lists walked, then sorted together (one launch per pass), then
+        // placed side by side; the dual list's scratch sits in the pairs buffer
+        uint64_t* salt2 = reinterpret_cast<uint64_t*>(pairs);
+        uint32_t* raT = reinterpret_cast<uint32_t*>(salt2 + P.cap_s);
+        uint32_t* rbT = raT + P.cap_s;
+        uint32_t* posT = rbT + P.cap_s;
+        RootArgs rt = ra;
+        rt.keys = st;
+        rt.d_n = &ctr->n_st;
+        rt.uf = uft;
+        rt.dual = 1;
+        rt.ra = raT;
+        rt.rb = rbT;
+        rt.pos = posT;
+        rt.sorted_pos = posT;
+        rt.d_n_before = &ctr->n_s0;
+        ra.keys = s0;
+        ra.d_n = &ctr->n_s0;
+        ra.uf = uf0;
+        ra.dual = 0;
+        ra.d_n_before = nullptr;
+        CP_TRY(launch_roots(ra, s));
+        CP_TRY(launch_roots(rt, s));
+        SortBufs two[2] = {sb, sb};
+        two[0].keys = s0;
+        two[0].d_count = &ctr->n_s0;
+        two[0].tile_ctr = ctr->sort_tile;
+        two[1].keys = st;
+        two[1].keys_alt = salt2;
+        two[1].vals = posT;
+        two[1].vals_alt = at<uint32_t>(ws, P.o_on);
+        two[1].d_count = &ctr->n_st;
+        two[1].hist = at<uint32_t>(ws, P.o_hist2);
+        two[1].status = at<uint64_t>(ws, P.o_status2);
+        CP_TRY(sort_keys_multi(two, 2, 0, 8, 1, s));
+        CP_TRY(launch_place_roots(ra, s));
+        CP_TRY(launch_place_roots(rt, s));
+    } else {
+        CP_TRY(prepare(0, nullptr));
+    }
     mark(2, s);
 
     UfParams up[2];
@@ -329,7 +374,7 @@ int run(const Plan& P, cp_pair* d_out, int64_t capacity, int64_t* h_out_count, i
     up[1].dual_cap = 0;
     up[1].dual = 1;
 
-    if (P.tab.n2d > 0) {
+    if (!joint) {
         // the H0 union-find appends positive edges of 2D items to the dual list
         // (cross-pruning): the dual list is prepared after it
         g_ev_joint = false;
@@ -340,9 +385,8 @@ int run(const Plan& P, cp_pair* d_out, int64_t capacity, int64_t* h_out_count, i
         CP_TRY(launch_uf(P.tab, &up[1], 1, s));
         mark(5, s);
     } else {
-        // volumes only: the two lists are independent; both union-finds share
-        // one launch and its rounds (the dual list after the H0 list)
-        CP_TRY(prepare(1, &ctr->n_s0));
+        // volumes only: both union-finds share one launch and its rounds (the
+        // dual list after the H0 list)
         mark(3, s);
         g_ev_joint = true;
         CP_TRY(launch_uf(P.tab, up, 2, s));
@@ -353,7 +397,18 @@ int run(const Plan& P, cp_pair* d_out, int64_t capacity, int64_t* h_out_count, i
     CP_TRY(launch_essential(P.tab, ctr, pairs, P.cap_p, s));
     uint32_t* pvals = at<uint32_t>(ws, P.o_pvals);
     uint32_t* pvalt = at<uint32_t>(ws, P.o_pvalt);
-    CP_TRY(launch_pair_keys(pairs, &ctr->n_pairs, P.cap_p, s0, pvals, s));
+    // output order (item, dim, birth cell): only as many key bytes as this call's
+    // item count and largest doubled grid need (4 for one 512^3 volume)
+    int cell_bits = 1, item_bits = 0;
+    for (int i = 0; i < P.tab.n; ++i) {
+        const Item& it = P.tab.it[i];
+        const int64_t G = int64_t(2 * it.D - 1) * (2 * it.H - 1) * (2 * it.W - 1);
+        while ((int64_t(1) << cell_bits) < G) ++cell_bits;
+    }
+    while ((1 << item_bits) < P.tab.n) ++item_bits;
+    int pair_passes = (item_bits + 1 + cell_bits + 7) / 8;
+    pair_passes += pair_passes & 1;  // an even count leaves the result in place
+    CP_TRY(launch_pair_keys(pairs, &ctr->n_pairs, P.cap_p, s0, pvals, cell_bits, s));
     sb.keys = s0;
     sb.keys_alt = salt;
     sb.vals = pvals;
@@ -361,7 +416,7 @@ int run(const Plan& P, cp_pair* d_out, int64_t capacity, int64_t* h_out_count, i
     sb.d_count = &ctr->n_pairs;
     sb.cap = P.cap_p;
     sb.tile_ctr = ctr->sort_tile + 16;
-    CP_TRY(sort_keys(sb, 0, 6, 17, s));
+    CP_TRY(sort_keys(sb, 0, pair_passes, 17, s));
     CP_TRY(launch_gather(pairs, pvals, &ctr->n_pairs, P.cap_p, d_out, capacity, d_out_count, ctr, s));
     mark(6, s);
 #undef CP_TRY

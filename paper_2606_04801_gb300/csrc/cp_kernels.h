@@ -41,7 +41,7 @@ struct SortBufs {
     const uint32_t* d_count;  // number of keys, on the device
     uint32_t cap;             // capacity of the key arrays
     uint32_t* hist;           // 8 x 256 scratch
-    uint64_t* status;         // sort_status_words(cap) scratch, zeroed once per call
+    uint64_t* status;         // sort_status_words(cap) scratch (cleared by the sort itself)
     uint32_t* tile_ctr;       // one ticket counter per pass, zeroed once per call
     Counters* ctr;
 };
@@ -49,6 +49,9 @@ size_t sort_status_words(uint32_t cap);
 constexpr int kSortTile = 4096;
 // Sorts bytes [first_byte, first_byte + npasses) of each key, npasses even.
 cudaError_t sort_keys(const SortBufs& b, int first_byte, int npasses, uint32_t epoch, cudaStream_t s);
+// The same over two lists at once (one launch per pass; separate buffers,
+// histograms and status words; the tile tickets of b[0]).
+cudaError_t sort_keys_multi(const SortBufs* b, int nl, int first_byte, int npasses, uint32_t epoch, cudaStream_t s);
 
 // ---- K3 union-find (deterministic reservations)
 struct UfParams {
@@ -107,7 +110,7 @@ cudaError_t launch_init(const ItemTable& tab, Counters* ctr, uint32_t* uft, uint
                         cudaStream_t s);
 cudaError_t launch_essential(const ItemTable& tab, Counters* ctr, cp_pair* pairs, uint32_t pair_cap, cudaStream_t s);
 cudaError_t launch_pair_keys(const cp_pair* pairs, const uint32_t* d_n, uint32_t cap, uint64_t* keys, uint32_t* vals,
-                             cudaStream_t s);
+                             int cell_bits, cudaStream_t s);
 cudaError_t launch_gather(const cp_pair* pairs, const uint32_t* vals, const uint32_t* d_n, uint32_t cap,
                           cp_pair* out, int64_t out_cap, int64_t* d_out_count, Counters* ctr, cudaStream_t s);
 cudaError_t launch_backward(const cp_pair* pairs, int64_t n, const float* gb, const float* gd, const int64_t* offs,

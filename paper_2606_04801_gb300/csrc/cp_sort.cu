@@ -23,29 +23,45 @@ constexpr int kKPT = kSortTile / kT;    // keys per thread (16)
 constexpr uint32_t kFlagAgg = 1u, kFlagIncl = 2u;
 constexpr int kLook = 16;               // look-back window: predecessor tiles read together
 
-__global__ void __launch_bounds__(kT) k_hist(const uint64_t* __restrict__ keys, const uint32_t* d_count, uint32_t cap,
-                                             uint32_t* __restrict__ hist, int first_byte, int npasses) {
+// Digit histograms of every pass, for one or two key lists, from one read;
+// also clears the look-back words the passes will use.
+struct HistArgs {
+    const uint64_t* keys[2];
+    const uint32_t* d_count[2];
+    uint32_t cap[2];
+    uint32_t* hist[2];        // npasses x 256 per list
+    uint64_t* status[2];      // look-back words: the ones this sort will use are cleared here
+    int nl, first_byte, npasses;
+};
+
+__global__ void __launch_bounds__(kT) k_hist(const __grid_constant__ HistArgs a) {
     __shared__ uint32_t h[8][256];
-    for (int i = threadIdx.x; i < 8 * 256; i += kT) (&h[0][0])[i] = 0;
-    __syncthreads();
-    uint32_t n = min(*d_count, cap);
-    for (uint32_t i = blockIdx.x * kT + threadIdx.x; i < n; i += gridDim.x * kT) {
-        uint64_t k = keys[i];
-        for (int p = 0; p < npasses; ++p) atomicAdd(&h[p][(k >> (8 * (first_byte + p))) & 255u], 1u);
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < npasses * 256; i += kT) {
-        uint32_t v = (&h[0][0])[i];
-        if (v) atomicAdd(hist + i, v);
+    for (int l = 0; l < a.nl; ++l) {
+        for (int i = threadIdx.x; i < 8 * 256; i += kT) (&h[0][0])[i] = 0;
+        __syncthreads();
+        const uint32_t n = min(*a.d_count[l], a.cap[l]);
+        const uint64_t* keys = a.keys[l];
+        const uint32_t nwords = (n + kSortTile - 1) / kSortTile * 256u;
+        for (uint32_t i = blockIdx.x * kT + threadIdx.x; i < nwords; i += gridDim.x * kT) a.status[l][i] = 0ull;
+        for (uint32_t i = blockIdx.x * kT + threadIdx.x; i < n; i += gridDim.x * kT) {
+            const uint64_t k = keys[i];
+            for (int p = 0; p < a.npasses; ++p) atomicAdd(&h[p][(k >> (8 * (a.first_byte + p))) & 255u], 1u);
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < a.npasses * 256; i += kT) {
+            const uint32_t v = (&h[0][0])[i];
+            if (v) atomicAdd(a.hist[l] + i, v);
+        }
+        __syncthreads();
     }
 }
 
-// exclusive scan of each pass's 256 digit counts (in place): warp p scans
-// pass p, 8 digits per lane, with shuffles (no block barriers)
-__global__ void __launch_bounds__(kT) k_hist_scan(uint32_t* hist, int npasses) {
-    const int p = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (p >= npasses) return;
-    uint32_t* h = hist + p * 256 + lane * 8;
+// exclusive scan of each pass's 256 digit counts (in place): one warp per
+// (list, pass), 8 digits per lane, with shuffles (no block barriers)
+__global__ void __launch_bounds__(512) k_hist_scan(uint32_t* hist0, uint32_t* hist1, int npasses, int nl) {
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (w >= npasses * nl) return;
+    uint32_t* h = (w >= npasses ? hist1 : hist0) + (w % npasses) * 256 + lane * 8;
     uint32_t v[8], sum = 0;
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
@@ -80,24 +96,56 @@ struct SortSmem {
     uint32_t tile;
 };
 
-__global__ void __launch_bounds__(kT) k_onesweep(const uint64_t* __restrict__ src, uint64_t* __restrict__ dst,
-                                                 const uint32_t* __restrict__ vsrc, uint32_t* __restrict__ vdst,
-                                                 const uint32_t* d_count, uint32_t cap,
-                                                 const uint32_t* __restrict__ digit_off, uint64_t* status,
-                                                 uint32_t* tile_ctr, int shift, uint32_t epoch, Counters* ctr) {
+// One digit pass over one or two key lists: tickets [0, tiles of list 0) are
+// list 0's tiles, the next ones list 1's, so a pass over both lists is one
+// launch (a pass is latency-bound at these sizes).
+struct SortList {
+    const uint64_t* src;
+    uint64_t* dst;
+    const uint32_t* vsrc;   // payload (nullptr: keys only)
+    uint32_t* vdst;
+    const uint32_t* d_count;
+    uint32_t cap;
+    const uint32_t* digit_off;  // this pass's exclusive digit offsets
+    uint64_t* status;           // look-back words of this list
+};
+struct SweepArgs {
+    SortList l[2];
+    int nl;
+    uint32_t* tile_ctr;
+    int shift;
+    uint32_t epoch;
+    Counters* ctr;
+};
+
+__global__ void __launch_bounds__(kT) k_onesweep(const __grid_constant__ SweepArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SortSmem& sm = *reinterpret_cast<SortSmem*>(smem_raw);
-    const uint32_t n = min(*d_count, cap);
-    const uint32_t ntiles = (n + kSortTile - 1) / kSortTile;
+    const uint32_t n0 = min(*a.l[0].d_count, a.l[0].cap);
+    const uint32_t n1 = a.nl > 1 ? min(*a.l[1].d_count, a.l[1].cap) : 0u;
+    const uint32_t nt0 = (n0 + kSortTile - 1) / kSortTile, nt1 = (n1 + kSortTile - 1) / kSortTile;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned lt_mask = (1u << lane) - 1u;
-    const bool has_vals = vsrc != nullptr;
+    const int shift = a.shift;
+    const uint32_t epoch = a.epoch;
     for (;;) {
-        if (threadIdx.x == 0) sm.tile = atomicAdd(tile_ctr, 1u);
+        if (threadIdx.x == 0) sm.tile = atomicAdd(a.tile_ctr, 1u);
         for (int i = threadIdx.x; i < kWarps * 256; i += kT) (&sm.whist[0][0])[i] = 0;
         __syncthreads();
-        const uint32_t tile = sm.tile;
-        if (tile >= ntiles) break;
+        const uint32_t ticket = sm.tile;
+        if (ticket >= nt0 + nt1) break;
+        const int li = ticket >= nt0 ? 1 : 0;
+        const SortList& L = a.l[li];
+        const uint32_t tile = li ? ticket - nt0 : ticket;
+        const uint32_t n = li ? n1 : n0;
+        const uint64_t* __restrict__ src = L.src;
+        uint64_t* __restrict__ dst = L.dst;
+        const uint32_t* __restrict__ vsrc = L.vsrc;
+        uint32_t* __restrict__ vdst = L.vdst;
+        uint64_t* status = L.status;
+        const uint32_t* __restrict__ digit_off = L.digit_off;
+        Counters* ctr = a.ctr;
+        const bool has_vals = vsrc != nullptr;
         const uint32_t base = tile * kSortTile;
         uint64_t key[kKPT];
         uint32_t val[kKPT];
@@ -217,8 +265,8 @@ int g_sort_blocks = 0;
 
 size_t sort_status_words(uint32_t cap) { return size_t((cap + kSortTile - 1) / kSortTile + 1) * 256; }
 
-cudaError_t sort_keys(const SortBufs& b, int first_byte, int npasses, uint32_t epoch, cudaStream_t s) {
-    if (npasses <= 0 || (npasses & 1) || first_byte + npasses > 8) return cudaErrorInvalidValue;
+cudaError_t sort_keys_multi(const SortBufs* b, int nl, int first_byte, int npasses, uint32_t epoch, cudaStream_t s) {
+    if (nl < 1 || nl > 2 || npasses <= 0 || (npasses & 1) || first_byte + npasses > 8) return cudaErrorInvalidValue;
     const size_t smem = sizeof(SortSmem);
     if (g_sort_blocks == 0) {
         cudaFuncSetAttribute(k_onesweep, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
@@ -226,23 +274,53 @@ cudaError_t sort_keys(const SortBufs& b, int first_byte, int npasses, uint32_t e
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_onesweep, kT, smem);
         g_sort_blocks = device_sm_count() * (per_sm > 0 ? per_sm : 1);
     }
-    cudaError_t e = cudaMemsetAsync(b.hist, 0, sizeof(uint32_t) * 8 * 256, s);
-    if (e != cudaSuccess) return e;
-    uint32_t max_tiles = (b.cap + kSortTile - 1) / kSortTile;
-    int hist_blocks = device_sm_count() * 2;
-    k_hist<<<hist_blocks, kT, 0, s>>>(b.keys, b.d_count, b.cap, b.hist, first_byte, npasses);
-    k_hist_scan<<<1, kT, 0, s>>>(b.hist, npasses);
+    HistArgs h;
+    uint32_t max_tiles = 0;
+    for (int l = 0; l < 2; ++l) {
+        const SortBufs& q = b[l < nl ? l : 0];
+        h.keys[l] = q.keys;
+        h.d_count[l] = q.d_count;
+        h.cap[l] = q.cap;
+        h.hist[l] = q.hist;
+        h.status[l] = q.status;
+    }
+    h.nl = nl;
+    h.first_byte = first_byte;
+    h.npasses = npasses;
+    for (int l = 0; l < nl; ++l) {
+        cudaError_t e = cudaMemsetAsync(b[l].hist, 0, sizeof(uint32_t) * 8 * 256, s);
+        if (e != cudaSuccess) return e;
+        max_tiles += (b[l].cap + kSortTile - 1) / kSortTile;
+    }
+    k_hist<<<device_sm_count() * 2, kT, 0, s>>>(h);
+    k_hist_scan<<<1, 512, 0, s>>>(b[0].hist, nl > 1 ? b[1].hist : b[0].hist, npasses, nl);
     note_launches(2 + npasses);
-    int grid = int(max_tiles < uint32_t(g_sort_blocks) ? (max_tiles ? max_tiles : 1) : g_sort_blocks);
+    const int grid = int(max_tiles < uint32_t(g_sort_blocks) ? (max_tiles ? max_tiles : 1) : g_sort_blocks);
     for (int p = 0; p < npasses; ++p) {
-        const uint64_t* src = (p & 1) ? b.keys_alt : b.keys;
-        uint64_t* dst = (p & 1) ? b.keys : b.keys_alt;
-        const uint32_t* vs = b.vals ? ((p & 1) ? b.vals_alt : b.vals) : nullptr;
-        uint32_t* vd = b.vals ? ((p & 1) ? b.vals : b.vals_alt) : nullptr;
-        k_onesweep<<<grid, kT, smem, s>>>(src, dst, vs, vd, b.d_count, b.cap, b.hist + p * 256, b.status,
-                                          b.tile_ctr + p, 8 * (first_byte + p), epoch + uint32_t(p), b.ctr);
+        SweepArgs a;
+        for (int l = 0; l < 2; ++l) {
+            const SortBufs& q = b[l < nl ? l : 0];
+            a.l[l].src = (p & 1) ? q.keys_alt : q.keys;
+            a.l[l].dst = (p & 1) ? q.keys : q.keys_alt;
+            a.l[l].vsrc = q.vals ? ((p & 1) ? q.vals_alt : q.vals) : nullptr;
+            a.l[l].vdst = q.vals ? ((p & 1) ? q.vals : q.vals_alt) : nullptr;
+            a.l[l].d_count = q.d_count;
+            a.l[l].cap = q.cap;
+            a.l[l].digit_off = q.hist + p * 256;
+            a.l[l].status = q.status;
+        }
+        a.nl = nl;
+        a.tile_ctr = b[0].tile_ctr + p;
+        a.shift = 8 * (first_byte + p);
+        a.epoch = epoch + uint32_t(p);
+        a.ctr = b[0].ctr;
+        k_onesweep<<<grid, kT, smem, s>>>(a);
     }
     return cudaGetLastError();
+}
+
+cudaError_t sort_keys(const SortBufs& b, int first_byte, int npasses, uint32_t epoch, cudaStream_t s) {
+    return sort_keys_multi(&b, 1, first_byte, npasses, epoch, s);
 }
 
 }  // namespace cp
