@@ -281,7 +281,10 @@ int cubical_persistence_uf_trace2(const void *d_workspace, int dual, uint32_t *h
  * then the total vertices, total top-cell slots, survivor capacity, H0 root
  * capacity and dual root capacity.  Forest words with the top bit set are
  * roots (low bits: root id).  Survivor and root counts are the 2nd to 5th
- * uint32 of the counters.  Returns 12 or a CP_ERR_* code.
+ * uint32 of the counters.  With cap >= 13 a 13th value follows: the byte
+ * offset of a uint32 counting the 3D pruning tasks whose image planes were
+ * loaded by TMA (the others use cp.async).  Returns the number of values
+ * written (12 or 13) or a CP_ERR_* code.
  */
 int cubical_persistence_debug_prune(int n_items, const float *const *h_images, const int32_t *ndims,
                                     const int64_t *dims, void *d_workspace, size_t ws_bytes, int64_t max_survivors,

@@ -5,6 +5,7 @@
 //        -> K2 sort (pairs, canonical order) -> gather.
 #include <algorithm>
 #include <atomic>
+#include <cstddef>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -58,6 +59,7 @@ int ensure_device_tables() {
 
 struct Plan {
     ItemTable tab;
+    TmaMaps tma;  // plane tensor maps of the 3D items that take TMA loads
     int64_t ntot = 0, ttot = 0;
     uint32_t cap_s = 0, cap_r0 = 0, cap_rt = 0, cap_p = 0, cap_big = 0;
     // byte offsets into the workspace
@@ -101,6 +103,7 @@ int make_plan(int n_items, const int32_t* ndims, const int64_t* dims, const floa
         it.toff = toff;
         it.T = (it.ndim == 3 ? D - 1 : 1) * (H - 1) * (W - 1);
         it.user = i;
+        it.tma = -1;
         voff += N;
         toff += it.T + 1;
         if (it.ndim == 2) {
@@ -126,6 +129,12 @@ int make_plan(int n_items, const int32_t* ndims, const int64_t* dims, const floa
     }
     P.tab.tiles2d = t2;
     P.tab.tiles3d = t3;
+    int ntma = 0;
+    for (int j = 0; j < n_items && imgs; ++j) {
+        Item& it = P.tab.it[j];
+        if (it.ndim == 3 && ntma < kMaxTma && encode_plane_map(&P.tma.m[ntma], it.img, it.D, it.H, it.W))
+            it.tma = ntma++;
+    }
     P.tab.rows2d = prune_tile_y2d();
     P.tab.zchunk3d = prune_tile_z3d();
     P.ntot = voff;
@@ -230,7 +239,7 @@ int run(const Plan& P, cp_pair* d_out, int64_t capacity, int64_t* h_out_count, i
         po.cap_r0 = P.cap_r0;
         po.cap_rt = P.cap_rt;
         po.ctr = ctr;
-        CP_TRY(launch_prune(P.tab, po, s));
+        CP_TRY(launch_prune(P.tab, po, P.tma, s));
         mark(1, s);
         return CP_OK;
     }
@@ -248,7 +257,7 @@ int run(const Plan& P, cp_pair* d_out, int64_t capacity, int64_t* h_out_count, i
     po.cap_r0 = P.cap_r0;
     po.cap_rt = P.cap_rt;
     po.ctr = ctr;
-    CP_TRY(launch_prune(P.tab, po, s));
+    CP_TRY(launch_prune(P.tab, po, P.tma, s));
     mark(1, s);
 
     // First-round root walks over the unsorted survivors (tile order), then the
@@ -537,11 +546,13 @@ int cubical_persistence_debug_layout(int n_items, const int32_t* ndims, const in
     Plan P;
     int rc = make_plan(n_items, ndims, dims, nullptr, max_survivors, P);
     if (rc != CP_OK) return rc;
-    const int64_t v[12] = {int64_t(P.o_ctr), int64_t(P.o_uf0),  int64_t(P.o_uft),  int64_t(P.o_s0),
+    const int64_t v[13] = {int64_t(P.o_ctr), int64_t(P.o_uf0),  int64_t(P.o_uft),  int64_t(P.o_s0),
                            int64_t(P.o_st),  int64_t(P.o_age0), int64_t(P.o_aget), int64_t(P.ntot),
-                           int64_t(P.ttot),  int64_t(P.cap_s),  int64_t(P.cap_r0), int64_t(P.cap_rt)};
-    for (int i = 0; i < 12; ++i) h_offsets[i] = v[i];
-    return 12;
+                           int64_t(P.ttot),  int64_t(P.cap_s),  int64_t(P.cap_r0), int64_t(P.cap_rt),
+                           int64_t(P.o_ctr + offsetof(Counters, tma_tasks))};
+    const int n = cap >= 13 ? 13 : 12;
+    for (int i = 0; i < n; ++i) h_offsets[i] = v[i];
+    return n;
 }
 
 size_t cubical_persistence_batched_workspace_size(int n_items, const int32_t* ndims, const int64_t* dims,

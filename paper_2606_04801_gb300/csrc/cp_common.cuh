@@ -31,7 +31,7 @@ struct Item {
     int32_t tile0;            // first pruning tile of the item (per kind)
     int32_t tx, ty, tz;       // pruning tiles along x, y, z
     int32_t user;             // the caller's index of the item
-    int32_t pad;
+    int32_t tma;              // 3D: index of the item's plane tensor map (TMA loads), or -1
 };
 
 struct ItemTable {
@@ -58,7 +58,8 @@ struct Counters {
     uint32_t act_count[2][3]; // active survivors of the next round (H0 / dual list), rotating
     uint32_t sort_tile[64];   // tile tickets of the sort passes of one call
     uint32_t find_ctr;        // work counter of the first union-find round's root walks
-    uint32_t pad[3];
+    uint32_t tma_tasks;       // 3D pruning tasks whose planes came by TMA (a check that the path runs)
+    uint32_t pad[2];
     unsigned long long gmin[kMaxItems];  // (ord bits << 32 | local vertex) of each item's minimum
     int64_t out_count;
     // union-find trace: active survivors and device time at the start of each

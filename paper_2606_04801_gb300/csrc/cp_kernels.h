@@ -1,6 +1,7 @@
 // Host-side interface between the C-ABI layer and the kernels.
 #pragma once
 #include <cstdint>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "cp_common.cuh"
@@ -30,7 +31,16 @@ int prune_tile_z3d();
 int set_tuning(int key, int value);
 int get_tuning(int key);
 cudaError_t upload_luts(const uint64_t* lut2d, const uint16_t* disp3d, const uint64_t* entries3d);
-cudaError_t launch_prune(const ItemTable& tab, const PruneOuts& po, cudaStream_t s);
+// Tensor maps for TMA loads of 3D planes (one per item that qualifies: width a
+// multiple of 4, 16-byte aligned image, at least 40 x 11 per plane); the other
+// items load their planes with cp.async.
+constexpr int kMaxTma = 64;
+struct TmaMaps {
+    CUtensorMap m[kMaxTma];
+};
+// Encodes the plane map of a D x H x W float volume; false if it cannot be used.
+bool encode_plane_map(CUtensorMap* map, const float* img, int64_t D, int64_t H, int64_t W);
+cudaError_t launch_prune(const ItemTable& tab, const PruneOuts& po, const TmaMaps& maps, cudaStream_t s);
 
 // ---- K2 radix sort (LSD, 8-bit digits, decoupled look-back)
 struct SortBufs {
@@ -46,7 +56,7 @@ struct SortBufs {
     Counters* ctr;
 };
 size_t sort_status_words(uint32_t cap);
-constexpr int kSortTile = 4096;
+constexpr int kSortTile = 2048;
 // Sorts bytes [first_byte, first_byte + npasses) of each key, npasses even.
 cudaError_t sort_keys(const SortBufs& b, int first_byte, int npasses, uint32_t epoch, cudaStream_t s);
 // The same over two lists at once (one launch per pass; separate buffers,

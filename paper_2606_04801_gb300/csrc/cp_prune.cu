@@ -91,10 +91,12 @@ __device__ __forceinline__ uint32_t collapse3(uint32_t raw) {
     return f | ed | co;
 }
 
-__device__ __forceinline__ uint2 lookup3(uint32_t rel) {
-    uint32_t b = (rel * 0x9E3779B1u) >> (32 - 12);
-    uint32_t d = __ldg(g_disp3d + b);
-    uint32_t s = ((rel ^ (d * 0x27D4EB2Fu)) * 0x85EBCA77u) >> (32 - 14);
+// Perfect hash of the 15,935 relevant masks: bucket -> displacement (a copy
+// of the 8 KB displacement table in shared memory) -> slot.
+__device__ __forceinline__ uint2 lookup3(uint32_t rel, const uint16_t* disp) {
+    const uint32_t b = (rel * 0x9E3779B1u) >> (32 - 12);
+    const uint32_t d = disp[b];
+    const uint32_t s = ((rel ^ (d * 0x27D4EB2Fu)) * 0x85EBCA77u) >> (32 - 14);
     return __ldg(g_entries3d + s);
 }
 
@@ -124,10 +126,14 @@ constexpr int kW3 = 9;                     // warps per CTA
 constexpr int kT3 = kW3 * 32;
 constexpr int kOX = 31, kOY = 8;           // owned columns / rows per CTA
 constexpr int kZC = 64;                    // default owned planes per task
-constexpr int kRW = 34, kRH = kW3 + 2, kRP = kRW * kRH;  // ring plane: cols x0-2.., rows y0-2..
+constexpr int kRW = 34, kRH = kW3 + 2, kRP = kRW * kRH;  // plane tile: cols x0-2 .. x0+31, rows y0-2 ..
+constexpr int kRS = 40;                    // ring row stride in floats (a TMA box row: x from a multiple of 4)
+constexpr int kSlot = 448;                 // ring slot in floats: kRH rows of kRS, padded to 128 bytes
 constexpr int kRing = 8, kAhead = 5;       // ring slots, planes in flight
-constexpr int kCapW0 = 32 * 5;             // staged H0 keys per warp (one step's maximum)
-constexpr int kCapWT = 32 * 7;             // staged dual keys per warp
+// staging per warp: flushed before a 32-lane slot would overflow it (small,
+// so that shared memory leaves L1 room for the lookup table)
+constexpr int kCapW0 = 64;                 // staged H0 keys per warp
+constexpr int kCapWT = 64;                 // staged dual keys per warp
 constexpr int kCapWR = 32;                 // staged roots per warp and kind
 
 struct WarpStage {
@@ -140,7 +146,9 @@ struct WarpStage {
 };
 
 struct Smem3 {
-    float ring[kRing][kRP];
+    float ring[kRing][kSlot];  // first: slots 128-byte aligned (TMA destinations)
+    uint64_t bar[kRing];       // mbarrier of each slot (TMA completion)
+    uint16_t disp[1 << 12];    // displacement table of the 3D perfect hash
     uint32_t codes[3][kW3][32];
     WarpStage ws[kW3];
 };
@@ -215,7 +223,7 @@ __device__ __forceinline__ void read_nbr(const float* plane, int ly, int lx, Nbr
 #pragma unroll
     for (int r = 0; r < 3; ++r)
 #pragma unroll
-        for (int c = 0; c < 3; ++c) P.v[r][c] = plane[(ly + r) * kRW + (lx + c)];
+        for (int c = 0; c < 3; ++c) P.v[r][c] = plane[(ly + r) * kRS + (lx + c)];
 }
 
 // raw mask: bit n = 9a + 3b + c set when the neighbour at plane a, row b,
@@ -246,9 +254,51 @@ __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-// Ring positions of this thread (at most two), fixed for a task.
+// ---- image plane ring, filled by TMA (one tensor copy per plane, completing
+// on the slot's mbarrier; out-of-image positions read NaN, which never
+// precedes anything, like +inf) or, for items without a tensor map, by
+// cp.async (out-of-image positions set to +inf once per task)
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return uint32_t(__cvta_generic_to_shared(p)); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait for a slot's copy; a copy that never lands flags the call.
+__device__ __forceinline__ void mbar_wait(uint64_t* bar, uint32_t parity, Counters* ctr) {
+    if (mbar_try_wait(bar, parity)) return;
+    const uint64_t t0 = global_timer_ns();
+    while (!mbar_try_wait(bar, parity)) {
+        if (global_timer_ns() - t0 > kWaitLimitNs) {
+            set_status(ctr, kStTimeout);
+            return;
+        }
+    }
+}
+__device__ __forceinline__ void tma_load_plane(float* dst, const CUtensorMap* map, uint64_t* bar, int x, int y, int z) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
+            smem_u32(dst)),
+        "l"(map), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Plane tile positions of this thread for the cp.async path (at most two),
+// fixed for a task.
 struct RingPos {
     uint32_t off0, off1;  // offset of the pixel in a plane
+    uint32_t dst0, dst1;  // position in a ring slot
     bool in0, in1;        // inside the image (x, y)
     bool has1;            // second position exists
 };
@@ -262,42 +312,75 @@ __device__ __forceinline__ void ring_positions(const Item& it, int x0, int y0, R
         const int gy = y0 - 2 + ly, gx = x0 - 2 + lx;
         const bool in = i < kRP && unsigned(gy) < unsigned(it.H) && unsigned(gx) < unsigned(it.W);
         const uint32_t off = in ? uint32_t(gy) * uint32_t(it.W) + uint32_t(gx) : 0u;
+        const uint32_t dst = uint32_t(ly * kRS + lx);
         if (k == 0) {
             rp.off0 = off;
+            rp.dst0 = dst;
             rp.in0 = in;
         } else {
             rp.off1 = off;
+            rp.dst1 = dst;
             rp.in1 = in;
             rp.has1 = i < kRP;
         }
     }
 }
 
-// Out-of-image positions read +inf (never precede anything): set once per
-// task in every slot; the copies below only fill in-image positions.
 __device__ __forceinline__ void ring_init(Smem3& sm, const RingPos& rp) {
     const float inf = __int_as_float(0x7F800000);
-    const int tid = threadIdx.x;
 #pragma unroll
     for (int s = 0; s < kRing; ++s) {
-        if (!rp.in0) sm.ring[s][tid] = inf;
-        if (rp.has1 && !rp.in1) sm.ring[s][tid + kT3] = inf;
+        if (!rp.in0) sm.ring[s][rp.dst0] = inf;
+        if (rp.has1 && !rp.in1) sm.ring[s][rp.dst1] = inf;
     }
 }
 
-__device__ __forceinline__ void issue_plane(Smem3& sm, const Item& it, int z, const RingPos& rp, uint32_t HW) {
-    float* plane = sm.ring[(z + kRing) & (kRing - 1)];
-    const int tid = threadIdx.x;
+// Where a task's planes come from.
+struct PlaneSrc {
+    const CUtensorMap* map;  // nullptr: cp.async path
+    int xs, ys;              // TMA box origin: x rounded down to a multiple of 4, y0 - 2
+    int zneed;               // last plane the task reads (TMA path loads no plane beyond it)
+};
+
+template <bool kTma>
+__device__ __forceinline__ void issue_plane(Smem3& sm, const Item& it, int z, const RingPos& rp, uint32_t HW,
+                                            const PlaneSrc& ps) {
+    const int slot = (z + kRing) & (kRing - 1);
+    float* plane = sm.ring[slot];
+    const float inf = __int_as_float(0x7F800000);
+    if constexpr (kTma) {
+        if (z > ps.zneed) return;
+        if (unsigned(z) < unsigned(it.D)) {
+            if (threadIdx.x == 0) {
+                // earlier generic-proxy accesses of the slot come before the copy
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                mbar_expect_tx(&sm.bar[slot], uint32_t(kRH * kRS * sizeof(float)));
+                tma_load_plane(plane, ps.map, &sm.bar[slot], ps.xs, ps.ys, z);
+            }
+        } else {  // a plane outside the volume: every position +inf
+            for (int i = threadIdx.x; i < kRH * kRS; i += kT3) plane[i] = inf;
+        }
+        return;
+    }
     if (unsigned(z) < unsigned(it.D)) {
         const float* base = it.img + uint32_t(z) * HW;
-        if (rp.in0) cp_async4(plane + tid, base + rp.off0);
-        if (rp.in1) cp_async4(plane + tid + kT3, base + rp.off1);
+        if (rp.in0) cp_async4(plane + rp.dst0, base + rp.off0);
+        if (rp.in1) cp_async4(plane + rp.dst1, base + rp.off1);
     } else {  // a plane outside the volume: every position +inf
-        const float inf = __int_as_float(0x7F800000);
-        if (rp.in0) plane[tid] = inf;
-        if (rp.in1) plane[tid + kT3] = inf;
+        if (rp.in0) plane[rp.dst0] = inf;
+        if (rp.in1) plane[rp.dst1] = inf;
     }
     cp_async_commit();
+}
+
+// Before reading plane z: wait for its TMA copy (cp.async planes are covered
+// by the wait_group and the barrier of the previous step).
+template <bool kTma>
+__device__ __forceinline__ void wait_plane(Smem3& sm, const Item& it, int z, uint32_t& par, Counters* ctr) {
+    if (!kTma || unsigned(z) >= unsigned(it.D)) return;
+    const int slot = z & (kRing - 1);
+    mbar_wait(&sm.bar[slot], (par >> slot) & 1u, ctr);
+    par ^= 1u << slot;
 }
 
 struct Col {
@@ -313,206 +396,238 @@ __device__ __forceinline__ uint32_t age_slot(uint32_t t) {
     return 18u * ((t >> 2) & 1u) + 6u * ((t >> 1) & 1u) + 2u * (t & 1u);
 }
 
-__global__ void __launch_bounds__(kT3, 4) k_prune3d(ItemTable tab, Outs o) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+// One task of the 3D pruning pass: a 31 x 8 column block of one item over a
+// chunk of planes (kTma: planes by TMA, else by cp.async; the two paths are
+// separate instantiations so that each keeps only its own state live).
+template <bool kTma>
+__device__ __forceinline__ void prune_task3d(Smem3& sm, const ItemTable& tab, const Outs& o, int ii, int ltask,
+                                             int warp, int lane, unsigned lt, WarpStage& ws, WarpCounts& cnt,
+                                             const CUtensorMap* map, uint32_t& par) {
+    const Item& it = tab.it[ii];
+    // task order: x segment fastest, then y segment, then z chunk
+    const int xs = ltask % it.tx;
+    const int rest = ltask / it.tx;
+    const int ys = rest % it.ty;
+    const int zc = rest / it.ty;
+    const int x0 = xs * kOX, y0 = ys * kOY;
+    Col cc;
+    cc.x = x0 - 1 + lane;
+    cc.y = y0 - 1 + warp;
+    cc.W = uint32_t(it.W);
+    cc.H = uint32_t(it.H);
+    cc.D = uint32_t(it.D);
+    cc.HW = cc.H * cc.W;
+    cc.W1 = cc.W - 1u;
+    cc.HW1 = (cc.H - 1u) * cc.W1;
+    cc.voff = uint32_t(it.voff);
+    cc.toff = uint32_t(it.toff);
+    cc.OUT = uint32_t(it.toff + it.T);
+    cc.in_xy = cc.x >= 0 && cc.y >= 0 && cc.x < it.W && cc.y < it.H;
+    cc.owned_xy = cc.in_xy && lane >= 1 && warp >= 1;
+    cc.cube_xy = cc.x >= 0 && cc.y >= 0 && cc.x < it.W - 1 && cc.y < it.H - 1 && lane <= 30 && warp <= kW3 - 2;
+    cc.bxy = (cc.y == 0 ? 4u : 0u) | (cc.y == it.H - 1 ? 8u : 0u) | (cc.x == 0 ? 16u : 0u) |
+             (cc.x == it.W - 1 ? 32u : 0u);
+    const int z0 = zc * tab.zchunk3d;
+    const int z1 = min(it.D, z0 + tab.zchunk3d);  // owned planes [z0, z1)
+    const int zlast = min(z1, it.D - 1);       // entries computed for planes [z0, zlast]
+    RingPos rp;
+    PlaneSrc src;
+    src.map = map;
+    src.xs = (x0 - 2) & ~3;
+    src.ys = y0 - 2;
+    src.zneed = zlast + 1;
+    if constexpr (!kTma) ring_positions(it, x0, y0, rp);
+    const int xo = kTma ? (x0 - 2) - src.xs : 0;  // column x0-2 within a slot row
+    if (kTma && threadIdx.x == 0) atomicAdd(&o.ctr->tma_tasks, 1u);
+    unsigned long long my_min = ~0ull;
+    uint32_t far = 0, far_t = 0;  // last H0 link / dual link written by this thread
+    __syncthreads();  // the rings may still be read by the previous task
+    if constexpr (!kTma) ring_init(sm, rp);
+#pragma unroll
+    for (int k = -1; k < kAhead; ++k) issue_plane<kTma>(sm, it, z0 + k, rp, cc.HW, src);
+    cp_async_wait<kAhead - 2>();  // planes z0-1 .. z0+1 have landed
+    __syncthreads();
+    Nbr A, B, C;
+    wait_plane<kTma>(sm, it, z0 - 1, par, o.ctr);
+    read_nbr(sm.ring[(z0 - 1 + kRing) & (kRing - 1)] + xo, warp, lane, A);
+    wait_plane<kTma>(sm, it, z0, par, o.ctr);
+    read_nbr(sm.ring[z0 & (kRing - 1)] + xo, warp, lane, B);
+    // One plane step: P (plane z-1) and Q (plane z) in registers, R gets plane
+    // z+1.  The loop below rotates the three register planes and the three
+    // codes slots (cs: plane z, ps: plane z-1), so nothing is copied.
+    auto step = [&](const Nbr& A, const Nbr& B, Nbr& C, const int z, const int cs, const int ps) {
+        issue_plane<kTma>(sm, it, z + kAhead, rp, cc.HW, src);
+        wait_plane<kTma>(sm, it, z + 1, par, o.ctr);
+        read_nbr(sm.ring[(z + 1) & (kRing - 1)] + xo, warp, lane, C);
+        // ---- lookup of (z, y, x)
+        const float cv = B.v[1][1];
+        const uint32_t raw = mask26(A, B, C);
+        const uint2 e = lookup3(collapse3(raw), sm.disp);
+        sm.codes[cs][warp][lane] = e.y;
+        const bool owned = cc.owned_xy && z < z1;
+        const uint32_t ord = ord_bits(cv);
+        const uint32_t vl = (uint32_t(z) * cc.H + uint32_t(cc.y)) * cc.W + uint32_t(cc.x);
+        const uint32_t vg = cc.voff + vl;
+        const int direct = int(e.x & 7u);
+        bool root0 = false;
+        if (owned) {
+            if (!(fabsf(cv) <= 3.40282347e38f)) set_status(o.ctr, kStNonfinite);
+            if (direct == 7) {
+                root0 = true;
+                far = vg;
+                const unsigned long long k = (unsigned long long)(uint64_t(ord) << 32 | vl);
+                my_min = k < my_min ? k : my_min;
+            } else {
+                // face slots: (-1,0,0) (0,-1,0) (0,0,-1) (0,0,1) (0,1,0) (1,0,0); a z-1 link
+                // continues the chain that the z-1 neighbour (same thread, previous
+                // step) started
+                const uint32_t mag = (direct == 0 || direct == 5) ? cc.HW : ((direct == 1 || direct == 4) ? cc.W : 1u);
+                const uint32_t u = direct < 3 ? vg - mag : vg + mag;
+                far = (direct == 0 && z > z0) ? far : u;
+                o.uf0[vg] = far;
+            }
+        }
+        const uint32_t h0s = owned ? (e.x >> 3) & 0x3Fu : 0u;
+        const uint32_t ds = owned ? (e.x >> 9) & 0xFFFu : 0u;
+        cp_async_wait<kAhead - 2>();  // plane z+2 has landed (for the next step)
+        __syncthreads();              // codes of plane z and image plane z+2 visible
+        // ---- the top cell with smallest corner (z-1, y, x)
+        bool rootT = false;
+        uint32_t rt_node = 0;
+        uint64_t rt_age = 0;
+        if (cc.cube_xy && z > z0) {
+            // largest of the 8 corners under (value, linear index), in index order
+            const float cvals[8] = {A.v[1][1], A.v[1][2], A.v[2][1], A.v[2][2],
+                                    B.v[1][1], B.v[1][2], B.v[2][1], B.v[2][2]};
+            int k = 0;
+            float best = cvals[0];
+#pragma unroll
+            for (int j = 1; j < 8; ++j) {
+                const bool ge = cvals[j] >= best;
+                best = ge ? cvals[j] : best;
+                k = ge ? j : k;
+            }
+            const int dz = k >> 2, dy = (k >> 1) & 1, dx = k & 1;
+            const uint32_t word = sm.codes[dz ? cs : ps][warp + dy][lane + dx];
+            const uint32_t t = uint32_t(7 - k);  // octant of the top cell as seen from m
+            const uint32_t code = (word >> (4u * t)) & 15u;
+            const uint32_t self = cc.toff + (uint32_t(z - 1) * (cc.H - 1u) + uint32_t(cc.y)) * cc.W1 + uint32_t(cc.x);
+            const int mz = z - 1 + dz, my = cc.y + dy, mx = cc.x + dx;
+            if (code == 8u) {
+                rootT = true;
+                rt_node = self;
+                far_t = self;
+                const uint32_t mg = cc.voff + (uint32_t(mz) * cc.H + uint32_t(my)) * cc.W + uint32_t(mx);
+                rt_age = make_key(ord_bits(best), mg, age_slot(t));
+            } else if (code < 8u) {
+                // the top cell across: octant `code` of m, smallest corner m - (negative axes)
+                const int tz = mz - int(((code >> 2) & 1u) ^ 1u);
+                const int ty = my - int(((code >> 1) & 1u) ^ 1u);
+                const int tx = mx - int((code & 1u) ^ 1u);
+                const bool out = unsigned(tz) >= cc.D - 1u || unsigned(ty) >= cc.H - 1u || unsigned(tx) >= cc.W1;
+                // a link to (z-2, y, x) continues the chain that this thread wrote for that
+                // top cell in the previous step
+                const bool chain = tz == z - 2 && ty == cc.y && tx == cc.x && z - 1 > z0;
+                far_t = chain ? far_t
+                              : (out ? cc.OUT : cc.toff + (uint32_t(tz) * (cc.H - 1u) + uint32_t(ty)) * cc.W1 + uint32_t(tx));
+                o.uft[self] = far_t;
+            } else {
+                far_t = kTag;
+                o.uft[self] = kTag;  // only reachable with non-finite input (flagged): keep the forest well formed
+            }
+        }
+        // ---- stage survivors and roots (rare in smooth fields)
+        if (__any_sync(0xFFFFFFFFu, root0 || rootT || (h0s | ds) != 0u)) {
+            const unsigned m_r0 = __ballot_sync(0xFFFFFFFFu, root0);
+            const unsigned m_rt = __ballot_sync(0xFFFFFFFFu, rootT);
+            const uint32_t or0 = __reduce_or_sync(0xFFFFFFFFu, h0s);
+            const uint32_t ort = __reduce_or_sync(0xFFFFFFFFu, ds);
+            if (cnt.r0 + __popc(m_r0) > uint32_t(kCapWR) || cnt.rt + __popc(m_rt) > uint32_t(kCapWR))
+                warp_flush(ws, cnt, o);
+            if (m_r0) {
+                if (root0) {
+                    const uint32_t p = cnt.r0 + __popc(m_r0 & lt);
+                    ws.r0node[p] = vg;
+                    ws.r0age[p] = make_key(ord, vg, 0);
+                }
+                cnt.r0 += __popc(m_r0);
+            }
+            if (m_rt) {
+                if (rootT) {
+                    const uint32_t p = cnt.rt + __popc(m_rt & lt);
+                    ws.rtnode[p] = rt_node;
+                    ws.rtage[p] = rt_age;
+                }
+                cnt.rt += __popc(m_rt);
+            }
+            uint32_t bits = or0;
+            while (bits) {
+                const int s = __ffs(bits) - 1;
+                bits &= bits - 1;
+                const bool mine = (h0s >> s) & 1u;
+                const unsigned m = __ballot_sync(0xFFFFFFFFu, mine);
+                if (cnt.s0 + __popc(m) > uint32_t(kCapW0)) warp_flush(ws, cnt, o);
+                if (mine) {
+                    const uint32_t n = s == 0 ? 4u : (s == 1 ? 10u : (s == 2 ? 12u : (s == 3 ? 14u : (s == 4 ? 16u : 22u))));
+                    ws.s0[cnt.s0 + __popc(m & lt)] = make_key(ord, vg, n);
+                }
+                cnt.s0 += __popc(m);
+            }
+            bits = ort;
+            while (bits) {
+                const int f = __ffs(bits) - 1;
+                bits &= bits - 1;
+                const bool mine = (ds >> f) & 1u;
+                const unsigned m = __ballot_sync(0xFFFFFFFFu, mine);
+                if (cnt.st + __popc(m) > uint32_t(kCapWT)) warp_flush(ws, cnt, o);
+                if (mine) {
+                    // facet slots 0..11 -> stencil bits 1,3,5,7,9,11,15,17,19,21,23,25
+                    const uint32_t n = f < 6 ? uint32_t(2 * f + 1) : uint32_t(2 * f + 3);
+                    ws.st[cnt.st + __popc(m & lt)] = ~make_key(ord, vg, n);
+                }
+                cnt.st += __popc(m);
+            }
+            __syncwarp();
+        }
+    };
+    for (int z = z0;;) {
+        step(A, B, C, z, 0, 2);
+        if (++z > zlast) break;
+        step(B, C, A, z, 1, 0);
+        if (++z > zlast) break;
+        step(C, A, B, z, 2, 1);
+        if (++z > zlast) break;
+    }
+    cp_async_wait<0>();
+    const unsigned long long w = warp_min_u64(my_min);
+    if (lane == 0 && w != ~0ull) atomicMin(&o.ctr->gmin[ii], w);
+}
+
+__global__ void __launch_bounds__(kT3, 4) k_prune3d(ItemTable tab, Outs o, const __grid_constant__ TmaMaps maps) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     Smem3& sm = *reinterpret_cast<Smem3*>(smem_raw);
     const int warp = threadIdx.x >> 5;
     const int lane = int(lane_id());
     const unsigned lt = (1u << lane) - 1u;
+    for (int i = threadIdx.x; i < (1 << 12); i += kT3) sm.disp[i] = g_disp3d[i];
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kRing; ++s) mbar_init(&sm.bar[s], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    // TMA destinations must be 128-byte aligned; otherwise every item takes the cp.async path
+    const bool tma_ok = (smem_u32(sm.ring) & 127u) == 0;
+    uint32_t par = 0;  // phase parity of each slot's mbarrier (every thread waits on every TMA plane)
     WarpStage& ws = sm.ws[warp];
     WarpCounts cnt = {0, 0, 0, 0};
     for (int task = blockIdx.x; task < tab.tiles3d; task += gridDim.x) {
         const int ii = tile_item(tab, tab.n2d, tab.n - 1, task);
         const Item& it = tab.it[ii];
         const int ltask = task - it.tile0;
-        // task order: x segment fastest, then y segment, then z chunk
-        const int xs = ltask % it.tx;
-        const int rest = ltask / it.tx;
-        const int ys = rest % it.ty;
-        const int zc = rest / it.ty;
-        const int x0 = xs * kOX, y0 = ys * kOY;
-        Col cc;
-        cc.x = x0 - 1 + lane;
-        cc.y = y0 - 1 + warp;
-        cc.W = uint32_t(it.W);
-        cc.H = uint32_t(it.H);
-        cc.D = uint32_t(it.D);
-        cc.HW = cc.H * cc.W;
-        cc.W1 = cc.W - 1u;
-        cc.HW1 = (cc.H - 1u) * cc.W1;
-        cc.voff = uint32_t(it.voff);
-        cc.toff = uint32_t(it.toff);
-        cc.OUT = uint32_t(it.toff + it.T);
-        cc.in_xy = cc.x >= 0 && cc.y >= 0 && cc.x < it.W && cc.y < it.H;
-        cc.owned_xy = cc.in_xy && lane >= 1 && warp >= 1;
-        cc.cube_xy = cc.x >= 0 && cc.y >= 0 && cc.x < it.W - 1 && cc.y < it.H - 1 && lane <= 30 && warp <= kW3 - 2;
-        cc.bxy = (cc.y == 0 ? 4u : 0u) | (cc.y == it.H - 1 ? 8u : 0u) | (cc.x == 0 ? 16u : 0u) |
-                 (cc.x == it.W - 1 ? 32u : 0u);
-        const int z0 = zc * tab.zchunk3d;
-        const int z1 = min(it.D, z0 + tab.zchunk3d);  // owned planes [z0, z1)
-        const int zlast = min(z1, it.D - 1);       // entries computed for planes [z0, zlast]
-        RingPos rp;
-        ring_positions(it, x0, y0, rp);
-        unsigned long long my_min = ~0ull;
-        uint32_t far = 0, far_t = 0;  // last H0 link / dual link written by this thread
-        __syncthreads();  // the rings may still be read by the previous task
-        ring_init(sm, rp);
-#pragma unroll
-        for (int k = -1; k < kAhead; ++k) issue_plane(sm, it, z0 + k, rp, cc.HW);
-        cp_async_wait<kAhead - 2>();  // planes z0-1 .. z0+1 have landed
-        __syncthreads();
-        Nbr A, B, C;
-        read_nbr(sm.ring[(z0 - 1 + kRing) & (kRing - 1)], warp, lane, A);
-        read_nbr(sm.ring[z0 & (kRing - 1)], warp, lane, B);
-        // One plane step: P (plane z-1) and Q (plane z) in registers, R gets plane
-        // z+1.  The loop below rotates the three register planes and the three
-        // codes slots (cs: plane z, ps: plane z-1), so nothing is copied.
-        auto step = [&](const Nbr& A, const Nbr& B, Nbr& C, const int z, const int cs, const int ps) {
-            issue_plane(sm, it, z + kAhead, rp, cc.HW);
-            read_nbr(sm.ring[(z + 1) & (kRing - 1)], warp, lane, C);
-            // ---- lookup of (z, y, x)
-            const float cv = B.v[1][1];
-            const uint32_t raw = mask26(A, B, C);
-            const uint2 e = lookup3(collapse3(raw));
-            sm.codes[cs][warp][lane] = e.y;
-            const bool owned = cc.owned_xy && z < z1;
-            const uint32_t ord = ord_bits(cv);
-            const uint32_t vl = (uint32_t(z) * cc.H + uint32_t(cc.y)) * cc.W + uint32_t(cc.x);
-            const uint32_t vg = cc.voff + vl;
-            const int direct = int(e.x & 7u);
-            bool root0 = false;
-            if (owned) {
-                if (!(fabsf(cv) <= 3.40282347e38f)) set_status(o.ctr, kStNonfinite);
-                if (direct == 7) {
-                    root0 = true;
-                    far = vg;
-                    const unsigned long long k = (unsigned long long)(uint64_t(ord) << 32 | vl);
-                    my_min = k < my_min ? k : my_min;
-                } else {
-                    // face slots: (-1,0,0) (0,-1,0) (0,0,-1) (0,0,1) (0,1,0) (1,0,0); a z-1 link
-                    // continues the chain that the z-1 neighbour (same thread, previous
-                    // step) started
-                    const uint32_t mag = (direct == 0 || direct == 5) ? cc.HW : ((direct == 1 || direct == 4) ? cc.W : 1u);
-                    const uint32_t u = direct < 3 ? vg - mag : vg + mag;
-                    far = (direct == 0 && z > z0) ? far : u;
-                    o.uf0[vg] = far;
-                }
-            }
-            const uint32_t h0s = owned ? (e.x >> 3) & 0x3Fu : 0u;
-            const uint32_t ds = owned ? (e.x >> 9) & 0xFFFu : 0u;
-            cp_async_wait<kAhead - 2>();  // plane z+2 has landed (for the next step)
-            __syncthreads();              // codes of plane z and image plane z+2 visible
-            // ---- the top cell with smallest corner (z-1, y, x)
-            bool rootT = false;
-            uint32_t rt_node = 0;
-            uint64_t rt_age = 0;
-            if (cc.cube_xy && z > z0) {
-                // largest of the 8 corners under (value, linear index), in index order
-                const float cvals[8] = {A.v[1][1], A.v[1][2], A.v[2][1], A.v[2][2],
-                                        B.v[1][1], B.v[1][2], B.v[2][1], B.v[2][2]};
-                int k = 0;
-                float best = cvals[0];
-#pragma unroll
-                for (int j = 1; j < 8; ++j) {
-                    const bool ge = cvals[j] >= best;
-                    best = ge ? cvals[j] : best;
-                    k = ge ? j : k;
-                }
-                const int dz = k >> 2, dy = (k >> 1) & 1, dx = k & 1;
-                const uint32_t word = sm.codes[dz ? cs : ps][warp + dy][lane + dx];
-                const uint32_t t = uint32_t(7 - k);  // octant of the top cell as seen from m
-                const uint32_t code = (word >> (4u * t)) & 15u;
-                const uint32_t self = cc.toff + (uint32_t(z - 1) * (cc.H - 1u) + uint32_t(cc.y)) * cc.W1 + uint32_t(cc.x);
-                const int mz = z - 1 + dz, my = cc.y + dy, mx = cc.x + dx;
-                if (code == 8u) {
-                    rootT = true;
-                    rt_node = self;
-                    far_t = self;
-                    const uint32_t mg = cc.voff + (uint32_t(mz) * cc.H + uint32_t(my)) * cc.W + uint32_t(mx);
-                    rt_age = make_key(ord_bits(best), mg, age_slot(t));
-                } else if (code < 8u) {
-                    // the top cell across: octant `code` of m, smallest corner m - (negative axes)
-                    const int tz = mz - int(((code >> 2) & 1u) ^ 1u);
-                    const int ty = my - int(((code >> 1) & 1u) ^ 1u);
-                    const int tx = mx - int((code & 1u) ^ 1u);
-                    const bool out = unsigned(tz) >= cc.D - 1u || unsigned(ty) >= cc.H - 1u || unsigned(tx) >= cc.W1;
-                    // a link to (z-2, y, x) continues the chain that this thread wrote for that
-                    // top cell in the previous step
-                    const bool chain = tz == z - 2 && ty == cc.y && tx == cc.x && z - 1 > z0;
-                    far_t = chain ? far_t
-                                  : (out ? cc.OUT : cc.toff + (uint32_t(tz) * (cc.H - 1u) + uint32_t(ty)) * cc.W1 + uint32_t(tx));
-                    o.uft[self] = far_t;
-                } else {
-                    far_t = kTag;
-                    o.uft[self] = kTag;  // only reachable with non-finite input (flagged): keep the forest well formed
-                }
-            }
-            // ---- stage survivors and roots (rare in smooth fields)
-            if (__any_sync(0xFFFFFFFFu, root0 || rootT || (h0s | ds) != 0u)) {
-                const unsigned m_r0 = __ballot_sync(0xFFFFFFFFu, root0);
-                const unsigned m_rt = __ballot_sync(0xFFFFFFFFu, rootT);
-                const uint32_t or0 = __reduce_or_sync(0xFFFFFFFFu, h0s);
-                const uint32_t ort = __reduce_or_sync(0xFFFFFFFFu, ds);
-                const uint32_t n0 = __reduce_add_sync(0xFFFFFFFFu, uint32_t(__popc(h0s)));  // <= 32 * 5
-                const uint32_t nt = __reduce_add_sync(0xFFFFFFFFu, uint32_t(__popc(ds)));   // <= 32 * 7
-                if (cnt.s0 + n0 > uint32_t(kCapW0) || cnt.st + nt > uint32_t(kCapWT) ||
-                    cnt.r0 + __popc(m_r0) > uint32_t(kCapWR) || cnt.rt + __popc(m_rt) > uint32_t(kCapWR))
-                    warp_flush(ws, cnt, o);
-                if (m_r0) {
-                    if (root0) {
-                        const uint32_t p = cnt.r0 + __popc(m_r0 & lt);
-                        ws.r0node[p] = vg;
-                        ws.r0age[p] = make_key(ord, vg, 0);
-                    }
-                    cnt.r0 += __popc(m_r0);
-                }
-                if (m_rt) {
-                    if (rootT) {
-                        const uint32_t p = cnt.rt + __popc(m_rt & lt);
-                        ws.rtnode[p] = rt_node;
-                        ws.rtage[p] = rt_age;
-                    }
-                    cnt.rt += __popc(m_rt);
-                }
-                uint32_t bits = or0;
-                while (bits) {
-                    const int s = __ffs(bits) - 1;
-                    bits &= bits - 1;
-                    const bool mine = (h0s >> s) & 1u;
-                    const unsigned m = __ballot_sync(0xFFFFFFFFu, mine);
-                    if (mine) {
-                        const uint32_t n = s == 0 ? 4u : (s == 1 ? 10u : (s == 2 ? 12u : (s == 3 ? 14u : (s == 4 ? 16u : 22u))));
-                        ws.s0[cnt.s0 + __popc(m & lt)] = make_key(ord, vg, n);
-                    }
-                    cnt.s0 += __popc(m);
-                }
-                bits = ort;
-                while (bits) {
-                    const int f = __ffs(bits) - 1;
-                    bits &= bits - 1;
-                    const bool mine = (ds >> f) & 1u;
-                    const unsigned m = __ballot_sync(0xFFFFFFFFu, mine);
-                    if (mine) {
-                        // facet slots 0..11 -> stencil bits 1,3,5,7,9,11,15,17,19,21,23,25
-                        const uint32_t n = f < 6 ? uint32_t(2 * f + 1) : uint32_t(2 * f + 3);
-                        ws.st[cnt.st + __popc(m & lt)] = ~make_key(ord, vg, n);
-                    }
-                    cnt.st += __popc(m);
-                }
-                __syncwarp();
-            }
-        };
-        for (int z = z0;;) {
-            step(A, B, C, z, 0, 2);
-            if (++z > zlast) break;
-            step(B, C, A, z, 1, 0);
-            if (++z > zlast) break;
-            step(C, A, B, z, 2, 1);
-            if (++z > zlast) break;
-        }
-        cp_async_wait<0>();
-        const unsigned long long w = warp_min_u64(my_min);
-        if (lane == 0 && w != ~0ull) atomicMin(&o.ctr->gmin[ii], w);
+        if (tma_ok && it.tma >= 0)
+            prune_task3d<true>(sm, tab, o, ii, ltask, warp, lane, lt, ws, cnt, &maps.m[it.tma], par);
+        else
+            prune_task3d<false>(sm, tab, o, ii, ltask, warp, lane, lt, ws, cnt, nullptr, par);
     }
     if (__any_sync(0xFFFFFFFFu, (cnt.s0 | cnt.st | cnt.r0 | cnt.rt) != 0)) warp_flush(ws, cnt, o);
 }
@@ -589,7 +704,7 @@ __device__ __forceinline__ void issue_row(float (*ring)[kRW2], const RowPos& p, 
 }
 
 __global__ void __launch_bounds__(kW2 * 32) k_prune2d(ItemTable tab, Outs o) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     Smem2& sm = *reinterpret_cast<Smem2*>(smem_raw);
     const int warp = threadIdx.x >> 5;
     const int lane = int(lane_id());
@@ -784,6 +899,32 @@ __global__ void __launch_bounds__(kW2 * 32) k_prune2d(ItemTable tab, Outs o) {
 // ---------------------------------------------------------------- host side
 size_t prune_smem2d() { return sizeof(Smem2); }
 size_t prune_smem3d() { return sizeof(Smem3); }
+
+bool encode_plane_map(CUtensorMap* map, const float* img, int64_t D, int64_t H, int64_t W) {
+    using Encode = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+    static Encode encode = nullptr;
+    static bool looked = false;
+    if (!looked) {
+        looked = true;
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            encode = reinterpret_cast<Encode>(fn);
+    }
+    // row stride a multiple of 16 bytes, 16-byte aligned base, a plane at least one box
+    if (!encode || !img || (W & 3) != 0 || (reinterpret_cast<uintptr_t>(img) & 15u) != 0 || W < kRS || H < kRH || D < 2)
+        return false;
+    const cuuint64_t dim[3] = {cuuint64_t(W), cuuint64_t(H), cuuint64_t(D)};
+    const cuuint64_t stride[2] = {cuuint64_t(W) * 4u, cuuint64_t(W) * cuuint64_t(H) * 4u};
+    const cuuint32_t box[3] = {cuuint32_t(kRS), cuuint32_t(kRH), 1u};
+    const cuuint32_t estride[3] = {1u, 1u, 1u};
+    return encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(img), dim, stride, box, estride,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NAN_REQUEST_ZERO_FMA) == CUDA_SUCCESS;
+}
 int prune_tile_x() { return kOX2; }
 int prune_tile_x3d() { return kOX; }
 int g_rows2d = 64, g_zchunk3d = kZC, g_ctas3d = 0;  // tuning (cp_set_tuning)
@@ -838,7 +979,7 @@ cudaError_t upload_luts(const uint64_t* lut2d, const uint16_t* disp3d, const uin
     return cudaMemcpyToSymbol(g_entries3d, packed, sizeof(packed));
 }
 
-cudaError_t launch_prune(const ItemTable& tab, const PruneOuts& po, cudaStream_t s) {
+cudaError_t launch_prune(const ItemTable& tab, const PruneOuts& po, const TmaMaps& maps, cudaStream_t s) {
     Outs o;
     o.uf0 = po.uf0;
     o.uft = po.uft;
@@ -874,7 +1015,7 @@ cudaError_t launch_prune(const ItemTable& tab, const PruneOuts& po, cudaStream_t
         int cap = blocks3d;
         if (g_ctas3d > 0) cap = device_sm_count() * g_ctas3d < blocks3d ? device_sm_count() * g_ctas3d : blocks3d;
         int grid = tab.tiles3d < cap ? tab.tiles3d : cap;
-        k_prune3d<<<grid, kT3, prune_smem3d(), s>>>(tab, o);
+        k_prune3d<<<grid, kT3, prune_smem3d(), s>>>(tab, o, maps);
         note_launches(1);
     }
     return cudaGetLastError();

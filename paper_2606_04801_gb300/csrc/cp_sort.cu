@@ -19,7 +19,7 @@ namespace {
 
 constexpr int kT = 256;                 // threads per CTA
 constexpr int kWarps = kT / 32;
-constexpr int kKPT = kSortTile / kT;    // keys per thread (16)
+constexpr int kKPT = kSortTile / kT;    // keys per thread (8)
 constexpr uint32_t kFlagAgg = 1u, kFlagIncl = 2u;
 constexpr int kLook = 16;               // look-back window: predecessor tiles read together
 

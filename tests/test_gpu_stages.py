@@ -31,10 +31,10 @@ def cp():
 
 
 def _roots(par):
-    par = np.asarray(par, dtype=np.int64)
-    r = par.copy()
+    """Root of every node, by pointer doubling (paths on plateaus can be long)."""
+    r = np.asarray(par, dtype=np.int64).copy()
     for _ in range(64):
-        nr = par[r]
+        nr = r[r]
         if np.array_equal(nr, r):
             return r
         r = nr
@@ -48,8 +48,8 @@ def _kernel_stage(cp, img):
     ptrs = (ctypes.c_void_p * 1)(t.data_ptr())
     ndims = (ctypes.c_int32 * 1)(nd)
     dims = (ctypes.c_int64 * 3)(*(([1] + list(img.shape)) if nd == 2 else list(img.shape)))
-    off = (ctypes.c_int64 * 12)()
-    assert lib.cubical_persistence_debug_layout(1, ndims, dims, 0, off, 12) == 12
+    off = (ctypes.c_int64 * 13)()
+    assert lib.cubical_persistence_debug_layout(1, ndims, dims, 0, off, 13) == 13
     ws_bytes = lib.cubical_persistence_batched_workspace_size(1, ndims, dims, 0)
     ws = torch.zeros(ws_bytes, dtype=torch.uint8, device="cuda")
     rc = lib.cubical_persistence_debug_prune(1, ptrs, ndims, dims, ctypes.c_void_p(ws.data_ptr()), ws_bytes, 0, None)
@@ -64,6 +64,7 @@ def _kernel_stage(cp, img):
     uft = w[off[2] : off[2] + 4 * ttot].view(np.uint32).astype(np.int64)
     s0 = np.sort(w[off[3] : off[3] + 8 * n_s0].view(np.uint64))
     st = np.sort(~w[off[4] : off[4] + 8 * n_st].view(np.uint64))
+    _check.tma_tasks = int(w[off[12] : off[12] + 4].view(np.uint32)[0])
     return uf0, uft, s0, st, n_r0, n_rt
 
 
@@ -106,3 +107,23 @@ def test_prune_stage_3d(cp, seed):
         _check(cp, lib, img)
     # a smooth volume deeper than one z chunk of the kernel (chains across chunks)
     _check(cp, lib, workloads.blurred((70, 9, 12), 2.0, 510 + seed))
+
+
+@pytest.mark.parametrize("seed", range(2))
+def test_prune_stage_3d_tma_planes(cp, seed):
+    """Volumes whose width is a multiple of 4 (and planes at least one 40 x 11
+    box) load their planes by TMA (out-of-image positions NaN); ragged tiles in
+    every axis; ties.  The same data one column wider (41: cp.async path) must
+    give the same survivors and roots."""
+    lib = cp.load()
+    rng = np.random.default_rng(600 + seed)
+    for shape in [(13, 12, 40), (9, 21, 44), (70, 11, 48)]:
+        img = rng.integers(0, 3, shape).astype(np.float32) if seed == 0 else workloads.blurred(shape, 1.5, 610 + seed)
+        _check(cp, lib, img)
+        D, H, W = shape
+        zc = lib.cp_get_tuning(1)
+        tasks = -(-W // 31) * -(-H // 8) * -(-D // zc)
+        assert _check.tma_tasks == tasks, ("TMA path not taken", _check.tma_tasks, tasks)
+    img = rng.random((10, 12, 41), dtype=np.float32)
+    _check(cp, lib, img)
+    assert _check.tma_tasks == 0
