@@ -202,6 +202,45 @@ def cpu_baseline(vol, budget_s=20.0):
     }
 
 
+def _oracle_item(a):
+    import oracle
+
+    oracle.persistence(a)
+    return a.size
+
+
+def batched_cpu_baseline(items, budget_s=10.0):
+    """The oracle as it stands on the batched workload's items, spread over all
+    host cores (a spawn pool): a bounded sample of the items (those up to 3 M
+    voxels, in workload order, up to about budget_s seconds of wall time)."""
+    import multiprocessing as mp
+
+    import oracle
+
+    oracle.build()
+    cores = os.cpu_count() or 1
+    cap = cores * budget_s * 0.3e6  # voxels the pool clears in the budget at ~0.3 Mvox/s per core
+    sample, total = [], 0
+    for a in items:
+        if a.size <= 3_000_000 and total + a.size <= cap:
+            sample.append(a)
+            total += a.size
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores) as pool:
+        pool.map(_oracle_item, sample[:cores])  # warm the workers (import, load the library)
+        t0 = time.perf_counter()
+        done = sum(pool.map(_oracle_item, sample, chunksize=1))
+        dt = time.perf_counter() - t0
+    return {
+        "value": done / dt / 1e6,
+        "unit": "Mvoxels/s",
+        "cores": cores,
+        "kind": "oracle",
+        "sample": f"{len(sample)} of {len(items)} items ({done / 1e6:.1f} M voxels, items up to 3 M voxels), "
+        f"one item per task in a pool of {cores} processes, {dt:.1f} s",
+    }
+
+
 def _batch_items():
     cache = "/tmp/cp_bench_batch_v1.npz"
     if os.path.exists(cache):
@@ -304,6 +343,33 @@ def batched_vs_plain(dev, steps: int, warmup: int):
     }
 
 
+def run_survivors():
+    """Survivor fractions (H0 and top-dimension survivors of the pruning pass
+    per vertex) and pair counts of every config, through the public API."""
+    import torch
+
+    import paper_2606_04801_gb300 as cp
+
+    out = {}
+    for name in ("2d_64_uniform", "2d_2048_grf", "3d_128", "3d_512_blurred", "batch"):
+        arrs = workloads.config(name)
+        if name == "batch":
+            d = cp.persistence_batched([torch.from_numpy(a).cuda() for a in arrs], with_stats=True)
+            n = sum(a.size for a in arrs)
+            rows = [("all", n, d.stats, len(d))]
+        else:
+            rows = []
+            for i, a in enumerate(arrs):
+                d = cp.persistence(torch.from_numpy(a).cuda(), with_stats=True)
+                rows.append((str(i), a.size, d.stats, len(d)))
+        for tag, n, st, npairs in rows:
+            out[f"{name}/{tag}"] = {"N": n, "h0_survivors_per_N": st["h0_survivors"] / n,
+                                    "top_survivors_per_N": st["top_survivors"] / n,
+                                    "h0_roots_per_N": st["h0_roots"] / n, "top_roots_per_N": st["top_roots"] / n,
+                                    "pairs": npairs, "h0_rounds": st["h0_rounds"], "top_rounds": st["top_rounds"]}
+    print(json.dumps({"metric": "survivor fractions S/N per config", "configs": out}), flush=True)
+
+
 def run_batched(args):
     """The batched workload alone: fwd + loss bwd of 64 images and 8 volumes of
     uneven sizes, one CUDA-graph launch per step (or eager with --eager)."""
@@ -343,6 +409,9 @@ def run_batched(args):
         torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
         t = float(tt.item())
     st = bp.status()
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = batched_cpu_baseline(items)
     if rank == 0:
         print(json.dumps({
             "metric": "Mvoxels/s fwd+bwd, batched workload (64 images + 8 volumes, uneven sizes)",
@@ -359,8 +428,10 @@ def run_batched(args):
             "data": "synthetic",
             "config": {"workload": "64 2D (sides 128-1024) + 8 3D (sides 64-192) blurred, rank-spaced; fwd + loss bwd",
                        "voxels": nvox, "graph": not args.eager, "status": st["rc"],
-                       "l2": "inputs (166 MiB) larger than L2; no flush", "parallelism": "replicas" if ws > 1 else "single"},
+                       "l2": "inputs (166 MiB) larger than L2; no flush", "parallelism": "replicas" if ws > 1 else "single",
+                       "survivor_fraction": (st["h0_survivors"] + st["top_survivors"]) / nvox},
             "clocks": clk.summary(),
+            "cpu_baseline": cpu,
         }), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
@@ -376,8 +447,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--side", type=int, default=512, help="cube side (512 is the benchmark; smaller for profiling)")
     ap.add_argument("--no-batched", action="store_true")
-    ap.add_argument("--workload", default="volume", choices=["volume", "batched"],
-                    help="volume: the 512^3 plain path (the headline line); batched: the batched fwd + bwd workload alone")
+    ap.add_argument("--workload", default="volume", choices=["volume", "batched", "survivors"],
+                    help="volume: the 512^3 plain path (the headline line); batched: the batched fwd + bwd workload "
+                    "alone; survivors: survivor fractions S/N of every config")
     ap.add_argument("--eager", action="store_true", help="batched workload without the CUDA graph (per-kernel profiling)")
     args = ap.parse_args()
     global SIDE
@@ -389,6 +461,9 @@ def main():
         return
     if args.workload == "batched":
         run_batched(args)
+        return
+    if args.workload == "survivors":
+        run_survivors()
         return
 
     import torch
@@ -584,6 +659,7 @@ def main():
         "batched": batched,
         "uf_trace": trace,
         "counts": {"pairs": int(cnt.value), "h0_survivors": s0, "top_survivors": stp, "h0_roots": r0, "top_roots": rt,
+                   "survivor_fraction": (s0 + stp) / N,
                    "h0_rounds": st["h0_rounds"], "top_rounds": st["top_rounds"]},
     }
     print(json.dumps(line), flush=True)
