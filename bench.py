@@ -53,6 +53,23 @@ def _volume(seed: int) -> np.ndarray:
     return v
 
 
+def job_time(local_s: float, world: int, device) -> float:
+    """Wall time of the job: the maximum over ranks (the job ends with its slowest rank)."""
+    if world <= 1:
+        return local_s
+    import torch
+
+    t = torch.tensor([local_s], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(units_per_rank_step: float, world: int, steps: int, seconds: float) -> float:
+    """Whole-job throughput in millions of units per second: every rank is a
+    replica that processes its own units each step (weak scaling)."""
+    return units_per_rank_step * world * steps / seconds / 1e6
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -403,11 +420,7 @@ def run_batched(args):
             bp.step()
         e1.record(stream)
         torch.cuda.synchronize(dev)
-    t = e0.elapsed_time(e1) / 1e3 / args.steps
-    if ws > 1:
-        tt = torch.tensor([t], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t = float(tt.item())
+    t = job_time(e0.elapsed_time(e1) / 1e3 / args.steps, ws, dev)
     st = bp.status()
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -415,7 +428,7 @@ def run_batched(args):
     if rank == 0:
         print(json.dumps({
             "metric": "Mvoxels/s fwd+bwd, batched workload (64 images + 8 volumes, uneven sizes)",
-            "value": nvox * ws / t / 1e6,
+            "value": job_value(nvox, ws, 1, t),
             "unit": "Mvoxels/s",
             "n_gpus": ws,
             "steps": args.steps,
@@ -545,12 +558,8 @@ def main():
         ev1.record(stream)
         barrier()
     launches = lib.cp_launch_count() - launches0
-    elapsed = ev0.elapsed_time(ev1) / 1e3
-    if ws > 1:
-        t = torch.tensor([elapsed], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        elapsed = float(t.item())
-    value = N * ws * args.steps / elapsed / 1e6
+    elapsed = job_time(ev0.elapsed_time(ev1) / 1e3, ws, dev)
+    value = job_value(N, ws, args.steps, elapsed)
 
     # ---------------- end to end: pinned host input -> device -> pairs + loss/grad -> loss on host
     lib.cp_profile(0)
@@ -567,12 +576,9 @@ def main():
             _ = float(loss.item())
         barrier()
         e2e_dt = time.perf_counter() - t0
-    if ws > 1:
-        t = torch.tensor([e2e_dt], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_dt = float(t.item())
+    e2e_dt = job_time(e2e_dt, ws, dev)
     e2e = None if not e2e_steps else {
-        "value": N * ws * e2e_steps / e2e_dt / 1e6,
+        "value": job_value(N, ws, e2e_steps, e2e_dt),
         "unit": "Mvoxels/s",
         "h2d_bytes_per_step": int(N * 4),
         "d2h_bytes_per_step": 8 + COUNTERS_BYTES,  # the loss, and the call's status/count block
