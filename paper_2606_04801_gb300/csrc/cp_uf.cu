@@ -108,21 +108,25 @@ __device__ __forceinline__ void reserve(uint64_t* res, uint32_t rid, uint64_t st
     atomicMax(reinterpret_cast<unsigned long long*>(res + rid), (unsigned long long)stamp);
 }
 
-// Grid-wide barrier for a cooperative launch (all CTAs co-resident).
-__device__ void grid_barrier(Counters* ctr, uint32_t nblocks) {
+// Grid-wide barrier for a cooperative launch (all CTAs co-resident): a
+// monotonic arrival counter (zeroed before the launch).  Barrier number e of
+// the launch is passed when the counter reaches e * nblocks, so it completes
+// as soon as the last CTA's arrival lands.  The wait is bounded.
+__device__ void grid_barrier(Counters* ctr, uint32_t nblocks, uint32_t& epoch) {
     __syncthreads();
+    ++epoch;
     if (threadIdx.x == 0) {
-        uint32_t gen = ld_acquire_u32(&ctr->bar_gen);
-        __threadfence();
-        uint32_t arrived = atomicAdd(&ctr->bar_count, 1u);
-        if (arrived == nblocks - 1) {
-            atomicExch(&ctr->bar_count, 0u);
-            __threadfence();
-            atomicAdd(&ctr->bar_gen, 1u);
-        } else {
-            bounded_wait_ne(&ctr->bar_gen, gen, ctr, kWaitLimitNs);
+        const uint32_t target = epoch * nblocks;
+        asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&ctr->bar_count) : "memory");
+        if (ld_acquire_u32(&ctr->bar_count) < target) {
+            const uint64_t t0 = global_timer_ns();
+            while (ld_acquire_u32(&ctr->bar_count) < target) {
+                if (global_timer_ns() - t0 > kWaitLimitNs) {
+                    set_status(ctr, kStTimeout);
+                    break;
+                }
+            }
         }
-        __threadfence();
     }
     __syncthreads();
 }
@@ -398,7 +402,7 @@ __device__ __forceinline__ void phase_a_mem(const UfKernelArgs& args, int q, uin
 // first kR items of each thread keep their phase-A results in registers, and
 // their loads are issued together.
 __device__ void uf_rounds(const UfKernelArgs& args, uint32_t n0, uint32_t n1, uint32_t base1, unsigned live,
-                          unsigned prefound) {
+                          unsigned prefound, uint32_t& epoch) {
     const ItemTable& tab = args.tab;
     Counters* ctr = args.p[0].ctr;
     const uint32_t nblocks = gridDim.x;
@@ -534,7 +538,7 @@ __device__ void uf_rounds(const UfKernelArgs& args, uint32_t n0, uint32_t n1, ui
                 if (lane == 0 && h) atomicAdd(&ctr->trace_hops[args.p[q].dual][round - 1], (unsigned long long)h);
             }
         }
-        grid_barrier(ctr, nblocks);
+        grid_barrier(ctr, nblocks, epoch);
         if (gtid == 0 && round <= uint32_t(kTraceRounds))
             for (int q = 0; q < 2; ++q)
                 if ((live >> q) & 1u) ctr->trace_ta[args.p[q].dual][round - 1] = global_timer_ns();
@@ -619,7 +623,7 @@ __device__ void uf_rounds(const UfKernelArgs& args, uint32_t n0, uint32_t n1, ui
                 p.nb[cur ^ 1][at] = __ldcg(p.onode + slot);
             }
         }
-        grid_barrier(ctr, nblocks);
+        grid_barrier(ctr, nblocks, epoch);
         // one thread reads the next round's counts and the status for the CTA,
         // so that every thread of the CTA takes the same path even after a
         // bounded wait has given up
@@ -681,19 +685,20 @@ __global__ void __launch_bounds__(kT) k_uf(const __grid_constant__ UfKernelArgs 
     // non-finite input leaves the forests unreliable: the call fails anyway
     if (ld_acquire_u32(&ctr->status) & (kStTimeout | kStNonfinite)) return;
     const uint32_t n0 = min(*args.p[0].d_nkeys, args.p[0].cap_keys);
+    uint32_t epoch = 0;  // grid barriers passed in this launch
     // k_roots / k_place_roots have walked the first round's paths of problem
     // 0, and of problem 1 when the two lists sit side by side
     if (args.nprob == 1) {
-        uf_rounds(args, n0, 0u, 0u, 1u, 1u);
+        uf_rounds(args, n0, 0u, 0u, 1u, 1u, epoch);
         return;
     }
     const uint32_t n1 = min(*args.p[1].d_nkeys, args.p[1].cap_keys);
     if (side_by_side(args, n0, n1)) {
-        uf_rounds(args, n0, n1, n0, 3u, 3u);
+        uf_rounds(args, n0, n1, n0, 3u, 3u, epoch);
     } else {  // one after the other, each with the whole scratch and log
-        uf_rounds(args, n0, 0u, 0u, 1u, 1u);
-        grid_barrier(ctr, gridDim.x);  // problem 0's log is read before problem 1 rewrites it
-        uf_rounds(args, 0u, n1, 0u, 2u, 0u);
+        uf_rounds(args, n0, 0u, 0u, 1u, 1u, epoch);
+        grid_barrier(ctr, gridDim.x, epoch);  // problem 0's log is read before problem 1 rewrites it
+        uf_rounds(args, 0u, n1, 0u, 2u, 0u, epoch);
     }
 }
 
@@ -736,6 +741,8 @@ cudaError_t launch_uf(const ItemTable& tab, const UfParams* p, int nprob, cudaSt
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
+    cudaError_t e = cudaMemsetAsync(&p[0].ctr->bar_count, 0, sizeof(uint32_t), s);
+    if (e != cudaSuccess) return e;
     note_launches(1);
     return cudaLaunchKernelEx(&cfg, k_uf, args);
 }
