@@ -29,7 +29,7 @@
  *    non-NULL the call waits for the stream once, to read the pair count and
  *    the status word back; with h_out_count == NULL it returns right after
  *    enqueueing, d_out_count (if non-NULL) receives the count on the device,
- *    and cubical_persistence_status() reads the status later.
+ *    and cubical_persistence_stats() reads the status later.
  *  - Return value: CP_OK (0) or a negative CP_ERR_* code.
  */
 #ifndef CUBICAL_PERSISTENCE_H
@@ -293,9 +293,10 @@ int cubical_persistence_debug_layout(int n_items, const int32_t *ndims, const in
                                      int64_t *h_offsets, int cap);
 
 /*
- * Failure-path test: a kernel waits, through the same bounded-wait routine
- * the grid barrier uses, on a workspace word that nothing sets, and gives up
- * after limit_us microseconds (1 .. 2,000,000).  Needs a workspace of at
+ * Failure-path test: a kernel waits, through the library's bounded-wait
+ * routine (every device-side wait gives up the same way, after 2 s in
+ * production), on a workspace word that nothing sets, and gives up after
+ * limit_us microseconds (1 .. 2,000,000).  Needs a workspace of at
  * least 4 KiB.  Returns CP_ERR_TIMEOUT when the wait gave up as designed
  * (the CUDA context stays usable), another code otherwise.  Waits for
  * `stream`.
