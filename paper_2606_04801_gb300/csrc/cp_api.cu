@@ -52,7 +52,9 @@ int ensure_device_tables() {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return CP_ERR_CUDA;
     if (dev < 64 && (g_dev_ready >> dev) & 1u) return CP_OK;
-    if (upload_luts(g_lut2d.data(), g_lut3d.disp.data(), g_lut3d.entry.data()) != cudaSuccess) return CP_ERR_CUDA;
+    const cudaError_t ue = upload_luts(g_lut2d.data(), g_lut3d.disp.data(), g_lut3d.entry.data(), g_lut3d.key.data());
+    if (ue == cudaErrorInvalidValue) return CP_ERR_INTERNAL;  // the table failed its consistency checks
+    if (ue != cudaSuccess) return CP_ERR_CUDA;
     if (dev < 64) g_dev_ready |= 1ull << dev;
     return CP_OK;
 }

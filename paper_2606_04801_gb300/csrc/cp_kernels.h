@@ -30,7 +30,8 @@ int prune_tile_y3d();
 int prune_tile_z3d();
 int set_tuning(int key, int value);
 int get_tuning(int key);
-cudaError_t upload_luts(const uint64_t* lut2d, const uint16_t* disp3d, const uint64_t* entries3d);
+cudaError_t upload_luts(const uint64_t* lut2d, const uint16_t* disp3d, const uint64_t* entries3d,
+                        const uint32_t* keys3d);
 // Tensor maps for TMA loads of 3D planes (one per item that qualifies: width a
 // multiple of 4, 16-byte aligned image, at least 40 x 11 per plane); the other
 // items load their planes with cp.async.

@@ -27,10 +27,18 @@ namespace cp {
 // a warp look up different entries, which constant memory would serialise).
 __device__ uint2 g_lut2d[256];  // same two-word entry layout as the 3D table
 __device__ uint16_t g_disp3d[1 << 12];
-// 3D entries as two 32-bit words for cheap decoding:
-//   x: direct (3 bits) | h0_surv << 3 (6) | dual_surv << 9 (12) | in_l << 21 (8)
-//   y: the eight 4-bit dual codes
-__device__ uint2 g_entries3d[1 << 14];  // perfect-hash slots of the 3D table (128 KB)
+// The 3D table in three parts, each indexed by the perfect-hash slot of the
+// relevant mask (the H0 direct link is not stored: it is the lowest face bit
+// of the relevant mask):
+//   g_codes3d: eight 4-bit fields, field t for top-cell slot t of L(v):
+//              0 = not in L(v); 1 + c = linked locally to top-cell slot c of
+//              v (it dies at zero persistence); 9 = survives locally
+//   g_sbits3d: one bit per slot: the class has H0 or dual survivors
+//   g_surv3d:  h0_surv | dual_surv << 6, read for survivor vertices only
+// The hot part (codes, 64 KB) stays in L1 far better than full entries would.
+__device__ uint32_t g_codes3d[1 << 14];
+__device__ uint32_t g_sbits3d[1 << 9];
+__device__ uint32_t g_surv3d[1 << 14];
 
 namespace {
 
@@ -93,12 +101,12 @@ __device__ __forceinline__ uint32_t collapse3(uint32_t raw) {
 
 // Perfect hash of the 15,935 relevant masks: bucket -> displacement (a copy
 // of the 8 KB displacement table in shared memory) -> slot.
-__device__ __forceinline__ uint2 lookup3(uint32_t rel, const uint16_t* disp) {
+__device__ __forceinline__ uint32_t hash_slot3(uint32_t rel, const uint16_t* disp) {
     const uint32_t b = (rel * 0x9E3779B1u) >> (32 - 12);
     const uint32_t d = disp[b];
-    const uint32_t s = ((rel ^ (d * 0x27D4EB2Fu)) * 0x85EBCA77u) >> (32 - 14);
-    return __ldg(g_entries3d + s);
+    return ((rel ^ (d * 0x27D4EB2Fu)) * 0x85EBCA77u) >> (32 - 14);
 }
+constexpr uint32_t kFaces3 = (1u << 4) | (1u << 10) | (1u << 12) | (1u << 14) | (1u << 16) | (1u << 22);
 
 }  // namespace
 
@@ -145,11 +153,24 @@ struct WarpStage {
     uint32_t rtnode[kCapWR];
 };
 
+// Dual link of a top cell, by (slot t of the top cell in its largest corner's
+// lower star, that corner's 4-bit code field v): x = offset of the linked top
+// cell in the item's top-cell index space; y = the moves (bit 0 -z, 1 -y,
+// 2 -x, 3 +x, 4 +y, 5 +z) and flags
+constexpr uint32_t kMvChain = 1u << 6;    // the only move is -z (the chain of this thread's column)
+constexpr uint32_t kMvRoot = 1u << 7;     // survives locally: a dual root
+constexpr uint32_t kMvInvalid = 1u << 8;  // no corner holds the top cell (non-finite input only)
+
 struct Smem3 {
     float ring[kRing][kSlot];  // first: slots 128-byte aligned (TMA destinations)
     uint64_t bar[kRing];       // mbarrier of each slot (TMA completion)
+    int2 tlink[8 * 16];        // dual links by (t, v), for the current item
+    int32_t h0link[24];        // H0 link offset by face bit n, for the current item
     uint16_t disp[1 << 12];    // displacement table of the 3D perfect hash
-    uint32_t codes[3][kW3][32];
+    uint32_t sbits[1 << 9];    // survivor bit of each slot
+    // per column and plane step: the code fields of the top cells on the +z
+    // side of the column's vertex at z-1 and on the -z side of its vertex at z
+    uint32_t q[3][kW3 + 1][32];
     WarpStage ws[kW3];
 };
 
@@ -389,7 +410,7 @@ struct Col {
     bool in_xy;      // (x, y) inside the image
     bool owned_xy;   // and owned by this CTA
     bool cube_xy;    // (x, y) is the smallest corner of a top cell written by this thread
-    uint32_t bxy;    // boundary bits (2: y==0, 3: y==H-1, 4: x==0, 5: x==W-1)
+    uint32_t bmv;    // moves that leave the image from this column's top cell (-y, -x, +x, +y)
 };
 
 __device__ __forceinline__ uint32_t age_slot(uint32_t t) {
@@ -425,8 +446,7 @@ __device__ __forceinline__ void prune_task3d(Smem3& sm, const ItemTable& tab, co
     cc.in_xy = cc.x >= 0 && cc.y >= 0 && cc.x < it.W && cc.y < it.H;
     cc.owned_xy = cc.in_xy && lane >= 1 && warp >= 1;
     cc.cube_xy = cc.x >= 0 && cc.y >= 0 && cc.x < it.W - 1 && cc.y < it.H - 1 && lane <= 30 && warp <= kW3 - 2;
-    cc.bxy = (cc.y == 0 ? 4u : 0u) | (cc.y == it.H - 1 ? 8u : 0u) | (cc.x == 0 ? 16u : 0u) |
-             (cc.x == it.W - 1 ? 32u : 0u);
+    cc.bmv = (cc.y == 0 ? 2u : 0u) | (cc.x == 0 ? 4u : 0u) | (cc.x == it.W - 2 ? 8u : 0u) | (cc.y == it.H - 2 ? 16u : 0u);
     const int z0 = zc * tab.zchunk3d;
     const int z1 = min(it.D, z0 + tab.zchunk3d);  // owned planes [z0, z1)
     const int zlast = min(z1, it.D - 1);       // entries computed for planes [z0, zlast]
@@ -441,8 +461,31 @@ __device__ __forceinline__ void prune_task3d(Smem3& sm, const ItemTable& tab, co
     if (kTma && threadIdx.x == 0) atomicAdd(&o.ctr->tma_tasks, 1u);
     unsigned long long my_min = ~0ull;
     uint32_t far = 0, far_t = 0;  // last H0 link / dual link written by this thread
-    __syncthreads();  // the rings may still be read by the previous task
+    uint32_t cprev = 0;           // code fields of this column's vertex one plane behind
+    __syncthreads();  // the rings and link tables may still be read by the previous task
     if constexpr (!kTma) ring_init(sm, rp);
+    if (threadIdx.x < 8 * 16) {
+        // top cell in slot t of its largest corner m, linked to slot c of m: the
+        // smallest corners differ by (bit of c) - (bit of t) along each axis
+        const int t = threadIdx.x >> 4, v = threadIdx.x & 15;
+        int2 d;
+        d.x = 0;
+        if (v >= 1 && v <= 8) {
+            const int c = v - 1;
+            const int dz = ((c >> 2) & 1) - ((t >> 2) & 1), dy = ((c >> 1) & 1) - ((t >> 1) & 1), dx = (c & 1) - (t & 1);
+            d.x = dz * int((cc.H - 1u) * cc.W1) + dy * int(cc.W1) + dx;
+            uint32_t mv = (dz < 0 ? 1u : 0u) | (dy < 0 ? 2u : 0u) | (dx < 0 ? 4u : 0u) | (dx > 0 ? 8u : 0u) |
+                          (dy > 0 ? 16u : 0u) | (dz > 0 ? 32u : 0u);
+            d.y = int(mv == 1u ? mv | kMvChain : mv);
+        } else {
+            d.y = int(v == 9 ? kMvRoot : kMvInvalid);
+        }
+        sm.tlink[threadIdx.x] = d;
+    } else if (threadIdx.x < 8 * 16 + 24) {
+        const int n = threadIdx.x - 8 * 16;
+        const int hw = int(cc.HW), w = int(cc.W);
+        sm.h0link[n] = n == 4 ? -hw : (n == 10 ? -w : (n == 12 ? -1 : (n == 14 ? 1 : (n == 16 ? w : (n == 22 ? hw : 0)))));
+    }
 #pragma unroll
     for (int k = -1; k < kAhead; ++k) issue_plane<kTma>(sm, it, z0 + k, rp, cc.HW, src);
     cp_async_wait<kAhead - 2>();  // planes z0-1 .. z0+1 have landed
@@ -454,90 +497,93 @@ __device__ __forceinline__ void prune_task3d(Smem3& sm, const ItemTable& tab, co
     read_nbr(sm.ring[z0 & (kRing - 1)] + xo, warp, lane, B);
     // One plane step: P (plane z-1) and Q (plane z) in registers, R gets plane
     // z+1.  The loop below rotates the three register planes and the three
-    // codes slots (cs: plane z, ps: plane z-1), so nothing is copied.
-    auto step = [&](const Nbr& A, const Nbr& B, Nbr& C, const int z, const int cs, const int ps) {
+    // column-word slots, so nothing is copied.
+    auto step = [&](const Nbr& A, const Nbr& B, Nbr& C, const int z, const int qs) {
         issue_plane<kTma>(sm, it, z + kAhead, rp, cc.HW, src);
         wait_plane<kTma>(sm, it, z + 1, par, o.ctr);
         read_nbr(sm.ring[(z + 1) & (kRing - 1)] + xo, warp, lane, C);
         // ---- lookup of (z, y, x)
         const float cv = B.v[1][1];
-        const uint32_t raw = mask26(A, B, C);
-        const uint2 e = lookup3(collapse3(raw), sm.disp);
-        sm.codes[cs][warp][lane] = e.y;
+        const uint32_t rel = collapse3(mask26(A, B, C));
+        const uint32_t slot = hash_slot3(rel, sm.disp);
+        const uint32_t codes = __ldg(g_codes3d + slot);
+        // top cells on the +z side of (z-1, y, x) are slots 4..7 of that vertex,
+        // those on the -z side of (z, y, x) slots 0..3 of this one
+        const uint32_t q = (cprev & 0xFFFF0000u) | (codes & 0x0000FFFFu);
+        sm.q[qs][warp][lane] = q;
+        cprev = codes;
         const bool owned = cc.owned_xy && z < z1;
         const uint32_t ord = ord_bits(cv);
         const uint32_t vl = (uint32_t(z) * cc.H + uint32_t(cc.y)) * cc.W + uint32_t(cc.x);
         const uint32_t vg = cc.voff + vl;
-        const int direct = int(e.x & 7u);
+        const uint32_t f0 = rel & kFaces3;  // the first edge of L(v) is its lowest face bit
         bool root0 = false;
         if (owned) {
             if (!(fabsf(cv) <= 3.40282347e38f)) set_status(o.ctr, kStNonfinite);
-            if (direct == 7) {
+            if (f0 == 0u) {
                 root0 = true;
                 far = vg;
                 const unsigned long long k = (unsigned long long)(uint64_t(ord) << 32 | vl);
                 my_min = k < my_min ? k : my_min;
             } else {
-                // face slots: (-1,0,0) (0,-1,0) (0,0,-1) (0,0,1) (0,1,0) (1,0,0); a z-1 link
-                // continues the chain that the z-1 neighbour (same thread, previous
-                // step) started
-                const uint32_t mag = (direct == 0 || direct == 5) ? cc.HW : ((direct == 1 || direct == 4) ? cc.W : 1u);
-                const uint32_t u = direct < 3 ? vg - mag : vg + mag;
-                far = (direct == 0 && z > z0) ? far : u;
+                // a link to (z-1, y, x) (face bit 4, the lowest) continues the chain
+                // that the z-1 neighbour (same thread, previous step) started
+                const uint32_t u = vg + uint32_t(sm.h0link[__ffs(f0) - 1]);
+                far = ((f0 & 16u) && z > z0) ? far : u;
                 o.uf0[vg] = far;
             }
         }
-        const uint32_t h0s = owned ? (e.x >> 3) & 0x3Fu : 0u;
-        const uint32_t ds = owned ? (e.x >> 9) & 0xFFFu : 0u;
+        // survivor fields (owned survivor vertices only; rare)
+        const bool sbit = owned && ((sm.sbits[slot >> 5] >> (slot & 31u)) & 1u);
+        const uint32_t sv = sbit ? __ldg(g_surv3d + slot) : 0u;
+        // ---- the top cell with smallest corner (z-1, y, x): exactly one of its
+        // 8 corners (the largest) holds it in its lower star; OR the corners'
+        // fields for it (slot 7-k of corner k = 4dz + 2dy + dx), this row's two
+        // columns now, the next row's after the barrier
+        constexpr uint32_t kM73 = 0xF000F000u, kM62 = 0x0F000F00u, kM51 = 0x00F000F0u, kM40 = 0x000F000Fu;
+        const uint32_t acc_row = (q & kM73) | (__shfl_down_sync(0xFFFFFFFFu, q, 1) & kM62);
         cp_async_wait<kAhead - 2>();  // plane z+2 has landed (for the next step)
-        __syncthreads();              // codes of plane z and image plane z+2 visible
-        // ---- the top cell with smallest corner (z-1, y, x)
+        __syncthreads();              // column words of plane step z and image plane z+2 visible
+        const uint32_t q10 = sm.q[qs][warp + 1][lane];
+        const uint32_t q11 = __shfl_down_sync(0xFFFFFFFFu, q10, 1);
         bool rootT = false;
         uint32_t rt_node = 0;
         uint64_t rt_age = 0;
         if (cc.cube_xy && z > z0) {
-            // largest of the 8 corners under (value, linear index), in index order
-            const float cvals[8] = {A.v[1][1], A.v[1][2], A.v[2][1], A.v[2][2],
-                                    B.v[1][1], B.v[1][2], B.v[2][1], B.v[2][2]};
-            int k = 0;
-            float best = cvals[0];
-#pragma unroll
-            for (int j = 1; j < 8; ++j) {
-                const bool ge = cvals[j] >= best;
-                best = ge ? cvals[j] : best;
-                k = ge ? j : k;
-            }
-            const int dz = k >> 2, dy = (k >> 1) & 1, dx = k & 1;
-            const uint32_t word = sm.codes[dz ? cs : ps][warp + dy][lane + dx];
-            const uint32_t t = uint32_t(7 - k);  // octant of the top cell as seen from m
-            const uint32_t code = (word >> (4u * t)) & 15u;
+            const uint32_t acc = acc_row | (q10 & kM51) | (q11 & kM40);
             const uint32_t self = cc.toff + (uint32_t(z - 1) * (cc.H - 1u) + uint32_t(cc.y)) * cc.W1 + uint32_t(cc.x);
-            const int mz = z - 1 + dz, my = cc.y + dy, mx = cc.x + dx;
-            if (code == 8u) {
+            uint32_t fs = 0;
+            int2 lk = make_int2(0, int(kMvInvalid));
+            if (acc != 0u) {
+                fs = uint32_t(31 - __clz(acc)) & 28u;  // 4 t: the field that is set
+                lk = sm.tlink[(fs << 2) | ((acc >> fs) & 15u)];
+            }
+            const uint32_t bits = uint32_t(lk.y);
+            if (!(bits & (kMvRoot | kMvInvalid))) {
+                const uint32_t bnd = cc.bmv | (z == 1 ? 1u : 0u) | (uint32_t(z) == cc.D - 1u ? 32u : 0u);
+                // a link to (z-2, y, x) continues the chain that this thread wrote for
+                // that top cell in the previous step
+                const bool chain = (bits & kMvChain) && z - 1 > z0;
+                far_t = chain ? far_t : ((bits & bnd) ? cc.OUT : self + uint32_t(lk.x));
+                o.uft[self] = far_t;
+            } else if (bits & kMvRoot) {
                 rootT = true;
                 rt_node = self;
                 far_t = self;
-                const uint32_t mg = cc.voff + (uint32_t(mz) * cc.H + uint32_t(my)) * cc.W + uint32_t(mx);
-                rt_age = make_key(ord_bits(best), mg, age_slot(t));
-            } else if (code < 8u) {
-                // the top cell across: octant `code` of m, smallest corner m - (negative axes)
-                const int tz = mz - int(((code >> 2) & 1u) ^ 1u);
-                const int ty = my - int(((code >> 1) & 1u) ^ 1u);
-                const int tx = mx - int((code & 1u) ^ 1u);
-                const bool out = unsigned(tz) >= cc.D - 1u || unsigned(ty) >= cc.H - 1u || unsigned(tx) >= cc.W1;
-                // a link to (z-2, y, x) continues the chain that this thread wrote for that
-                // top cell in the previous step
-                const bool chain = tz == z - 2 && ty == cc.y && tx == cc.x && z - 1 > z0;
-                far_t = chain ? far_t
-                              : (out ? cc.OUT : cc.toff + (uint32_t(tz) * (cc.H - 1u) + uint32_t(ty)) * cc.W1 + uint32_t(tx));
-                o.uft[self] = far_t;
+                const uint32_t t = fs >> 2, k = 7u - t;  // m = corner k
+                const uint32_t dz = k >> 2, dy = (k >> 1) & 1u, dx = k & 1u;
+                const Nbr& P = dz ? B : A;
+                const float mv = dy ? (dx ? P.v[2][2] : P.v[2][1]) : (dx ? P.v[1][2] : P.v[1][1]);
+                const uint32_t mg = cc.voff + ((uint32_t(z - 1) + dz) * cc.H + uint32_t(cc.y) + dy) * cc.W + uint32_t(cc.x) + dx;
+                rt_age = make_key(ord_bits(mv), mg, age_slot(t));
             } else {
                 far_t = kTag;
                 o.uft[self] = kTag;  // only reachable with non-finite input (flagged): keep the forest well formed
             }
         }
         // ---- stage survivors and roots (rare in smooth fields)
-        if (__any_sync(0xFFFFFFFFu, root0 || rootT || (h0s | ds) != 0u)) {
+        if (__any_sync(0xFFFFFFFFu, root0 || rootT || sv != 0u)) {
+            const uint32_t h0s = sv & 0x3Fu, ds = sv >> 6;
             const unsigned m_r0 = __ballot_sync(0xFFFFFFFFu, root0);
             const unsigned m_rt = __ballot_sync(0xFFFFFFFFu, rootT);
             const uint32_t or0 = __reduce_or_sync(0xFFFFFFFFu, h0s);
@@ -591,11 +637,11 @@ __device__ __forceinline__ void prune_task3d(Smem3& sm, const ItemTable& tab, co
         }
     };
     for (int z = z0;;) {
-        step(A, B, C, z, 0, 2);
+        step(A, B, C, z, 0);
         if (++z > zlast) break;
-        step(B, C, A, z, 1, 0);
+        step(B, C, A, z, 1);
         if (++z > zlast) break;
-        step(C, A, B, z, 2, 1);
+        step(C, A, B, z, 2);
         if (++z > zlast) break;
     }
     cp_async_wait<0>();
@@ -610,6 +656,7 @@ __global__ void __launch_bounds__(kT3, 4) k_prune3d(ItemTable tab, Outs o, const
     const int lane = int(lane_id());
     const unsigned lt = (1u << lane) - 1u;
     for (int i = threadIdx.x; i < (1 << 12); i += kT3) sm.disp[i] = g_disp3d[i];
+    for (int i = threadIdx.x; i < (1 << 9); i += kT3) sm.sbits[i] = g_sbits3d[i];
     if (threadIdx.x == 0) {
         for (int s = 0; s < kRing; ++s) mbar_init(&sm.bar[s], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -967,16 +1014,48 @@ static uint2 pack_entry(uint64_t v) {
     return r;
 }
 
-cudaError_t upload_luts(const uint64_t* lut2d, const uint16_t* disp3d, const uint64_t* entries3d) {
+cudaError_t upload_luts(const uint64_t* lut2d, const uint16_t* disp3d, const uint64_t* entries3d,
+                        const uint32_t* keys3d) {
     uint2 p2[256];
     for (int i = 0; i < 256; ++i) p2[i] = pack_entry(lut2d[i]);
     cudaError_t e = cudaMemcpyToSymbol(g_lut2d, p2, sizeof(p2));
     if (e != cudaSuccess) return e;
     e = cudaMemcpyToSymbol(g_disp3d, disp3d, sizeof(uint16_t) * (1 << 12));
     if (e != cudaSuccess) return e;
-    static uint2 packed[1 << 14];
-    for (int i = 0; i < (1 << 14); ++i) packed[i] = pack_entry(entries3d[i]);
-    return cudaMemcpyToSymbol(g_entries3d, packed, sizeof(packed));
+    // 3D: the device form of each slot's entry (see g_codes3d)
+    static uint32_t codes[1 << 14], surv[1 << 14], sbits[1 << 9];
+    constexpr uint32_t kFaceBits[6] = {4, 10, 12, 14, 16, 22};
+    for (int i = 0; i < (1 << 9); ++i) sbits[i] = 0;
+    for (int i = 0; i < (1 << 14); ++i) {
+        const uint64_t v = entries3d[i];
+        codes[i] = surv[i] = 0;
+        if (keys3d[i] == 0xFFFFFFFFu) continue;  // empty slot
+        const uint32_t rel = keys3d[i];
+        // the kernel takes the direct edge as the lowest face bit of the mask
+        uint32_t direct = 7;
+        for (int s = 0; s < 6 && direct == 7; ++s)
+            if ((rel >> kFaceBits[s]) & 1u) direct = uint32_t(s);
+        if (direct != uint32_t(v & 7u)) return cudaErrorInvalidValue;
+        uint32_t c = 0;
+        for (int t = 0; t < 8; ++t) {
+            const uint32_t code = uint32_t((v >> (9 + 4 * t)) & 0xFu);
+            uint32_t f;
+            if (code == 15u) f = 0;            // not in L(v)
+            else if (code == 8u) f = 9;        // survives locally
+            else if (code < 8u && code != uint32_t(t)) f = code + 1u;
+            else return cudaErrorInvalidValue;
+            c |= f << (4 * t);
+        }
+        codes[i] = c;
+        const uint32_t h0s = uint32_t((v >> 3) & 0x3Fu), ds = uint32_t((v >> 41) & 0xFFFu);
+        surv[i] = h0s | (ds << 6);
+        if (surv[i]) sbits[i >> 5] |= 1u << (i & 31);
+    }
+    e = cudaMemcpyToSymbol(g_codes3d, codes, sizeof(codes));
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpyToSymbol(g_surv3d, surv, sizeof(surv));
+    if (e != cudaSuccess) return e;
+    return cudaMemcpyToSymbol(g_sbits3d, sbits, sizeof(sbits));
 }
 
 cudaError_t launch_prune(const ItemTable& tab, const PruneOuts& po, const TmaMaps& maps, cudaStream_t s) {
