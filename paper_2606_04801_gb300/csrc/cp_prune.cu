@@ -459,6 +459,9 @@ __device__ __forceinline__ void prune_task3d(Smem3& sm, const ItemTable& tab, co
     if constexpr (!kTma) ring_positions(it, x0, y0, rp);
     const int xo = kTma ? (x0 - 2) - src.xs : 0;  // column x0-2 within a slot row
     if (kTma && threadIdx.x == 0) atomicAdd(&o.ctr->tma_tasks, 1u);
+    // global vertex index and top-cell index of this column in plane 0
+    const uint32_t colv = cc.voff + uint32_t(cc.y) * cc.W + uint32_t(cc.x);
+    const uint32_t colt = cc.toff + uint32_t(cc.y) * cc.W1 + uint32_t(cc.x);
     unsigned long long my_min = ~0ull;
     uint32_t far = 0, far_t = 0;  // last H0 link / dual link written by this thread
     uint32_t cprev = 0;           // code fields of this column's vertex one plane behind
@@ -514,8 +517,7 @@ __device__ __forceinline__ void prune_task3d(Smem3& sm, const ItemTable& tab, co
         cprev = codes;
         const bool owned = cc.owned_xy && z < z1;
         const uint32_t ord = ord_bits(cv);
-        const uint32_t vl = (uint32_t(z) * cc.H + uint32_t(cc.y)) * cc.W + uint32_t(cc.x);
-        const uint32_t vg = cc.voff + vl;
+        const uint32_t vg = colv + uint32_t(z) * cc.HW;
         const uint32_t f0 = rel & kFaces3;  // the first edge of L(v) is its lowest face bit
         bool root0 = false;
         if (owned) {
@@ -523,7 +525,7 @@ __device__ __forceinline__ void prune_task3d(Smem3& sm, const ItemTable& tab, co
             if (f0 == 0u) {
                 root0 = true;
                 far = vg;
-                const unsigned long long k = (unsigned long long)(uint64_t(ord) << 32 | vl);
+                const unsigned long long k = (unsigned long long)(uint64_t(ord) << 32 | (vg - uint32_t(it.voff)));
                 my_min = k < my_min ? k : my_min;
             } else {
                 // a link to (z-1, y, x) (face bit 4, the lowest) continues the chain
@@ -551,7 +553,7 @@ __device__ __forceinline__ void prune_task3d(Smem3& sm, const ItemTable& tab, co
         uint64_t rt_age = 0;
         if (cc.cube_xy && z > z0) {
             const uint32_t acc = acc_row | (q10 & kM51) | (q11 & kM40);
-            const uint32_t self = cc.toff + (uint32_t(z - 1) * (cc.H - 1u) + uint32_t(cc.y)) * cc.W1 + uint32_t(cc.x);
+            const uint32_t self = colt + uint32_t(z - 1) * cc.HW1;
             uint32_t fs = 0;
             int2 lk = make_int2(0, int(kMvInvalid));
             if (acc != 0u) {
@@ -574,7 +576,7 @@ __device__ __forceinline__ void prune_task3d(Smem3& sm, const ItemTable& tab, co
                 const uint32_t dz = k >> 2, dy = (k >> 1) & 1u, dx = k & 1u;
                 const Nbr& P = dz ? B : A;
                 const float mv = dy ? (dx ? P.v[2][2] : P.v[2][1]) : (dx ? P.v[1][2] : P.v[1][1]);
-                const uint32_t mg = cc.voff + ((uint32_t(z - 1) + dz) * cc.H + uint32_t(cc.y) + dy) * cc.W + uint32_t(cc.x) + dx;
+                const uint32_t mg = colv + (uint32_t(z - 1) + dz) * cc.HW + dy * uint32_t(it.W) + dx;
                 rt_age = make_key(ord_bits(mv), mg, age_slot(t));
             } else {
                 far_t = kTag;
