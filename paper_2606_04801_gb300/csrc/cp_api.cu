@@ -458,15 +458,35 @@ int single(int ndim, const float* d_image, const int64_t* dims, cp_pair* d_out, 
 void note_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 int device_sm_count() {
-    static int cached[64] = {0};
+    static std::atomic<int> cached[64];
     int dev = 0;
     cudaGetDevice(&dev);
-    if (dev >= 0 && dev < 64 && cached[dev]) return cached[dev];
+    if (dev >= 0 && dev < 64) {
+        const int c = cached[dev].load(std::memory_order_relaxed);
+        if (c) return c;
+    }
     int n = 0;
     cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
     if (n <= 0) n = 1;
-    if (dev >= 0 && dev < 64) cached[dev] = n;
+    if (dev >= 0 && dev < 64) cached[dev].store(n, std::memory_order_relaxed);
     return n;
+}
+
+int device_cached(int slot, int (*init)()) {
+    static std::atomic<int> cache[64][kCacheSlots];
+    static std::mutex mu;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64 || slot < 0 || slot >= kCacheSlots) return init();
+    int v = cache[dev][slot].load(std::memory_order_acquire);
+    if (v) return v;
+    std::lock_guard<std::mutex> lk(mu);
+    v = cache[dev][slot].load(std::memory_order_relaxed);
+    if (!v) {
+        v = init();
+        cache[dev][slot].store(v, std::memory_order_release);
+    }
+    return v;
 }
 
 }  // namespace cp

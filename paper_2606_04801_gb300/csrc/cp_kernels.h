@@ -128,6 +128,10 @@ cudaError_t launch_backward(const cp_pair* pairs, int64_t n, const float* gb, co
                             double* acc, float* grad, int64_t n_pixels, cudaStream_t s);
 
 int device_sm_count();
+// init() run once per device and slot (thread-safe), its result cached: the
+// launch set-up of a kernel (attributes, occupancy-derived grid size).
+enum { kCachePrune3d, kCachePrune2d, kCacheSort, kCacheUf, kCacheRoots, kCacheSlots };
+int device_cached(int slot, int (*init)());
 
 // Kernel launches made by the library (for the benchmark's launch count).
 void note_launches(int n);

@@ -953,16 +953,14 @@ bool encode_plane_map(CUtensorMap* map, const float* img, int64_t D, int64_t H, 
     using Encode = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-    static Encode encode = nullptr;
-    static bool looked = false;
-    if (!looked) {
-        looked = true;
+    static const Encode encode = []() -> Encode {  // looked up once (thread-safe initialisation)
         void* fn = nullptr;
         cudaDriverEntryPointQueryResult q;
         if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) == cudaSuccess &&
             q == cudaDriverEntryPointSuccess)
-            encode = reinterpret_cast<Encode>(fn);
-    }
+            return reinterpret_cast<Encode>(fn);
+        return nullptr;
+    }();
     // row stride a multiple of 16 bytes, 16-byte aligned base, a plane at least one box
     if (!encode || !img || (W & 3) != 0 || (reinterpret_cast<uintptr_t>(img) & 15u) != 0 || W < kRS || H < kRH || D < 2)
         return false;
@@ -1074,19 +1072,18 @@ cudaError_t launch_prune(const ItemTable& tab, const PruneOuts& po, const TmaMap
     o.cap_r0 = po.cap_r0;
     o.cap_rt = po.cap_rt;
     o.ctr = po.ctr;
-    static bool attr_set = false;
-    static int blocks3d = 0, blocks2d = 0;
-    if (!attr_set) {
-        cudaFuncSetAttribute(k_prune2d, cudaFuncAttributeMaxDynamicSharedMemorySize, int(prune_smem2d()));
+    const int blocks3d = device_cached(kCachePrune3d, [] {
         cudaFuncSetAttribute(k_prune3d, cudaFuncAttributeMaxDynamicSharedMemorySize, int(prune_smem3d()));
         int per_sm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_prune3d, kT3, prune_smem3d());
-        blocks3d = device_sm_count() * (per_sm > 0 ? per_sm : 1);
-        int per_sm2 = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, k_prune2d, kW2 * 32, prune_smem2d());
-        blocks2d = device_sm_count() * (per_sm2 > 0 ? per_sm2 : 1);
-        attr_set = true;
-    }
+        return device_sm_count() * (per_sm > 0 ? per_sm : 1);
+    });
+    const int blocks2d = device_cached(kCachePrune2d, [] {
+        cudaFuncSetAttribute(k_prune2d, cudaFuncAttributeMaxDynamicSharedMemorySize, int(prune_smem2d()));
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_prune2d, kW2 * 32, prune_smem2d());
+        return device_sm_count() * (per_sm > 0 ? per_sm : 1);
+    });
     if (tab.tiles2d > 0) {
         const int need2 = (tab.tiles2d + kW2 - 1) / kW2;
         k_prune2d<<<need2 < blocks2d ? need2 : blocks2d, kW2 * 32, prune_smem2d(), s>>>(tab, o);

@@ -259,8 +259,6 @@ __global__ void __launch_bounds__(kT) k_onesweep(const __grid_constant__ SweepAr
     }
 }
 
-int g_sort_blocks = 0;
-
 }  // namespace
 
 size_t sort_status_words(uint32_t cap) { return size_t((cap + kSortTile - 1) / kSortTile + 1) * 256; }
@@ -268,12 +266,12 @@ size_t sort_status_words(uint32_t cap) { return size_t((cap + kSortTile - 1) / k
 cudaError_t sort_keys_multi(const SortBufs* b, int nl, int first_byte, int npasses, uint32_t epoch, cudaStream_t s) {
     if (nl < 1 || nl > 2 || npasses <= 0 || (npasses & 1) || first_byte + npasses > 8) return cudaErrorInvalidValue;
     const size_t smem = sizeof(SortSmem);
-    if (g_sort_blocks == 0) {
-        cudaFuncSetAttribute(k_onesweep, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    const int sort_blocks = device_cached(kCacheSort, [] {
+        cudaFuncSetAttribute(k_onesweep, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sizeof(SortSmem)));
         int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_onesweep, kT, smem);
-        g_sort_blocks = device_sm_count() * (per_sm > 0 ? per_sm : 1);
-    }
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_onesweep, kT, sizeof(SortSmem));
+        return device_sm_count() * (per_sm > 0 ? per_sm : 1);
+    });
     HistArgs h;
     uint32_t max_tiles = 0;
     for (int l = 0; l < 2; ++l) {
@@ -295,7 +293,7 @@ cudaError_t sort_keys_multi(const SortBufs* b, int nl, int first_byte, int npass
     k_hist<<<device_sm_count() * 2, kT, 0, s>>>(h);
     k_hist_scan<<<1, 512, 0, s>>>(b[0].hist, nl > 1 ? b[1].hist : b[0].hist, npasses, nl);
     note_launches(2 + npasses);
-    const int grid = int(max_tiles < uint32_t(g_sort_blocks) ? (max_tiles ? max_tiles : 1) : g_sort_blocks);
+    const int grid = int(max_tiles < uint32_t(sort_blocks) ? (max_tiles ? max_tiles : 1) : sort_blocks);
     for (int p = 0; p < npasses; ++p) {
         SweepArgs a;
         for (int l = 0; l < 2; ++l) {

@@ -702,27 +702,24 @@ __global__ void __launch_bounds__(kT) k_uf(const __grid_constant__ UfKernelArgs 
     }
 }
 
-int g_uf_blocks = 0, g_find_blocks = 0;
-
 int find_blocks() {
-    if (g_find_blocks == 0) {
+    return device_cached(kCacheRoots, [] {
         int per_sm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_roots, kFT, 0);
-        g_find_blocks = device_sm_count() * (per_sm > 0 ? per_sm : 1);
-    }
-    return g_find_blocks;
+        return device_sm_count() * (per_sm > 0 ? per_sm : 1);
+    });
 }
 
 }  // namespace
 
 cudaError_t launch_uf(const ItemTable& tab, const UfParams* p, int nprob, cudaStream_t s) {
     if (nprob < 1 || nprob > 2) return cudaErrorInvalidValue;
-    if (g_uf_blocks == 0) {
+    const int uf_blocks = device_cached(kCacheUf, [] {
         int per_sm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_uf, kT, 0);
-        if (per_sm <= 0) return cudaErrorLaunchOutOfResources;
-        g_uf_blocks = device_sm_count() * per_sm;
-    }
+        return per_sm > 0 ? device_sm_count() * per_sm : -1;
+    });
+    if (uf_blocks <= 0) return cudaErrorLaunchOutOfResources;
     UfKernelArgs args;
     args.tab = tab;
     args.p[0] = p[0];
@@ -732,7 +729,7 @@ cudaError_t launch_uf(const ItemTable& tab, const UfParams* p, int nprob, cudaSt
     // launched through cudaLaunchKernelEx so that it can also be captured
     // into a CUDA graph
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(g_uf_blocks);
+    cfg.gridDim = dim3(uf_blocks);
     cfg.blockDim = dim3(kT);
     cfg.dynamicSmemBytes = 0;
     cfg.stream = s;
