@@ -511,21 +511,32 @@ def main():
     loss = torch.zeros(1, dtype=torch.float64, device=dev)
     bws = lib.cubical_persistence_loss_backward_workspace_size(N)
     bwsp = torch.empty(bws, dtype=torch.uint8, device=dev)
-    cnt = ctypes.c_int64(0)
+    dcount = torch.zeros(1, dtype=torch.int64, device=dev)
 
     def step(src):
+        # forward and loss backward with the pair count kept on the device: no
+        # host round trip inside the step (the device status is checked by
+        # cubical_persistence_stats after the timed steps, and after every
+        # end-to-end step)
         rc = lib.cubical_persistence_3d(
-            ctypes.c_void_p(src.data_ptr()), dims, ctypes.c_void_p(out.data_ptr()), cap, ctypes.byref(cnt), None,
-            ctypes.c_void_p(wsp.data_ptr()), ws_bytes, ms, sp,
+            ctypes.c_void_p(src.data_ptr()), dims, ctypes.c_void_p(out.data_ptr()), cap, None,
+            ctypes.c_void_p(dcount.data_ptr()), ctypes.c_void_p(wsp.data_ptr()), ws_bytes, ms, sp,
         )
         if rc != 0:
             raise cp.CpError(rc, "forward")
         rc = lib.cubical_persistence_loss_backward(
-            ctypes.c_void_p(out.data_ptr()), cnt.value, None, ctypes.c_float(TAU), ctypes.c_void_p(loss.data_ptr()), None,
-            ctypes.c_void_p(grad.data_ptr()), N, ctypes.c_void_p(bwsp.data_ptr()), bws, sp,
+            ctypes.c_void_p(out.data_ptr()), cap, ctypes.c_void_p(dcount.data_ptr()), ctypes.c_float(TAU),
+            ctypes.c_void_p(loss.data_ptr()), None, ctypes.c_void_p(grad.data_ptr()), N, ctypes.c_void_p(bwsp.data_ptr()),
+            bws, sp,
         )
         if rc != 0:
             raise cp.CpError(rc, "loss backward")
+
+    def checked(what):
+        st = cp.api._stats(wsp)  # reads the call's status/count block back
+        if st["rc"] != 0:
+            raise cp.CpError(st["rc"], what)
+        return st
 
     def barrier():
         torch.cuda.synchronize(dev)
@@ -539,7 +550,7 @@ def main():
     for _ in range(args.warmup):
         step(x)
     barrier()
-    st = cp.api._stats(wsp)
+    st = checked("warm-up steps")
     k1_ms = []
     stage_sum = [0.0] * 6
     launches0 = lib.cp_launch_count()
@@ -557,6 +568,7 @@ def main():
                     stage_sum[i] += stage[i]
         ev1.record(stream)
         barrier()
+    checked("timed steps")
     launches = lib.cp_launch_count() - launches0
     elapsed = job_time(ev0.elapsed_time(ev1) / 1e3, ws, dev)
     value = job_value(N, ws, args.steps, elapsed)
@@ -568,42 +580,54 @@ def main():
     # streams).  The serial form (copy, compute, read back, one after the other) is reported beside.
     lib.cp_profile(0)
     e2e_steps = 0 if args.no_e2e else max(3, min(args.steps, 10))
-    e2e_dt = e2e_serial_dt = 1.0
+    e2e_reps = 3  # each form timed three times, alternating; the median is reported
+    e2e_dts, e2e_serial_dts = [], []
     if e2e_steps:
         host = torch.from_numpy(vol).pin_memory()
         xb = [torch.empty_like(x), torch.empty_like(x)]
         cs = torch.cuda.Stream(dev)
         copied = [torch.cuda.Event(), torch.cuda.Event()]
         consumed = [torch.cuda.Event(), torch.cuda.Event()]
-        barrier()
-        t0 = time.perf_counter()
-        with torch.cuda.stream(cs):
-            xb[0].copy_(host, non_blocking=True)
-            copied[0].record(cs)
-        for i in range(e2e_steps):
-            b = i % 2
-            if i + 1 < e2e_steps:
-                nb = 1 - b
-                if i >= 1:
-                    cs.wait_event(consumed[nb])  # step i-1 has finished reading that buffer
-                with torch.cuda.stream(cs):
-                    xb[nb].copy_(host, non_blocking=True)
-                    copied[nb].record(cs)
-            stream.wait_event(copied[b])
-            step(xb[b])
-            consumed[b].record(stream)
-            _ = float(loss.item())
-        barrier()
-        e2e_dt = time.perf_counter() - t0
-        t0 = time.perf_counter()
-        for _ in range(e2e_steps):
-            xb[0].copy_(host, non_blocking=True)
-            step(xb[0])
-            _ = float(loss.item())
-        barrier()
-        e2e_serial_dt = time.perf_counter() - t0
-    e2e_dt = job_time(e2e_dt, ws, dev)
-    e2e_serial_dt = job_time(e2e_serial_dt, ws, dev)
+
+        def pipelined():
+            barrier()
+            t0 = time.perf_counter()
+            with torch.cuda.stream(cs):
+                xb[0].copy_(host, non_blocking=True)
+                copied[0].record(cs)
+            for i in range(e2e_steps):
+                b = i % 2
+                if i + 1 < e2e_steps:
+                    nb = 1 - b
+                    if i >= 1:
+                        cs.wait_event(consumed[nb])  # step i-1 has finished reading that buffer
+                    with torch.cuda.stream(cs):
+                        xb[nb].copy_(host, non_blocking=True)
+                        copied[nb].record(cs)
+                stream.wait_event(copied[b])
+                step(xb[b])
+                consumed[b].record(stream)
+                checked("end-to-end step")
+                _ = float(loss.item())
+            barrier()
+            return time.perf_counter() - t0
+
+        def serial():
+            barrier()
+            t0 = time.perf_counter()
+            for _ in range(e2e_steps):
+                xb[0].copy_(host, non_blocking=True)
+                step(xb[0])
+                checked("end-to-end step")
+                _ = float(loss.item())
+            barrier()
+            return time.perf_counter() - t0
+
+        for _ in range(e2e_reps):
+            e2e_dts.append(pipelined())
+            e2e_serial_dts.append(serial())
+    e2e_dt = job_time(statistics.median(e2e_dts) if e2e_dts else 1.0, ws, dev)
+    e2e_serial_dt = job_time(statistics.median(e2e_serial_dts) if e2e_serial_dts else 1.0, ws, dev)
     e2e = None if not e2e_steps else {
         "value": job_value(N, ws, e2e_steps, e2e_dt),
         "unit": "Mvoxels/s",
@@ -611,6 +635,8 @@ def main():
         "d2h_bytes_per_step": 8 + COUNTERS_BYTES,  # the loss, and the call's status/count block
         "pipeline": "double-buffered: step i+1's H2D copy on a second stream overlaps step i",
         "serial_value": job_value(N, ws, e2e_steps, e2e_serial_dt),
+        "repeats": f"median of {e2e_reps} runs of {e2e_steps} steps per form",
+        "runs_ms_per_step": [round(1e3 * t / e2e_steps, 3) for t in e2e_dts],
     }
     if ws > 1:
         torch.distributed.barrier()
@@ -693,7 +719,7 @@ def main():
         },
         "batched": batched,
         "uf_trace": trace,
-        "counts": {"pairs": int(cnt.value), "h0_survivors": s0, "top_survivors": stp, "h0_roots": r0, "top_roots": rt,
+        "counts": {"pairs": st["pairs"], "h0_survivors": s0, "top_survivors": stp, "h0_roots": r0, "top_roots": rt,
                    "survivor_fraction": (s0 + stp) / N,
                    "h0_rounds": st["h0_rounds"], "top_rounds": st["top_rounds"]},
     }
