@@ -1,4 +1,4 @@
-"""CPU oracle for V-filtration cubical persistence (H0 + top dimension).
+"""CPU oracle for V- and T-filtration cubical persistence (H0 + top dimension).
 
 TEST INFRASTRUCTURE ONLY: the test-suite, the smoke check and the benchmark's
 CPU-baseline leg are the only callers.  The product package never imports
@@ -63,6 +63,8 @@ def _load():
                 ctypes.c_void_p,
                 ctypes.c_int64,
             ]
+            lib.oracle_persistence_t.restype = ctypes.c_int64
+            lib.oracle_persistence_t.argtypes = lib.oracle_persistence.argtypes
             lib.oracle_cell_key.restype = ctypes.c_int
             lib.oracle_cell_key.argtypes = [
                 ctypes.c_void_p,
@@ -94,6 +96,28 @@ def persistence(img, keep_zero: bool = False) -> np.ndarray:
         raise ValueError(f"oracle: {ERRORS.get(int(n), n)}")
     out = np.zeros(int(n), dtype=PAIR_DTYPE)
     m = lib.oracle_persistence(a.ctypes.data, a.ndim, dims.ctypes.data, int(keep_zero), out.ctypes.data, int(n))
+    if m != n:
+        raise RuntimeError("oracle: pair count changed between calls")
+    return out
+
+
+def persistence_t(img, keep_zero: bool = False) -> np.ndarray:
+    """Persistence pairs of a 2D or 3D float32 image under the T-filtration
+    (pixel values on the top cells; see ``cp_oracle.c``).
+
+    Same output as ``persistence``; cells are indices in the doubled grid of
+    the T-complex (extents 2n+1), pixels the top cells the cells enter with.
+    """
+    lib = _load()
+    a = np.ascontiguousarray(img, dtype=np.float32)
+    if a.ndim not in (2, 3):
+        raise ValueError("image must be 2D or 3D")
+    dims = np.asarray(a.shape, dtype=np.int64)
+    n = lib.oracle_persistence_t(a.ctypes.data, a.ndim, dims.ctypes.data, int(keep_zero), None, 0)
+    if n < 0:
+        raise ValueError(f"oracle: {ERRORS.get(int(n), n)}")
+    out = np.zeros(int(n), dtype=PAIR_DTYPE)
+    m = lib.oracle_persistence_t(a.ctypes.data, a.ndim, dims.ctypes.data, int(keep_zero), out.ctypes.data, int(n))
     if m != n:
         raise RuntimeError("oracle: pair count changed between calls")
     return out

@@ -367,3 +367,268 @@ int oracle_cell_key(const float *img, int ndim, const int64_t *dims, int64_t cel
     *dim = k.dim;
     return 0;
 }
+
+/* ==================================================================== T-filtration
+ *
+ * T-construction (Sec. 2.2): the pixel values sit on the top cells -- the
+ * unit squares (2D) or cubes (3D) of the lattice [0,H]x[0,W] (x[0,D]) -- and
+ * every lower-dimensional cell takes the smallest value among the top cells
+ * that contain it (f_T).  The paper leaves the T-filtration to future work
+ * (Sec. 6); the refined order used here is the reading that mirrors the V
+ * one: a cell enters with the top cell of smallest (value, linear pixel
+ * index) containing it, p(s); inside the set of cells entering with one top
+ * cell, lower dimension first, then ascending doubled-grid index:
+ *   R_T(s) = (f(p), p, dim s, idx s).
+ * It is a filtration order: a face is contained in every top cell that holds
+ * its coface, so its p is no later, and when equal its dimension is lower.
+ * The doubled grid of the T-complex has extents 2n+1 along each image axis
+ * (lattice points at even, pixels at odd coordinates); the cell with doubled
+ * coordinates (Z, Y, X) has index (Z*(2H+1) + Y)*(2W+1) + X (Z = 0 in 2D).
+ *   - H0: Kruskal over every edge in ascending R_T; a merging edge kills the
+ *     younger root (larger R_T), a root being the oldest vertex of its class.
+ *   - Top dimension: the dual union-find of Sec. 3.1 / Appendix A on this
+ *     complex: top cells plus the outside vertex, facets in descending R_T,
+ *     the younger representative (smaller R_T) paired with the facet.
+ *   - Pairs with equal birth and death values are omitted; one essential H0
+ *     class (the oldest vertex, +inf).
+ * Pixels carried by the pairs are p(birth cell) and p(death cell).
+ */
+typedef struct {
+    const float *f;
+    int ndim;
+    int64_t D, H, W;    /* pixel extents, D = 1 in 2D */
+    int64_t GD, GH, GW; /* doubled extents: 2n+1 per image axis, GD = 1 in 2D */
+} tgrid_t;
+
+static void tcell_coords(const tgrid_t *g, int64_t c, int64_t *Z, int64_t *Y, int64_t *X) {
+    *X = c % g->GW;
+    *Y = (c / g->GW) % g->GH;
+    *Z = c / (g->GW * g->GH);
+}
+
+static int tcell_dim(const tgrid_t *g, int64_t c) {
+    int64_t Z, Y, X;
+    tcell_coords(g, c, &Z, &Y, &X);
+    return (int)((g->ndim == 3 ? (Z & 1) : 0) + (Y & 1) + (X & 1));
+}
+
+/* pixels along one axis that contain doubled coordinate C: one at an odd C,
+   the (up to) two on either side at an even C */
+static int axis_pixels(int64_t C, int64_t n, int64_t *k) {
+    if (C & 1) {
+        k[0] = (C - 1) / 2;
+        return 1;
+    }
+    int m = 0;
+    if (C / 2 - 1 >= 0) k[m++] = C / 2 - 1;
+    if (C / 2 < n) k[m++] = C / 2;
+    return m;
+}
+
+/* p(s): the top cell containing s that is smallest under (f, linear index). */
+static int64_t tcell_min_pixel(const tgrid_t *g, int64_t c) {
+    int64_t Z, Y, X, kz[2] = {0, 0}, ky[2], kx[2];
+    tcell_coords(g, c, &Z, &Y, &X);
+    int nz = g->ndim == 3 ? axis_pixels(Z, g->D, kz) : 1;
+    int ny = axis_pixels(Y, g->H, ky), nx = axis_pixels(X, g->W, kx);
+    int64_t best = -1;
+    for (int a = 0; a < nz; ++a)
+        for (int b = 0; b < ny; ++b)
+            for (int e = 0; e < nx; ++e) {
+                int64_t p = (kz[a] * g->H + ky[b]) * g->W + kx[e];
+                if (best < 0 || g->f[p] < g->f[best] || (g->f[p] == g->f[best] && p < best)) best = p;
+            }
+    return best;
+}
+
+static rkey tcell_key(const tgrid_t *g, int64_t c) {
+    rkey k;
+    k.m = tcell_min_pixel(g, c);
+    k.fm = g->f[k.m];
+    k.dim = tcell_dim(g, c);
+    k.idx = c;
+    return k;
+}
+
+/* Dense id of a lattice point (all image-axis coordinates even). */
+static int64_t tvertex_id(const tgrid_t *g, int64_t Z, int64_t Y, int64_t X) {
+    return ((Z / 2) * (g->H + 1) + Y / 2) * (g->W + 1) + X / 2;
+}
+
+/* Dense id of a top cell (all image-axis coordinates odd). */
+static int64_t tpixel_id(const tgrid_t *g, int64_t Z, int64_t Y, int64_t X) {
+    int64_t z = g->ndim == 3 ? (Z - 1) / 2 : 0;
+    return (z * g->H + (Y - 1) / 2) * g->W + (X - 1) / 2;
+}
+
+static int h0_pairs_t(const tgrid_t *g, oracle_pair *out, int64_t cap, int64_t *n, int keep_zero) {
+    int64_t ncells = g->GD * g->GH * g->GW;
+    int64_t NV = (g->ndim == 3 ? g->D + 1 : 1) * (g->H + 1) * (g->W + 1);
+    int64_t nedges = 0;
+    for (int64_t c = 0; c < ncells; ++c)
+        if (tcell_dim(g, c) == 1) ++nedges;
+    rkey *edges = (rkey *)malloc(sizeof(rkey) * (size_t)(nedges ? nedges : 1));
+    rkey *vkey = (rkey *)malloc(sizeof(rkey) * (size_t)NV);
+    int64_t *parent = (int64_t *)malloc(sizeof(int64_t) * (size_t)NV);
+    if (!edges || !vkey || !parent) {
+        free(edges);
+        free(vkey);
+        free(parent);
+        return ORACLE_ENOMEM;
+    }
+    int64_t k = 0;
+    for (int64_t c = 0; c < ncells; ++c) {
+        int dim = tcell_dim(g, c);
+        if (dim == 1) edges[k++] = tcell_key(g, c);
+        if (dim == 0) {
+            int64_t Z, Y, X;
+            tcell_coords(g, c, &Z, &Y, &X);
+            vkey[tvertex_id(g, Z, Y, X)] = tcell_key(g, c);
+        }
+    }
+    qsort(edges, (size_t)nedges, sizeof(rkey), rkey_cmp);
+    for (int64_t v = 0; v < NV; ++v) parent[v] = v;
+    for (int64_t i = 0; i < nedges; ++i) {
+        int64_t Z, Y, X;
+        tcell_coords(g, edges[i].idx, &Z, &Y, &X);
+        /* the two endpoints: the one odd coordinate stepped down and up */
+        int64_t a, b;
+        if (X & 1) {
+            a = tvertex_id(g, Z, Y, X - 1);
+            b = tvertex_id(g, Z, Y, X + 1);
+        } else if (Y & 1) {
+            a = tvertex_id(g, Z, Y - 1, X);
+            b = tvertex_id(g, Z, Y + 1, X);
+        } else {
+            a = tvertex_id(g, Z - 1, Y, X);
+            b = tvertex_id(g, Z + 1, Y, X);
+        }
+        int64_t ra = uf_find(parent, a), rb = uf_find(parent, b);
+        if (ra == rb) continue;
+        int64_t young = rkey_less(&vkey[ra], &vkey[rb]) ? rb : ra;
+        int64_t old = young == ra ? rb : ra;
+        parent[young] = old;
+        emit(out, cap, n, keep_zero, vkey[young].fm, edges[i].fm, vkey[young].idx, edges[i].idx, vkey[young].m,
+             edges[i].m, 0);
+    }
+    int64_t oldest = 0;
+    for (int64_t v = 1; v < NV; ++v)
+        if (rkey_less(&vkey[v], &vkey[oldest])) oldest = v;
+    emit(out, cap, n, 1, vkey[oldest].fm, INFINITY, vkey[oldest].idx, -1, vkey[oldest].m, -1, 0);
+    free(edges);
+    free(vkey);
+    free(parent);
+    return 0;
+}
+
+static int top_pairs_t(const tgrid_t *g, oracle_pair *out, int64_t cap, int64_t *n, int keep_zero) {
+    int d = g->ndim;
+    int64_t ncells = g->GD * g->GH * g->GW;
+    int64_t T = g->D * g->H * g->W;
+    int64_t OUT = T;
+    int64_t nfacets = 0;
+    for (int64_t c = 0; c < ncells; ++c)
+        if (tcell_dim(g, c) == d - 1) ++nfacets;
+    rkey *facets = (rkey *)malloc(sizeof(rkey) * (size_t)(nfacets ? nfacets : 1));
+    int64_t *parent = (int64_t *)malloc(sizeof(int64_t) * (size_t)(T + 1));
+    rkey *rep = (rkey *)malloc(sizeof(rkey) * (size_t)(T + 1));
+    int64_t *tcell = (int64_t *)malloc(sizeof(int64_t) * (size_t)(T + 1));
+    if (!facets || !parent || !rep || !tcell) {
+        free(facets);
+        free(parent);
+        free(rep);
+        free(tcell);
+        return ORACLE_ENOMEM;
+    }
+    int64_t k = 0;
+    for (int64_t c = 0; c < ncells; ++c) {
+        int dim = tcell_dim(g, c);
+        if (dim == d - 1) facets[k++] = tcell_key(g, c);
+        if (dim == d) {
+            int64_t Z, Y, X;
+            tcell_coords(g, c, &Z, &Y, &X);
+            int64_t t = tpixel_id(g, Z, Y, X);
+            rep[t] = tcell_key(g, c);
+            tcell[t] = c;
+        }
+    }
+    qsort(facets, (size_t)nfacets, sizeof(rkey), rkey_cmp);
+    for (int64_t t = 0; t <= T; ++t) parent[t] = t;
+    for (int64_t i = nfacets - 1; i >= 0; --i) {
+        int64_t Z, Y, X;
+        tcell_coords(g, facets[i].idx, &Z, &Y, &X);
+        int64_t C[3] = {Z, Y, X}, G[3] = {g->GD, g->GH, g->GW};
+        int64_t co[2];
+        int nco = 0;
+        for (int ax = 3 - d; ax < 3; ++ax) {
+            if (C[ax] & 1) continue;
+            for (int s = -1; s <= 1; s += 2) {
+                int64_t q[3] = {C[0], C[1], C[2]};
+                q[ax] += s;
+                co[nco++] = (q[ax] < 0 || q[ax] >= G[ax]) ? OUT : tpixel_id(g, q[0], q[1], q[2]);
+            }
+        }
+        int64_t ra = uf_find(parent, co[0]), rb = uf_find(parent, co[1]);
+        if (ra == rb) continue;
+        int64_t young, old;
+        if (ra == OUT) {
+            young = rb;
+            old = ra;
+        } else if (rb == OUT) {
+            young = ra;
+            old = rb;
+        } else if (rkey_less(&rep[ra], &rep[rb])) {
+            young = ra;
+            old = rb;
+        } else {
+            young = rb;
+            old = ra;
+        }
+        parent[young] = old;
+        emit(out, cap, n, keep_zero, facets[i].fm, rep[young].fm, facets[i].idx, tcell[young], facets[i].m,
+             rep[young].m, d - 1);
+    }
+    free(facets);
+    free(parent);
+    free(rep);
+    free(tcell);
+    return 0;
+}
+
+/*
+ * Persistence pairs of one image under the T-filtration.  Same arguments,
+ * output and errors as oracle_persistence; every extent may be 1 here (a
+ * single top cell is a complex), cells are indices in the T doubled grid.
+ */
+int64_t oracle_persistence_t(const float *img, int ndim, const int64_t *dims, int keep_zero, oracle_pair *out,
+                             int64_t cap) {
+    if (!img || !dims || (ndim != 2 && ndim != 3)) return ORACLE_EARG;
+    tgrid_t g;
+    g.ndim = ndim;
+    g.D = ndim == 3 ? dims[0] : 1;
+    g.H = dims[ndim - 2];
+    g.W = dims[ndim - 1];
+    if (g.H < 1 || g.W < 1 || g.D < 1) return ORACLE_EARG;
+    g.GD = ndim == 3 ? 2 * g.D + 1 : 1;
+    g.GH = 2 * g.H + 1;
+    g.GW = 2 * g.W + 1;
+    int64_t N = g.D * g.H * g.W;
+    float *f = (float *)malloc(sizeof(float) * (size_t)N);
+    if (!f) return ORACLE_ENOMEM;
+    for (int64_t i = 0; i < N; ++i) {
+        float x = img[i];
+        if (!isfinite(x)) {
+            free(f);
+            return ORACLE_ENONFINITE;
+        }
+        f[i] = x == 0.0f ? 0.0f : x;
+    }
+    g.f = f;
+    int64_t n = 0;
+    int rc = h0_pairs_t(&g, out, cap, &n, keep_zero);
+    if (rc == 0) rc = top_pairs_t(&g, out, cap, &n, keep_zero);
+    free(f);
+    if (rc) return rc;
+    if (out && n <= cap) qsort(out, (size_t)n, sizeof(oracle_pair), pair_cmp);
+    return n;
+}
