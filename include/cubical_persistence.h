@@ -158,6 +158,40 @@ int cubical_persistence_3d(const float *d_image, const int64_t dims[3], cp_pair 
                            int64_t max_survivors, void *stream);
 
 /*
+ * T-filtration (the T-construction of Sec. 2.2; the paper leaves it to future
+ * work in Sec. 6): the pixel values sit on the top cells of the lattice
+ * complex [0,H]x[0,W] (x[0,D]), and every other cell takes the smallest value
+ * of the top cells that contain it.  Refined order: a cell enters with the
+ * top cell of smallest (value, linear pixel index) that contains it, then by
+ * dimension, then by index in the T doubled grid, whose extents are 2n+1 per
+ * axis (lattice points at even, pixels at odd coordinates; the cell with
+ * doubled coordinates (Z, Y, X) has index (Z*(2H+1) + Y)*(2W+1) + X, Z = 0
+ * in 2D).  Pairs: H0 (essential class: the oldest vertex, death +inf, death
+ * cell -1) and the top dimension (H1 in 2D, H2 in 3D); pixels are the top
+ * cells the birth and death cells enter with, so the backward entries apply
+ * unchanged.
+ * Computed by duality with the V pipeline on J = -image, flipped along every
+ * axis, inside a one-voxel frame below every value: T-H0 is the V top
+ * dimension of J, the T top dimension is V-H0 of J.
+ *  - dims: every extent >= 1; (D+2)(H+2)(W+2) (3D) or (H+2)(W+2) (2D) at
+ *    most 2^27.
+ *  - Every pixel must be below the largest finite float (the frame value
+ *    lies below -max): otherwise CP_ERR_NONFINITE, as for NaN and +-inf.
+ *  - capacity: D*H*W + (D+1)(H+1)(W+1) always suffices.
+ *  - d_workspace: ws_bytes >= cubical_persistence_t_workspace_size(); it
+ *    holds the V workspace of J (so cubical_persistence_stats() reads this
+ *    call's counters from it), then J.
+ * Other arguments, ownership and errors as for cubical_persistence_2d.
+ */
+size_t cubical_persistence_t_workspace_size(int ndim, const int64_t *dims, int64_t max_survivors);
+int cubical_persistence_t_2d(const float *d_image, const int64_t dims[2], cp_pair *d_out_pairs, int64_t capacity,
+                             int64_t *h_out_count, int64_t *d_out_count, void *d_workspace, size_t ws_bytes,
+                             int64_t max_survivors, void *stream);
+int cubical_persistence_t_3d(const float *d_image, const int64_t dims[3], cp_pair *d_out_pairs, int64_t capacity,
+                             int64_t *h_out_count, int64_t *d_out_count, void *d_workspace, size_t ws_bytes,
+                             int64_t max_survivors, void *stream);
+
+/*
  * Batched form: n_items independent images and volumes of any sizes in one
  * pass (one lookup pass, one sort and one union-find per dimension for the
  * whole batch; unions never cross items).

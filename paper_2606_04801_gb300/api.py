@@ -26,15 +26,15 @@ def _stream_ptr(device) -> int:
     return int(torch.cuda.current_stream(device).cuda_stream)
 
 
-def _check_image(img: torch.Tensor):
+def _check_image(img: torch.Tensor, min_extent: int = 2):
     if not isinstance(img, torch.Tensor) or not img.is_cuda:
         raise TypeError("image must be a CUDA tensor")
     if img.dtype != torch.float32:
         raise TypeError("image must be float32")
     if img.dim() not in (2, 3):
         raise ValueError("image must be 2D (H, W) or 3D (D, H, W)")
-    if any(s < 2 for s in img.shape):
-        raise ValueError("every axis must be at least 2 long")
+    if any(s < min_extent for s in img.shape):
+        raise ValueError(f"every axis must be at least {min_extent} long")
 
 
 @dataclass
@@ -98,23 +98,40 @@ def _grow(st: dict, ms: int, n_total: int) -> int:
     return int(need * 1.25) + 65536
 
 
-def persistence(img: torch.Tensor, max_survivors: int = 0, with_stats: bool = False) -> Diagram:
-    """Exact H0 and top-dimension pairs of one image or volume (sorted by (dim, birth cell))."""
-    _check_image(img)
+def persistence(img: torch.Tensor, max_survivors: int = 0, with_stats: bool = False, filtration: str = "V") -> Diagram:
+    """Exact H0 and top-dimension pairs of one image or volume (sorted by (dim, birth cell)).
+
+    filtration "V": pixels are the vertices, a cell takes the largest value of
+    its vertices.  "T": pixels are the top cells, a cell takes the smallest
+    value of the top cells that contain it (cells then index the T doubled
+    grid, extents 2n+1; every extent may be 1)."""
+    if filtration not in ("V", "T"):
+        raise ValueError("filtration must be 'V' or 'T'")
+    _check_image(img, min_extent=1 if filtration == "T" else 2)
     lib = _lib.load()
     img = img.contiguous()
     nd = img.dim()
     dims = (ctypes.c_int64 * nd)(*img.shape)
     n = img.numel()
-    fn = lib.cubical_persistence_2d if nd == 2 else lib.cubical_persistence_3d
+    tmode = filtration == "T"
+    if tmode:
+        fn = lib.cubical_persistence_t_2d if nd == 2 else lib.cubical_persistence_t_3d
+        wsize = lib.cubical_persistence_t_workspace_size
+        n_all = n + int(np.prod([s + 1 for s in img.shape]))
+        n_j = int(np.prod([s + 2 for s in img.shape]))
+    else:
+        fn = lib.cubical_persistence_2d if nd == 2 else lib.cubical_persistence_3d
+        wsize = lib.cubical_persistence_workspace_size
+        n_all = n + int(np.prod([s - 1 for s in img.shape])) + 1
+        n_j = n
     ms = int(max_survivors)
     for _ in range(4):
-        ws_bytes = lib.cubical_persistence_workspace_size(nd, dims, ms)
+        ws_bytes = wsize(nd, dims, ms)
         if ws_bytes == 0:
             raise CpError(_lib.CP_ERR_ARG, "workspace size")
         ws = torch.empty(ws_bytes, dtype=torch.uint8, device=img.device)
-        eff = ms if ms > 0 else n // 2 + 65536
-        cap = min(n + int(np.prod([s - 1 for s in img.shape])) + 1, eff + 4096)
+        eff = ms if ms > 0 else n_j // 2 + 65536
+        cap = min(n_all, eff + 4096)
         out = torch.empty((cap, 8), dtype=torch.int32, device=img.device)
         cnt = ctypes.c_int64(0)
         rc = fn(
@@ -122,10 +139,10 @@ def persistence(img: torch.Tensor, max_survivors: int = 0, with_stats: bool = Fa
             ctypes.c_void_p(ws.data_ptr()), ws_bytes, ms, ctypes.c_void_p(_stream_ptr(img.device)),
         )
         if rc == CP_ERR_CAPACITY:
-            ms = _grow(_stats(ws), eff, n)
+            ms = _grow(_stats(ws), eff, n_j)
             continue
         if rc != CP_OK:
-            raise CpError(rc, "cubical_persistence")
+            raise CpError(rc, "cubical_persistence" + ("_t" if tmode else ""))
         return Diagram(out[: cnt.value], _stats(ws) if with_stats else None)
     raise CpError(CP_ERR_CAPACITY, "cubical_persistence (after growing the workspace)")
 
@@ -196,8 +213,8 @@ def pairs_backward(raw: torch.Tensor, grad_birth: torch.Tensor, grad_death: torc
 
 class _DiagramFn(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, img, max_survivors):
-        d = persistence(img.detach(), max_survivors)
+    def forward(ctx, img, max_survivors, filtration):
+        d = persistence(img.detach(), max_survivors, filtration=filtration)
         ctx.save_for_backward(d.raw)
         ctx.shape = img.shape
         ctx.mark_non_differentiable(d.raw)
@@ -212,9 +229,9 @@ class _DiagramFn(torch.autograd.Function):
         if gd is None:
             gd = torch.zeros(raw.shape[0], dtype=torch.float32, device=raw.device)
         g = pairs_backward(raw, gb, gd, n)
-        return g.view(ctx.shape), None
+        return g.view(ctx.shape), None, None
 
 
-def diagram(img: torch.Tensor, max_survivors: int = 0):
-    """(birth, death, raw): birth and death are differentiable in img."""
-    return _DiagramFn.apply(img, max_survivors)
+def diagram(img: torch.Tensor, max_survivors: int = 0, filtration: str = "V"):
+    """(birth, death, raw): birth and death are differentiable in img (V or T filtration)."""
+    return _DiagramFn.apply(img, max_survivors, filtration)

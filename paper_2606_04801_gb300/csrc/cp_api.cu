@@ -199,8 +199,15 @@ int status_to_code(uint32_t st) {
     return CP_OK;
 }
 
+// T-filtration calls: the original image's extents and the frame-value key
+// (run() then maps the pairs of J back before the output sort).
+struct TMode {
+    TDims dims;
+    const uint32_t* acc;
+};
+
 int run(const Plan& P, cp_pair* d_out, int64_t capacity, int64_t* h_out_count, int64_t* d_out_count, void* ws,
-        size_t ws_bytes, cudaStream_t s, bool prune_only = false) {
+        size_t ws_bytes, cudaStream_t s, bool prune_only = false, const TMode* tm = nullptr) {
     if (!ws || ws_bytes < P.bytes || (!d_out && capacity > 0) || capacity < 0) return CP_ERR_ARG;
     int rc = ensure_device_tables();
     if (rc != CP_OK) return rc;
@@ -413,9 +420,12 @@ int run(const Plan& P, cp_pair* d_out, int64_t capacity, int64_t* h_out_count, i
     int cell_bits = 1, item_bits = 0;
     for (int i = 0; i < P.tab.n; ++i) {
         const Item& it = P.tab.it[i];
-        const int64_t G = int64_t(2 * it.D - 1) * (2 * it.H - 1) * (2 * it.W - 1);
+        int64_t G = int64_t(2 * it.D - 1) * (2 * it.H - 1) * (2 * it.W - 1);
+        if (tm)  // the T-complex of the original image (odd extents: the all-ones key is never a cell)
+            G = (tm->dims.ndim == 3 ? 2 * tm->dims.D + 1 : 1) * (2 * tm->dims.H + 1) * (2 * tm->dims.W + 1);
         while ((int64_t(1) << cell_bits) < G) ++cell_bits;
     }
+    if (tm) CP_TRY(launch_t_map(pairs, &ctr->n_pairs, P.cap_p, tm->dims, tm->acc, cell_bits, &ctr->t_keep, s));
     while ((1 << item_bits) < P.tab.n) ++item_bits;
     int pair_passes = (item_bits + 1 + cell_bits + 7) / 8;
     pair_passes += pair_passes & 1;  // an even count leaves the result in place
@@ -428,7 +438,8 @@ int run(const Plan& P, cp_pair* d_out, int64_t capacity, int64_t* h_out_count, i
     sb.cap = P.cap_p;
     sb.tile_ctr = ctr->sort_tile + 16;
     CP_TRY(sort_keys(sb, 0, pair_passes, 17, s));
-    CP_TRY(launch_gather(pairs, pvals, &ctr->n_pairs, P.cap_p, d_out, capacity, d_out_count, ctr, s));
+    CP_TRY(launch_gather(pairs, pvals, tm ? &ctr->t_keep : &ctr->n_pairs, P.cap_p, d_out, capacity, d_out_count, ctr,
+                         s));
     mark(6, s);
 #undef CP_TRY
     if (h_out_count) {
@@ -451,6 +462,61 @@ int single(int ndim, const float* d_image, const int64_t* dims, cp_pair* d_out, 
     int rc = make_plan(1, &nd, d3, &d_image, max_survivors, P);
     if (rc != CP_OK) return rc;
     return run(P, d_out, capacity, h_out_count, d_out_count, ws, ws_bytes, static_cast<cudaStream_t>(stream));
+}
+
+// T-filtration: workspace = [the V workspace of J][256 B scratch][J].
+
+bool t_extents(int ndim, const int64_t* dims, TDims& t, int64_t jd3[3]) {
+    if ((ndim != 2 && ndim != 3) || !dims) return false;
+    t.ndim = ndim;
+    t.D = ndim == 3 ? dims[0] : 1;
+    t.H = dims[ndim - 2];
+    t.W = dims[ndim - 1];
+    if (t.D < 1 || t.H < 1 || t.W < 1) return false;
+    jd3[0] = ndim == 3 ? t.D + 2 : 1;
+    jd3[1] = t.H + 2;
+    jd3[2] = t.W + 2;
+    return true;
+}
+
+size_t t_workspace(int ndim, const int64_t* dims, int64_t max_survivors, size_t* v_bytes) {
+    TDims t;
+    int64_t jd3[3];
+    if (!t_extents(ndim, dims, t, jd3)) return 0;
+    int32_t nd = ndim;
+    Plan P;
+    if (make_plan(1, &nd, jd3, nullptr, max_survivors, P) != CP_OK) return 0;
+    if (v_bytes) *v_bytes = P.bytes;
+    return align_up(P.bytes) + 256 + sizeof(float) * size_t(jd3[0] * jd3[1] * jd3[2]);
+}
+
+int t_single(int ndim, const float* d_image, const int64_t* dims, cp_pair* d_out, int64_t capacity,
+             int64_t* h_out_count, int64_t* d_out_count, void* ws, size_t ws_bytes, int64_t max_survivors,
+             void* stream) {
+    if (!d_image || !ws) return CP_ERR_ARG;
+    TDims t;
+    int64_t jd3[3];
+    if (!t_extents(ndim, dims, t, jd3)) return CP_ERR_ARG;
+    size_t v_bytes = 0;
+    const size_t need = t_workspace(ndim, dims, max_survivors, &v_bytes);
+    if (need == 0) return CP_ERR_ARG;
+    if (ws_bytes < need) return CP_ERR_ARG;
+    int rc = ensure_device_tables();
+    if (rc != CP_OK) return rc;
+    char* base = static_cast<char*>(ws);
+    uint32_t* acc = reinterpret_cast<uint32_t*>(base + align_up(v_bytes));
+    float* J = reinterpret_cast<float*>(base + align_up(v_bytes) + 256);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (launch_t_build(d_image, t, J, acc, s) != cudaSuccess) return CP_ERR_CUDA;
+    int32_t nd = ndim;
+    const float* jimg = J;
+    Plan P;
+    rc = make_plan(1, &nd, jd3, &jimg, max_survivors, P);
+    if (rc != CP_OK) return rc;
+    TMode tm;
+    tm.dims = t;
+    tm.acc = acc;
+    return run(P, d_out, capacity, h_out_count, d_out_count, ws, v_bytes, s, false, &tm);
 }
 
 }  // namespace
@@ -550,6 +616,24 @@ int cubical_persistence_3d(const float* d_image, const int64_t dims[3], cp_pair*
                            int64_t max_survivors, void* stream) {
     return single(3, d_image, dims, d_out_pairs, capacity, h_out_count, d_out_count, d_workspace, ws_bytes,
                   max_survivors, stream);
+}
+
+size_t cubical_persistence_t_workspace_size(int ndim, const int64_t* dims, int64_t max_survivors) {
+    return t_workspace(ndim, dims, max_survivors, nullptr);
+}
+
+int cubical_persistence_t_2d(const float* d_image, const int64_t dims[2], cp_pair* d_out_pairs, int64_t capacity,
+                             int64_t* h_out_count, int64_t* d_out_count, void* d_workspace, size_t ws_bytes,
+                             int64_t max_survivors, void* stream) {
+    return t_single(2, d_image, dims, d_out_pairs, capacity, h_out_count, d_out_count, d_workspace, ws_bytes,
+                    max_survivors, stream);
+}
+
+int cubical_persistence_t_3d(const float* d_image, const int64_t dims[3], cp_pair* d_out_pairs, int64_t capacity,
+                             int64_t* h_out_count, int64_t* d_out_count, void* d_workspace, size_t ws_bytes,
+                             int64_t max_survivors, void* stream) {
+    return t_single(3, d_image, dims, d_out_pairs, capacity, h_out_count, d_out_count, d_workspace, ws_bytes,
+                    max_survivors, stream);
 }
 
 int cubical_persistence_debug_prune(int n_items, const float* const* h_images, const int32_t* ndims,

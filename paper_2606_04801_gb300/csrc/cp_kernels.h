@@ -119,6 +119,18 @@ cudaError_t launch_uf(const ItemTable& tab, const UfParams* p, int nprob, cudaSt
 // ---- K4 emission, K5 backward
 cudaError_t launch_init(const ItemTable& tab, Counters* ctr, uint32_t* uft, uint64_t* aget, uint64_t* rest,
                         cudaStream_t s);
+// T-filtration by duality (cp_tfilt.cu): the image I's extents (D = 1 in 2D).
+struct TDims {
+    int ndim;
+    int64_t D, H, W;
+};
+// acc <- the largest ord key of I; J <- -I flipped along every axis, inside a
+// one-voxel frame below every value of -I (extents +2 along each image axis).
+cudaError_t launch_t_build(const float* img, const TDims& t, float* J, uint32_t* acc, cudaStream_t s);
+// V pairs of J -> T pairs of I, in place; the frame's class gets the last sort
+// key (birth cell 2^cell_bits - 1) and *d_keep the count without it.
+cudaError_t launch_t_map(cp_pair* pairs, const uint32_t* d_n, uint32_t cap, const TDims& t, const uint32_t* acc,
+                         int cell_bits, uint32_t* d_keep, cudaStream_t s);
 cudaError_t launch_essential(const ItemTable& tab, Counters* ctr, cp_pair* pairs, uint32_t pair_cap, cudaStream_t s);
 cudaError_t launch_pair_keys(const cp_pair* pairs, const uint32_t* d_n, uint32_t cap, uint64_t* keys, uint32_t* vals,
                              int cell_bits, cudaStream_t s);

@@ -1,0 +1,160 @@
+// T-filtration by duality.
+//
+// Under the T-construction (Sec. 2.2) the pixel values sit on the top cells
+// of the lattice complex and every other cell takes the smallest value of the
+// top cells that contain it.  The paper leaves this filtration to future work
+// (Sec. 6), noting that its duality argument carries over.  This file computes
+// it with the V-filtration pipeline, through the duality between the
+// T-complex of an image I and the V-complex of
+//     J = -I, flipped along every axis, padded with a one-voxel frame whose
+//         value lies below every value of -I.
+// A T-cell of dimension k is dual to a V-cell of J of dimension d-k (a T top
+// cell to a J vertex, a T vertex to a J top cell); f_T(s) = -f_V(s*), and with
+// the flip, increasing order in one complex is decreasing order in the other,
+// ties included (the top cell a T-cell enters with is the vertex of J that
+// its dual cell enters with; the doubled-grid indices reverse).  So:
+//   - the T-filtration's H0 union-find (Kruskal over T-edges) is the dual
+//     union-find of the V top dimension on J (J top cells = T vertices,
+//     J facets = T edges); its last merge, into the outside through a frame
+//     facet, is the T essential class;
+//   - the T top-dimension dual union-find (T top cells + outside) is the V
+//     H0 union-find on J (J vertices = T top cells, the frame = the outside);
+//     the frame's own class is the V essential class and is dropped.
+// A V pair (b, d) becomes the T pair (-d, -b) with its cells and pixels
+// exchanged and mapped back: doubled coordinate a of J becomes 2n+1-a of the
+// T grid, vertex coordinate c of J becomes pixel n-c of I.
+//
+// Kernels: the largest value of I (for the frame value), J itself, and the
+// in-place mapping of the V pairs before the canonical output sort.
+#include "cp_common.cuh"
+#include "cp_kernels.h"
+
+namespace cp {
+namespace {
+
+constexpr int kTT = 256;
+
+__global__ void __launch_bounds__(kTT) k_t_max(const float* __restrict__ img, int64_t n, uint32_t* acc) {
+    uint32_t m = 0;
+    for (int64_t i = int64_t(blockIdx.x) * kTT + threadIdx.x; i < n; i += int64_t(gridDim.x) * kTT)
+        m = max(m, ord_bits(__ldg(img + i)));
+    m = __reduce_max_sync(0xFFFFFFFFu, m);
+    if ((threadIdx.x & 31u) == 0 && m) atomicMax(acc, m);
+}
+
+// The frame value: the float just below -max(I), the smallest value of -I.
+// (When max(I) is the largest finite float this is -inf, which the pruning
+// pass rejects as non-finite.)
+__device__ __forceinline__ float frame_value(const uint32_t* acc) {
+    const float neg_max = -ord_float(*acc);
+    return ord_float(ord_bits(neg_max) - 1u);
+}
+
+__global__ void __launch_bounds__(kTT) k_t_build(const float* __restrict__ img, TDims t, float* __restrict__ J,
+                                                 const uint32_t* acc) {
+    const int64_t Dj = t.ndim == 3 ? t.D + 2 : 1, Hj = t.H + 2, Wj = t.W + 2;
+    const int64_t nj = Dj * Hj * Wj;
+    const float pad = frame_value(acc);
+    for (int64_t j = int64_t(blockIdx.x) * kTT + threadIdx.x; j < nj; j += int64_t(gridDim.x) * kTT) {
+        const int64_t x = j % Wj, y = (j / Wj) % Hj, z = j / (Wj * Hj);
+        const bool frame = x == 0 || x == Wj - 1 || y == 0 || y == Hj - 1 || (t.ndim == 3 && (z == 0 || z == Dj - 1));
+        float v = pad;
+        if (!frame) {
+            const int64_t iz = t.ndim == 3 ? t.D - z : 0;
+            v = -__ldg(img + (iz * t.H + (t.H - y)) * t.W + (t.W - x));
+        }
+        J[j] = v;
+    }
+}
+
+// Doubled-grid index in J -> doubled-grid index in the T-complex of I.
+__device__ __forceinline__ int32_t t_cell(const TDims& t, int32_t vc) {
+    if (vc < 0) return -1;
+    const int64_t GWv = 2 * (t.W + 2) - 1, GHv = 2 * (t.H + 2) - 1;
+    const int64_t X = vc % GWv, Y = (vc / GWv) % GHv, Z = vc / (GWv * GHv);
+    const int64_t GWt = 2 * t.W + 1, GHt = 2 * t.H + 1, GDt = t.ndim == 3 ? 2 * t.D + 1 : 1;
+    const int64_t tx = GWt - X, ty = GHt - Y, tz = t.ndim == 3 ? GDt - Z : 0;
+    if (tx < 0 || tx >= GWt || ty < 0 || ty >= GHt || tz < 0 || tz >= GDt) return -1;  // a frame cell
+    return int32_t((tz * GHt + ty) * GWt + tx);
+}
+
+// Vertex of J -> pixel of I.
+__device__ __forceinline__ int32_t t_pixel(const TDims& t, int32_t vp) {
+    if (vp < 0) return -1;
+    const int64_t Wj = t.W + 2, Hj = t.H + 2;
+    const int64_t x = vp % Wj, y = (vp / Wj) % Hj, z = vp / (Wj * Hj);
+    const int64_t iz = t.ndim == 3 ? t.D - z : 0;
+    return int32_t((iz * t.H + (t.H - y)) * t.W + (t.W - x));
+}
+
+__device__ __forceinline__ float neg_canon(float v) {
+    const float r = -v;
+    return r == 0.0f ? 0.0f : r;  // -0.0 reads as +0.0
+}
+
+__global__ void __launch_bounds__(kTT) k_t_map(cp_pair* __restrict__ pairs, const uint32_t* d_n, uint32_t cap, TDims t,
+                                               const uint32_t* acc, int cell_bits, uint32_t* d_keep) {
+    const uint32_t n = min(*d_n, cap);
+    const float pad = frame_value(acc);
+    const int top = t.ndim - 1;
+    for (uint32_t i = blockIdx.x * kTT + threadIdx.x; i < n; i += gridDim.x * kTT) {
+        const cp_pair p = pairs[i];
+        cp_pair q;
+        q.item = p.item;
+        if (p.dim == 0 && p.death_cell < 0) {
+            // the frame's class (the outside of the T-complex): dropped; its key
+            // sorts after every kept pair, outside the kept count
+            q = p;
+            q.dim = top;
+            q.birth_cell = int32_t((1u << cell_bits) - 1u);
+        } else if (p.dim == top && p.birth == pad) {
+            // the last merge into the outside, through a frame facet: the T
+            // essential class, born at the T vertex dual to the dying top cell
+            q.dim = 0;
+            q.birth = neg_canon(p.death);
+            q.death = __int_as_float(0x7F800000);
+            q.birth_cell = t_cell(t, p.death_cell);
+            q.death_cell = -1;
+            q.birth_pixel = t_pixel(t, p.death_pixel);
+            q.death_pixel = -1;
+        } else {
+            q.dim = p.dim == 0 ? top : 0;
+            q.birth = neg_canon(p.death);
+            q.death = neg_canon(p.birth);
+            q.birth_cell = t_cell(t, p.death_cell);
+            q.death_cell = t_cell(t, p.birth_cell);
+            q.birth_pixel = t_pixel(t, p.death_pixel);
+            q.death_pixel = t_pixel(t, p.birth_pixel);
+        }
+        pairs[i] = q;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) *d_keep = n > 0 ? n - 1u : 0u;
+}
+
+int grid_of(int64_t n) {
+    const int64_t b = (n + kTT - 1) / kTT;
+    const int64_t cap = int64_t(device_sm_count()) * 8;
+    return int(b < 1 ? 1 : (b < cap ? b : cap));
+}
+
+}  // namespace
+
+cudaError_t launch_t_build(const float* img, const TDims& t, float* J, uint32_t* acc, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(acc, 0, sizeof(uint32_t), s);
+    if (e != cudaSuccess) return e;
+    const int64_t n = (t.ndim == 3 ? t.D : 1) * t.H * t.W;
+    const int64_t nj = (t.ndim == 3 ? t.D + 2 : 1) * (t.H + 2) * (t.W + 2);
+    k_t_max<<<grid_of(n), kTT, 0, s>>>(img, n, acc);
+    k_t_build<<<grid_of(nj), kTT, 0, s>>>(img, t, J, acc);
+    note_launches(2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_t_map(cp_pair* pairs, const uint32_t* d_n, uint32_t cap, const TDims& t, const uint32_t* acc,
+                         int cell_bits, uint32_t* d_keep, cudaStream_t s) {
+    k_t_map<<<grid_of(cap), kTT, 0, s>>>(pairs, d_n, cap, t, acc, cell_bits, d_keep);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+}  // namespace cp

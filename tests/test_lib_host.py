@@ -143,3 +143,24 @@ def test_tuning_arguments(lib):
         finally:
             assert lib.cp_set_tuning(key, old) == 0
     assert lib.cp_get_tuning(99) == -1 and lib.cp_set_tuning(99, 1) == -1
+
+
+def test_t_workspace_sizes(lib):
+    """The T-filtration workspace holds the V workspace of the padded dual
+    image plus the image itself; every extent may be 1; bad arguments give 0."""
+    import ctypes
+
+    def size(fn, *dims):
+        d = (ctypes.c_int64 * len(dims))(*dims)
+        return getattr(lib, fn)(len(dims), d, 0)
+
+    for dims in [(1, 1), (1, 7), (5, 3), (64, 64), (1, 1, 1), (3, 1, 4), (20, 30, 40)]:
+        padded = tuple(n + 2 for n in dims)
+        t = size("cubical_persistence_t_workspace_size", *dims)
+        v = size("cubical_persistence_workspace_size", *padded)
+        assert v > 0 and t >= v + 4 * int(np.prod(padded)), (dims, t, v)
+    assert size("cubical_persistence_t_workspace_size", 0, 5) == 0
+    assert size("cubical_persistence_t_workspace_size", 4, 0, 5) == 0
+    # the padded volume must stay within 2^27 vertices: 510^3 pads to 512^3
+    assert size("cubical_persistence_t_workspace_size", 511, 511, 511) == 0
+    assert size("cubical_persistence_t_workspace_size", 510, 510, 510) > 0
