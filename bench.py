@@ -450,6 +450,133 @@ def run_batched(args):
         torch.distributed.destroy_process_group()
 
 
+def run_tfilt(args):
+    """T-filtration workload: a 510^3 blurred volume (the padded dual image the
+    V pipeline runs on is exactly 512^3), forward + total-persistence loss
+    backward, device-resident input; the T oracle on a crop as the CPU line."""
+    import torch
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        torch.distributed.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import paper_2606_04801_gb300 as cp
+    from paper_2606_04801_gb300 import _lib
+
+    lib = _lib.load()
+    side = min(SIDE, 510)
+    cache = f"/tmp/cp_bench_tvol_{side}_{SIGMA}_{rank}.npy"
+    vol = np.load(cache) if os.path.exists(cache) else workloads.blurred((side,) * 3, SIGMA, rank)
+    if not os.path.exists(cache):
+        np.save(cache, vol)
+    N = vol.size
+    x = torch.from_numpy(vol).to(dev)
+    from paper_2606_04801_gb300 import autotune
+
+    autotune.autotune([x])  # the dual image falls in the same shape class
+    stream = torch.cuda.current_stream(dev)
+    sp = ctypes.c_void_p(int(stream.cuda_stream))
+    dims = (ctypes.c_int64 * 3)(side, side, side)
+    ws_bytes = lib.cubical_persistence_t_workspace_size(3, dims, 0)
+    wsp = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
+    cap = (side + 2) ** 3 // 2 + 65536 + 4096
+    out = torch.empty((cap, 8), dtype=torch.int32, device=dev)
+    grad = torch.empty(N, dtype=torch.float32, device=dev)
+    loss = torch.zeros(1, dtype=torch.float64, device=dev)
+    bws = lib.cubical_persistence_loss_backward_workspace_size(N)
+    bwsp = torch.empty(bws, dtype=torch.uint8, device=dev)
+    dcount = torch.zeros(1, dtype=torch.int64, device=dev)
+
+    def step():
+        rc = lib.cubical_persistence_t_3d(
+            ctypes.c_void_p(x.data_ptr()), dims, ctypes.c_void_p(out.data_ptr()), cap, None,
+            ctypes.c_void_p(dcount.data_ptr()), ctypes.c_void_p(wsp.data_ptr()), ws_bytes, 0, sp,
+        )
+        if rc != 0:
+            raise cp.CpError(rc, "T forward")
+        rc = lib.cubical_persistence_loss_backward(
+            ctypes.c_void_p(out.data_ptr()), cap, ctypes.c_void_p(dcount.data_ptr()), ctypes.c_float(TAU),
+            ctypes.c_void_p(loss.data_ptr()), None, ctypes.c_void_p(grad.data_ptr()), N, ctypes.c_void_p(bwsp.data_ptr()),
+            bws, sp,
+        )
+        if rc != 0:
+            raise cp.CpError(rc, "loss backward")
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    st = cp.api._stats(wsp)
+    if st["rc"] != 0:
+        raise cp.CpError(st["rc"], "T warm-up")
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    gpu_index = int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[local]) if os.environ.get("CUDA_VISIBLE_DEVICES") else local
+    launches0 = lib.cp_launch_count()
+    lib.cp_profile(1)
+    stage = (ctypes.c_float * 6)()
+    stage_sum = [0.0] * 6
+    with Clocks(gpu_index) as clk:
+        torch.cuda.synchronize(dev)
+        if ws > 1:
+            torch.distributed.barrier()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step()
+            if lib.cp_stage_times(stage, 6) == 6:
+                for i in range(6):
+                    stage_sum[i] += stage[i]
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        if ws > 1:
+            torch.distributed.barrier()
+    launches = lib.cp_launch_count() - launches0
+    st = cp.api._stats(wsp)
+    if st["rc"] != 0:
+        raise cp.CpError(st["rc"], "T timed steps")
+    elapsed = job_time(ev0.elapsed_time(ev1) / 1e3, ws, dev)
+    value = job_value(N, ws, args.steps, elapsed)
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle
+
+        oracle.build()
+        c = 64
+        crop = np.ascontiguousarray(vol[:c, :c, :c])
+        t0 = time.perf_counter()
+        oracle.persistence_t(crop)
+        dt = time.perf_counter() - t0
+        c2 = min(160, int(c * max(1.0, (10.0 / max(dt, 1e-3)) ** (1 / 3) * 0.8)))
+        if c2 > c:
+            crop = np.ascontiguousarray(vol[:c2, :c2, :c2])
+            t0 = time.perf_counter()
+            oracle.persistence_t(crop)
+            dt = time.perf_counter() - t0
+            c = c2
+        cpu = {"value": crop.size / dt / 1e6, "unit": "Mvoxels/s", "cores": 1, "kind": "oracle",
+               "sample": f"{c}^3 crop of the {side}^3 volume, T-filtration H0 + H2 pairs, single-threaded C oracle, {dt:.1f} s"}
+    if rank == 0:
+        print(json.dumps({
+            "metric": f"Mvoxels/s, T-filtration H0 + H2 pairs ({side}^3 fp32), fwd + loss bwd",
+            "value": value, "unit": "Mvoxels/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"3D {side}^3 float32 blurred noise (sigma 3 vox), T-filtration (dual image {side + 2}^3), "
+                                   "fwd + total-persistence loss bwd", "status": st["rc"], "pairs": st["pairs"],
+                       "h0_survivors": st["h0_survivors"], "top_survivors": st["top_survivors"],
+                       "h0_roots": st["h0_roots"], "top_roots": st["top_roots"],
+                       "rounds": [st["h0_rounds"], st["top_rounds"]],
+                       "l2": "input larger than L2; no flush", "parallelism": "replicas" if ws > 1 else "single"},
+            "gpu_launches": launches,
+            "clocks": clk.summary(),
+            "stages_ms": {k: v / args.steps for k, v in zip(["prune", "sort", "uf", "-", "-", "emit_and_map"], stage_sum)
+                          if k != "-"},
+            "cpu_baseline": cpu,
+        }), flush=True)
+    lib.cp_profile(0)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -460,9 +587,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--side", type=int, default=512, help="cube side (512 is the benchmark; smaller for profiling)")
     ap.add_argument("--no-batched", action="store_true")
-    ap.add_argument("--workload", default="volume", choices=["volume", "batched", "survivors"],
+    ap.add_argument("--workload", default="volume", choices=["volume", "batched", "survivors", "tfilt"],
                     help="volume: the 512^3 plain path (the headline line); batched: the batched fwd + bwd workload "
-                    "alone; survivors: survivor fractions S/N of every config")
+                    "alone; survivors: survivor fractions S/N of every config; tfilt: the T-filtration on 510^3")
     ap.add_argument("--eager", action="store_true", help="batched workload without the CUDA graph (per-kernel profiling)")
     args = ap.parse_args()
     global SIDE
@@ -477,6 +604,9 @@ def main():
         return
     if args.workload == "survivors":
         run_survivors()
+        return
+    if args.workload == "tfilt":
+        run_tfilt(args)
         return
 
     import torch

@@ -175,8 +175,9 @@ int cubical_persistence_3d(const float *d_image, const int64_t dims[3], cp_pair 
  * dimension of J, the T top dimension is V-H0 of J.
  *  - dims: every extent >= 1; (D+2)(H+2)(W+2) (3D) or (H+2)(W+2) (2D) at
  *    most 2^27.
- *  - Every pixel must be below the largest finite float (the frame value
- *    lies below -max): otherwise CP_ERR_NONFINITE, as for NaN and +-inf.
+ *  - Every pixel must be below the largest finite float (the frame sits at
+ *    -FLT_MAX and must come first): otherwise CP_ERR_NONFINITE, as for NaN
+ *    and +-inf.
  *  - capacity: D*H*W + (D+1)(H+1)(W+1) always suffices.
  *  - d_workspace: ws_bytes >= cubical_persistence_t_workspace_size(); it
  *    holds the V workspace of J (so cubical_persistence_stats() reads this

@@ -199,11 +199,11 @@ int status_to_code(uint32_t st) {
     return CP_OK;
 }
 
-// T-filtration calls: the original image's extents and the frame-value key
-// (run() then maps the pairs of J back before the output sort).
+// T-filtration calls: the original image's extents and the input check's
+// flag (run() then maps the pairs of J back before the output sort).
 struct TMode {
     TDims dims;
-    const uint32_t* acc;
+    const uint32_t* bad;
 };
 
 int run(const Plan& P, cp_pair* d_out, int64_t capacity, int64_t* h_out_count, int64_t* d_out_count, void* ws,
@@ -267,6 +267,7 @@ int run(const Plan& P, cp_pair* d_out, int64_t capacity, int64_t* h_out_count, i
     po.cap_rt = P.cap_rt;
     po.ctr = ctr;
     CP_TRY(launch_prune(P.tab, po, P.tma, s));
+    if (tm) CP_TRY(launch_t_flatten(uf0, tm->dims, s));
     mark(1, s);
 
     // First-round root walks over the unsorted survivors (tile order), then the
@@ -425,7 +426,7 @@ int run(const Plan& P, cp_pair* d_out, int64_t capacity, int64_t* h_out_count, i
             G = (tm->dims.ndim == 3 ? 2 * tm->dims.D + 1 : 1) * (2 * tm->dims.H + 1) * (2 * tm->dims.W + 1);
         while ((int64_t(1) << cell_bits) < G) ++cell_bits;
     }
-    if (tm) CP_TRY(launch_t_map(pairs, &ctr->n_pairs, P.cap_p, tm->dims, tm->acc, cell_bits, &ctr->t_keep, s));
+    if (tm) CP_TRY(launch_t_map(pairs, &ctr->n_pairs, P.cap_p, tm->dims, tm->bad, cell_bits, ctr, s));
     while ((1 << item_bits) < P.tab.n) ++item_bits;
     int pair_passes = (item_bits + 1 + cell_bits + 7) / 8;
     pair_passes += pair_passes & 1;  // an even count leaves the result in place
@@ -504,10 +505,10 @@ int t_single(int ndim, const float* d_image, const int64_t* dims, cp_pair* d_out
     int rc = ensure_device_tables();
     if (rc != CP_OK) return rc;
     char* base = static_cast<char*>(ws);
-    uint32_t* acc = reinterpret_cast<uint32_t*>(base + align_up(v_bytes));
+    uint32_t* bad = reinterpret_cast<uint32_t*>(base + align_up(v_bytes));
     float* J = reinterpret_cast<float*>(base + align_up(v_bytes) + 256);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    if (launch_t_build(d_image, t, J, acc, s) != cudaSuccess) return CP_ERR_CUDA;
+    if (launch_t_build(d_image, t, J, bad, s) != cudaSuccess) return CP_ERR_CUDA;
     int32_t nd = ndim;
     const float* jimg = J;
     Plan P;
@@ -515,7 +516,7 @@ int t_single(int ndim, const float* d_image, const int64_t* dims, cp_pair* d_out
     if (rc != CP_OK) return rc;
     TMode tm;
     tm.dims = t;
-    tm.acc = acc;
+    tm.bad = bad;
     return run(P, d_out, capacity, h_out_count, d_out_count, ws, v_bytes, s, false, &tm);
 }
 

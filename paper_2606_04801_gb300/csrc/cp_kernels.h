@@ -124,13 +124,17 @@ struct TDims {
     int ndim;
     int64_t D, H, W;
 };
-// acc <- the largest ord key of I; J <- -I flipped along every axis, inside a
-// one-voxel frame below every value of -I (extents +2 along each image axis).
-cudaError_t launch_t_build(const float* img, const TDims& t, float* J, uint32_t* acc, cudaStream_t s);
+// J <- -I flipped along every axis, inside a one-voxel frame at -FLT_MAX
+// (extents +2 along each image axis); *bad <- 1 if a pixel is not below
+// FLT_MAX (the frame would not come first).
+cudaError_t launch_t_build(const float* img, const TDims& t, float* J, uint32_t* bad, cudaStream_t s);
+// After the pruning pass: every frame vertex's H0 link points at vertex 0.
+cudaError_t launch_t_flatten(uint32_t* uf0, const TDims& t, cudaStream_t s);
 // V pairs of J -> T pairs of I, in place; the frame's class gets the last sort
-// key (birth cell 2^cell_bits - 1) and *d_keep the count without it.
-cudaError_t launch_t_map(cp_pair* pairs, const uint32_t* d_n, uint32_t cap, const TDims& t, const uint32_t* acc,
-                         int cell_bits, uint32_t* d_keep, cudaStream_t s);
+// key (birth cell 2^cell_bits - 1), ctr->t_keep the count without it, and a
+// set *bad flags the call as non-finite.
+cudaError_t launch_t_map(cp_pair* pairs, const uint32_t* d_n, uint32_t cap, const TDims& t, const uint32_t* bad,
+                         int cell_bits, Counters* ctr, cudaStream_t s);
 cudaError_t launch_essential(const ItemTable& tab, Counters* ctr, cp_pair* pairs, uint32_t pair_cap, cudaStream_t s);
 cudaError_t launch_pair_keys(const cp_pair* pairs, const uint32_t* d_n, uint32_t cap, uint64_t* keys, uint32_t* vals,
                              int cell_bits, cudaStream_t s);

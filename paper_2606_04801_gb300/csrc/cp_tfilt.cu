@@ -24,8 +24,9 @@
 // exchanged and mapped back: doubled coordinate a of J becomes 2n+1-a of the
 // T grid, vertex coordinate c of J becomes pixel n-c of I.
 //
-// Kernels: the largest value of I (for the frame value), J itself, and the
-// in-place mapping of the V pairs before the canonical output sort.
+// Kernels: J itself (with a check that every pixel lies below the largest
+// finite float, so that the frame comes first), and the in-place mapping of
+// the V pairs before the canonical output sort.
 #include "cp_common.cuh"
 #include "cp_kernels.h"
 
@@ -33,37 +34,70 @@ namespace cp {
 namespace {
 
 constexpr int kTT = 256;
+// The frame value: below every value of -I as long as every pixel is below
+// the largest finite float (a pixel at that float, or above it, is flagged).
+constexpr float kFrame = -3.40282347e38f;
 
-__global__ void __launch_bounds__(kTT) k_t_max(const float* __restrict__ img, int64_t n, uint32_t* acc) {
-    uint32_t m = 0;
-    for (int64_t i = int64_t(blockIdx.x) * kTT + threadIdx.x; i < n; i += int64_t(gridDim.x) * kTT)
-        m = max(m, ord_bits(__ldg(img + i)));
-    m = __reduce_max_sync(0xFFFFFFFFu, m);
-    if ((threadIdx.x & 31u) == 0 && m) atomicMax(acc, m);
-}
-
-// The frame value: the float just below -max(I), the smallest value of -I.
-// (When max(I) is the largest finite float this is -inf, which the pruning
-// pass rejects as non-finite.)
-__device__ __forceinline__ float frame_value(const uint32_t* acc) {
-    const float neg_max = -ord_float(*acc);
-    return ord_float(ord_bits(neg_max) - 1u);
-}
-
+// J row by row (one division per row; consecutive threads write consecutive
+// x and read consecutive, reversed, pixels of the mirrored row of I).
 __global__ void __launch_bounds__(kTT) k_t_build(const float* __restrict__ img, TDims t, float* __restrict__ J,
-                                                 const uint32_t* acc) {
+                                                 uint32_t* bad) {
     const int64_t Dj = t.ndim == 3 ? t.D + 2 : 1, Hj = t.H + 2, Wj = t.W + 2;
-    const int64_t nj = Dj * Hj * Wj;
-    const float pad = frame_value(acc);
-    for (int64_t j = int64_t(blockIdx.x) * kTT + threadIdx.x; j < nj; j += int64_t(gridDim.x) * kTT) {
-        const int64_t x = j % Wj, y = (j / Wj) % Hj, z = j / (Wj * Hj);
-        const bool frame = x == 0 || x == Wj - 1 || y == 0 || y == Hj - 1 || (t.ndim == 3 && (z == 0 || z == Dj - 1));
-        float v = pad;
-        if (!frame) {
-            const int64_t iz = t.ndim == 3 ? t.D - z : 0;
-            v = -__ldg(img + (iz * t.H + (t.H - y)) * t.W + (t.W - x));
+    const int64_t rows = Dj * Hj;
+    bool flag = false;
+    for (int64_t r = blockIdx.x; r < rows; r += gridDim.x) {
+        const int64_t z = r / Hj, y = r - z * Hj;
+        const bool frame_row = y == 0 || y == Hj - 1 || (t.ndim == 3 && (z == 0 || z == Dj - 1));
+        const int64_t iz = t.ndim == 3 ? t.D - z : 0;
+        const float* in = img + (iz * t.H + (t.H - y)) * t.W;  // dereferenced only inside the image
+        float* out = J + r * Wj;
+        for (int64_t x = threadIdx.x; x < Wj; x += kTT) {
+            float v = kFrame;
+            if (!frame_row && x > 0 && x < Wj - 1) {
+                const float a = __ldg(in + (t.W - x));
+                flag |= !(a < 3.40282347e38f);  // NaN, +inf, the largest float: the frame would not lie below
+                v = -a;
+            }
+            out[x] = v;
         }
-        J[j] = v;
+    }
+    if (__any_sync(0xFFFFFFFFu, flag) && (threadIdx.x & 31u) == 0) atomicOr(bad, 1u);
+}
+
+// After the pruning pass: every frame vertex of J points straight at vertex
+// 0, the frame's root.  The frame is one tree of equal values in which the
+// pruning pass links each vertex to an earlier neighbour; its chains along y
+// and x run the whole length of a face, and every walk from a basin that
+// drains to the border would otherwise follow them.  Vertex 0 is an ancestor
+// of every frame vertex (every frame vertex but 0 has an earlier neighbour in
+// the frame, and equal values order by index), so the shortcut changes no root.
+__global__ void __launch_bounds__(kTT) k_t_flatten(uint32_t* __restrict__ uf0, TDims t) {
+    const int64_t Dj = t.ndim == 3 ? t.D + 2 : 1, Hj = t.H + 2, Wj = t.W + 2;
+    // whole frame rows, one block per row: both y faces of every plane, and
+    // the two z faces (3D)
+    const int64_t zf = t.ndim == 3 ? 2 * Hj : 0;  // rows of the two z faces
+    const int64_t nrows = zf + 2 * (t.ndim == 3 ? Dj - 2 : 1);
+    for (int64_t f = blockIdx.x; f < nrows; f += gridDim.x) {
+        int64_t z, y;
+        if (f < zf) {
+            z = f < Hj ? 0 : Dj - 1;
+            y = f % Hj;
+        } else {
+            const int64_t g = f - zf;
+            z = t.ndim == 3 ? 1 + g / 2 : 0;
+            y = (g & 1) ? Hj - 1 : 0;
+        }
+        uint32_t* row = uf0 + (z * Hj + y) * Wj;
+        for (int64_t x = threadIdx.x; x < Wj; x += kTT)
+            if (z != 0 || y != 0 || x != 0) row[x] = 0u;
+    }
+    // the two x faces of the other rows
+    const int64_t zi = t.ndim == 3 ? Dj - 2 : 1, yi = Hj - 2;
+    const int64_t nside = 2 * zi * yi;
+    for (int64_t k = int64_t(blockIdx.x) * kTT + threadIdx.x; k < nside; k += int64_t(gridDim.x) * kTT) {
+        const int64_t q = k >> 1;
+        const int64_t z = t.ndim == 3 ? 1 + q / yi : 0, y = 1 + q % yi;
+        uf0[(z * Hj + y) * Wj + ((k & 1) ? Wj - 1 : 0)] = 0u;
     }
 }
 
@@ -93,9 +127,8 @@ __device__ __forceinline__ float neg_canon(float v) {
 }
 
 __global__ void __launch_bounds__(kTT) k_t_map(cp_pair* __restrict__ pairs, const uint32_t* d_n, uint32_t cap, TDims t,
-                                               const uint32_t* acc, int cell_bits, uint32_t* d_keep) {
+                                               const uint32_t* bad, int cell_bits, Counters* ctr) {
     const uint32_t n = min(*d_n, cap);
-    const float pad = frame_value(acc);
     const int top = t.ndim - 1;
     for (uint32_t i = blockIdx.x * kTT + threadIdx.x; i < n; i += gridDim.x * kTT) {
         const cp_pair p = pairs[i];
@@ -107,7 +140,7 @@ __global__ void __launch_bounds__(kTT) k_t_map(cp_pair* __restrict__ pairs, cons
             q = p;
             q.dim = top;
             q.birth_cell = int32_t((1u << cell_bits) - 1u);
-        } else if (p.dim == top && p.birth == pad) {
+        } else if (p.dim == top && p.birth == kFrame) {
             // the last merge into the outside, through a frame facet: the T
             // essential class, born at the T vertex dual to the dying top cell
             q.dim = 0;
@@ -128,7 +161,10 @@ __global__ void __launch_bounds__(kTT) k_t_map(cp_pair* __restrict__ pairs, cons
         }
         pairs[i] = q;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) *d_keep = n > 0 ? n - 1u : 0u;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        ctr->t_keep = n > 0 ? n - 1u : 0u;
+        if (*bad) set_status(ctr, kStNonfinite);
+    }
 }
 
 int grid_of(int64_t n) {
@@ -139,20 +175,25 @@ int grid_of(int64_t n) {
 
 }  // namespace
 
-cudaError_t launch_t_build(const float* img, const TDims& t, float* J, uint32_t* acc, cudaStream_t s) {
-    cudaError_t e = cudaMemsetAsync(acc, 0, sizeof(uint32_t), s);
+cudaError_t launch_t_build(const float* img, const TDims& t, float* J, uint32_t* bad, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(bad, 0, sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
-    const int64_t n = (t.ndim == 3 ? t.D : 1) * t.H * t.W;
-    const int64_t nj = (t.ndim == 3 ? t.D + 2 : 1) * (t.H + 2) * (t.W + 2);
-    k_t_max<<<grid_of(n), kTT, 0, s>>>(img, n, acc);
-    k_t_build<<<grid_of(nj), kTT, 0, s>>>(img, t, J, acc);
-    note_launches(2);
+    const int64_t rows = (t.ndim == 3 ? t.D + 2 : 1) * (t.H + 2);
+    const int64_t cap = int64_t(device_sm_count()) * 16;
+    k_t_build<<<int(rows < cap ? rows : cap), kTT, 0, s>>>(img, t, J, bad);
+    note_launches(1);
     return cudaGetLastError();
 }
 
-cudaError_t launch_t_map(cp_pair* pairs, const uint32_t* d_n, uint32_t cap, const TDims& t, const uint32_t* acc,
-                         int cell_bits, uint32_t* d_keep, cudaStream_t s) {
-    k_t_map<<<grid_of(cap), kTT, 0, s>>>(pairs, d_n, cap, t, acc, cell_bits, d_keep);
+cudaError_t launch_t_flatten(uint32_t* uf0, const TDims& t, cudaStream_t s) {
+    k_t_flatten<<<device_sm_count() * 8, kTT, 0, s>>>(uf0, t);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_t_map(cp_pair* pairs, const uint32_t* d_n, uint32_t cap, const TDims& t, const uint32_t* bad,
+                         int cell_bits, Counters* ctr, cudaStream_t s) {
+    k_t_map<<<grid_of(cap), kTT, 0, s>>>(pairs, d_n, cap, t, bad, cell_bits, ctr);
     note_launches(1);
     return cudaGetLastError();
 }
