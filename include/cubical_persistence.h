@@ -191,6 +191,19 @@ int cubical_persistence_t_2d(const float *d_image, const int64_t dims[2], cp_pai
 int cubical_persistence_t_3d(const float *d_image, const int64_t dims[3], cp_pair *d_out_pairs, int64_t capacity,
                              int64_t *h_out_count, int64_t *d_out_count, void *d_workspace, size_t ws_bytes,
                              int64_t max_survivors, void *stream);
+/*
+ * Batched T-filtration: n_items images and volumes (arguments laid out as
+ * for cubical_persistence_batched, every extent >= 1, each padded item within
+ * 2^27 vertices) in one pass; pairs carry their item index, cells and pixels
+ * are item-local (T doubled grid).  Workspace:
+ * cubical_persistence_t_batched_workspace_size().
+ */
+size_t cubical_persistence_t_batched_workspace_size(int n_items, const int32_t *ndims, const int64_t *dims,
+                                                    int64_t max_survivors);
+int cubical_persistence_t_batched(int n_items, const float *const *h_images, const int32_t *ndims,
+                                  const int64_t *dims, cp_pair *d_out_pairs, int64_t capacity, int64_t *h_out_count,
+                                  int64_t *d_out_count, void *d_workspace, size_t ws_bytes, int64_t max_survivors,
+                                  void *stream);
 
 /*
  * Batched form: n_items independent images and volumes of any sizes in one

@@ -66,6 +66,11 @@ _SIGS = {
     "cubical_persistence_t_workspace_size": (ctypes.c_size_t, [ctypes.c_int, _P, _I64]),
     "cubical_persistence_t_2d": (ctypes.c_int, [_P, _P, _P, _I64, _P, _P, _P, ctypes.c_size_t, _I64, _P]),
     "cubical_persistence_t_3d": (ctypes.c_int, [_P, _P, _P, _I64, _P, _P, _P, ctypes.c_size_t, _I64, _P]),
+    "cubical_persistence_t_batched_workspace_size": (ctypes.c_size_t, [ctypes.c_int, _P, _P, _I64]),
+    "cubical_persistence_t_batched": (
+        ctypes.c_int,
+        [ctypes.c_int, _P, _P, _P, _P, _I64, _P, _P, _P, ctypes.c_size_t, _I64, _P],
+    ),
     "cubical_persistence_batched_workspace_size": (ctypes.c_size_t, [ctypes.c_int, _P, _P, _I64]),
     "cubical_persistence_batched": (
         ctypes.c_int,

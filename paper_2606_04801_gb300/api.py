@@ -147,14 +147,19 @@ def persistence(img: torch.Tensor, max_survivors: int = 0, with_stats: bool = Fa
     raise CpError(CP_ERR_CAPACITY, "cubical_persistence (after growing the workspace)")
 
 
-def persistence_batched(imgs: Sequence[torch.Tensor], max_survivors: int = 0, with_stats: bool = False) -> Diagram:
-    """Pairs of many images and volumes in one pass; each pair carries its item index."""
+def persistence_batched(imgs: Sequence[torch.Tensor], max_survivors: int = 0, with_stats: bool = False,
+                        filtration: str = "V") -> Diagram:
+    """Pairs of many images and volumes in one pass; each pair carries its item index.
+    filtration as for persistence()."""
     if not imgs:
         raise ValueError("empty batch")
+    if filtration not in ("V", "T"):
+        raise ValueError("filtration must be 'V' or 'T'")
+    tmode = filtration == "T"
     lib = _lib.load()
     imgs = [im.contiguous() for im in imgs]
     for im in imgs:
-        _check_image(im)
+        _check_image(im, min_extent=1 if tmode else 2)
     dev = imgs[0].device
     k = len(imgs)
     if k > _lib.CP_MAX_ITEMS:
@@ -165,19 +170,25 @@ def persistence_batched(imgs: Sequence[torch.Tensor], max_survivors: int = 0, wi
     for im in imgs:
         flat += ([1] + list(im.shape)) if im.dim() == 2 else list(im.shape)
     dims = (ctypes.c_int64 * (3 * k))(*flat)
-    n = sum(im.numel() for im in imgs)
-    t = sum(int(np.prod([s - 1 for s in im.shape])) + 1 for im in imgs)
+    if tmode:
+        n = sum(int(np.prod([s + 2 for s in im.shape])) for im in imgs)  # the dual images' vertices
+        t = sum(im.numel() + int(np.prod([s + 1 for s in im.shape])) for im in imgs)
+        wsize, fn = lib.cubical_persistence_t_batched_workspace_size, lib.cubical_persistence_t_batched
+    else:
+        n = sum(im.numel() for im in imgs)
+        t = n + sum(int(np.prod([s - 1 for s in im.shape])) + 1 for im in imgs)
+        wsize, fn = lib.cubical_persistence_batched_workspace_size, lib.cubical_persistence_batched
     ms = int(max_survivors)
     for _ in range(4):
-        ws_bytes = lib.cubical_persistence_batched_workspace_size(k, ndims, dims, ms)
+        ws_bytes = wsize(k, ndims, dims, ms)
         if ws_bytes == 0:
             raise CpError(_lib.CP_ERR_ARG, "batched workspace size")
         ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
         eff = ms if ms > 0 else n // 2 + 65536
-        cap = min(n + t, eff + 2 * k + 4096)
+        cap = min(t, eff + 2 * k + 4096)
         out = torch.empty((cap, 8), dtype=torch.int32, device=dev)
         cnt = ctypes.c_int64(0)
-        rc = lib.cubical_persistence_batched(
+        rc = fn(
             k, ptrs, ndims, dims, ctypes.c_void_p(out.data_ptr()), cap, ctypes.byref(cnt), None,
             ctypes.c_void_p(ws.data_ptr()), ws_bytes, ms, ctypes.c_void_p(_stream_ptr(dev)),
         )
@@ -185,7 +196,7 @@ def persistence_batched(imgs: Sequence[torch.Tensor], max_survivors: int = 0, wi
             ms = _grow(_stats(ws), eff, n)
             continue
         if rc != CP_OK:
-            raise CpError(rc, "cubical_persistence_batched")
+            raise CpError(rc, "cubical_persistence_batched" + ("_t" if tmode else ""))
         return Diagram(out[: cnt.value], _stats(ws) if with_stats else None)
     raise CpError(CP_ERR_CAPACITY, "cubical_persistence_batched (after growing the workspace)")
 

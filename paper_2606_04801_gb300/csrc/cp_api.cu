@@ -199,10 +199,11 @@ int status_to_code(uint32_t st) {
     return CP_OK;
 }
 
-// T-filtration calls: the original image's extents and the input check's
-// flag (run() then maps the pairs of J back before the output sort).
+// T-filtration calls: the images' extents and dual images, and the input
+// check's flag (run() flattens the frames after the pruning pass and maps the
+// pairs of J back before the output sort).
 struct TMode {
-    TDims dims;
+    TItems items;
     const uint32_t* bad;
 };
 
@@ -267,7 +268,7 @@ int run(const Plan& P, cp_pair* d_out, int64_t capacity, int64_t* h_out_count, i
     po.cap_rt = P.cap_rt;
     po.ctr = ctr;
     CP_TRY(launch_prune(P.tab, po, P.tma, s));
-    if (tm) CP_TRY(launch_t_flatten(uf0, tm->dims, s));
+    if (tm) CP_TRY(launch_t_flatten(uf0, tm->items, s));
     mark(1, s);
 
     // First-round root walks over the unsorted survivors (tile order), then the
@@ -422,12 +423,15 @@ int run(const Plan& P, cp_pair* d_out, int64_t capacity, int64_t* h_out_count, i
     for (int i = 0; i < P.tab.n; ++i) {
         const Item& it = P.tab.it[i];
         int64_t G = int64_t(2 * it.D - 1) * (2 * it.H - 1) * (2 * it.W - 1);
-        if (tm)  // the T-complex of the original image (odd extents: the all-ones key is never a cell)
-            G = (tm->dims.ndim == 3 ? 2 * tm->dims.D + 1 : 1) * (2 * tm->dims.H + 1) * (2 * tm->dims.W + 1);
+        if (tm) {  // the T-complex of the original image
+            const TDims& d = tm->items.d[it.user];
+            G = (d.ndim == 3 ? 2 * d.D + 1 : 1) * (2 * d.H + 1) * (2 * d.W + 1);
+        }
         while ((int64_t(1) << cell_bits) < G) ++cell_bits;
     }
-    if (tm) CP_TRY(launch_t_map(pairs, &ctr->n_pairs, P.cap_p, tm->dims, tm->bad, cell_bits, ctr, s));
-    while ((1 << item_bits) < P.tab.n) ++item_bits;
+    if (tm) CP_TRY(launch_t_map(pairs, &ctr->n_pairs, P.cap_p, tm->items, tm->bad, ctr, s));
+    // T calls: one more item index, for the dropped frame classes
+    while ((1 << item_bits) < P.tab.n + (tm ? 1 : 0)) ++item_bits;
     int pair_passes = (item_bits + 1 + cell_bits + 7) / 8;
     pair_passes += pair_passes & 1;  // an even count leaves the result in place
     CP_TRY(launch_pair_keys(pairs, &ctr->n_pairs, P.cap_p, s0, pvals, cell_bits, s));
@@ -465,59 +469,81 @@ int single(int ndim, const float* d_image, const int64_t* dims, cp_pair* d_out, 
     return run(P, d_out, capacity, h_out_count, d_out_count, ws, ws_bytes, static_cast<cudaStream_t>(stream));
 }
 
-// T-filtration: workspace = [the V workspace of J][256 B scratch][J].
-
-bool t_extents(int ndim, const int64_t* dims, TDims& t, int64_t jd3[3]) {
-    if ((ndim != 2 && ndim != 3) || !dims) return false;
-    t.ndim = ndim;
-    t.D = ndim == 3 ? dims[0] : 1;
-    t.H = dims[ndim - 2];
-    t.W = dims[ndim - 1];
-    if (t.D < 1 || t.H < 1 || t.W < 1) return false;
-    jd3[0] = ndim == 3 ? t.D + 2 : 1;
-    jd3[1] = t.H + 2;
-    jd3[2] = t.W + 2;
+// T-filtration: workspace = [the V workspace of the dual images][256 B
+// scratch][J of item 0][J of item 1]... (each 256-byte aligned).
+bool t_extents(int n_items, const int32_t* ndims, const int64_t* dims, TItems& t, std::vector<int64_t>& jdims) {
+    if (n_items < 1 || n_items > kMaxItems || !ndims || !dims) return false;
+    t.n = n_items;
+    jdims.assign(size_t(3 * n_items), 1);
+    for (int i = 0; i < n_items; ++i) {
+        if (ndims[i] != 2 && ndims[i] != 3) return false;
+        TDims& d = t.d[i];
+        d.ndim = ndims[i];
+        d.D = d.ndim == 3 ? dims[3 * i] : 1;
+        d.H = dims[3 * i + 1];
+        d.W = dims[3 * i + 2];
+        if (d.D < 1 || d.H < 1 || d.W < 1) return false;
+        jdims[3 * i] = d.ndim == 3 ? d.D + 2 : 1;
+        jdims[3 * i + 1] = d.H + 2;
+        jdims[3 * i + 2] = d.W + 2;
+    }
     return true;
 }
 
-size_t t_workspace(int ndim, const int64_t* dims, int64_t max_survivors, size_t* v_bytes) {
-    TDims t;
-    int64_t jd3[3];
-    if (!t_extents(ndim, dims, t, jd3)) return 0;
-    int32_t nd = ndim;
+size_t t_workspace(int n_items, const int32_t* ndims, const int64_t* dims, int64_t max_survivors,
+                   size_t* v_bytes) {
+    TItems t;
+    std::vector<int64_t> jd;
+    if (!t_extents(n_items, ndims, dims, t, jd)) return 0;
     Plan P;
-    if (make_plan(1, &nd, jd3, nullptr, max_survivors, P) != CP_OK) return 0;
+    if (make_plan(n_items, ndims, jd.data(), nullptr, max_survivors, P) != CP_OK) return 0;
     if (v_bytes) *v_bytes = P.bytes;
-    return align_up(P.bytes) + 256 + sizeof(float) * size_t(jd3[0] * jd3[1] * jd3[2]);
+    size_t b = align_up(P.bytes) + 256;
+    for (int i = 0; i < n_items; ++i) b += align_up(sizeof(float) * size_t(jd[3 * i] * jd[3 * i + 1] * jd[3 * i + 2]));
+    return b;
+}
+
+int t_run(int n_items, const float* const* h_images, const int32_t* ndims, const int64_t* dims, cp_pair* d_out,
+          int64_t capacity, int64_t* h_out_count, int64_t* d_out_count, void* ws, size_t ws_bytes,
+          int64_t max_survivors, void* stream) {
+    if (!h_images || !ws) return CP_ERR_ARG;
+    TMode tm;
+    std::vector<int64_t> jd;
+    if (!t_extents(n_items, ndims, dims, tm.items, jd)) return CP_ERR_ARG;
+    size_t v_bytes = 0;
+    const size_t need = t_workspace(n_items, ndims, dims, max_survivors, &v_bytes);
+    if (need == 0 || ws_bytes < need) return CP_ERR_ARG;
+    int rc = ensure_device_tables();
+    if (rc != CP_OK) return rc;
+    char* base = static_cast<char*>(ws);
+    uint32_t* bad = reinterpret_cast<uint32_t*>(base + align_up(v_bytes));
+    size_t off = align_up(v_bytes) + 256;
+    std::vector<const float*> jptr(static_cast<size_t>(n_items));
+    for (int i = 0; i < n_items; ++i) {
+        if (!h_images[i]) return CP_ERR_ARG;
+        tm.items.img[i] = h_images[i];
+        tm.items.J[i] = reinterpret_cast<float*>(base + off);
+        jptr[size_t(i)] = tm.items.J[i];
+        off += align_up(sizeof(float) * size_t(jd[3 * i] * jd[3 * i + 1] * jd[3 * i + 2]));
+    }
+    Plan P;
+    rc = make_plan(n_items, ndims, jd.data(), jptr.data(), max_survivors, P);
+    if (rc != CP_OK) return rc;
+    for (int j = 0; j < P.tab.n; ++j) tm.items.voff[P.tab.it[j].user] = P.tab.it[j].voff;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (launch_t_build(tm.items, bad, s) != cudaSuccess) return CP_ERR_CUDA;
+    tm.bad = bad;
+    return run(P, d_out, capacity, h_out_count, d_out_count, ws, v_bytes, s, false, &tm);
 }
 
 int t_single(int ndim, const float* d_image, const int64_t* dims, cp_pair* d_out, int64_t capacity,
              int64_t* h_out_count, int64_t* d_out_count, void* ws, size_t ws_bytes, int64_t max_survivors,
              void* stream) {
-    if (!d_image || !ws) return CP_ERR_ARG;
-    TDims t;
-    int64_t jd3[3];
-    if (!t_extents(ndim, dims, t, jd3)) return CP_ERR_ARG;
-    size_t v_bytes = 0;
-    const size_t need = t_workspace(ndim, dims, max_survivors, &v_bytes);
-    if (need == 0) return CP_ERR_ARG;
-    if (ws_bytes < need) return CP_ERR_ARG;
-    int rc = ensure_device_tables();
-    if (rc != CP_OK) return rc;
-    char* base = static_cast<char*>(ws);
-    uint32_t* bad = reinterpret_cast<uint32_t*>(base + align_up(v_bytes));
-    float* J = reinterpret_cast<float*>(base + align_up(v_bytes) + 256);
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    if (launch_t_build(d_image, t, J, bad, s) != cudaSuccess) return CP_ERR_CUDA;
-    int32_t nd = ndim;
-    const float* jimg = J;
-    Plan P;
-    rc = make_plan(1, &nd, jd3, &jimg, max_survivors, P);
-    if (rc != CP_OK) return rc;
-    TMode tm;
-    tm.dims = t;
-    tm.bad = bad;
-    return run(P, d_out, capacity, h_out_count, d_out_count, ws, v_bytes, s, false, &tm);
+    if (!d_image || !dims || (ndim != 2 && ndim != 3)) return CP_ERR_ARG;
+    const int32_t nd = ndim;
+    const int64_t d3[3] = {ndim == 3 ? dims[0] : 1, dims[ndim - 2], dims[ndim - 1]};
+    return t_run(1, &d_image, &nd, d3, d_out, capacity, h_out_count, d_out_count, ws, ws_bytes, max_survivors,
+                 stream);
 }
 
 }  // namespace
@@ -620,7 +646,23 @@ int cubical_persistence_3d(const float* d_image, const int64_t dims[3], cp_pair*
 }
 
 size_t cubical_persistence_t_workspace_size(int ndim, const int64_t* dims, int64_t max_survivors) {
-    return t_workspace(ndim, dims, max_survivors, nullptr);
+    if ((ndim != 2 && ndim != 3) || !dims) return 0;
+    const int32_t nd = ndim;
+    const int64_t d3[3] = {ndim == 3 ? dims[0] : 1, dims[ndim - 2], dims[ndim - 1]};
+    return t_workspace(1, &nd, d3, max_survivors, nullptr);
+}
+
+size_t cubical_persistence_t_batched_workspace_size(int n_items, const int32_t* ndims, const int64_t* dims,
+                                                    int64_t max_survivors) {
+    return t_workspace(n_items, ndims, dims, max_survivors, nullptr);
+}
+
+int cubical_persistence_t_batched(int n_items, const float* const* h_images, const int32_t* ndims,
+                                  const int64_t* dims, cp_pair* d_out_pairs, int64_t capacity, int64_t* h_out_count,
+                                  int64_t* d_out_count, void* d_workspace, size_t ws_bytes, int64_t max_survivors,
+                                  void* stream) {
+    return t_run(n_items, h_images, ndims, dims, d_out_pairs, capacity, h_out_count, d_out_count, d_workspace,
+                 ws_bytes, max_survivors, stream);
 }
 
 int cubical_persistence_t_2d(const float* d_image, const int64_t dims[2], cp_pair* d_out_pairs, int64_t capacity,

@@ -119,22 +119,29 @@ cudaError_t launch_uf(const ItemTable& tab, const UfParams* p, int nprob, cudaSt
 // ---- K4 emission, K5 backward
 cudaError_t launch_init(const ItemTable& tab, Counters* ctr, uint32_t* uft, uint64_t* aget, uint64_t* rest,
                         cudaStream_t s);
-// T-filtration by duality (cp_tfilt.cu): the image I's extents (D = 1 in 2D).
+// T-filtration by duality (cp_tfilt.cu), per item by the caller's index.
 struct TDims {
     int ndim;
-    int64_t D, H, W;
+    int64_t D, H, W;  // the image's extents (D = 1 in 2D)
 };
-// J <- -I flipped along every axis, inside a one-voxel frame at -FLT_MAX
-// (extents +2 along each image axis); *bad <- 1 if a pixel is not below
-// FLT_MAX (the frame would not come first).
-cudaError_t launch_t_build(const float* img, const TDims& t, float* J, uint32_t* bad, cudaStream_t s);
-// After the pruning pass: every frame vertex's H0 link points at vertex 0.
-cudaError_t launch_t_flatten(uint32_t* uf0, const TDims& t, cudaStream_t s);
-// V pairs of J -> T pairs of I, in place; the frame's class gets the last sort
-// key (birth cell 2^cell_bits - 1), ctr->t_keep the count without it, and a
-// set *bad flags the call as non-finite.
-cudaError_t launch_t_map(cp_pair* pairs, const uint32_t* d_n, uint32_t cap, const TDims& t, const uint32_t* bad,
-                         int cell_bits, Counters* ctr, cudaStream_t s);
+struct TItems {
+    int n;
+    TDims d[kMaxItems];
+    const float* img[kMaxItems];  // the image
+    float* J[kMaxItems];          // its dual image: extents +2 along each image axis
+    int64_t voff[kMaxItems];      // J's first vertex in the call's vertex space
+};
+// J <- -image flipped along every axis, inside a one-voxel frame at -FLT_MAX;
+// *bad <- 1 if a pixel is not below FLT_MAX (the frame would not come first).
+cudaError_t launch_t_build(const TItems& t, uint32_t* bad, cudaStream_t s);
+// After the pruning pass: every frame vertex's H0 link points at the item's
+// vertex 0.
+cudaError_t launch_t_flatten(uint32_t* uf0, const TItems& t, cudaStream_t s);
+// V pairs of J -> T pairs of the images, in place; each item's frame class
+// gets item index n (it sorts after every kept pair), ctr->t_keep the count
+// without them, and a set *bad flags the call as non-finite.
+cudaError_t launch_t_map(cp_pair* pairs, const uint32_t* d_n, uint32_t cap, const TItems& t, const uint32_t* bad,
+                         Counters* ctr, cudaStream_t s);
 cudaError_t launch_essential(const ItemTable& tab, Counters* ctr, cp_pair* pairs, uint32_t pair_cap, cudaStream_t s);
 cudaError_t launch_pair_keys(const cp_pair* pairs, const uint32_t* d_n, uint32_t cap, uint64_t* keys, uint32_t* vals,
                              int cell_bits, cudaStream_t s);

@@ -38,23 +38,27 @@ constexpr int kTT = 256;
 // the largest finite float (a pixel at that float, or above it, is flagged).
 constexpr float kFrame = -3.40282347e38f;
 
-// J row by row (one division per row; consecutive threads write consecutive
-// x and read consecutive, reversed, pixels of the mirrored row of I).
-__global__ void __launch_bounds__(kTT) k_t_build(const float* __restrict__ img, TDims t, float* __restrict__ J,
-                                                 uint32_t* bad) {
-    const int64_t Dj = t.ndim == 3 ? t.D + 2 : 1, Hj = t.H + 2, Wj = t.W + 2;
+// J row by row, item blockIdx.y (one division per row; consecutive threads
+// write consecutive x and read consecutive, reversed, pixels of the mirrored
+// row of the image).
+__global__ void __launch_bounds__(kTT) k_t_build(const __grid_constant__ TItems t, uint32_t* bad) {
+    const int item = blockIdx.y;
+    const TDims& d = t.d[item];
+    const float* __restrict__ img = t.img[item];
+    float* __restrict__ J = t.J[item];
+    const int64_t Dj = d.ndim == 3 ? d.D + 2 : 1, Hj = d.H + 2, Wj = d.W + 2;
     const int64_t rows = Dj * Hj;
     bool flag = false;
     for (int64_t r = blockIdx.x; r < rows; r += gridDim.x) {
         const int64_t z = r / Hj, y = r - z * Hj;
-        const bool frame_row = y == 0 || y == Hj - 1 || (t.ndim == 3 && (z == 0 || z == Dj - 1));
-        const int64_t iz = t.ndim == 3 ? t.D - z : 0;
-        const float* in = img + (iz * t.H + (t.H - y)) * t.W;  // dereferenced only inside the image
+        const bool frame_row = y == 0 || y == Hj - 1 || (d.ndim == 3 && (z == 0 || z == Dj - 1));
+        const int64_t iz = d.ndim == 3 ? d.D - z : 0;
+        const float* in = img + (iz * d.H + (d.H - y)) * d.W;  // dereferenced only inside the image
         float* out = J + r * Wj;
         for (int64_t x = threadIdx.x; x < Wj; x += kTT) {
             float v = kFrame;
             if (!frame_row && x > 0 && x < Wj - 1) {
-                const float a = __ldg(in + (t.W - x));
+                const float a = __ldg(in + (d.W - x));
                 flag |= !(a < 3.40282347e38f);  // NaN, +inf, the largest float: the frame would not lie below
                 v = -a;
             }
@@ -64,19 +68,24 @@ __global__ void __launch_bounds__(kTT) k_t_build(const float* __restrict__ img, 
     if (__any_sync(0xFFFFFFFFu, flag) && (threadIdx.x & 31u) == 0) atomicOr(bad, 1u);
 }
 
-// After the pruning pass: every frame vertex of J points straight at vertex
-// 0, the frame's root.  The frame is one tree of equal values in which the
-// pruning pass links each vertex to an earlier neighbour; its chains along y
-// and x run the whole length of a face, and every walk from a basin that
-// drains to the border would otherwise follow them.  Vertex 0 is an ancestor
-// of every frame vertex (every frame vertex but 0 has an earlier neighbour in
-// the frame, and equal values order by index), so the shortcut changes no root.
-__global__ void __launch_bounds__(kTT) k_t_flatten(uint32_t* __restrict__ uf0, TDims t) {
-    const int64_t Dj = t.ndim == 3 ? t.D + 2 : 1, Hj = t.H + 2, Wj = t.W + 2;
+// After the pruning pass: every frame vertex of J points straight at J's
+// vertex 0, the frame's root.  The frame is one tree of equal values in which
+// the pruning pass links each vertex to an earlier neighbour; its chains
+// along y and x run the whole length of a face, and every walk from a basin
+// that drains to the border would otherwise follow them.  Vertex 0 is an
+// ancestor of every frame vertex (every frame vertex but 0 has an earlier
+// neighbour in the frame, and equal values order by index), so the shortcut
+// changes no root.  Item blockIdx.y.
+__global__ void __launch_bounds__(kTT) k_t_flatten(uint32_t* __restrict__ uf0, const __grid_constant__ TItems t) {
+    const int item = blockIdx.y;
+    const TDims& d = t.d[item];
+    uint32_t* __restrict__ uf = uf0 + t.voff[item];
+    const uint32_t root = uint32_t(t.voff[item]);
+    const int64_t Dj = d.ndim == 3 ? d.D + 2 : 1, Hj = d.H + 2, Wj = d.W + 2;
     // whole frame rows, one block per row: both y faces of every plane, and
     // the two z faces (3D)
-    const int64_t zf = t.ndim == 3 ? 2 * Hj : 0;  // rows of the two z faces
-    const int64_t nrows = zf + 2 * (t.ndim == 3 ? Dj - 2 : 1);
+    const int64_t zf = d.ndim == 3 ? 2 * Hj : 0;  // rows of the two z faces
+    const int64_t nrows = zf + 2 * (d.ndim == 3 ? Dj - 2 : 1);
     for (int64_t f = blockIdx.x; f < nrows; f += gridDim.x) {
         int64_t z, y;
         if (f < zf) {
@@ -84,20 +93,20 @@ __global__ void __launch_bounds__(kTT) k_t_flatten(uint32_t* __restrict__ uf0, T
             y = f % Hj;
         } else {
             const int64_t g = f - zf;
-            z = t.ndim == 3 ? 1 + g / 2 : 0;
+            z = d.ndim == 3 ? 1 + g / 2 : 0;
             y = (g & 1) ? Hj - 1 : 0;
         }
-        uint32_t* row = uf0 + (z * Hj + y) * Wj;
+        uint32_t* row = uf + (z * Hj + y) * Wj;
         for (int64_t x = threadIdx.x; x < Wj; x += kTT)
-            if (z != 0 || y != 0 || x != 0) row[x] = 0u;
+            if (z != 0 || y != 0 || x != 0) row[x] = root;
     }
     // the two x faces of the other rows
-    const int64_t zi = t.ndim == 3 ? Dj - 2 : 1, yi = Hj - 2;
+    const int64_t zi = d.ndim == 3 ? Dj - 2 : 1, yi = Hj - 2;
     const int64_t nside = 2 * zi * yi;
     for (int64_t k = int64_t(blockIdx.x) * kTT + threadIdx.x; k < nside; k += int64_t(gridDim.x) * kTT) {
         const int64_t q = k >> 1;
-        const int64_t z = t.ndim == 3 ? 1 + q / yi : 0, y = 1 + q % yi;
-        uf0[(z * Hj + y) * Wj + ((k & 1) ? Wj - 1 : 0)] = 0u;
+        const int64_t z = d.ndim == 3 ? 1 + q / yi : 0, y = 1 + q % yi;
+        uf[(z * Hj + y) * Wj + ((k & 1) ? Wj - 1 : 0)] = root;
     }
 }
 
@@ -126,20 +135,24 @@ __device__ __forceinline__ float neg_canon(float v) {
     return r == 0.0f ? 0.0f : r;  // -0.0 reads as +0.0
 }
 
-__global__ void __launch_bounds__(kTT) k_t_map(cp_pair* __restrict__ pairs, const uint32_t* d_n, uint32_t cap, TDims t,
-                                               const uint32_t* bad, int cell_bits, Counters* ctr) {
+__global__ void __launch_bounds__(kTT) k_t_map(cp_pair* __restrict__ pairs, const uint32_t* d_n, uint32_t cap,
+                                               const __grid_constant__ TItems ti, const uint32_t* bad,
+                                               Counters* ctr) {
     const uint32_t n = min(*d_n, cap);
-    const int top = t.ndim - 1;
     for (uint32_t i = blockIdx.x * kTT + threadIdx.x; i < n; i += gridDim.x * kTT) {
         const cp_pair p = pairs[i];
+        const TDims& t = ti.d[(p.item >= 0 && p.item < ti.n) ? p.item : 0];
+        const int top = t.ndim - 1;
         cp_pair q;
         q.item = p.item;
         if (p.dim == 0 && p.death_cell < 0) {
-            // the frame's class (the outside of the T-complex): dropped; its key
-            // sorts after every kept pair, outside the kept count
+            // an item's frame class (the outside of its T-complex): dropped; its
+            // item index one past the last sorts it after every kept pair,
+            // outside the kept count
             q = p;
-            q.dim = top;
-            q.birth_cell = int32_t((1u << cell_bits) - 1u);
+            q.item = ti.n;
+            q.dim = 0;
+            q.birth_cell = 0;
         } else if (p.dim == top && p.birth == kFrame) {
             // the last merge into the outside, through a frame facet: the T
             // essential class, born at the T vertex dual to the dying top cell
@@ -162,7 +175,7 @@ __global__ void __launch_bounds__(kTT) k_t_map(cp_pair* __restrict__ pairs, cons
         pairs[i] = q;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-        ctr->t_keep = n > 0 ? n - 1u : 0u;
+        ctr->t_keep = n > uint32_t(ti.n) ? n - uint32_t(ti.n) : 0u;  // one frame class per item
         if (*bad) set_status(ctr, kStNonfinite);
     }
 }
@@ -175,25 +188,27 @@ int grid_of(int64_t n) {
 
 }  // namespace
 
-cudaError_t launch_t_build(const float* img, const TDims& t, float* J, uint32_t* bad, cudaStream_t s) {
+cudaError_t launch_t_build(const TItems& t, uint32_t* bad, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(bad, 0, sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
-    const int64_t rows = (t.ndim == 3 ? t.D + 2 : 1) * (t.H + 2);
-    const int64_t cap = int64_t(device_sm_count()) * 16;
-    k_t_build<<<int(rows < cap ? rows : cap), kTT, 0, s>>>(img, t, J, bad);
+    if (t.n < 1 || t.n > kMaxItems) return cudaErrorInvalidValue;
+    const int gx = (device_sm_count() * 16 + t.n - 1) / t.n;
+    k_t_build<<<dim3(gx, t.n), kTT, 0, s>>>(t, bad);
     note_launches(1);
     return cudaGetLastError();
 }
 
-cudaError_t launch_t_flatten(uint32_t* uf0, const TDims& t, cudaStream_t s) {
-    k_t_flatten<<<device_sm_count() * 8, kTT, 0, s>>>(uf0, t);
+cudaError_t launch_t_flatten(uint32_t* uf0, const TItems& t, cudaStream_t s) {
+    if (t.n < 1 || t.n > kMaxItems) return cudaErrorInvalidValue;
+    const int gx = (device_sm_count() * 8 + t.n - 1) / t.n;
+    k_t_flatten<<<dim3(gx, t.n), kTT, 0, s>>>(uf0, t);
     note_launches(1);
     return cudaGetLastError();
 }
 
-cudaError_t launch_t_map(cp_pair* pairs, const uint32_t* d_n, uint32_t cap, const TDims& t, const uint32_t* bad,
-                         int cell_bits, Counters* ctr, cudaStream_t s) {
-    k_t_map<<<grid_of(cap), kTT, 0, s>>>(pairs, d_n, cap, t, bad, cell_bits, ctr);
+cudaError_t launch_t_map(cp_pair* pairs, const uint32_t* d_n, uint32_t cap, const TItems& t, const uint32_t* bad,
+                         Counters* ctr, cudaStream_t s) {
+    k_t_map<<<grid_of(cap), kTT, 0, s>>>(pairs, d_n, cap, t, bad, ctr);
     note_launches(1);
     return cudaGetLastError();
 }

@@ -135,3 +135,28 @@ def test_t_gradient(cp):
         want[r["death_pixel"]] += g
         want[r["birth_pixel"]] -= g
     np.testing.assert_allclose(x.grad.cpu().numpy().ravel(), want.astype(np.float32), rtol=1e-6, atol=1e-6)
+
+
+def test_t_batched_mixed(cp):
+    """Images and volumes of uneven sizes (extents of 1 included) in one
+    T-filtration call: each item's pairs equal the oracle's for that item,
+    in (item, dim, birth cell) order."""
+    rng = np.random.default_rng(609)
+    items = []
+    for k in range(14):
+        if k % 3 == 2:
+            shape = tuple(int(v) for v in rng.integers(1, 14, 3))
+        else:
+            shape = tuple(int(v) for v in rng.integers(1, 60, 2))
+        img = rng.integers(0, 3, shape).astype(np.float32) if rng.random() < 0.4 else rng.random(shape, dtype=np.float32)
+        items.append(img)
+    items.append(workloads.blurred((40, 33, 29), 2.0, 610))
+    d = cp.persistence_batched([torch.from_numpy(a).cuda() for a in items], filtration="T")
+    got = d.numpy()
+    assert np.all(np.diff(got["item"]) >= 0)
+    for i, a in enumerate(items):
+        g = got[got["item"] == i]
+        w = oracle.persistence_t(a)
+        assert len(g) == len(w), (i, a.shape, len(g), len(w))
+        for k in FIELDS:
+            assert np.array_equal(g[k], w[k]), (i, a.shape, k)
