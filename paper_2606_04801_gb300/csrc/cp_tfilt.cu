@@ -38,9 +38,11 @@ constexpr int kTT = 256;
 // the largest finite float (a pixel at that float, or above it, is flagged).
 constexpr float kFrame = -3.40282347e38f;
 
-// J row by row, item blockIdx.y (one division per row; consecutive threads
-// write consecutive x and read consecutive, reversed, pixels of the mirrored
-// row of the image).
+// J four rows at a time, item blockIdx.y (the rows' divisions once per group;
+// consecutive threads write consecutive x and read consecutive, reversed,
+// pixels of the mirrored rows of the image; four loads in flight per thread).
+constexpr int kTRows = 4;
+
 __global__ void __launch_bounds__(kTT) k_t_build(const __grid_constant__ TItems t, uint32_t* bad) {
     const int item = blockIdx.y;
     const TDims& d = t.d[item];
@@ -49,20 +51,32 @@ __global__ void __launch_bounds__(kTT) k_t_build(const __grid_constant__ TItems 
     const int64_t Dj = d.ndim == 3 ? d.D + 2 : 1, Hj = d.H + 2, Wj = d.W + 2;
     const int64_t rows = Dj * Hj;
     bool flag = false;
-    for (int64_t r = blockIdx.x; r < rows; r += gridDim.x) {
-        const int64_t z = r / Hj, y = r - z * Hj;
-        const bool frame_row = y == 0 || y == Hj - 1 || (d.ndim == 3 && (z == 0 || z == Dj - 1));
-        const int64_t iz = d.ndim == 3 ? d.D - z : 0;
-        const float* in = img + (iz * d.H + (d.H - y)) * d.W;  // dereferenced only inside the image
-        float* out = J + r * Wj;
+    for (int64_t r0 = int64_t(blockIdx.x) * kTRows; r0 < rows; r0 += int64_t(gridDim.x) * kTRows) {
+        const float* in[kTRows];
+        bool live[kTRows];  // an image row (else a frame row, or past the end)
+#pragma unroll
+        for (int k = 0; k < kTRows; ++k) {
+            const int64_t r = r0 + k;
+            const int64_t z = r / Hj, y = r - z * Hj;
+            live[k] = r < rows && y != 0 && y != Hj - 1 && (d.ndim != 3 || (z != 0 && z != Dj - 1));
+            const int64_t iz = d.ndim == 3 ? d.D - z : 0;
+            in[k] = img + (iz * d.H + (d.H - y)) * d.W;  // dereferenced only when live
+        }
         for (int64_t x = threadIdx.x; x < Wj; x += kTT) {
-            float v = kFrame;
-            if (!frame_row && x > 0 && x < Wj - 1) {
-                const float a = __ldg(in + (d.W - x));
-                flag |= !(a < 3.40282347e38f);  // NaN, +inf, the largest float: the frame would not lie below
-                v = -a;
+            const bool inner = x > 0 && x < Wj - 1;
+            float a[kTRows];
+#pragma unroll
+            for (int k = 0; k < kTRows; ++k) a[k] = (live[k] && inner) ? __ldg(in[k] + (d.W - x)) : 0.0f;
+#pragma unroll
+            for (int k = 0; k < kTRows; ++k) {
+                if (r0 + k >= rows) break;
+                float v = kFrame;
+                if (live[k] && inner) {
+                    flag |= !(a[k] < 3.40282347e38f);  // NaN, +inf, the largest float: the frame would not lie below
+                    v = -a[k];
+                }
+                J[(r0 + k) * Wj + x] = v;
             }
-            out[x] = v;
         }
     }
     if (__any_sync(0xFFFFFFFFu, flag) && (threadIdx.x & 31u) == 0) atomicOr(bad, 1u);
