@@ -8,7 +8,7 @@ its backward scatter -- with no host round trip.  With `graph=True` the step
 is captured once into a CUDA graph and each `step()` is a single graph
 launch.
 
-    bp = BatchedPersistence([(512, 384), (128, 96, 80), ...], tau=0.05)
+    bp = BatchedPersistence([(512, 384), (128, 96, 80), ...], tau=0.05)   # filtration="T" as well
     bp.load([img0, vol1, ...])        # copies the inputs in
     loss, grad = bp.step()            # device tensors (grad packed per item)
     pairs = bp.pairs()                # Diagram with an `item` field
@@ -28,14 +28,17 @@ from .api import Diagram, _stats
 
 class BatchedPersistence:
     def __init__(self, shapes: Sequence[Sequence[int]], tau: float = 0.05, device=None, max_survivors: int = 0,
-                 graph: bool = True):
+                 graph: bool = True, filtration: str = "V"):
         if not shapes or len(shapes) > _lib.CP_MAX_ITEMS:
             raise ValueError(f"between 1 and {_lib.CP_MAX_ITEMS} items")
+        if filtration not in ("V", "T"):
+            raise ValueError("filtration must be 'V' or 'T'")
+        self.tmode = filtration == "T"
         self.lib = _lib.load()
         self.dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         self.shapes = [tuple(int(v) for v in s) for s in shapes]
         for s in self.shapes:
-            if len(s) not in (2, 3) or min(s) < 2:
+            if len(s) not in (2, 3) or min(s) < (1 if self.tmode else 2):
                 raise ValueError(f"bad shape {s}")
         self.tau = float(tau)
         self.k = len(self.shapes)
@@ -62,13 +65,20 @@ class BatchedPersistence:
 
     def _plan(self, ms: int):
         self.ms = ms
-        ws = self.lib.cubical_persistence_batched_workspace_size(self.k, self._ndims, self._dims, ms)
+        wsize = (self.lib.cubical_persistence_t_batched_workspace_size if self.tmode
+                 else self.lib.cubical_persistence_batched_workspace_size)
+        ws = wsize(self.k, self._ndims, self._dims, ms)
         if ws == 0:
             raise CpError(_lib.CP_ERR_ARG, "batched workspace size")
         self.ws = torch.empty(ws, dtype=torch.uint8, device=self.dev)
-        eff = ms if ms > 0 else self.total // 2 + 65536
-        tops = sum(int(np.prod([v - 1 for v in s])) + 1 for s in self.shapes)
-        self.cap = min(self.total + tops, eff + 2 * self.k + 4096)
+        if self.tmode:  # the dual images' vertices; T vertices + top cells per item
+            nv = sum(int(np.prod([v + 2 for v in s])) for s in self.shapes)
+            bound = sum(int(np.prod(s)) + int(np.prod([v + 1 for v in s])) for s in self.shapes)
+        else:
+            nv = self.total
+            bound = self.total + sum(int(np.prod([v - 1 for v in s])) + 1 for s in self.shapes)
+        eff = ms if ms > 0 else nv // 2 + 65536
+        self.cap = min(bound, eff + 2 * self.k + 4096)
         self.out = torch.empty((self.cap, 8), dtype=torch.int32, device=self.dev)
         self.graph = None
 
@@ -81,12 +91,13 @@ class BatchedPersistence:
     def _enqueue(self, stream_ptr: int):
         lib = self.lib
         sp = ctypes.c_void_p(stream_ptr)
-        rc = lib.cubical_persistence_batched(
+        fn = lib.cubical_persistence_t_batched if self.tmode else lib.cubical_persistence_batched
+        rc = fn(
             self.k, self._ptrs, self._ndims, self._dims, ctypes.c_void_p(self.out.data_ptr()), self.cap, None,
             ctypes.c_void_p(self.d_count.data_ptr()), ctypes.c_void_p(self.ws.data_ptr()), self.ws.numel(), self.ms, sp,
         )
         if rc != CP_OK:
-            raise CpError(rc, "cubical_persistence_batched")
+            raise CpError(rc, "cubical_persistence_batched" + ("_t" if self.tmode else ""))
         rc = lib.cubical_persistence_loss_backward(
             ctypes.c_void_p(self.out.data_ptr()), self.cap, ctypes.c_void_p(self.d_count.data_ptr()),
             ctypes.c_float(self.tau), ctypes.c_void_p(self.loss.data_ptr()),

@@ -160,3 +160,38 @@ def test_t_batched_mixed(cp):
         assert len(g) == len(w), (i, a.shape, len(g), len(w))
         for k in FIELDS:
             assert np.array_equal(g[k], w[k]), (i, a.shape, k)
+
+
+def test_t_batched_graph_step(cp):
+    """The batched forward + loss + backward of the T-filtration as one CUDA
+    graph: pairs per item equal the oracle's, the loss is their total
+    persistence above tau, and the gradient scatters to their pixels."""
+    rng = np.random.default_rng(611)
+    items = [rng.random((23, 31), dtype=np.float32), workloads.blurred((12, 14, 10), 1.5, 612),
+             rng.integers(0, 3, (1, 17)).astype(np.float32), rng.random((5, 1, 7), dtype=np.float32)]
+    tau = 0.05
+    bp = cp.BatchedPersistence([a.shape for a in items], tau=tau, filtration="T", graph=True)
+    bp.load([torch.from_numpy(a) for a in items])
+    loss, grad = bp.step()
+    loss, grad = bp.step()  # a replay of the captured graph
+    torch.cuda.synchronize()
+    got = bp.pairs().numpy()
+    want_loss = 0.0
+    grads = bp.grads()
+    for i, a in enumerate(items):
+        g = got[got["item"] == i]
+        w = oracle.persistence_t(a)
+        assert len(g) == len(w)
+        for k in FIELDS:
+            assert np.array_equal(g[k], w[k]), (i, k)
+        ref = np.zeros(a.size, dtype=np.float64)
+        for r in w:
+            if r["death_cell"] < 0:
+                continue
+            pers = float(r["death"]) - float(r["birth"])
+            if pers > tau:
+                want_loss += pers * pers
+                ref[r["death_pixel"]] += 2.0 * pers
+                ref[r["birth_pixel"]] -= 2.0 * pers
+        np.testing.assert_allclose(grads[i].cpu().numpy().ravel(), ref.astype(np.float32), rtol=1e-6, atol=1e-6)
+    assert abs(float(loss.item()) - want_loss) <= 1e-9 * max(1.0, want_loss)
