@@ -17,6 +17,7 @@ import argparse
 import ctypes
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -191,6 +192,21 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def _host():
+    """The host the CPU baseline ran on: logical CPUs and the CPU model."""
+    model = platform.processor() or platform.machine()
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                k, _, v = line.partition(":")
+                if k.strip() in ("model name", "Model", "CPU part") and v.strip():
+                    model = v.strip()
+                    break
+    except OSError:
+        pass
+    return {"nproc": os.cpu_count(), "cpu": model, "machine": platform.machine()}
+
+
 def cpu_baseline(vol, budget_s=20.0):
     """The oracle as it stands, timed on this host (1 thread) on a crop of the volume."""
     import oracle
@@ -214,6 +230,7 @@ def cpu_baseline(vol, budget_s=20.0):
         "value": crop.size / dt / 1e6,
         "unit": "Mvoxels/s",
         "cores": 1,
+        "host": _host(),
         "kind": "oracle",
         "sample": f"{side}^3 crop of the 512^3 volume, H0 + H2 pairs, single-threaded C oracle, {dt:.1f} s",
     }
@@ -252,6 +269,7 @@ def batched_cpu_baseline(items, budget_s=10.0):
         "value": done / dt / 1e6,
         "unit": "Mvoxels/s",
         "cores": cores,
+        "host": _host(),
         "kind": "oracle",
         "sample": f"{len(sample)} of {len(items)} items ({done / 1e6:.1f} M voxels, items up to 3 M voxels), "
         f"one item per task in a pool of {cores} processes, {dt:.1f} s",
@@ -552,7 +570,7 @@ def run_tfilt(args):
             oracle.persistence_t(crop)
             dt = time.perf_counter() - t0
             c = c2
-        cpu = {"value": crop.size / dt / 1e6, "unit": "Mvoxels/s", "cores": 1, "kind": "oracle",
+        cpu = {"value": crop.size / dt / 1e6, "unit": "Mvoxels/s", "cores": 1, "host": _host(), "kind": "oracle",
                "sample": f"{c}^3 crop of the {side}^3 volume, T-filtration H0 + H2 pairs, single-threaded C oracle, {dt:.1f} s"}
     if rank == 0:
         print(json.dumps({
@@ -802,6 +820,7 @@ def main():
         "limiter": "issue/ALU (ncu: issue slots 66% busy, ALU pipe 61%, DRAM 8%)",
         "peak_source": peak_kind,
         "algorithmic_bytes": alg,
+        "read_lower_bound_bytes": 4 * N,  # the image read once, nothing written
         "k1_ms": k1 * 1e3 if k1 else None,
     }
     trace = {}
