@@ -184,6 +184,7 @@ def run_reference(args):
             "value": value,
             "unit": "Mvoxels/s",
             "cores": 1,
+            "host": _host(),
             "kind": "oracle",
             "sample": f"{side}^3 crop of the 512^3 blurred volume (same recipe), H0 + H2 pairs",
         },
