@@ -164,6 +164,11 @@ constexpr uint32_t kMvInvalid = 1u << 8;  // no corner holds the top cell (non-f
 struct Smem3 {
     float ring[kRing][kSlot];  // first: slots 128-byte aligned (TMA destinations)
     uint64_t bar[kRing];       // mbarrier of each slot (TMA completion)
+    const CUtensorMap* tma_map;  // the current task's plane source (read by the issuing thread only)
+    int tma_xs, tma_ys;
+    // the current task's constants, read where used (fewer live registers)
+    uint32_t t_HW, t_HW1, t_OUT;
+    int t_z0, t_z1, t_D, t_zneed;
     int2 tlink[8 * 16];        // dual links by (t, v), for the current item
     int32_t h0link[24];        // H0 link offset by face bit n, for the current item
     uint16_t disp[1 << 12];    // displacement table of the 3D perfect hash
@@ -171,6 +176,7 @@ struct Smem3 {
     // per column and plane step: the code fields of the top cells on the +z
     // side of the column's vertex at z-1 and on the -z side of its vertex at z
     uint32_t q[3][kW3 + 1][32];
+    unsigned long long tmin[kT3];  // each thread's smallest H0 root key in the current task (rarely touched)
     WarpStage ws[kW3];
 };
 
@@ -376,7 +382,7 @@ __device__ __forceinline__ void issue_plane(Smem3& sm, const Item& it, int z, co
                 // earlier generic-proxy accesses of the slot come before the copy
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 mbar_expect_tx(&sm.bar[slot], uint32_t(kRH * kRS * sizeof(float)));
-                tma_load_plane(plane, ps.map, &sm.bar[slot], ps.xs, ps.ys, z);
+                tma_load_plane(plane, sm.tma_map, &sm.bar[slot], sm.tma_xs, sm.tma_ys, z);
             }
         } else {  // a plane outside the volume: every position +inf
             for (int i = threadIdx.x; i < kRH * kRS; i += kT3) plane[i] = inf;
@@ -458,14 +464,29 @@ __device__ __forceinline__ void prune_task3d(Smem3& sm, const ItemTable& tab, co
     src.zneed = zlast + 1;
     if constexpr (!kTma) ring_positions(it, x0, y0, rp);
     const int xo = kTma ? (x0 - 2) - src.xs : 0;  // column x0-2 within a slot row
+    if (kTma && threadIdx.x == 0) {
+        sm.tma_map = map;
+        sm.tma_xs = src.xs;
+        sm.tma_ys = src.ys;
+    }
     if (kTma && threadIdx.x == 0) atomicAdd(&o.ctr->tma_tasks, 1u);
     // global vertex index and top-cell index of this column in plane 0
     const uint32_t colv = cc.voff + uint32_t(cc.y) * cc.W + uint32_t(cc.x);
     const uint32_t colt = cc.toff + uint32_t(cc.y) * cc.W1 + uint32_t(cc.x);
-    unsigned long long my_min = ~0ull;
     uint32_t far = 0, far_t = 0;  // last H0 link / dual link written by this thread
     uint32_t cprev = 0;           // code fields of this column's vertex one plane behind
-    __syncthreads();  // the rings and link tables may still be read by the previous task
+    __syncthreads();  // the rings, link tables and task constants may still be read by the previous task
+    if (threadIdx.x == 0) {
+        sm.t_HW = cc.HW;
+        sm.t_HW1 = cc.HW1;
+        sm.t_OUT = cc.OUT;
+        sm.t_z0 = z0;
+        sm.t_z1 = z1;
+        sm.t_D = it.D;
+        sm.t_zneed = zlast + 1;
+    }
+    __syncthreads();  // the task constants are read from here on
+    sm.tmin[threadIdx.x] = ~0ull;
     if constexpr (!kTma) ring_init(sm, rp);
     if (threadIdx.x < 8 * 16) {
         // top cell in slot t of its largest corner m, linked to slot c of m: the
@@ -515,9 +536,9 @@ __device__ __forceinline__ void prune_task3d(Smem3& sm, const ItemTable& tab, co
         const uint32_t q = (cprev & 0xFFFF0000u) | (codes & 0x0000FFFFu);
         sm.q[qs][warp][lane] = q;
         cprev = codes;
-        const bool owned = cc.owned_xy && z < z1;
+        const bool owned = cc.owned_xy && z < sm.t_z1;
         const uint32_t ord = ord_bits(cv);
-        const uint32_t vg = colv + uint32_t(z) * cc.HW;
+        const uint32_t vg = colv + uint32_t(z) * sm.t_HW;
         const uint32_t f0 = rel & kFaces3;  // the first edge of L(v) is its lowest face bit
         bool root0 = false;
         if (owned) {
@@ -526,12 +547,12 @@ __device__ __forceinline__ void prune_task3d(Smem3& sm, const ItemTable& tab, co
                 root0 = true;
                 far = vg;
                 const unsigned long long k = (unsigned long long)(uint64_t(ord) << 32 | (vg - uint32_t(it.voff)));
-                my_min = k < my_min ? k : my_min;
+                if (k < sm.tmin[threadIdx.x]) sm.tmin[threadIdx.x] = k;
             } else {
                 // a link to (z-1, y, x) (face bit 4, the lowest) continues the chain
                 // that the z-1 neighbour (same thread, previous step) started
                 const uint32_t u = vg + uint32_t(sm.h0link[__ffs(f0) - 1]);
-                far = ((f0 & 16u) && z > z0) ? far : u;
+                far = ((f0 & 16u) && z > sm.t_z0) ? far : u;
                 o.uf0[vg] = far;
             }
         }
@@ -553,7 +574,7 @@ __device__ __forceinline__ void prune_task3d(Smem3& sm, const ItemTable& tab, co
         uint64_t rt_age = 0;
         if (cc.cube_xy && z > z0) {
             const uint32_t acc = acc_row | (q10 & kM51) | (q11 & kM40);
-            const uint32_t self = colt + uint32_t(z - 1) * cc.HW1;
+            const uint32_t self = colt + uint32_t(z - 1) * sm.t_HW1;
             uint32_t fs = 0;
             int2 lk = make_int2(0, int(kMvInvalid));
             if (acc != 0u) {
@@ -565,8 +586,8 @@ __device__ __forceinline__ void prune_task3d(Smem3& sm, const ItemTable& tab, co
                 const uint32_t bnd = cc.bmv | (z == 1 ? 1u : 0u) | (uint32_t(z) == cc.D - 1u ? 32u : 0u);
                 // a link to (z-2, y, x) continues the chain that this thread wrote for
                 // that top cell in the previous step
-                const bool chain = (bits & kMvChain) && z - 1 > z0;
-                far_t = chain ? far_t : ((bits & bnd) ? cc.OUT : self + uint32_t(lk.x));
+                const bool chain = (bits & kMvChain) && z - 1 > sm.t_z0;
+                far_t = chain ? far_t : ((bits & bnd) ? sm.t_OUT : self + uint32_t(lk.x));
                 o.uft[self] = far_t;
             } else if (bits & kMvRoot) {
                 rootT = true;
@@ -647,7 +668,7 @@ __device__ __forceinline__ void prune_task3d(Smem3& sm, const ItemTable& tab, co
         if (++z > zlast) break;
     }
     cp_async_wait<0>();
-    const unsigned long long w = warp_min_u64(my_min);
+    const unsigned long long w = warp_min_u64(sm.tmin[threadIdx.x]);
     if (lane == 0 && w != ~0ull) atomicMin(&o.ctr->gmin[ii], w);
 }
 
