@@ -338,8 +338,7 @@ int run(const Plan& P, cp_pair* d_out, int64_t capacity, int64_t* h_out_count, i
         ra.uf = uf0;
         ra.dual = 0;
         ra.d_n_before = nullptr;
-        CP_TRY(launch_roots(ra, s));
-        CP_TRY(launch_roots(rt, s));
+        CP_TRY(launch_roots2(ra, rt, s));
         SortBufs two[2] = {sb, sb};
         two[0].keys = s0;
         two[0].d_count = &ctr->n_s0;

@@ -109,6 +109,8 @@ struct RootArgs {
     Counters* ctr;
 };
 cudaError_t launch_roots(const RootArgs& r, cudaStream_t s);
+// Both lists' first-round walks in one launch (one work counter over both).
+cudaError_t launch_roots2(const RootArgs& r0, const RootArgs& r1, cudaStream_t s);
 cudaError_t launch_place_roots(const RootArgs& r, cudaStream_t s);
 
 // One problem, or two (H0 and dual of a call without 2D items) carried through

@@ -320,6 +320,75 @@ __global__ void __launch_bounds__(kFT) k_roots(const __grid_constant__ RootArgs 
     if (lane == 0 && hops) atomicAdd(&ctr->trace_hops[r.dual][0], (unsigned long long)hops);
 }
 
+// Both lists' first-round walks in one launch (volumes): warps take 32
+// survivors at a time from one counter running over the H0 list and then the
+// dual list, so the long walks of one list overlap those of the other instead
+// of following them.  Each lane walks its own list's forest.
+__global__ void __launch_bounds__(kFT) k_roots2(const __grid_constant__ RootArgs r0,
+                                                const __grid_constant__ RootArgs r1) {
+    Counters* ctr = r0.ctr;
+    if (ld_acquire_u32(&ctr->status) & (kStTimeout | kStNonfinite)) return;
+    const uint32_t n0 = min(*r0.d_n, r0.cap), n1 = min(*r1.d_n, r1.cap);
+    const uint32_t n = n0 + n1;
+    const unsigned lane = lane_id();
+    uint32_t hops[2] = {0, 0};
+    for (;;) {
+        uint32_t base = 0;
+        if (lane == 0) base = atomicAdd(&ctr->find_ctr, 32u);
+        base = __shfl_sync(0xFFFFFFFFu, base, 0);
+        if (base >= n) break;
+        const uint32_t g = base + lane;
+        const bool live = g < n;
+        const int l = g >= n0 ? 1 : 0;  // this lane's list
+        const RootArgs& r = l ? r1 : r0;
+        const uint32_t i = l ? g - n0 : g;
+        uint32_t node[2] = {0, 0}, par[2] = {kTag, kTag};
+        if (live) {
+            uint64_t key = r.keys[i];
+            if (r.dual) key = ~key;
+            int item;
+            endpoints(r0.tab, key, r.dual, node[0], node[1], item);
+            par[0] = __ldcg(r.uf + node[0]);
+            par[1] = __ldcg(r.uf + node[1]);
+        }
+        uint64_t t0 = 0;
+        uint32_t steps = 0;
+        for (;;) {
+            bool more = false;
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                if (!(par[k] & kTag)) {
+                    node[k] = par[k];
+                    par[k] = __ldcg(r.uf + node[k]);
+                    more = true;
+                }
+            }
+            if (!more) break;
+            ++hops[l];
+            if ((++steps & 1023u) == 0) {
+                const uint64_t now = global_timer_ns();
+                if (t0 == 0) t0 = now;
+                else if (now - t0 > kWaitLimitNs) {  // only a corrupted forest gets here
+                    set_status(ctr, kStTimeout);
+                    par[0] = par[1] = kTag;
+                    break;
+                }
+            }
+        }
+        if (live) {
+            __stcg(r.ra + i, par[0] & ~kTag);
+            __stcg(r.rb + i, par[1] & ~kTag);
+            __stcg(r.pos + i, i);
+        }
+    }
+    for (int l = 0; l < 2; ++l) {
+        uint32_t h = hops[l];
+        for (int o = 16; o > 0; o >>= 1) h += __shfl_xor_sync(0xFFFFFFFFu, h, o);
+        const int d = (l ? r1 : r0).dual;
+        if (lane == 0 && h) atomicAdd(&ctr->trace_hops[d][0], (unsigned long long)h);
+    }
+}
+
 // The first active list of a problem from the sorted positions: slot off + j
 // gets sorted survivor j and the root ids of its endpoints.  The dual list of
 // a call without 2D items sits after the H0 list (off = the H0 count) when
@@ -748,6 +817,14 @@ cudaError_t launch_roots(const RootArgs& r, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(&r.ctr->find_ctr, 0, sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
     k_roots<<<find_blocks(), kFT, 0, s>>>(r);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_roots2(const RootArgs& r0, const RootArgs& r1, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(&r0.ctr->find_ctr, 0, sizeof(uint32_t), s);
+    if (e != cudaSuccess) return e;
+    k_roots2<<<find_blocks(), kFT, 0, s>>>(r0, r1);
     note_launches(1);
     return cudaGetLastError();
 }
