@@ -469,6 +469,128 @@ def run_batched(args):
         torch.distributed.destroy_process_group()
 
 
+def run_2d(args):
+    """2D configuration: the 2048x2048 Gaussian random field (sigma 8 px) and
+    the same field at 256 levels (heavy ties), fwd + total-persistence loss
+    bwd on each, device-resident input; the pruning pass's roofline (2D K1)
+    and the oracle on one host core on a crop."""
+    import torch
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        torch.distributed.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import paper_2606_04801_gb300 as cp
+    from paper_2606_04801_gb300 import _lib, autotune
+
+    lib = _lib.load()
+    imgs = workloads.config("2d_2048_grf")
+    names = ["grf", "grf_256_levels"]
+    H, W = imgs[0].shape
+    N = H * W
+    T = (H - 1) * (W - 1)
+    stream = torch.cuda.current_stream(dev)
+    sp = ctypes.c_void_p(int(stream.cuda_stream))
+    dims = (ctypes.c_int64 * 2)(H, W)
+    ws_bytes = lib.cubical_persistence_workspace_size(2, dims, 0)
+    wsp = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
+    cap = N // 2 + 65536 + 4096
+    out = torch.empty((cap, 8), dtype=torch.int32, device=dev)
+    grad = torch.empty(N, dtype=torch.float32, device=dev)
+    loss = torch.zeros(1, dtype=torch.float64, device=dev)
+    bws = lib.cubical_persistence_loss_backward_workspace_size(N)
+    bwsp = torch.empty(bws, dtype=torch.uint8, device=dev)
+    dcount = torch.zeros(1, dtype=torch.int64, device=dev)
+    peak, peak_kind = _peaks()
+    lines = {}
+    for name, img in zip(names, imgs):
+        x = torch.from_numpy(img).to(dev)
+        autotune.autotune([x])
+
+        def step():
+            rc = lib.cubical_persistence_2d(
+                ctypes.c_void_p(x.data_ptr()), dims, ctypes.c_void_p(out.data_ptr()), cap, None,
+                ctypes.c_void_p(dcount.data_ptr()), ctypes.c_void_p(wsp.data_ptr()), ws_bytes, 0, sp,
+            )
+            if rc != 0:
+                raise cp.CpError(rc, "2D forward")
+            rc = lib.cubical_persistence_loss_backward(
+                ctypes.c_void_p(out.data_ptr()), cap, ctypes.c_void_p(dcount.data_ptr()), ctypes.c_float(TAU),
+                ctypes.c_void_p(loss.data_ptr()), None, ctypes.c_void_p(grad.data_ptr()), N,
+                ctypes.c_void_p(bwsp.data_ptr()), bws, sp,
+            )
+            if rc != 0:
+                raise cp.CpError(rc, "loss backward")
+
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize(dev)
+        lib.cp_profile(1)
+        stage = (ctypes.c_float * 6)()
+        k1 = []
+        # the image (16 MiB) fits in L2: each timed step starts from a flushed L2
+        # (a 256 MiB write between steps, outside the timed events)
+        flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        total = 0.0
+        for _ in range(args.steps):
+            flush.zero_()
+            ev0.record(stream)
+            step()
+            ev1.record(stream)
+            torch.cuda.synchronize(dev)
+            total += ev0.elapsed_time(ev1) / 1e3
+            if lib.cp_stage_times(stage, 6) == 6:
+                k1.append(stage[0])
+        lib.cp_profile(0)
+        st = cp.api._stats(wsp)
+        if st["rc"] != 0:
+            raise cp.CpError(st["rc"], "2D timed steps")
+        elapsed = job_time(total, ws, dev)
+        k1s = statistics.mean(k1) / 1e3 if k1 else None
+        alg = 4 * N + 4 * N + 4 * (T + 1) + 8 * (st["h0_survivors"] + st["top_survivors"]) + 16 * (st["h0_roots"] + st["top_roots"])
+        lines[name] = {
+            "value": job_value(N, ws, args.steps, elapsed), "ms_per_step": elapsed / args.steps * 1e3,
+            "k1_ms": k1s * 1e3 if k1s else None,
+            "roofline": {"bound": "hbm", "achieved": alg / k1s / 1e9 if k1s else None, "peak": peak, "unit": "GB/s",
+                         "frac": alg / k1s / 1e9 / peak if (k1s and peak) else None, "kernel": "k_prune2d",
+                         "peak_source": peak_kind, "algorithmic_bytes": alg},
+            "counts": {k: st[k] for k in ("pairs", "h0_survivors", "top_survivors", "h0_roots", "top_roots",
+                                          "h0_rounds", "top_rounds")},
+        }
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle
+
+        oracle.build()
+        c = 512
+        crop = np.ascontiguousarray(imgs[0][:c, :c])
+        t0 = time.perf_counter()
+        oracle.persistence(crop)
+        dt = time.perf_counter() - t0
+        cpu = {"value": crop.size / dt / 1e6, "unit": "Mvoxels/s", "cores": 1, "host": _host(), "kind": "oracle",
+               "sample": f"{c}x{c} crop of the 2048x2048 field, H0 + H1 pairs, single-threaded C oracle, {dt:.1f} s"}
+    if rank == 0:
+        main = lines["grf"]
+        print(json.dumps({
+            "metric": "Mpixels/s, H0 + H1 pairs (2048x2048 fp32 Gaussian random field, sigma 8), fwd + loss bwd",
+            "value": main["value"], "unit": "Mpixels/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": main["ms_per_step"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "2D 2048x2048 float32 Gaussian random field (sigma 8 px, min-max normalised), "
+                                   "and the same field at 256 levels; fwd + total-persistence loss bwd",
+                       "l2": "input (16 MiB) smaller than L2: L2 flushed (256 MiB write) before every timed step, "
+                             "each step timed alone",
+                       "parallelism": "replicas" if ws > 1 else "single"},
+            "roofline": main["roofline"],
+            "per_image": lines,
+            "cpu_baseline": cpu,
+        }), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
 def run_tfilt(args):
     """T-filtration workload: a 510^3 blurred volume (the padded dual image the
     V pipeline runs on is exactly 512^3), forward + total-persistence loss
@@ -606,9 +728,10 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--side", type=int, default=512, help="cube side (512 is the benchmark; smaller for profiling)")
     ap.add_argument("--no-batched", action="store_true")
-    ap.add_argument("--workload", default="volume", choices=["volume", "batched", "survivors", "tfilt"],
+    ap.add_argument("--workload", default="volume", choices=["volume", "batched", "survivors", "tfilt", "2d"],
                     help="volume: the 512^3 plain path (the headline line); batched: the batched fwd + bwd workload "
-                    "alone; survivors: survivor fractions S/N of every config; tfilt: the T-filtration on 510^3")
+                    "alone; survivors: survivor fractions S/N of every config; tfilt: the T-filtration on 510^3; "
+                    "2d: the 2048x2048 random field and its 256-level form")
     ap.add_argument("--eager", action="store_true", help="batched workload without the CUDA graph (per-kernel profiling)")
     args = ap.parse_args()
     global SIDE
@@ -626,6 +749,9 @@ def main():
         return
     if args.workload == "tfilt":
         run_tfilt(args)
+        return
+    if args.workload == "2d":
+        run_2d(args)
         return
 
     import torch
