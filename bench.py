@@ -558,11 +558,31 @@ def run_2d(args):
         st = cp.api._stats(wsp)
         if st["rc"] != 0:
             raise cp.CpError(st["rc"], "2D timed steps")
+        eager_elapsed = job_time(total, ws, dev)
+        # the same step captured once into a CUDA graph (the library's batched
+        # form with one item): a single image's step is a chain of ~40 short
+        # launches, and the graph removes the gaps between them
+        bp = cp.BatchedPersistence([img.shape], tau=TAU, device=dev, graph=True)
+        bp.load([torch.from_numpy(img)])
+        for _ in range(args.warmup):
+            bp.step()
+        torch.cuda.synchronize(dev)
+        total = 0.0
+        for _ in range(args.steps):
+            flush.zero_()
+            ev0.record(stream)
+            bp.step()
+            ev1.record(stream)
+            torch.cuda.synchronize(dev)
+            total += ev0.elapsed_time(ev1) / 1e3
+        if bp.status()["rc"] != 0:
+            raise cp.CpError(bp.status()["rc"], "2D graph steps")
         elapsed = job_time(total, ws, dev)
         k1s = statistics.mean(k1) / 1e3 if k1 else None
         alg = 4 * N + 4 * N + 4 * (T + 1) + 8 * (st["h0_survivors"] + st["top_survivors"]) + 16 * (st["h0_roots"] + st["top_roots"])
         lines[name] = {
             "value": job_value(N, ws, args.steps, elapsed), "ms_per_step": elapsed / args.steps * 1e3,
+            "eager_ms_per_step": eager_elapsed / args.steps * 1e3,
             "k1_ms": k1s * 1e3 if k1s else None,
             "roofline": {"bound": "hbm", "achieved": alg / k1s / 1e9 if k1s else None, "peak": peak, "unit": "GB/s",
                          "frac": alg / k1s / 1e9 / peak if (k1s and peak) else None, "kernel": "k_prune2d",
@@ -590,6 +610,8 @@ def run_2d(args):
             "dtype": "f32", "data": "synthetic",
             "config": {"workload": "2D 2048x2048 float32 Gaussian random field (sigma 8 px, min-max normalised), "
                                    "and the same field at 256 levels; fwd + total-persistence loss bwd",
+                       "graph": "the step as one CUDA graph (BatchedPersistence with one item); eager_ms_per_step "
+                                "per image beside it",
                        "l2": "input (16 MiB) smaller than L2: L2 flushed (256 MiB write) before every timed step, "
                              "each step timed alone",
                        "parallelism": "replicas" if ws > 1 else "single"},
