@@ -164,3 +164,28 @@ def test_t_workspace_sizes(lib):
     # the padded volume must stay within 2^27 vertices: 510^3 pads to 512^3
     assert size("cubical_persistence_t_workspace_size", 511, 511, 511) == 0
     assert size("cubical_persistence_t_workspace_size", 510, 510, 510) > 0
+
+
+def test_t_entry_argument_errors(lib):
+    """The T-filtration entries reject bad arguments before touching a device."""
+    import ctypes
+
+    dims2 = (ctypes.c_int64 * 2)(4, 5)
+    dims3 = (ctypes.c_int64 * 3)(3, 4, 5)
+    bad2 = (ctypes.c_int64 * 2)(0, 5)
+    fake = ctypes.c_void_p(0x1000)  # never dereferenced: every call below fails its checks first
+    # null image / null workspace
+    assert lib.cubical_persistence_t_2d(None, dims2, fake, 10, None, None, fake, 1 << 20, 0, None) == -1
+    assert lib.cubical_persistence_t_3d(fake, dims3, fake, 10, None, None, None, 1 << 20, 0, None) == -1
+    # an extent of 0
+    assert lib.cubical_persistence_t_2d(fake, bad2, fake, 10, None, None, fake, 1 << 20, 0, None) == -1
+    # a workspace smaller than the size the entry asks for
+    need = lib.cubical_persistence_t_workspace_size(2, dims2, 0)
+    assert lib.cubical_persistence_t_2d(fake, dims2, fake, 10, None, None, fake, need - 1, 0, None) == -1
+    # batched: no items, too many items, a bad rank
+    nd = (ctypes.c_int32 * 1)(4)
+    d3 = (ctypes.c_int64 * 3)(1, 4, 5)
+    ptrs = (ctypes.c_void_p * 1)(0x1000)
+    assert lib.cubical_persistence_t_batched(0, ptrs, nd, d3, fake, 10, None, None, fake, 1 << 20, 0, None) == -1
+    assert lib.cubical_persistence_t_batched(1, ptrs, nd, d3, fake, 10, None, None, fake, 1 << 20, 0, None) == -1
+    assert lib.cubical_persistence_t_batched_workspace_size(129, nd, d3, 0) == 0
