@@ -1,4 +1,5 @@
-"""CPU oracle for V- and T-filtration cubical persistence (H0 + top dimension).
+"""CPU oracle for V- and T-filtration cubical persistence (H0 + top dimension,
+and H1 of volumes).
 
 TEST INFRASTRUCTURE ONLY: the test-suite, the smoke check and the benchmark's
 CPU-baseline leg are the only callers.  The product package never imports
@@ -65,6 +66,8 @@ def _load():
             ]
             lib.oracle_persistence_t.restype = ctypes.c_int64
             lib.oracle_persistence_t.argtypes = lib.oracle_persistence.argtypes
+            lib.oracle_persistence_full.restype = ctypes.c_int64
+            lib.oracle_persistence_full.argtypes = lib.oracle_persistence.argtypes
             lib.oracle_cell_key.restype = ctypes.c_int
             lib.oracle_cell_key.argtypes = [
                 ctypes.c_void_p,
@@ -79,6 +82,21 @@ def _load():
     return _lib
 
 
+def _call(fn, img, keep_zero):
+    a = np.ascontiguousarray(img, dtype=np.float32)
+    if a.ndim not in (2, 3):
+        raise ValueError("image must be 2D or 3D")
+    dims = np.asarray(a.shape, dtype=np.int64)
+    n = fn(a.ctypes.data, a.ndim, dims.ctypes.data, int(keep_zero), None, 0)
+    if n < 0:
+        raise ValueError(f"oracle: {ERRORS.get(int(n), n)}")
+    out = np.zeros(int(n), dtype=PAIR_DTYPE)
+    m = fn(a.ctypes.data, a.ndim, dims.ctypes.data, int(keep_zero), out.ctypes.data, int(n))
+    if m != n:
+        raise RuntimeError("oracle: pair count changed between calls")
+    return out
+
+
 def persistence(img, keep_zero: bool = False) -> np.ndarray:
     """Persistence pairs of a 2D (H, W) or 3D (D, H, W) float32 image.
 
@@ -86,19 +104,14 @@ def persistence(img, keep_zero: bool = False) -> np.ndarray:
     Cell indices are doubled-grid indices; the essential H0 class has
     death = +inf and death_cell = death_pixel = -1.
     """
-    lib = _load()
-    a = np.ascontiguousarray(img, dtype=np.float32)
-    if a.ndim not in (2, 3):
-        raise ValueError("image must be 2D or 3D")
-    dims = np.asarray(a.shape, dtype=np.int64)
-    n = lib.oracle_persistence(a.ctypes.data, a.ndim, dims.ctypes.data, int(keep_zero), None, 0)
-    if n < 0:
-        raise ValueError(f"oracle: {ERRORS.get(int(n), n)}")
-    out = np.zeros(int(n), dtype=PAIR_DTYPE)
-    m = lib.oracle_persistence(a.ctypes.data, a.ndim, dims.ctypes.data, int(keep_zero), out.ctypes.data, int(n))
-    if m != n:
-        raise RuntimeError("oracle: pair count changed between calls")
-    return out
+    return _call(_load().oracle_persistence, img, keep_zero)
+
+
+def persistence_full(img, keep_zero: bool = False) -> np.ndarray:
+    """As ``persistence``, plus the H1 pairs of a volume (dim 1), from the
+    column reduction of the square-edge boundary matrix.  Equal to
+    ``persistence`` for a 2D image."""
+    return _call(_load().oracle_persistence_full, img, keep_zero)
 
 
 def persistence_t(img, keep_zero: bool = False) -> np.ndarray:
@@ -108,19 +121,7 @@ def persistence_t(img, keep_zero: bool = False) -> np.ndarray:
     Same output as ``persistence``; cells are indices in the doubled grid of
     the T-complex (extents 2n+1), pixels the top cells the cells enter with.
     """
-    lib = _load()
-    a = np.ascontiguousarray(img, dtype=np.float32)
-    if a.ndim not in (2, 3):
-        raise ValueError("image must be 2D or 3D")
-    dims = np.asarray(a.shape, dtype=np.int64)
-    n = lib.oracle_persistence_t(a.ctypes.data, a.ndim, dims.ctypes.data, int(keep_zero), None, 0)
-    if n < 0:
-        raise ValueError(f"oracle: {ERRORS.get(int(n), n)}")
-    out = np.zeros(int(n), dtype=PAIR_DTYPE)
-    m = lib.oracle_persistence_t(a.ctypes.data, a.ndim, dims.ctypes.data, int(keep_zero), out.ctypes.data, int(n))
-    if m != n:
-        raise RuntimeError("oracle: pair count changed between calls")
-    return out
+    return _call(_load().oracle_persistence_t, img, keep_zero)
 
 
 def cell_key(img, cell: int):

@@ -1,7 +1,7 @@
 /*
  * Plain, slow, single-threaded CPU oracle for V-filtration cubical persistence
  * over F2 on 2D and 3D images: the H0 pairs and the top-dimension pairs
- * (H1 in 2D, H2 in 3D).
+ * (H1 in 2D, H2 in 3D), and for volumes also the middle dimension (H1 in 3D).
  *
  * TEST INFRASTRUCTURE ONLY.  Only the test-suite, the smoke check and the CPU
  * baseline leg of the benchmark may load this code.  The product path never
@@ -33,6 +33,12 @@
  *     facet is paired with the younger of the two component representatives
  *     (Appendix A.4 pairing rule), the representative of a component being
  *     its top cell with the largest R.
+ *   - H1 of a volume (oracle_persistence_full): the textbook column
+ *     reduction over F2 (Sec. 2.1) of the boundary matrix of all squares
+ *     (columns, ascending R) over all edges (rows, ascending R), nothing
+ *     cleared or pruned.  A column that reduces to zero is a square that
+ *     closes a 2-cycle (it is paired in H2); a nonzero reduced column pairs
+ *     its lowest edge (the one with the largest R) with its square.
  *   - Pairs whose birth and death values are equal are omitted (Sec. 2.3,
  *     last paragraph).  One essential H0 class (global minimum, +inf) is
  *     reported.
@@ -299,6 +305,116 @@ static int top_pairs(const grid_t *g, oracle_pair *out, int64_t cap, int64_t *n,
     return 0;
 }
 
+
+/* ---- H1 of a volume: column reduction of the square-edge boundary matrix ---- */
+
+/* Symmetric difference of two ascending arrays (F2 column addition). */
+static int64_t *symdiff(const int64_t *a, int64_t na, const int64_t *b, int64_t nb, int64_t *nout) {
+    int64_t *o = (int64_t *)malloc(sizeof(int64_t) * (size_t)(na + nb > 0 ? na + nb : 1));
+    if (!o) return NULL;
+    int64_t i = 0, j = 0, k = 0;
+    while (i < na || j < nb) {
+        if (j >= nb || (i < na && a[i] < b[j])) o[k++] = a[i++];
+        else if (i >= na || b[j] < a[i]) o[k++] = b[j++];
+        else { /* equal entries cancel */
+            ++i;
+            ++j;
+        }
+    }
+    *nout = k;
+    return o;
+}
+
+static int cmp_i64(const void *pa, const void *pb) {
+    int64_t a = *(const int64_t *)pa, b = *(const int64_t *)pb;
+    return a < b ? -1 : (a > b ? 1 : 0);
+}
+
+static int h1_pairs(const grid_t *g, oracle_pair *out, int64_t cap, int64_t *n, int keep_zero) {
+    int64_t ncells = g->GD * g->GH * g->GW;
+    int64_t nedges = 0, nsq = 0;
+    for (int64_t c = 0; c < ncells; ++c) {
+        int d = cell_dim(g, c);
+        if (d == 1) ++nedges;
+        if (d == 2) ++nsq;
+    }
+    rkey *edges = (rkey *)malloc(sizeof(rkey) * (size_t)(nedges ? nedges : 1));
+    rkey *sq = (rkey *)malloc(sizeof(rkey) * (size_t)(nsq ? nsq : 1));
+    int64_t *erank = (int64_t *)malloc(sizeof(int64_t) * (size_t)ncells); /* edge cell -> row (rank in R) */
+    int64_t *owner = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nedges ? nedges : 1)); /* row -> column */
+    int64_t **col = (int64_t **)calloc((size_t)(nsq ? nsq : 1), sizeof(int64_t *));
+    int64_t *len = (int64_t *)calloc((size_t)(nsq ? nsq : 1), sizeof(int64_t));
+    int rc = 0;
+    if (!edges || !sq || !erank || !owner || !col || !len) {
+        rc = ORACLE_ENOMEM;
+        goto done;
+    }
+    int64_t ke = 0, ks = 0;
+    for (int64_t c = 0; c < ncells; ++c) {
+        int d = cell_dim(g, c);
+        if (d == 1) edges[ke++] = cell_key(g, c);
+        if (d == 2) sq[ks++] = cell_key(g, c);
+    }
+    qsort(edges, (size_t)nedges, sizeof(rkey), rkey_cmp);
+    qsort(sq, (size_t)nsq, sizeof(rkey), rkey_cmp);
+    for (int64_t i = 0; i < nedges; ++i) {
+        erank[edges[i].idx] = i;
+        owner[i] = -1;
+    }
+    for (int64_t j = 0; j < nsq; ++j) {
+        /* the boundary of square j: step each of its two odd coordinates by -1 and +1 */
+        int64_t Z, Y, X;
+        cell_coords(g, sq[j].idx, &Z, &Y, &X);
+        int64_t C[3] = {Z, Y, X};
+        int64_t *c = (int64_t *)malloc(sizeof(int64_t) * 4);
+        if (!c) {
+            rc = ORACLE_ENOMEM;
+            goto done;
+        }
+        int64_t nc = 0;
+        for (int ax = 0; ax < 3; ++ax) {
+            if (!(C[ax] & 1)) continue;
+            for (int s = -1; s <= 1; s += 2) {
+                int64_t q[3] = {C[0], C[1], C[2]};
+                q[ax] += s;
+                c[nc++] = erank[(q[0] * g->GH + q[1]) * g->GW + q[2]];
+            }
+        }
+        qsort(c, (size_t)nc, sizeof(int64_t), cmp_i64);
+        /* add earlier reduced columns while the lowest row has an owner */
+        while (nc > 0 && owner[c[nc - 1]] >= 0) {
+            int64_t k = owner[c[nc - 1]], nn = 0;
+            int64_t *r = symdiff(c, nc, col[k], len[k], &nn);
+            free(c);
+            if (!r) {
+                rc = ORACLE_ENOMEM;
+                goto done;
+            }
+            c = r;
+            nc = nn;
+        }
+        if (nc == 0) { /* closes a 2-cycle: paired in H2, not here */
+            free(c);
+            continue;
+        }
+        const rkey *e = &edges[c[nc - 1]];
+        owner[c[nc - 1]] = j;
+        col[j] = c;
+        len[j] = nc;
+        emit(out, cap, n, keep_zero, e->fm, sq[j].fm, e->idx, sq[j].idx, e->m, sq[j].m, 1);
+    }
+done:
+    if (col)
+        for (int64_t j = 0; j < nsq; ++j) free(col[j]);
+    free(col);
+    free(len);
+    free(owner);
+    free(erank);
+    free(sq);
+    free(edges);
+    return rc;
+}
+
 static int pair_cmp(const void *pa, const void *pb) {
     const oracle_pair *a = (const oracle_pair *)pa, *b = (const oracle_pair *)pb;
     if (a->dim != b->dim) return a->dim < b->dim ? -1 : 1;
@@ -315,8 +431,8 @@ static int pair_cmp(const void *pa, const void *pb) {
  * Returns the number of pairs (which may exceed cap: then only cap were
  * written and the call should be repeated), or a negative error.
  */
-int64_t oracle_persistence(const float *img, int ndim, const int64_t *dims, int keep_zero, oracle_pair *out,
-                           int64_t cap) {
+static int64_t persistence_v(const float *img, int ndim, const int64_t *dims, int keep_zero, oracle_pair *out,
+                             int64_t cap, int with_h1) {
     if (!img || !dims || (ndim != 2 && ndim != 3)) return ORACLE_EARG;
     grid_t g;
     g.ndim = ndim;
@@ -341,11 +457,27 @@ int64_t oracle_persistence(const float *img, int ndim, const int64_t *dims, int 
     g.f = f;
     int64_t n = 0;
     int rc = h0_pairs(&g, out, cap, &n, keep_zero);
+    if (rc == 0 && with_h1 && ndim == 3) rc = h1_pairs(&g, out, cap, &n, keep_zero);
     if (rc == 0) rc = top_pairs(&g, out, cap, &n, keep_zero);
     free(f);
     if (rc) return rc;
     if (out && n <= cap) qsort(out, (size_t)n, sizeof(oracle_pair), pair_cmp);
     return n;
+}
+
+int64_t oracle_persistence(const float *img, int ndim, const int64_t *dims, int keep_zero, oracle_pair *out,
+                           int64_t cap) {
+    return persistence_v(img, ndim, dims, keep_zero, out, cap, 0);
+}
+
+/*
+ * The whole diagram: as oracle_persistence, plus the H1 pairs of a volume
+ * (dim 1, between the H0 and the H2 pairs in the output order).  For a 2D
+ * image it equals oracle_persistence (H1 is the top dimension there).
+ */
+int64_t oracle_persistence_full(const float *img, int ndim, const int64_t *dims, int keep_zero, oracle_pair *out,
+                                int64_t cap) {
+    return persistence_v(img, ndim, dims, keep_zero, out, cap, 1);
 }
 
 /* Refined key of one cell, exposed so tests can check that R is a filtration order. */

@@ -275,7 +275,7 @@ def test_euler_characteristic_2d():
 
 
 def test_euler_characteristic_3d_with_brute_h1():
-    """chi(K_t) = b0 - b1 + b2, with b1 from the full reduction (3D H1 is not in the oracle)."""
+    """chi(K_t) = b0 - b1 + b2, with b1 from the brute-force reduction of the whole complex."""
     rng = np.random.default_rng(12)
     for _ in range(4):
         img = rng.integers(0, 4, (3, 4, 3)).astype(np.float32)
