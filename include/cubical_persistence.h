@@ -224,6 +224,50 @@ int cubical_persistence_batched(int n_items, const float *const *h_images, const
                                 void *stream);
 
 /*
+ * The whole diagram of volumes: the pairs of cubical_persistence_3d /
+ * _batched plus the H1 pairs of every 3D item (dim 1; zero persistence
+ * omitted; birth cell an edge, death cell a square, pixels their largest
+ * vertices).  Sec. 4.2 leaves the middle dimension of a volume to a matrix
+ * reduction over the cells that H0 and H2 leave unpaired; here it is the F2
+ * column reduction (Sec. 2.1) of the boundary matrix of the squares not
+ * paired in H2 over the edges not paired in H0, in the refined order of
+ * Sec. 2.3, run in parallel rounds on the device.  2D items get their plain
+ * diagram.  Output order (item, dim, birth cell) as for the other calls.
+ *  pool_entries : device pool entries (8 bytes each) for the columns that
+ *                 additions create, beyond the 4 per column they start
+ *                 with; 0 picks 4 per column + 65536.  A call that runs out
+ *                 returns CP_ERR_CAPACITY (repeat with a larger pool).
+ *  capacity     : E + (D-1)(H-1)(W-1) + 1 always suffices for a volume
+ *                 (E = its edges).
+ *  d_workspace  : ws_bytes >= cubical_persistence_full_workspace_size() /
+ *                 cubical_persistence_full_batched_workspace_size().
+ * Other arguments, ownership and errors as for cubical_persistence_3d and
+ * cubical_persistence_batched.  CP_ERR_INTERNAL reports a failed count
+ * check (merging edges N - 1, squares paired in H2 (D-1)(H-1)(W-1), one
+ * column per unpaired edge).
+ */
+size_t cubical_persistence_full_workspace_size(int ndim, const int64_t *dims, int64_t max_survivors,
+                                               int64_t pool_entries);
+int cubical_persistence_full_3d(const float *d_image, const int64_t dims[3], cp_pair *d_out_pairs, int64_t capacity,
+                                int64_t *h_out_count, int64_t *d_out_count, void *d_workspace, size_t ws_bytes,
+                                int64_t max_survivors, int64_t pool_entries, void *stream);
+size_t cubical_persistence_full_batched_workspace_size(int n_items, const int32_t *ndims, const int64_t *dims,
+                                                       int64_t max_survivors, int64_t pool_entries);
+int cubical_persistence_full_batched(int n_items, const float *const *h_images, const int32_t *ndims,
+                                     const int64_t *dims, cp_pair *d_out_pairs, int64_t capacity,
+                                     int64_t *h_out_count, int64_t *d_out_count, void *d_workspace, size_t ws_bytes,
+                                     int64_t max_survivors, int64_t pool_entries, void *stream);
+/*
+ * The H1 stage of the last full call on this workspace (same item, size
+ * and pool arguments as that call; waits for `stream`): h_info[0] columns,
+ * [1] reduction rounds, [2] pool entries used, [3] pool entries available.
+ * cap >= 4.
+ */
+int cubical_persistence_full_info(const void *d_workspace, int n_items, const int32_t *ndims, const int64_t *dims,
+                                  int64_t max_survivors, int64_t pool_entries, int64_t *h_info, int cap,
+                                  void *stream);
+
+/*
  * Counters and status of the last call that used this workspace (waits for
  * `stream`).  Returns the CP_* code the call would report.
  */

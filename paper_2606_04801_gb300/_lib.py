@@ -76,6 +76,17 @@ _SIGS = {
         ctypes.c_int,
         [ctypes.c_int, _P, _P, _P, _P, _I64, _P, _P, _P, ctypes.c_size_t, _I64, _P],
     ),
+    "cubical_persistence_full_workspace_size": (ctypes.c_size_t, [ctypes.c_int, _P, _I64, _I64]),
+    "cubical_persistence_full_3d": (ctypes.c_int, [_P, _P, _P, _I64, _P, _P, _P, ctypes.c_size_t, _I64, _I64, _P]),
+    "cubical_persistence_full_batched_workspace_size": (ctypes.c_size_t, [ctypes.c_int, _P, _P, _I64, _I64]),
+    "cubical_persistence_full_batched": (
+        ctypes.c_int,
+        [ctypes.c_int, _P, _P, _P, _P, _I64, _P, _P, _P, ctypes.c_size_t, _I64, _I64, _P],
+    ),
+    "cubical_persistence_full_info": (
+        ctypes.c_int,
+        [_P, ctypes.c_int, _P, _P, _I64, _I64, _P, ctypes.c_int, _P],
+    ),
     "cubical_persistence_stats": (ctypes.c_int, [_P, ctypes.POINTER(CpStats), _P]),
     "cubical_persistence_backward_workspace_size": (ctypes.c_size_t, [_I64]),
     "cubical_persistence_backward": (ctypes.c_int, [_P, _I64, _P, _P, _P, _P, _I64, _P, ctypes.c_size_t, _P]),

@@ -201,6 +201,102 @@ def persistence_batched(imgs: Sequence[torch.Tensor], max_survivors: int = 0, wi
     raise CpError(CP_ERR_CAPACITY, "cubical_persistence_batched (after growing the workspace)")
 
 
+def _full_call(imgs: Sequence[torch.Tensor], single: bool, max_survivors: int, pool_entries: int,
+               with_stats: bool) -> Diagram:
+    """The whole diagram (H0, H1 of the volumes, top dimension) of one volume
+    (single) or of a batch; grows the survivor bound, the column pool and the
+    output until they fit."""
+    lib = _lib.load()
+    dev = imgs[0].device
+    k = len(imgs)
+    ptrs = (ctypes.c_void_p * k)(*[im.data_ptr() for im in imgs])
+    ndims = (ctypes.c_int32 * k)(*[im.dim() for im in imgs])
+    flat = []
+    for im in imgs:
+        flat += ([1] + list(im.shape)) if im.dim() == 2 else list(im.shape)
+    dims = (ctypes.c_int64 * (3 * k))(*flat)
+    n = sum(im.numel() for im in imgs)
+    bound = 0  # pairs before the zero-persistence filter: every edge and top cell, plus one
+    for im in imgs:
+        sh = list(im.shape)
+        edges = sum(int(np.prod([s - (1 if a == b else 0) for b, s in enumerate(sh)])) for a in range(len(sh)))
+        bound += edges + int(np.prod([s - 1 for s in sh])) + 1
+    ms, pool = int(max_survivors), int(pool_entries)
+    cap = min(bound, n + 2 * k + 4096)
+    sp = ctypes.c_void_p(_stream_ptr(dev))
+    for _ in range(8):
+        if single:
+            ws_bytes = lib.cubical_persistence_full_workspace_size(3, dims, ms, pool)
+        else:
+            ws_bytes = lib.cubical_persistence_full_batched_workspace_size(k, ndims, dims, ms, pool)
+        if ws_bytes == 0:
+            raise CpError(_lib.CP_ERR_ARG, "full workspace size")
+        ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
+        out = torch.empty((cap, 8), dtype=torch.int32, device=dev)
+        cnt = ctypes.c_int64(0)
+        wsp = ctypes.c_void_p(ws.data_ptr())
+        if single:
+            rc = lib.cubical_persistence_full_3d(
+                ctypes.c_void_p(imgs[0].data_ptr()), dims, ctypes.c_void_p(out.data_ptr()), cap, ctypes.byref(cnt),
+                None, wsp, ws_bytes, ms, pool, sp,
+            )
+        else:
+            rc = lib.cubical_persistence_full_batched(
+                k, ptrs, ndims, dims, ctypes.c_void_p(out.data_ptr()), cap, ctypes.byref(cnt), None, wsp, ws_bytes,
+                ms, pool, sp,
+            )
+        if rc == CP_ERR_CAPACITY:
+            grew = False
+            info = (ctypes.c_int64 * 4)()  # the H1 stage of this call (its layout needs this call's bounds)
+            info_rc = lib.cubical_persistence_full_info(wsp, k, ndims, dims, ms, pool, info, 4, sp)
+            st = _stats(ws)
+            eff = ms if ms > 0 else n // 2 + 65536
+            need = max(st["h0_survivors"], st["top_survivors"], 2 * st["h0_roots"], 2 * st["top_roots"])
+            if need > eff:
+                ms = _grow(st, eff, n)
+                grew = True
+            if info_rc == CP_OK and info[2] > info[3]:
+                base = 4 * int(info[0])
+                pool = 2 * max(int(info[2]) - base, int(info[3]) - base)
+                grew = True
+            if cnt.value > cap:
+                cap = int(cnt.value) + 1024
+                grew = True
+            if not grew:
+                raise CpError(rc, "cubical_persistence_full")
+            continue
+        if rc != CP_OK:
+            raise CpError(rc, "cubical_persistence_full")
+        return Diagram(out[: cnt.value], _stats(ws) if with_stats else None)
+    raise CpError(CP_ERR_CAPACITY, "cubical_persistence_full (after growing the workspace)")
+
+
+def persistence_full(img: torch.Tensor, max_survivors: int = 0, pool_entries: int = 0,
+                     with_stats: bool = False) -> Diagram:
+    """Every dimension of one volume: H0, H1 and H2 pairs (V-filtration,
+    sorted by (dim, birth cell)); a 2D image gets its plain diagram.  H1 comes
+    from the F2 reduction of the squares not paired in H2 over the edges not
+    paired in H0, on the device; pool_entries sizes its column pool (0: the
+    default, grown on demand)."""
+    _check_image(img)
+    if img.dim() == 2:
+        return persistence(img, max_survivors, with_stats)
+    return _full_call([img.contiguous()], True, max_survivors, pool_entries, with_stats)
+
+
+def persistence_full_batched(imgs: Sequence[torch.Tensor], max_survivors: int = 0, pool_entries: int = 0,
+                             with_stats: bool = False) -> Diagram:
+    """persistence_full over many images and volumes in one pass (pairs carry their item index)."""
+    if not imgs:
+        raise ValueError("empty batch")
+    if len(imgs) > _lib.CP_MAX_ITEMS:
+        raise ValueError(f"at most {_lib.CP_MAX_ITEMS} items per call")
+    imgs = [im.contiguous() for im in imgs]
+    for im in imgs:
+        _check_image(im)
+    return _full_call(imgs, False, max_survivors, pool_entries, with_stats)
+
+
 def pairs_backward(raw: torch.Tensor, grad_birth: torch.Tensor, grad_death: torch.Tensor, n_pixels: int,
                    item_offsets: Optional[torch.Tensor] = None) -> torch.Tensor:
     """dL/dimage (flat, float32) from dL/dbirth and dL/ddeath of each pair."""
@@ -224,8 +320,13 @@ def pairs_backward(raw: torch.Tensor, grad_birth: torch.Tensor, grad_death: torc
 
 class _DiagramFn(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, img, max_survivors, filtration):
-        d = persistence(img.detach(), max_survivors, filtration=filtration)
+    def forward(ctx, img, max_survivors, filtration, full):
+        if full:
+            if filtration != "V":
+                raise ValueError("the full diagram is computed for the V-filtration")
+            d = persistence_full(img.detach(), max_survivors)
+        else:
+            d = persistence(img.detach(), max_survivors, filtration=filtration)
         ctx.save_for_backward(d.raw)
         ctx.shape = img.shape
         ctx.mark_non_differentiable(d.raw)
@@ -240,9 +341,10 @@ class _DiagramFn(torch.autograd.Function):
         if gd is None:
             gd = torch.zeros(raw.shape[0], dtype=torch.float32, device=raw.device)
         g = pairs_backward(raw, gb, gd, n)
-        return g.view(ctx.shape), None, None
+        return g.view(ctx.shape), None, None, None
 
 
-def diagram(img: torch.Tensor, max_survivors: int = 0, filtration: str = "V"):
-    """(birth, death, raw): birth and death are differentiable in img (V or T filtration)."""
-    return _DiagramFn.apply(img, max_survivors, filtration)
+def diagram(img: torch.Tensor, max_survivors: int = 0, filtration: str = "V", full: bool = False):
+    """(birth, death, raw): birth and death are differentiable in img (V or T
+    filtration; full=True adds the H1 pairs of a volume, V only)."""
+    return _DiagramFn.apply(img, max_survivors, filtration, full)

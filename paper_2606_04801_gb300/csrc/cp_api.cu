@@ -2,6 +2,7 @@
 // and the enqueueing of the pipeline
 //   init -> K1 prune -> K2 sort (H0) -> K3 H0 union-find (+ 2D cross-pruning)
 //        -> K2 sort (dual) -> K3 dual union-find -> essential pairs
+//        [-> H1 of the volumes: columns, sort, reduction, pairs]
 //        -> K2 sort (pairs, canonical order) -> gather.
 #include <algorithm>
 #include <atomic>
@@ -68,13 +69,23 @@ struct Plan {
     size_t o_ctr, o_uf0, o_uft, o_s0, o_st, o_salt, o_age0, o_res0, o_aget, o_rest;
     size_t o_act0, o_act1, o_yn, o_on, o_na0, o_na1, o_nb0, o_nb1, o_pairs, o_pvals, o_pvalt, o_hist, o_status;
     size_t o_hist2, o_status2;
+    // H1 of the volumes (calls that ask for it): see H1Bufs
+    bool h1 = false;
+    uint32_t h1_mcap = 0, h1_neg = 0, h1_posq = 0;
+    uint64_t h1_pool = 0;
+    size_t h1_words = 0;
+    size_t o_h1_neg, o_h1_pos, o_h1_ctl, o_h1_ck, o_h1_cka, o_h1_hist, o_h1_status, o_h1_off, o_h1_len, o_h1_l0,
+        o_h1_l1, o_h1_piv, o_h1_pool;
     size_t bytes = 0;
 };
 
 size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
 
+// h1: also lay out the H1 stage of the 3D items, with h1_pool pool entries
+// for merged columns beyond the 4 per column of the start (0: 4 per column +
+// 65536).
 int make_plan(int n_items, const int32_t* ndims, const int64_t* dims, const float* const* imgs,
-              int64_t max_survivors, Plan& P) {
+              int64_t max_survivors, Plan& P, bool h1 = false, int64_t h1_pool = 0) {
     if (n_items <= 0 || n_items > kMaxItems || !ndims || !dims) return CP_ERR_ARG;
     std::memset(&P.tab, 0, sizeof(P.tab));
     P.tab.n = n_items;
@@ -85,6 +96,7 @@ int make_plan(int n_items, const int32_t* ndims, const int64_t* dims, const floa
             if (ndims[i] == (k == 0 ? 2 : 3)) order.push_back(i);
     if (int(order.size()) != n_items) return CP_ERR_ARG;
     int64_t voff = 0, toff = 0, edges = 0, facets = 0;
+    int64_t h1_cols = 0, h1_neg = 0, h1_posq = 0;  // 3D items: sums of E - N + 1, N - 1, (D-1)(H-1)(W-1)
     int32_t t2 = 0, t3 = 0;
     for (int j = 0; j < n_items; ++j) {
         int i = order[j];
@@ -126,6 +138,9 @@ int make_plan(int n_items, const int32_t* ndims, const int64_t* dims, const floa
             P.tab.n3d++;
             edges += D * H * (W - 1) + D * (H - 1) * W + (D - 1) * H * W;
             facets += D * (H - 1) * (W - 1) + (D - 1) * H * (W - 1) + (D - 1) * (H - 1) * W;
+            h1_cols += D * H * (W - 1) + D * (H - 1) * W + (D - 1) * H * W - N + 1;
+            h1_neg += N - 1;
+            h1_posq += it.T;
         }
         if (voff > (int64_t(1) << kVBits) || toff > (int64_t(1) << kVBits) + kMaxItems) return CP_ERR_ARG;
     }
@@ -148,6 +163,15 @@ int make_plan(int n_items, const int32_t* ndims, const int64_t* dims, const floa
     P.cap_r0 = uint32_t(std::min<int64_t>(ms / 2 + n_items + 1024, voff + 1));
     P.cap_rt = uint32_t(std::min<int64_t>(ms / 2 + n_items + 1024, toff + 1));
     P.cap_p = P.cap_r0 + P.cap_rt;
+    P.h1 = h1 && h1_cols > 0;
+    if (P.h1) {
+        if (h1_pool < 0 || int64_t(P.cap_p) + h1_cols > int64_t(0xFFFFFFFF) - 65536) return CP_ERR_ARG;
+        P.h1_mcap = uint32_t(h1_cols);
+        P.h1_neg = uint32_t(h1_neg);
+        P.h1_posq = uint32_t(h1_posq);
+        P.h1_pool = 4ull * uint64_t(h1_cols) + uint64_t(h1_pool > 0 ? h1_pool : 4 * h1_cols + 65536);
+        P.cap_p += P.h1_mcap;  // H1 pairs (the nonzero ones are far fewer)
+    }
     P.cap_big = std::max(P.cap_s, P.cap_p);
     size_t o = 0;
     auto take = [&](size_t bytes) {
@@ -182,6 +206,23 @@ int make_plan(int n_items, const int32_t* ndims, const int64_t* dims, const floa
     P.o_status = take(sizeof(uint64_t) * sort_status_words(P.cap_big));
     P.o_hist2 = take(sizeof(uint32_t) * 8 * 256);
     P.o_status2 = take(sizeof(uint64_t) * sort_status_words(P.cap_s));
+    if (P.h1) {
+        const size_t m = P.h1_mcap;
+        P.h1_words = (3 * size_t(P.ntot) + 31) / 32;
+        P.o_h1_neg = take(sizeof(uint32_t) * P.h1_words);
+        P.o_h1_pos = take(sizeof(uint32_t) * P.h1_words);
+        P.o_h1_ctl = take(sizeof(H1Ctl));
+        P.o_h1_ck = take(sizeof(uint64_t) * m);
+        P.o_h1_cka = take(sizeof(uint64_t) * m);
+        P.o_h1_hist = take(sizeof(uint32_t) * 8 * 256);
+        P.o_h1_status = take(sizeof(uint64_t) * sort_status_words(P.h1_mcap));
+        P.o_h1_off = take(sizeof(uint64_t) * m);
+        P.o_h1_len = take(sizeof(uint32_t) * m);
+        P.o_h1_l0 = take(sizeof(uint32_t) * m);
+        P.o_h1_l1 = take(sizeof(uint32_t) * m);
+        P.o_h1_piv = take(sizeof(uint32_t) * 3 * size_t(P.ntot));
+        P.o_h1_pool = take(sizeof(uint64_t) * P.h1_pool);
+    }
     P.bytes = o;
     return CP_OK;
 }
@@ -252,6 +293,31 @@ int run(const Plan& P, cp_pair* d_out, int64_t capacity, int64_t* h_out_count, i
         CP_TRY(launch_prune(P.tab, po, P.tma, s));
         mark(1, s);
         return CP_OK;
+    }
+
+    H1Bufs hb = {};
+    if (P.h1) {
+        hb.neg_e = at<uint32_t>(ws, P.o_h1_neg);
+        hb.pos_q = at<uint32_t>(ws, P.o_h1_pos);
+        hb.map_words = P.h1_words;
+        hb.ctl = at<H1Ctl>(ws, P.o_h1_ctl);
+        hb.ckeys = at<uint64_t>(ws, P.o_h1_ck);
+        hb.ckeys_alt = at<uint64_t>(ws, P.o_h1_cka);
+        hb.hist = at<uint32_t>(ws, P.o_h1_hist);
+        hb.status = at<uint64_t>(ws, P.o_h1_status);
+        hb.off = at<uint64_t>(ws, P.o_h1_off);
+        hb.len = at<uint32_t>(ws, P.o_h1_len);
+        hb.list[0] = at<uint32_t>(ws, P.o_h1_l0);
+        hb.list[1] = at<uint32_t>(ws, P.o_h1_l1);
+        hb.pivot = at<uint32_t>(ws, P.o_h1_piv);
+        hb.pool = at<uint64_t>(ws, P.o_h1_pool);
+        hb.pool_cap = P.h1_pool;
+        hb.mcap = P.h1_mcap;
+        hb.exp_neg_e = P.h1_neg;
+        hb.exp_pos_q = P.h1_posq;
+        // the union-finds mark their committed survivors in these
+        CP_TRY(cudaMemsetAsync(hb.neg_e, 0, sizeof(uint32_t) * P.h1_words, s));
+        CP_TRY(cudaMemsetAsync(hb.pos_q, 0, sizeof(uint32_t) * P.h1_words, s));
     }
 
     PruneOuts po;
@@ -392,6 +458,8 @@ int run(const Plan& P, cp_pair* d_out, int64_t capacity, int64_t* h_out_count, i
     up[1].d_ndual = nullptr;
     up[1].dual_cap = 0;
     up[1].dual = 1;
+    up[0].h1flags = P.h1 ? hb.neg_e : nullptr;
+    up[1].h1flags = P.h1 ? hb.pos_q : nullptr;
 
     if (!joint) {
         // the H0 union-find appends positive edges of 2D items to the dual list
@@ -414,6 +482,7 @@ int run(const Plan& P, cp_pair* d_out, int64_t capacity, int64_t* h_out_count, i
     }
 
     CP_TRY(launch_essential(P.tab, ctr, pairs, P.cap_p, s));
+    if (P.h1) CP_TRY(launch_h1(P.tab, hb, ctr, pairs, P.cap_p, s));
     uint32_t* pvals = at<uint32_t>(ws, P.o_pvals);
     uint32_t* pvalt = at<uint32_t>(ws, P.o_pvalt);
     // output order (item, dim, birth cell): only as many key bytes as this call's
@@ -431,9 +500,10 @@ int run(const Plan& P, cp_pair* d_out, int64_t capacity, int64_t* h_out_count, i
     if (tm) CP_TRY(launch_t_map(pairs, &ctr->n_pairs, P.cap_p, tm->items, tm->bad, ctr, s));
     // T calls: one more item index, for the dropped frame classes
     while ((1 << item_bits) < P.tab.n + (tm ? 1 : 0)) ++item_bits;
-    int pair_passes = (item_bits + 1 + cell_bits + 7) / 8;
+    const int dim_bits = P.h1 ? 2 : 1;
+    int pair_passes = (item_bits + dim_bits + cell_bits + 7) / 8;
     pair_passes += pair_passes & 1;  // an even count leaves the result in place
-    CP_TRY(launch_pair_keys(pairs, &ctr->n_pairs, P.cap_p, s0, pvals, cell_bits, s));
+    CP_TRY(launch_pair_keys(pairs, &ctr->n_pairs, P.cap_p, s0, pvals, cell_bits, dim_bits, s));
     sb.keys = s0;
     sb.keys_alt = salt;
     sb.vals = pvals;
@@ -458,12 +528,12 @@ int run(const Plan& P, cp_pair* d_out, int64_t capacity, int64_t* h_out_count, i
 
 int single(int ndim, const float* d_image, const int64_t* dims, cp_pair* d_out, int64_t capacity,
            int64_t* h_out_count, int64_t* d_out_count, void* ws, size_t ws_bytes, int64_t max_survivors,
-           void* stream) {
+           void* stream, bool h1 = false, int64_t h1_pool = 0) {
     if (!d_image || !dims) return CP_ERR_ARG;
     int32_t nd = ndim;
     int64_t d3[3] = {ndim == 3 ? dims[0] : 1, dims[ndim - 2], dims[ndim - 1]};
     Plan P;
-    int rc = make_plan(1, &nd, d3, &d_image, max_survivors, P);
+    int rc = make_plan(1, &nd, d3, &d_image, max_survivors, P, h1, h1_pool);
     if (rc != CP_OK) return rc;
     return run(P, d_out, capacity, h_out_count, d_out_count, ws, ws_bytes, static_cast<cudaStream_t>(stream));
 }
@@ -719,6 +789,69 @@ int cubical_persistence_batched(int n_items, const float* const* h_images, const
     if (rc != CP_OK) return rc;
     return run(P, d_out_pairs, capacity, h_out_count, d_out_count, d_workspace, ws_bytes,
                static_cast<cudaStream_t>(stream));
+}
+
+size_t cubical_persistence_full_batched_workspace_size(int n_items, const int32_t* ndims, const int64_t* dims,
+                                                       int64_t max_survivors, int64_t pool_entries) {
+    Plan P;
+    if (make_plan(n_items, ndims, dims, nullptr, max_survivors, P, true, pool_entries) != CP_OK) return 0;
+    return P.bytes;
+}
+
+int cubical_persistence_full_batched(int n_items, const float* const* h_images, const int32_t* ndims,
+                                     const int64_t* dims, cp_pair* d_out_pairs, int64_t capacity,
+                                     int64_t* h_out_count, int64_t* d_out_count, void* d_workspace, size_t ws_bytes,
+                                     int64_t max_survivors, int64_t pool_entries, void* stream) {
+    if (!h_images) return CP_ERR_ARG;
+    Plan P;
+    int rc = make_plan(n_items, ndims, dims, h_images, max_survivors, P, true, pool_entries);
+    if (rc != CP_OK) return rc;
+    return run(P, d_out_pairs, capacity, h_out_count, d_out_count, d_workspace, ws_bytes,
+               static_cast<cudaStream_t>(stream));
+}
+
+size_t cubical_persistence_full_workspace_size(int ndim, const int64_t* dims, int64_t max_survivors,
+                                               int64_t pool_entries) {
+    if ((ndim != 2 && ndim != 3) || !dims) return 0;
+    const int32_t nd = ndim;
+    const int64_t d3[3] = {ndim == 3 ? dims[0] : 1, dims[ndim - 2], dims[ndim - 1]};
+    return cubical_persistence_full_batched_workspace_size(1, &nd, d3, max_survivors, pool_entries);
+}
+
+int cubical_persistence_full_3d(const float* d_image, const int64_t dims[3], cp_pair* d_out_pairs, int64_t capacity,
+                                int64_t* h_out_count, int64_t* d_out_count, void* d_workspace, size_t ws_bytes,
+                                int64_t max_survivors, int64_t pool_entries, void* stream) {
+    return single(3, d_image, dims, d_out_pairs, capacity, h_out_count, d_out_count, d_workspace, ws_bytes,
+                  max_survivors, stream, true, pool_entries);
+}
+
+int cubical_persistence_full_info(const void* d_workspace, int n_items, const int32_t* ndims, const int64_t* dims,
+                                  int64_t max_survivors, int64_t pool_entries, int64_t* h_info, int cap,
+                                  void* stream) {
+    if (!d_workspace || !h_info || cap < 4) return CP_ERR_ARG;
+    Plan P;
+    int rc = make_plan(n_items, ndims, dims, nullptr, max_survivors, P, true, pool_entries);
+    if (rc != CP_OK) return rc;
+    h_info[0] = h_info[1] = h_info[2] = 0;
+    h_info[3] = int64_t(P.h1_pool);
+    if (!P.h1) return CP_OK;
+    H1Ctl c;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (cudaMemcpyAsync(&c, static_cast<const char*>(d_workspace) + P.o_h1_ctl, sizeof(c), cudaMemcpyDeviceToHost,
+                        s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return CP_ERR_CUDA;
+    h_info[0] = c.m;
+    h_info[1] = c.rounds;
+    h_info[2] = int64_t(4ull * P.h1_mcap + c.grown);
+    if (cap >= 9) {
+        h_info[4] = c.neg_e;
+        h_info[5] = c.pos_q;
+        h_info[6] = c.pos_e;
+        h_info[7] = int64_t(P.o_h1_neg);
+        h_info[8] = int64_t(P.o_h1_pos);
+    }
+    return CP_OK;
 }
 
 int cubical_persistence_stats(const void* d_workspace, cp_stats* h_stats, void* stream) {

@@ -52,11 +52,13 @@ __global__ void k_essential(ItemTable tab, Counters* ctr, cp_pair* pairs, uint32
 // Sort key of the canonical output order (item, dim, birth cell), packed in
 // as few bits as the call needs: birth cells take cell_bits bits.
 __global__ void k_pair_keys(const cp_pair* __restrict__ pairs, const uint32_t* d_n, uint32_t cap,
-                            uint64_t* __restrict__ keys, uint32_t* __restrict__ vals, int cell_bits) {
+                            uint64_t* __restrict__ keys, uint32_t* __restrict__ vals, int cell_bits,
+                            int dim_bits) {
     uint32_t n = min(*d_n, cap);
     for (uint32_t i = blockIdx.x * kT + threadIdx.x; i < n; i += gridDim.x * kT) {
         const cp_pair& p = pairs[i];
-        keys[i] = (uint64_t(uint32_t(p.item)) << (cell_bits + 1)) | (uint64_t(p.dim > 0 ? 1u : 0u) << cell_bits) |
+        const uint32_t dc = dim_bits == 1 ? (p.dim > 0 ? 1u : 0u) : uint32_t(p.dim);
+        keys[i] = (uint64_t(uint32_t(p.item)) << (cell_bits + dim_bits)) | (uint64_t(dc) << cell_bits) |
                   uint32_t(p.birth_cell);
         vals[i] = i;
     }
@@ -214,8 +216,8 @@ cudaError_t launch_essential(const ItemTable& tab, Counters* ctr, cp_pair* pairs
 }
 
 cudaError_t launch_pair_keys(const cp_pair* pairs, const uint32_t* d_n, uint32_t cap, uint64_t* keys, uint32_t* vals,
-                             int cell_bits, cudaStream_t s) {
-    k_pair_keys<<<grid_for(cap), kT, 0, s>>>(pairs, d_n, cap, keys, vals, cell_bits);
+                             int cell_bits, int dim_bits, cudaStream_t s) {
+    k_pair_keys<<<grid_for(cap), kT, 0, s>>>(pairs, d_n, cap, keys, vals, cell_bits, dim_bits);
     note_launches(1);
     return cudaGetLastError();
 }

@@ -1,0 +1,492 @@
+// H1 of volumes: the middle dimension of a 3D image, by matrix reduction over
+// the cells that the H0 and H2 computations leave unpaired (Sec. 4.2 computes
+// H0 and the top dimension by union-find and names the dimension between
+// them as the one left to a reduction of the boundary matrix).
+//
+// Over F2 the 1-dimensional pairs come from the column reduction (Sec. 2.1)
+// of the boundary matrix of the squares (columns) over the edges (rows), both
+// in the fully refined order (Sec. 2.3).  Two restrictions keep every pair:
+//   - a square that creates a 2-cycle (a merging facet of the dual graph,
+//     paired in H2) has a column that reduces to zero: it is left out;
+//   - an edge that merges two H0 classes is never the lowest entry of a
+//     column during the reduction (every column is a 1-cycle, and the
+//     youngest edge of a cycle joins vertices that the rest of the cycle
+//     already connects, so it does not merge), hence deleting those rows
+//     changes no lowest entry and no column addition: they are left out.
+// One column per square not paired in H2, one row per edge not paired in H0:
+// equally many (the Euler characteristic of a box is 1), and every column
+// reduces to a nonzero column whose lowest entry is its partner.
+//
+// Which cells those are: what the pruning pass settles inside one lower
+// star, recomputed here from the image (each vertex's first lower face
+// neighbour gives a merging edge; the squares of a lower star that join two
+// classes of its cubes, at most one of which reaches outside the star, merge
+// in the dual graph), and the survivors that the union-finds commit, which
+// they mark in the same bitmaps.  The counts are checked: N - 1 merging edges
+// and (D-1)(H-1)(W-1) squares paired in H2 per volume.
+//
+// The reduction runs in rounds inside one cooperative kernel.  A column is a
+// descending array of edge keys (the refined keys of Sec. 2.3), lowest entry
+// first; columns are ranked by their square's key (the filtration order).
+// In a round every column whose lowest entry changed bids for that row with
+// an atomic minimum of its rank in a per-edge pivot word; every column that
+// loses a bid, or is displaced by an older one, then adds the winner of its
+// row (all such additions at once, into fresh pool space), so its lowest
+// entry drops, and it bids again in the next round.  Adding an older column
+// with the same lowest entry is a left-to-right column operation, so once all
+// lowest entries are distinct the pairs are those of the sequential
+// reduction, whatever the order of additions.  Rounds end when no bid is
+// lost.  Every wait is bounded; pool overflow and failed checks set a status
+// bit and stop the rounds.
+#include "cp_common.cuh"
+#include "cp_kernels.h"
+
+namespace cp {
+namespace {
+
+constexpr int kHT = 256;  // threads per CTA of the element-wise kernels
+constexpr int kRT = 512;  // threads per CTA of the reduction
+constexpr uint32_t kNone = 0xFFFFFFFFu;
+constexpr uint32_t kMaxRounds = 1u << 20;
+// A bounded wait that gave up earlier leaves the sorted columns unreliable;
+// non-finite input leaves the order unreliable: the call fails anyway.
+constexpr uint32_t kStSkip = kStTimeout | kStNonfinite;
+
+// Vertex order inside an item: (ord f, local id).
+__device__ __forceinline__ uint64_t vkey(const float* img, int64_t v) {
+    return (uint64_t(ord_bits(__ldg(img + v))) << 32) | uint64_t(v);
+}
+
+__device__ __forceinline__ int n3(int dz, int dy, int dx) { return (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1); }
+
+__device__ __forceinline__ void set_bit(uint32_t* map, uint32_t id) { atomicOr(map + (id >> 5), 1u << (id & 31u)); }
+__device__ __forceinline__ bool get_bit(const uint32_t* map, uint32_t id) {
+    return (__ldg(map + (id >> 5)) >> (id & 31u)) & 1u;
+}
+
+__device__ __forceinline__ int64_t axis_step(const Item& it, int a) {
+    return a == 0 ? 1 : (a == 1 ? int64_t(it.W) : int64_t(it.W) * it.H);
+}
+
+// Key of the edge from local vertex u along axis a.
+__device__ __forceinline__ uint64_t edge_key(const Item& it, int64_t u, int a) {
+    const int64_t w = u + axis_step(it, a);
+    const uint64_t ku = vkey(it.img, u), kw = vkey(it.img, w);
+    const bool hi = kw > ku;  // m is the far end: the edge lies on its -a side
+    const int64_t m = hi ? w : u;
+    const int s = hi ? -1 : 1;
+    const int n = n3(a == 2 ? s : 0, a == 1 ? s : 0, a == 0 ? s : 0);
+    return make_key(uint32_t((hi ? kw : ku) >> 32), uint64_t(it.voff + m), uint32_t(n));
+}
+
+// Key of the square with lowest corner u (local) and normal axis a.
+__device__ __forceinline__ uint64_t square_key(const Item& it, int64_t u, int a) {
+    const int p = a == 0 ? 1 : 0, q = a == 2 ? 1 : 2;  // the spanned axes
+    const int64_t sp = axis_step(it, p), sq = axis_step(it, q);
+    uint64_t km = 0;
+    int bp = 0, bq = 0;
+    for (int c = 0; c < 4; ++c) {
+        const int cp = c & 1, cq = c >> 1;
+        const uint64_t k = vkey(it.img, u + cp * sp + cq * sq);
+        if (c == 0 || k > km) {
+            km = k;
+            bp = cp;
+            bq = cq;
+        }
+    }
+    int o[3] = {0, 0, 0};  // offset of the square's centre from m, per axis (x, y, z)
+    o[p] = bp ? -1 : 1;
+    o[q] = bq ? -1 : 1;
+    const int64_t m = u + bp * sp + bq * sq;
+    return make_key(uint32_t(km >> 32), uint64_t(it.voff + m), uint32_t(n3(o[2], o[1], o[0])));
+}
+
+__device__ __forceinline__ uint32_t edge_id(const ItemTable& tab, uint64_t key) {
+    return cell_id3(tab.it[item_of_vertex(tab, key_vertex(key))], key, false);
+}
+
+__device__ __forceinline__ int32_t cell_index(const Item& it, uint64_t key) {
+    const int64_t lv = int64_t(key_vertex(key)) - it.voff;
+    const int x = int(lv % it.W), y = int((lv / it.W) % it.H), z = int(lv / (int64_t(it.W) * it.H));
+    int dz, dy, dx;
+    stencil_off(3, int(key_low(key)), dz, dy, dx);
+    return int32_t(doubled_index(it, z, y, x, dz, dy, dx));
+}
+
+// ---- the direct pairs' cells, from the image
+__global__ void __launch_bounds__(kHT) k_h1_direct(const __grid_constant__ ItemTable tab, H1Bufs b, int64_t v0,
+                                                   int64_t v1) {
+    for (int64_t g = v0 + int64_t(blockIdx.x) * kHT + threadIdx.x; g < v1; g += int64_t(gridDim.x) * kHT) {
+        const Item& it = tab.it[item_of_vertex(tab, uint32_t(g))];
+        const int64_t W = it.W, HW = int64_t(it.H) * it.W;
+        const int64_t v = g - it.voff;
+        const int x = int(v % W), y = int((v / W) % it.H), z = int(v / HW);
+        const uint64_t kv = vkey(it.img, v);
+        // the first lower face neighbour (by stencil index) gives the edge
+        // that merges v into an older class
+        {
+            const int fz[6] = {-1, 0, 0, 0, 0, 1}, fy[6] = {0, -1, 0, 0, 1, 0}, fx[6] = {0, 0, -1, 1, 0, 0};
+            for (int k = 0; k < 6; ++k) {
+                const int nz = z + fz[k], ny = y + fy[k], nx = x + fx[k];
+                if (nz < 0 || nz >= it.D || ny < 0 || ny >= it.H || nx < 0 || nx >= it.W) continue;
+                const int64_t u = v + fz[k] * HW + fy[k] * W + fx[k];
+                if (vkey(it.img, u) < kv) {
+                    const int axis = fx[k] ? 0 : (fy[k] ? 1 : 2);
+                    set_bit(b.neg_e, uint32_t(3 * (it.voff + (u < v ? u : v)) + axis));
+                    break;
+                }
+            }
+        }
+        // the lower star of v: its squares in descending order, with a
+        // union-find over its 8 octant cubes (a cube outside the box is the
+        // outside vertex); cubes not in the star and the outside are older
+        // than every cube in it and their classes are not known here.  The
+        // star's cells are consecutive in the filtration order and its cubes
+        // enter it as singletons, so a square that joins two classes of which
+        // at least one has touched nothing outside the star merges them: a
+        // 2-cycle is born (Sec. 3.1 dual graph).  Joins of two classes that
+        // both reach outside are left to the dual union-find's survivors.
+        uint32_t low = 0;  // bit n3(o): the neighbour at offset o is lower
+        for (int n = 0; n < 27; ++n) {
+            const int dz = n / 9 - 1, dy = (n / 3) % 3 - 1, dx = n % 3 - 1;
+            const int nz = z + dz, ny = y + dy, nx = x + dx;
+            if (n == 13 || nz < 0 || nz >= it.D || ny < 0 || ny >= it.H || nx < 0 || nx >= it.W) continue;
+            if (vkey(it.img, v + dz * HW + dy * W + dx) < kv) low |= 1u << n;
+        }
+        if (low == 0u) continue;
+        uint8_t node[8];   // octant (bit 2: +z, bit 1: +y, bit 0: +x) -> union-find node (8: the outside)
+        uint8_t par[9];
+        uint16_t ext = 1u << 8;  // bit k: node k's class reaches outside the star
+        for (int oc = 0; oc < 8; ++oc) {
+            const int sz = (oc & 4) ? 1 : -1, sy = (oc & 2) ? 1 : -1, sx = (oc & 1) ? 1 : -1;
+            const int cz = z + (sz < 0 ? -1 : 0), cy = y + (sy < 0 ? -1 : 0), cx = x + (sx < 0 ? -1 : 0);
+            par[oc] = uint8_t(oc);
+            if (cz < 0 || cz >= it.D - 1 || cy < 0 || cy >= it.H - 1 || cx < 0 || cx >= it.W - 1) {
+                node[oc] = 8;
+                continue;
+            }
+            node[oc] = uint8_t(oc);
+            bool in_star = true;  // its 7 other corners are lower
+            for (int c = 1; c < 8; ++c)
+                in_star = in_star && ((low >> n3((c >> 2) * sz, ((c >> 1) & 1) * sy, (c & 1) * sx)) & 1u);
+            if (!in_star) ext |= uint16_t(1u << oc);
+        }
+        par[8] = 8;
+        // the 12 squares through v by stencil index, descending
+        const int8_t sqo[12][3] = {{1, 1, 0},  {1, 0, 1},  {1, 0, -1},  {1, -1, 0},  {0, 1, 1},   {0, 1, -1},
+                                   {0, -1, 1}, {0, -1, -1}, {-1, 1, 0}, {-1, 0, 1}, {-1, 0, -1}, {-1, -1, 0}};
+        for (int k = 0; k < 12; ++k) {
+            const int oz = sqo[k][0], oy = sqo[k][1], ox = sqo[k][2];
+            // in the star: its three other corners are lower (and in the box)
+            const bool in_star = ((low >> n3(oz, oy, ox)) & 1u) && ((low >> n3(oz, 0, 0)) & 1u || oz == 0) &&
+                                 ((low >> n3(0, oy, 0)) & 1u || oy == 0) && ((low >> n3(0, 0, ox)) & 1u || ox == 0);
+            if (!in_star) continue;
+            const int a = oz == 0 ? 2 : (oy == 0 ? 1 : 0);  // normal axis
+            // its two cubes: the normal component at -1 and at +1
+            const int base = (oz > 0 ? 4 : 0) | (oy > 0 ? 2 : 0) | (ox > 0 ? 1 : 0);
+            const int bit = a == 2 ? 4 : (a == 1 ? 2 : 1);
+            int ra = node[base & ~bit], rb = node[base | bit];
+            while (par[ra] != ra) ra = par[ra];
+            while (par[rb] != rb) rb = par[rb];
+            if (ra == rb) continue;
+            if (!(((ext >> ra) & 1u) && ((ext >> rb) & 1u))) {
+                const int64_t lo = v + (oz < 0 ? -HW : 0) + (oy < 0 ? -W : 0) + (ox < 0 ? -1 : 0);
+                set_bit(b.pos_q, uint32_t(3 * (it.voff + lo) + a));
+            }
+            par[ra] = uint8_t(rb);
+            if ((ext >> ra) & 1u) ext |= uint16_t(1u << rb);
+        }
+    }
+}
+
+// ---- the columns: every square not paired in H2, with the check counts
+__global__ void __launch_bounds__(kHT) k_h1_cols(const __grid_constant__ ItemTable tab, H1Bufs b, int64_t v0,
+                                                 int64_t v1) {
+    uint32_t ne = 0, pe = 0, pq = 0;
+    for (int64_t base = v0 + int64_t(blockIdx.x) * kHT; base < v1; base += int64_t(gridDim.x) * kHT) {
+        const int64_t g = base + threadIdx.x;
+        const bool live = g < v1;
+        const Item& it = tab.it[item_of_vertex(tab, uint32_t(live ? g : v0))];
+        const int64_t v = g - it.voff;
+        const int x = int(v % it.W), y = int((v / it.W) % it.H), z = int(v / (int64_t(it.W) * it.H));
+        const bool room[3] = {x < it.W - 1, y < it.H - 1, z < it.D - 1};
+        for (int a = 0; a < 3; ++a) {
+            const uint32_t id = uint32_t(3 * g + a);
+            if (live && room[a]) {
+                if (get_bit(b.neg_e, id)) ++ne;
+                else ++pe;
+            }
+            bool want = false;
+            uint64_t key = 0;
+            if (live && room[a == 0 ? 1 : 0] && room[a == 2 ? 1 : 2]) {
+                if (get_bit(b.pos_q, id)) {
+                    ++pq;
+                } else {
+                    want = true;
+                    key = square_key(it, v, a);
+                }
+            }
+            const uint32_t pos = warp_append(&b.ctl->m, want);
+            if (want && pos < b.mcap) b.ckeys[pos] = key;
+        }
+    }
+    ne = __reduce_add_sync(0xFFFFFFFFu, ne);
+    pe = __reduce_add_sync(0xFFFFFFFFu, pe);
+    pq = __reduce_add_sync(0xFFFFFFFFu, pq);
+    if (lane_id() == 0) {
+        if (ne) atomicAdd(&b.ctl->neg_e, ne);
+        if (pe) atomicAdd(&b.ctl->pos_e, pe);
+        if (pq) atomicAdd(&b.ctl->pos_q, pq);
+    }
+}
+
+// ---- column c (rank c of the sorted keys): the square's unmarked edges,
+// descending; 4 pool entries per column
+__global__ void __launch_bounds__(kHT) k_h1_build(const __grid_constant__ ItemTable tab, H1Bufs b, Counters* ctr) {
+    const H1Ctl* ctl = b.ctl;
+    if (ld_acquire_u32(&ctr->status) & kStSkip) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0 &&
+        (ctl->m != b.mcap || ctl->pos_e != b.mcap || ctl->neg_e != b.exp_neg_e || ctl->pos_q != b.exp_pos_q))
+        set_status(ctr, kStInternal);
+    const uint32_t M = min(ctl->m, b.mcap);
+    for (uint32_t c = blockIdx.x * kHT + threadIdx.x; c < M; c += gridDim.x * kHT) {
+        const uint64_t key = b.ckeys[c];
+        const Item& it = tab.it[item_of_vertex(tab, key_vertex(key))];
+        const uint32_t sid = cell_id3(it, key, true);
+        const int a = int(sid % 3u);
+        const int64_t L = int64_t(sid / 3u) - it.voff;  // lowest corner (local)
+        const int p = a == 0 ? 1 : 0, q = a == 2 ? 1 : 2;
+        const int64_t cu[4] = {L, L, L + axis_step(it, q), L + axis_step(it, p)};
+        const int ax[4] = {p, q, p, q};
+        uint64_t e[4];
+        uint32_t n = 0;
+        for (int k = 0; k < 4; ++k) {
+            if (get_bit(b.neg_e, uint32_t(3 * (it.voff + cu[k]) + ax[k]))) continue;
+            uint64_t ek = edge_key(it, cu[k], ax[k]);
+            uint32_t j = n++;
+            while (j > 0 && e[j - 1] < ek) {  // insertion, descending
+                e[j] = e[j - 1];
+                --j;
+            }
+            e[j] = ek;
+        }
+        for (uint32_t k = 0; k < n; ++k) b.pool[4ull * c + k] = e[k];
+        b.off[c] = 4ull * c;
+        b.len[c] = n;
+        if (n == 0) set_status(ctr, kStInternal);  // a column of a square not paired in H2 cannot vanish
+    }
+}
+
+struct ReduceArgs {
+    ItemTable tab;
+    H1Bufs b;
+    Counters* ctr;
+};
+
+// Column c lost its row to an older column: add that column (F2: the
+// symmetric difference; the common lowest entry cancels).
+__device__ void add_winner(const ReduceArgs& a, uint32_t c, uint32_t r) {
+    const H1Bufs& b = a.b;
+    const uint64_t oc = __ldcg(b.off + c);
+    const uint32_t lc = __ldcg(b.len + c);
+    const uint64_t low = __ldcg(b.pool + oc);
+    const uint32_t p = __ldcg(b.pivot + edge_id(a.tab, low));
+    if (p >= c) {  // only after an earlier error
+        set_status(a.ctr, kStInternal);
+        atomicOr(&b.ctl->stop[r & 1u], 1u);
+        return;
+    }
+    const uint64_t op = __ldcg(b.off + p);
+    const uint32_t lp = __ldcg(b.len + p);
+    const uint64_t need = uint64_t(lc) + lp - 2u;
+    const uint64_t base = 4ull * b.mcap;
+    uint64_t at = 0;
+    if (need) {
+        at = atomicAdd(&b.ctl->grown, (unsigned long long)need);
+        if (base + at + need > b.pool_cap) {
+            set_status(a.ctr, kStCapacity);
+            atomicOr(&b.ctl->stop[r & 1u], 1u);
+            return;
+        }
+    }
+    uint64_t* out = b.pool + base + at;
+    uint32_t i = 1, j = 1, k = 0;
+    uint64_t x = i < lc ? __ldcg(b.pool + oc + i) : 0, y = j < lp ? __ldcg(b.pool + op + j) : 0;
+    while (i < lc || j < lp) {
+        if (j >= lp || (i < lc && x > y)) {
+            out[k++] = x;
+            ++i;
+            x = i < lc ? __ldcg(b.pool + oc + i) : 0;
+        } else if (i >= lc || y > x) {
+            out[k++] = y;
+            ++j;
+            y = j < lp ? __ldcg(b.pool + op + j) : 0;
+        } else {
+            ++i;
+            ++j;
+            x = i < lc ? __ldcg(b.pool + oc + i) : 0;
+            y = j < lp ? __ldcg(b.pool + op + j) : 0;
+        }
+    }
+    __stcg(b.off + c, base + at);
+    __stcg(b.len + c, k);
+    if (k == 0) {
+        set_status(a.ctr, kStInternal);
+        atomicOr(&b.ctl->stop[r & 1u], 1u);
+    }
+}
+
+__global__ void __launch_bounds__(kRT) k_h1_reduce(const __grid_constant__ ReduceArgs a) {
+    const H1Bufs& b = a.b;
+    Counters* ctr = a.ctr;
+    H1Ctl* ctl = b.ctl;
+    if (ld_acquire_u32(&ctr->status) & kStSkip) return;  // set before the launch: every CTA returns
+    const uint32_t nblocks = gridDim.x, gstride = nblocks * kRT, gtid = blockIdx.x * kRT + threadIdx.x;
+    __shared__ uint32_t sh_n, sh_stop;
+    uint32_t epoch = 0;
+    uint32_t nchg = min(ctl->m, b.mcap);  // round 0: every column, by rank
+    for (uint32_t r = 0;; ++r) {
+        uint32_t* work = b.list[r & 1u];
+        const uint32_t* chg = b.list[(r & 1u) ^ 1u];
+        uint32_t* wcnt = &ctl->cnt[r % 3u];
+        // ---- bids: the oldest column of each row keeps it
+        for (uint32_t i0 = blockIdx.x * kRT; i0 < nchg; i0 += gstride) {
+            const uint32_t i = i0 + threadIdx.x;
+            uint32_t lose = kNone;
+            if (i < nchg) {
+                const uint32_t c = r == 0 ? i : __ldcg(chg + i);
+                if (__ldcg(b.len + c) != 0u) {
+                    const uint64_t low = __ldcg(b.pool + __ldcg(b.off + c));
+                    const uint32_t old = atomicMin(b.pivot + edge_id(a.tab, low), c);
+                    if (old < c) lose = c;            // an older column holds the row
+                    else if (old != kNone) lose = old;  // c displaces a younger holder
+                }
+            }
+            const uint32_t pos = warp_append(wcnt, lose != kNone);
+            if (lose != kNone && pos < b.mcap) work[pos] = lose;
+        }
+        grid_barrier(ctr, nblocks, epoch);
+        // one thread reads the round's outcome for the CTA, so that every CTA
+        // takes the same path (the stop word of the previous round is
+        // complete; this round's merges write the other one)
+        if (threadIdx.x == 0) {
+            sh_n = ld_acquire_u32(wcnt);
+            sh_stop = (r > 0 ? ld_acquire_u32(&ctl->stop[(r - 1u) & 1u]) : 0u) |
+                      (ld_acquire_u32(&ctr->status) & kStTimeout);
+        }
+        __syncthreads();
+        const uint32_t nw = min(sh_n, b.mcap);
+        const bool stop = sh_stop != 0u;
+        __syncthreads();
+        if (nw == 0u || stop || r + 1u >= kMaxRounds) {
+            if (gtid == 0) {
+                ctl->rounds = r + 1u;
+                if (nw != 0u && !stop) set_status(ctr, kStInternal);
+            }
+            break;
+        }
+        if (gtid == 0) ctl->cnt[(r + 1u) % 3u] = 0u;  // the next round's bids (last read two rounds ago)
+        // ---- every losing column adds the winner of its row
+        for (uint32_t i = gtid; i < nw; i += gstride) add_winner(a, __ldcg(work + i), r);
+        grid_barrier(ctr, nblocks, epoch);
+        nchg = nw;
+    }
+}
+
+// ---- the pairs (lowest entry, square) with nonzero persistence
+__global__ void __launch_bounds__(kHT) k_h1_emit(const __grid_constant__ ItemTable tab, H1Bufs b, Counters* ctr,
+                                                 cp_pair* pairs, uint32_t cap) {
+    if (ld_acquire_u32(&ctr->status) & kStSkip) return;
+    const uint32_t M = min(b.ctl->m, b.mcap);
+    for (uint32_t i0 = blockIdx.x * kHT; i0 < M; i0 += gridDim.x * kHT) {
+        const uint32_t c = i0 + threadIdx.x;
+        bool emit = false;
+        cp_pair pr;
+        if (c < M && b.len[c] != 0u) {
+            const uint64_t ek = b.pool[b.off[c]], sk = b.ckeys[c];
+            const float fb = ord_float(uint32_t(ek >> 32)), fd = ord_float(uint32_t(sk >> 32));
+            if (fb != fd) {  // zero persistence: omitted (Sec. 2.3)
+                const Item& it = tab.it[item_of_vertex(tab, key_vertex(sk))];
+                pr.birth = fb;
+                pr.death = fd;
+                pr.birth_cell = cell_index(it, ek);
+                pr.death_cell = cell_index(it, sk);
+                pr.birth_pixel = int32_t(int64_t(key_vertex(ek)) - it.voff);
+                pr.death_pixel = int32_t(int64_t(key_vertex(sk)) - it.voff);
+                pr.dim = 1;
+                pr.item = it.user;
+                emit = true;
+            }
+        }
+        const uint32_t pp = warp_append(&ctr->n_pairs, emit);
+        if (emit) {
+            if (pp < cap) pairs[pp] = pr;
+            else set_status(ctr, kStCapacity);
+        }
+    }
+}
+
+int grid_of(int64_t n) {
+    const int64_t blocks = (n + kHT - 1) / kHT;
+    const int64_t cap = int64_t(device_sm_count()) * 8;
+    return int(blocks < 1 ? 1 : (blocks < cap ? blocks : cap));
+}
+
+}  // namespace
+
+cudaError_t launch_h1(const ItemTable& tab, const H1Bufs& b, Counters* ctr, cp_pair* pairs, uint32_t pair_cap,
+                      cudaStream_t s) {
+    if (tab.n3d < 1) return cudaSuccess;
+    const int64_t v0 = tab.it[tab.n2d].voff;
+    const Item& last = tab.it[tab.n - 1];
+    const int64_t v1 = last.voff + int64_t(last.D) * last.H * last.W;
+    const int reduce_blocks = device_cached(kCacheH1, [] {
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_h1_reduce, kRT, 0);
+        return per_sm > 0 ? device_sm_count() * per_sm : -1;
+    });
+    if (reduce_blocks <= 0) return cudaErrorLaunchOutOfResources;
+    cudaError_t e = cudaMemsetAsync(b.ctl, 0, sizeof(H1Ctl), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b.pivot, 0xFF, sizeof(uint32_t) * size_t(3 * v1), s);
+    if (e != cudaSuccess) return e;
+    k_h1_direct<<<grid_of(v1 - v0), kHT, 0, s>>>(tab, b, v0, v1);
+    k_h1_cols<<<grid_of(v1 - v0), kHT, 0, s>>>(tab, b, v0, v1);
+    note_launches(2);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    SortBufs sb;
+    sb.keys = b.ckeys;
+    sb.keys_alt = b.ckeys_alt;
+    sb.vals = nullptr;
+    sb.vals_alt = nullptr;
+    sb.d_count = &b.ctl->m;
+    sb.cap = b.mcap;
+    sb.hist = b.hist;
+    sb.status = b.status;
+    sb.tile_ctr = ctr->sort_tile + 24;
+    sb.ctr = ctr;
+    if ((e = sort_keys(sb, 0, 8, 25, s)) != cudaSuccess) return e;
+    k_h1_build<<<grid_of(b.mcap), kHT, 0, s>>>(tab, b, ctr);
+    note_launches(1);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    ReduceArgs ra;
+    ra.tab = tab;
+    ra.b = b;
+    ra.ctr = ctr;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(reduce_blocks);
+    cfg.blockDim = dim3(kRT);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if ((e = cudaMemsetAsync(&ctr->bar_count, 0, sizeof(uint32_t), s)) != cudaSuccess) return e;
+    if ((e = cudaLaunchKernelEx(&cfg, k_h1_reduce, ra)) != cudaSuccess) return e;
+    k_h1_emit<<<grid_of(b.mcap), kHT, 0, s>>>(tab, b, ctr, pairs, pair_cap);
+    note_launches(2);
+    return cudaGetLastError();
+}
+
+}  // namespace cp

@@ -86,6 +86,9 @@ struct UfParams {
     uint32_t dual_cap;
     Counters* ctr;
     int dual;                 // 0: H0 (ascending, larger age dies); 1: dual (smaller age dies)
+    // H1 of volumes: bit cell_id3 of every committed survivor of a 3D item
+    // (H0: a negative edge; dual: a square that creates a 2-cycle), or nullptr
+    uint32_t* h1flags = nullptr;
 };
 // First-round root walks, before the sort (k_roots: ra / rb / pos per unsorted
 // survivor), and the first active list from the sorted positions
@@ -118,6 +121,44 @@ cudaError_t launch_place_roots(const RootArgs& r, cudaStream_t s);
 // side by side when both fit, else they run one after the other.
 cudaError_t launch_uf(const ItemTable& tab, const UfParams* p, int nprob, cudaStream_t s);
 
+// ---- H1 of volumes (cp_h1.cu): column reduction of the square-edge boundary
+// matrix restricted to the squares that do not create 2-cycles and the edges
+// that do not merge components.
+struct H1Ctl {
+    uint32_t m;                   // columns (squares) appended
+    uint32_t cnt[3];              // work-list counters of the reduction rounds (rotating)
+    uint32_t neg_e, pos_q, pos_e; // checks: marked edges, marked squares, unmarked edges
+    uint32_t rounds;              // reduction rounds run
+    uint32_t stop[2];             // a round's merges hit an error (read one round later, by parity)
+    unsigned long long grown;     // pool entries taken by merged columns
+    unsigned long long pad[3];
+};
+struct H1Bufs {
+    uint32_t* neg_e;         // bitmap over edge ids (cell_id3): edge kills an H0 class
+    uint32_t* pos_q;         // bitmap over square ids: square creates a 2-cycle
+    size_t map_words;        // words per bitmap
+    H1Ctl* ctl;
+    uint64_t* ckeys;         // column keys (unmarked squares), sorted ascending
+    uint64_t* ckeys_alt;
+    uint32_t* hist;
+    uint64_t* status;
+    uint64_t* off;           // per column: offset of its entries in pool
+    uint32_t* len;           // per column: entry count
+    uint32_t* list[2];       // columns changed in a round (ping-pong)
+    uint32_t* pivot;         // per edge id: the oldest column whose lowest entry it is
+    uint64_t* pool;          // column entries (edge keys, descending); columns 4 apart, then merged ones
+    uint64_t pool_cap;
+    uint32_t mcap;           // columns expected: sum over 3D items of E - N + 1
+    uint32_t exp_neg_e;      // sum over 3D items of N - 1
+    uint32_t exp_pos_q;      // sum over 3D items of (D-1)(H-1)(W-1)
+};
+// After the union-finds have marked their committed survivors in the two
+// bitmaps (zeroed before them): marks the direct pairs' cells, lists and
+// sorts the columns, builds and reduces them, and appends the H1 pairs (zero
+// persistence omitted) to pairs.
+cudaError_t launch_h1(const ItemTable& tab, const H1Bufs& b, Counters* ctr, cp_pair* pairs, uint32_t pair_cap,
+                      cudaStream_t s);
+
 // ---- K4 emission, K5 backward
 cudaError_t launch_init(const ItemTable& tab, Counters* ctr, uint32_t* uft, uint64_t* aget, uint64_t* rest,
                         cudaStream_t s);
@@ -145,8 +186,9 @@ cudaError_t launch_t_flatten(uint32_t* uf0, const TItems& t, cudaStream_t s);
 cudaError_t launch_t_map(cp_pair* pairs, const uint32_t* d_n, uint32_t cap, const TItems& t, const uint32_t* bad,
                          Counters* ctr, cudaStream_t s);
 cudaError_t launch_essential(const ItemTable& tab, Counters* ctr, cp_pair* pairs, uint32_t pair_cap, cudaStream_t s);
+// dim_bits 1: dimension 0 or top; 2: dimension 0, 1 or 2 (calls with H1)
 cudaError_t launch_pair_keys(const cp_pair* pairs, const uint32_t* d_n, uint32_t cap, uint64_t* keys, uint32_t* vals,
-                             int cell_bits, cudaStream_t s);
+                             int cell_bits, int dim_bits, cudaStream_t s);
 cudaError_t launch_gather(const cp_pair* pairs, const uint32_t* vals, const uint32_t* d_n, uint32_t cap,
                           cp_pair* out, int64_t out_cap, int64_t* d_out_count, Counters* ctr, cudaStream_t s);
 cudaError_t launch_backward(const cp_pair* pairs, int64_t n, const float* gb, const float* gd, const int64_t* offs,
@@ -155,7 +197,7 @@ cudaError_t launch_backward(const cp_pair* pairs, int64_t n, const float* gb, co
 int device_sm_count();
 // init() run once per device and slot (thread-safe), its result cached: the
 // launch set-up of a kernel (attributes, occupancy-derived grid size).
-enum { kCachePrune3d, kCachePrune2d, kCacheSort, kCacheUf, kCacheRoots, kCacheSlots };
+enum { kCachePrune3d, kCachePrune2d, kCacheSort, kCacheUf, kCacheRoots, kCacheH1, kCacheSlots };
 int device_cached(int slot, int (*init)());
 
 // Kernel launches made by the library (for the benchmark's launch count).

@@ -108,40 +108,6 @@ __device__ __forceinline__ void reserve(uint64_t* res, uint32_t rid, uint64_t st
     atomicMax(reinterpret_cast<unsigned long long*>(res + rid), (unsigned long long)stamp);
 }
 
-// Grid-wide barrier for a cooperative launch (all CTAs co-resident): a
-// monotonic arrival counter (zeroed before the launch).  Barrier number e of
-// the launch is passed when the counter reaches e * nblocks, so it completes
-// as soon as the last CTA's arrival lands.  The wait is bounded.
-__device__ void grid_barrier(Counters* ctr, uint32_t nblocks, uint32_t& epoch) {
-    __syncthreads();
-    ++epoch;
-    if (threadIdx.x == 0) {
-        const uint32_t target = epoch * nblocks;
-        asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&ctr->bar_count) : "memory");
-        if (ld_acquire_u32(&ctr->bar_count) < target) {
-            const uint64_t t0 = global_timer_ns();
-            while (ld_acquire_u32(&ctr->bar_count) < target) {
-                if (global_timer_ns() - t0 > kWaitLimitNs) {
-                    set_status(ctr, kStTimeout);
-                    break;
-                }
-            }
-        }
-    }
-    __syncthreads();
-}
-
-// warp-aggregated append of one element per active lane
-__device__ __forceinline__ uint32_t warp_append(uint32_t* counter, bool want) {
-    unsigned m = __ballot_sync(0xFFFFFFFFu, want);
-    if (!m) return 0;
-    int leader = __ffs(m) - 1;
-    uint32_t base = 0;
-    if (int(lane_id()) == leader) base = atomicAdd(counter, uint32_t(__popc(m)));
-    base = __shfl_sync(0xFFFFFFFFu, base, leader);
-    return base + __popc(m & ((1u << lane_id()) - 1u));
-}
-
 // Endpoints of survivor key k (H0: the edge's two vertices; dual: the two top
 // cells on either side of the facet, or the item's outside vertex).
 __device__ __forceinline__ void endpoints(const ItemTable& tab, uint64_t k, int dual, uint32_t& a, uint32_t& b,
@@ -736,6 +702,10 @@ __device__ void uf_rounds(const UfKernelArgs& args, uint32_t n0, uint32_t n1, ui
                     uint64_t key = p.keys[i];
                     if (p.dual) key = ~key;
                     const int item = item_of_vertex(tab, key_vertex(key));
+                    if (p.h1flags && tab.it[item].ndim == 3) {
+                        const uint32_t id = cell_id3(tab.it[item], key, p.dual != 0);
+                        atomicOr(p.h1flags + (id >> 5), 1u << (id & 31u));
+                    }
                     emit_pair(p, tab, key, item, uint32_t(e), &emit, pr);
                 }
             }

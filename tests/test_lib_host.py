@@ -166,6 +166,35 @@ def test_t_workspace_sizes(lib):
     assert size("cubical_persistence_t_workspace_size", 510, 510, 510) > 0
 
 
+def test_full_workspace_sizes(lib):
+    """The full-diagram workspace adds the H1 stage to the plain one for a
+    volume (bitmaps, columns, pivots, pool: it grows with the pool); a 2D
+    image has no H1 stage; bad arguments give 0."""
+    import ctypes
+
+    def full(dims, pool=0):
+        d = (ctypes.c_int64 * len(dims))(*dims)
+        return lib.cubical_persistence_full_workspace_size(len(dims), d, 0, pool)
+
+    def plain(dims):
+        d = (ctypes.c_int64 * len(dims))(*dims)
+        return lib.cubical_persistence_workspace_size(len(dims), d, 0)
+
+    for dims in [(2, 2, 2), (3, 4, 5), (20, 30, 40)]:
+        D, H, W = dims
+        cols = D * H * (W - 1) + D * (H - 1) * W + (D - 1) * H * W - D * H * W + 1
+        f, p = full(dims), plain(dims)
+        # at least: two pool regions of 4 entries per column, keys, offsets, pivots
+        assert f >= p + 8 * 8 * cols + 16 * cols + 12 * D * H * W, (dims, f, p)
+        assert full(dims, 10**6) - full(dims, 1) >= 8 * (10**6 - 1) - 256
+    assert full((17, 19)) == plain((17, 19))
+    assert full((1, 5, 5)) == 0 and full((4, 0, 5)) == 0
+    assert full((3, 4, 5), -1) == 0
+    n = (ctypes.c_int32 * 2)(3, 2)
+    d = (ctypes.c_int64 * 6)(4, 5, 6, 1, 7, 8)
+    assert lib.cubical_persistence_full_batched_workspace_size(2, n, d, 0, 0) > lib.cubical_persistence_batched_workspace_size(2, n, d, 0)
+
+
 def test_t_entry_argument_errors(lib):
     """The T-filtration entries reject bad arguments before touching a device."""
     import ctypes
