@@ -18,7 +18,7 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libcp_gb300.so")
 CU = ["cp_prune.cu", "cp_sort.cu", "cp_uf.cu", "cp_emit.cu", "cp_api.cu", "cp_noalloc.cu", "cp_tfilt.cu", "cp_h1.cu"]
 CPP = ["cp_lut.cpp"]
-HEADERS = ["cp_common.cuh", "cp_kernels.h", "cp_lut.h", os.path.join("..", "..", "include", "cubical_persistence.h")]
+HEADERS = ["cp_common.cuh", "cp_grid.cuh", "cp_kernels.h", "cp_lut.h", os.path.join("..", "..", "include", "cubical_persistence.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

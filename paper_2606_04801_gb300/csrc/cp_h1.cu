@@ -39,6 +39,7 @@
 // lost.  Every wait is bounded; pool overflow and failed checks set a status
 // bit and stop the rounds.
 #include "cp_common.cuh"
+#include "cp_grid.cuh"
 #include "cp_kernels.h"
 
 namespace cp {

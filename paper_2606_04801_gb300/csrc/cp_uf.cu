@@ -29,6 +29,7 @@
 // a per-survivor log; the pairs are written from the log in one parallel pass
 // after the last round.
 #include "cp_common.cuh"
+#include "cp_grid.cuh"
 #include "cp_kernels.h"
 
 namespace cp {
