@@ -750,6 +750,151 @@ def run_tfilt(args):
         torch.distributed.destroy_process_group()
 
 
+def run_full(args):
+    """The whole diagram of the benchmark volume (512^3 blurred, sigma 3): H0,
+    H1 and H2 pairs, forward + total-persistence loss backward, device-resident
+    input; the oracle's full diagram on a crop as the CPU line."""
+    import torch
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        torch.distributed.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import paper_2606_04801_gb300 as cp
+    from paper_2606_04801_gb300 import _lib
+
+    lib = _lib.load()
+    side = SIDE
+    vol = _volume(rank)
+    N = vol.size
+    x = torch.from_numpy(vol).to(dev)
+    from paper_2606_04801_gb300 import autotune
+
+    autotune.autotune([x])
+    stream = torch.cuda.current_stream(dev)
+    sp = ctypes.c_void_p(int(stream.cuda_stream))
+    dims = (ctypes.c_int64 * 3)(side, side, side)
+    one = (ctypes.c_int32 * 1)(3)
+    pool = 0
+    ws_bytes = lib.cubical_persistence_full_workspace_size(3, dims, 0, pool)
+    wsp = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
+    cap = side ** 3 + 65536
+    out = torch.empty((cap, 8), dtype=torch.int32, device=dev)
+    grad = torch.empty(N, dtype=torch.float32, device=dev)
+    loss = torch.zeros(1, dtype=torch.float64, device=dev)
+    bws = lib.cubical_persistence_loss_backward_workspace_size(N)
+    bwsp = torch.empty(bws, dtype=torch.uint8, device=dev)
+    dcount = torch.zeros(1, dtype=torch.int64, device=dev)
+
+    def step():
+        rc = lib.cubical_persistence_full_3d(
+            ctypes.c_void_p(x.data_ptr()), dims, ctypes.c_void_p(out.data_ptr()), cap, None,
+            ctypes.c_void_p(dcount.data_ptr()), ctypes.c_void_p(wsp.data_ptr()), ws_bytes, 0, pool, sp,
+        )
+        if rc != 0:
+            raise cp.CpError(rc, "full forward")
+        rc = lib.cubical_persistence_loss_backward(
+            ctypes.c_void_p(out.data_ptr()), cap, ctypes.c_void_p(dcount.data_ptr()), ctypes.c_float(TAU),
+            ctypes.c_void_p(loss.data_ptr()), None, ctypes.c_void_p(grad.data_ptr()), N, ctypes.c_void_p(bwsp.data_ptr()),
+            bws, sp,
+        )
+        if rc != 0:
+            raise cp.CpError(rc, "loss backward")
+
+    def h1_info():
+        info = (ctypes.c_int64 * 10)()
+        rc = lib.cubical_persistence_full_info(ctypes.c_void_p(wsp.data_ptr()), 1, one, dims, 0, pool, info, 10, sp)
+        if rc != 0:
+            raise cp.CpError(rc, "full info")
+        return [int(v) for v in info]
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    st = cp.api._stats(wsp)
+    if st["rc"] != 0:
+        raise cp.CpError(st["rc"], f"full warm-up (H1 stage: {h1_info()[:4]})")
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    gpu_index = int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[local]) if os.environ.get("CUDA_VISIBLE_DEVICES") else local
+    launches0 = lib.cp_launch_count()
+    with Clocks(gpu_index) as clk:
+        torch.cuda.synchronize(dev)
+        if ws > 1:
+            torch.distributed.barrier()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step()
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        if ws > 1:
+            torch.distributed.barrier()
+    launches = lib.cp_launch_count() - launches0
+    st = cp.api._stats(wsp)
+    if st["rc"] != 0:
+        raise cp.CpError(st["rc"], "full timed steps")
+    info = h1_info()
+    elapsed = job_time(ev0.elapsed_time(ev1) / 1e3, ws, dev)
+    value = job_value(N, ws, args.steps, elapsed)
+    # the plain H0 + H2 call on the same volume, for the H1 stage's share
+    pws = lib.cubical_persistence_workspace_size(3, dims, 0)
+    pwsp = torch.empty(pws, dtype=torch.uint8, device=dev)
+
+    def plain():
+        rc = lib.cubical_persistence_3d(ctypes.c_void_p(x.data_ptr()), dims, ctypes.c_void_p(out.data_ptr()), cap, None,
+                                        ctypes.c_void_p(dcount.data_ptr()), ctypes.c_void_p(pwsp.data_ptr()), pws, 0, sp)
+        if rc != 0:
+            raise cp.CpError(rc, "plain forward")
+
+    for _ in range(3):
+        plain()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        plain()
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    plain_ms = ev0.elapsed_time(ev1) / args.steps
+    del pwsp
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle
+
+        oracle.build()
+        c = 32
+        crop = np.ascontiguousarray(vol[:c, :c, :c])
+        t0 = time.perf_counter()
+        oracle.persistence_full(crop)
+        dt = time.perf_counter() - t0
+        c2 = min(64, int(c * max(1.0, (8.0 / max(dt, 1e-3)) ** (1 / 3) * 0.8)))
+        if c2 > c:
+            crop = np.ascontiguousarray(vol[:c2, :c2, :c2])
+            t0 = time.perf_counter()
+            oracle.persistence_full(crop)
+            dt = time.perf_counter() - t0
+            c = c2
+        cpu = {"value": crop.size / dt / 1e6, "unit": "Mvoxels/s", "cores": 1, "host": _host(), "kind": "oracle",
+               "sample": f"{c}^3 crop of the {side}^3 volume, H0 + H1 + H2 pairs (H1 by the textbook column "
+                         f"reduction), single-threaded C oracle, {dt:.1f} s"}
+    if rank == 0:
+        print(json.dumps({
+            "metric": f"Mvoxels/s, H0 + H1 + H2 pairs ({side}^3 fp32), fwd + loss bwd",
+            "value": value, "unit": "Mvoxels/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"3D {side}^3 float32 blurred noise (sigma 3 vox), whole diagram (H0, H1, H2), "
+                                   "fwd + total-persistence loss bwd", "status": st["rc"], "pairs": st["pairs"],
+                       "h1_columns": info[0], "h1_columns_leaving_their_star": info[9], "h1_rounds": info[1],
+                       "h1_pool_entries_used": info[2], "h1_pool_entries": info[3],
+                       "plain_h0_h2_forward_ms": plain_ms,
+                       "l2": "input larger than L2; no flush", "parallelism": "replicas" if ws > 1 else "single"},
+            "gpu_launches": launches,
+            "clocks": clk.summary(),
+            "cpu_baseline": cpu,
+        }), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -760,10 +905,11 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--side", type=int, default=512, help="cube side (512 is the benchmark; smaller for profiling)")
     ap.add_argument("--no-batched", action="store_true")
-    ap.add_argument("--workload", default="volume", choices=["volume", "batched", "survivors", "tfilt", "2d"],
+    ap.add_argument("--workload", default="volume", choices=["volume", "batched", "survivors", "tfilt", "2d", "full"],
                     help="volume: the 512^3 plain path (the headline line); batched: the batched fwd + bwd workload "
                     "alone; survivors: survivor fractions S/N of every config; tfilt: the T-filtration on 510^3; "
-                    "2d: the 2048x2048 random field and its 256-level form")
+                    "2d: the 2048x2048 random field and its 256-level form; full: the whole diagram (H0, H1, H2) "
+                    "of the 512^3 volume")
     ap.add_argument("--eager", action="store_true", help="batched workload without the CUDA graph (per-kernel profiling)")
     args = ap.parse_args()
     global SIDE
@@ -784,6 +930,9 @@ def main():
         return
     if args.workload == "2d":
         run_2d(args)
+        return
+    if args.workload == "full":
+        run_full(args)
         return
 
     import torch

@@ -231,12 +231,15 @@ int cubical_persistence_batched(int n_items, const float *const *h_images, const
  * reduction over the cells that H0 and H2 leave unpaired; here it is the F2
  * column reduction (Sec. 2.1) of the boundary matrix of the squares not
  * paired in H2 over the edges not paired in H0, in the refined order of
- * Sec. 2.3, run in parallel rounds on the device.  2D items get their plain
- * diagram.  Output order (item, dim, birth cell) as for the other calls.
+ * Sec. 2.3, on the device: first inside each lower star (a star's cells are
+ * consecutive in that order), then, for the columns whose lowest entry
+ * leaves their star, in parallel rounds.  2D items get their plain diagram.
+ * Output order (item, dim, birth cell) as for the other calls.
  *  pool_entries : device pool entries (8 bytes each) for the columns that
- *                 additions create, beyond the 4 per column they start
- *                 with; 0 picks 4 per column + 65536.  A call that runs out
- *                 returns CP_ERR_CAPACITY (repeat with a larger pool).
+ *                 additions across stars create (each addition writes
+ *                 its result anew); 0 picks 4 per column + 2^20.  A call
+ *                 that runs out returns
+ *                 CP_ERR_CAPACITY (repeat with a larger pool).
  *  capacity     : E + (D-1)(H-1)(W-1) + 1 always suffices for a volume
  *                 (E = its edges).
  *  d_workspace  : ws_bytes >= cubical_persistence_full_workspace_size() /
@@ -260,7 +263,11 @@ int cubical_persistence_full_batched(int n_items, const float *const *h_images, 
 /*
  * The H1 stage of the last full call on this workspace (same item, size
  * and pool arguments as that call; waits for `stream`): h_info[0] columns,
- * [1] reduction rounds, [2] pool entries used, [3] pool entries available.
+ * [1] reduction rounds, [2] pool entries used, [3] pool entries available;
+ * with cap >= 10 also [4] edges paired in H0, [5] squares paired in H2,
+ * [6] edges not paired in H0, [7] and [8] the byte offsets of the two
+ * bitmaps of those edges and squares (bit 3 * lowest corner + axis) in the
+ * workspace, [9] columns whose lowest entry left their lower star.
  * cap >= 4.
  */
 int cubical_persistence_full_info(const void *d_workspace, int n_items, const int32_t *ndims, const int64_t *dims,

@@ -256,8 +256,7 @@ def _full_call(imgs: Sequence[torch.Tensor], single: bool, max_survivors: int, p
                 ms = _grow(st, eff, n)
                 grew = True
             if info_rc == CP_OK and info[2] > info[3]:
-                base = 4 * int(info[0])
-                pool = 2 * max(int(info[2]) - base, int(info[3]) - base)
+                pool = 2 * max(int(info[2]), int(info[3]))
                 grew = True
             if cnt.value > cap:
                 cap = int(cnt.value) + 1024

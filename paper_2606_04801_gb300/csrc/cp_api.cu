@@ -74,16 +74,15 @@ struct Plan {
     uint32_t h1_mcap = 0, h1_neg = 0, h1_posq = 0;
     uint64_t h1_pool = 0;
     size_t h1_words = 0;
-    size_t o_h1_neg, o_h1_pos, o_h1_ctl, o_h1_ck, o_h1_cka, o_h1_hist, o_h1_status, o_h1_off, o_h1_len, o_h1_l0,
-        o_h1_l1, o_h1_piv, o_h1_pool;
+    size_t o_h1_neg, o_h1_pos, o_h1_ctl, o_h1_cmask, o_h1_coff, o_h1_clen, o_h1_ccap, o_h1_list0, o_h1_l0, o_h1_l1,
+        o_h1_piv, o_h1_pool;
     size_t bytes = 0;
 };
 
 size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
 
 // h1: also lay out the H1 stage of the 3D items, with h1_pool pool entries
-// for merged columns beyond the 4 per column of the start (0: 4 per column +
-// 65536).
+// for the columns that additions create (0: 4 per column + 2^20).
 int make_plan(int n_items, const int32_t* ndims, const int64_t* dims, const float* const* imgs,
               int64_t max_survivors, Plan& P, bool h1 = false, int64_t h1_pool = 0) {
     if (n_items <= 0 || n_items > kMaxItems || !ndims || !dims) return CP_ERR_ARG;
@@ -169,7 +168,7 @@ int make_plan(int n_items, const int32_t* ndims, const int64_t* dims, const floa
         P.h1_mcap = uint32_t(h1_cols);
         P.h1_neg = uint32_t(h1_neg);
         P.h1_posq = uint32_t(h1_posq);
-        P.h1_pool = 4ull * uint64_t(h1_cols) + uint64_t(h1_pool > 0 ? h1_pool : 4 * h1_cols + 65536);
+        P.h1_pool = uint64_t(h1_pool > 0 ? h1_pool : 4 * h1_cols + (int64_t(1) << 20));
         P.cap_p += P.h1_mcap;  // H1 pairs (the nonzero ones are far fewer)
     }
     P.cap_big = std::max(P.cap_s, P.cap_p);
@@ -211,16 +210,16 @@ int make_plan(int n_items, const int32_t* ndims, const int64_t* dims, const floa
         P.h1_words = (3 * size_t(P.ntot) + 31) / 32;
         P.o_h1_neg = take(sizeof(uint32_t) * P.h1_words);
         P.o_h1_pos = take(sizeof(uint32_t) * P.h1_words);
+        const size_t ids = 3 * size_t(P.ntot);  // edge and square ids
         P.o_h1_ctl = take(sizeof(H1Ctl));
-        P.o_h1_ck = take(sizeof(uint64_t) * m);
-        P.o_h1_cka = take(sizeof(uint64_t) * m);
-        P.o_h1_hist = take(sizeof(uint32_t) * 8 * 256);
-        P.o_h1_status = take(sizeof(uint64_t) * sort_status_words(P.h1_mcap));
-        P.o_h1_off = take(sizeof(uint64_t) * m);
-        P.o_h1_len = take(sizeof(uint32_t) * m);
+        P.o_h1_cmask = take(sizeof(uint32_t) * ids);
+        P.o_h1_coff = take(sizeof(uint64_t) * ids);
+        P.o_h1_clen = take(sizeof(uint32_t) * ids);
+        P.o_h1_ccap = take(sizeof(uint32_t) * ids);
+        P.o_h1_list0 = take(sizeof(uint32_t) * m);
         P.o_h1_l0 = take(sizeof(uint32_t) * m);
         P.o_h1_l1 = take(sizeof(uint32_t) * m);
-        P.o_h1_piv = take(sizeof(uint32_t) * 3 * size_t(P.ntot));
+        P.o_h1_piv = take(sizeof(uint64_t) * ids);
         P.o_h1_pool = take(sizeof(uint64_t) * P.h1_pool);
     }
     P.bytes = o;
@@ -301,15 +300,14 @@ int run(const Plan& P, cp_pair* d_out, int64_t capacity, int64_t* h_out_count, i
         hb.pos_q = at<uint32_t>(ws, P.o_h1_pos);
         hb.map_words = P.h1_words;
         hb.ctl = at<H1Ctl>(ws, P.o_h1_ctl);
-        hb.ckeys = at<uint64_t>(ws, P.o_h1_ck);
-        hb.ckeys_alt = at<uint64_t>(ws, P.o_h1_cka);
-        hb.hist = at<uint32_t>(ws, P.o_h1_hist);
-        hb.status = at<uint64_t>(ws, P.o_h1_status);
-        hb.off = at<uint64_t>(ws, P.o_h1_off);
-        hb.len = at<uint32_t>(ws, P.o_h1_len);
+        hb.cmask = at<uint32_t>(ws, P.o_h1_cmask);
+        hb.coff = at<uint64_t>(ws, P.o_h1_coff);
+        hb.clen = at<uint32_t>(ws, P.o_h1_clen);
+        hb.ccap = at<uint32_t>(ws, P.o_h1_ccap);
+        hb.list0 = at<uint32_t>(ws, P.o_h1_list0);
         hb.list[0] = at<uint32_t>(ws, P.o_h1_l0);
         hb.list[1] = at<uint32_t>(ws, P.o_h1_l1);
-        hb.pivot = at<uint32_t>(ws, P.o_h1_piv);
+        hb.pivot = at<uint64_t>(ws, P.o_h1_piv);
         hb.pool = at<uint64_t>(ws, P.o_h1_pool);
         hb.pool_cap = P.h1_pool;
         hb.mcap = P.h1_mcap;
@@ -843,13 +841,14 @@ int cubical_persistence_full_info(const void* d_workspace, int n_items, const in
         return CP_ERR_CUDA;
     h_info[0] = c.m;
     h_info[1] = c.rounds;
-    h_info[2] = int64_t(4ull * P.h1_mcap + c.grown);
-    if (cap >= 9) {
+    h_info[2] = int64_t(c.grown);
+    if (cap >= 10) {
         h_info[4] = c.neg_e;
         h_info[5] = c.pos_q;
         h_info[6] = c.pos_e;
         h_info[7] = int64_t(P.o_h1_neg);
         h_info[8] = int64_t(P.o_h1_pos);
+        h_info[9] = c.nl;
     }
     return CP_OK;
 }

@@ -25,19 +25,26 @@
 // they mark in the same bitmaps.  The counts are checked: N - 1 merging edges
 // and (D-1)(H-1)(W-1) squares paired in H2 per volume.
 //
-// The reduction runs in rounds inside one cooperative kernel.  A column is a
-// descending array of edge keys (the refined keys of Sec. 2.3), lowest entry
-// first; columns are ranked by their square's key (the filtration order).
-// In a round every column whose lowest entry changed bids for that row with
-// an atomic minimum of its rank in a per-edge pivot word; every column that
-// loses a bid, or is displaced by an older one, then adds the winner of its
-// row (all such additions at once, into fresh pool space), so its lowest
-// entry drops, and it bids again in the next round.  Adding an older column
-// with the same lowest entry is a left-to-right column operation, so once all
-// lowest entries are distinct the pairs are those of the sequential
-// reduction, whatever the order of additions.  Rounds end when no bid is
-// lost.  Every wait is bounded; pool overflow and failed checks set a status
-// bit and stop the rounds.
+// The reduction runs in two parts.  Inside each lower star L(m) first: its
+// cells are consecutive in the filtration order, and no column of an earlier
+// star holds an edge of L(m), so the sequential reduction of L(m)'s columns
+// (in order, each adding the earlier column that holds its lowest entry)
+// is exact for as long as a column's lowest entry is an edge through m.  One
+// thread per vertex does it on 32-bit masks over the 30 edges of the star
+// (6 through m, 24 that miss it).  A column that ends holding an edge
+// through m is final: its pair has zero persistence, and the column is the
+// pivot of that edge.  The others (their lowest entry left the star: exactly
+// the pairs of nonzero persistence) are reduced across stars in rounds
+// inside one cooperative kernel: every column whose lowest entry changed
+// bids for that row with an atomic minimum of its key (the filtration order)
+// in a per-edge pivot word; every column that loses a bid, or is displaced
+// by an older one, then adds the winner of its row (all such additions at
+// once), so its lowest entry drops, and it bids again in the next round.
+// Adding an older column with the same lowest entry is a left-to-right
+// column operation, so once all lowest entries are distinct the pairs are
+// those of the sequential reduction, whatever the order of additions.
+// Rounds end when no bid is lost.  Every wait is bounded; pool overflow and
+// failed checks set a status bit and stop the rounds.
 #include "cp_common.cuh"
 #include "cp_grid.cuh"
 #include "cp_kernels.h"
@@ -200,81 +207,197 @@ __global__ void __launch_bounds__(kHT) k_h1_direct(const __grid_constant__ ItemT
     }
 }
 
-// ---- the columns: every square not paired in H2, with the check counts
-__global__ void __launch_bounds__(kHT) k_h1_cols(const __grid_constant__ ItemTable tab, H1Bufs b, int64_t v0,
-                                                 int64_t v1) {
-    uint32_t ne = 0, pe = 0, pq = 0;
+// ---- the slots of a lower star L(m): the 6 edges through m (slot 24 + f,
+// faces by stencil index ascending) and, for each of the 12 squares through
+// m (k by stencil index ascending), its two edges that miss m (slots 2k and
+// 2k + 1).  Edges through m come after every edge that misses m in the
+// filtration order, and among themselves in face order.
+__device__ const int8_t kSqA[12][3] = {{-1, -1, 0}, {-1, 0, -1}, {-1, 0, 1}, {-1, 1, 0}, {0, -1, -1}, {0, -1, 1},
+                                       {0, 1, -1},  {0, 1, 1},   {1, -1, 0}, {1, 0, -1}, {1, 0, 1},  {1, 1, 0}};
+__device__ const int8_t kFace[6][3] = {{-1, 0, 0}, {0, -1, 0}, {0, 0, -1}, {0, 0, 1}, {0, 1, 0}, {1, 0, 0}};
+constexpr uint32_t kThrough = 0x3Fu << 24;
+
+__device__ __forceinline__ int face_of(int dz, int dy, int dx) {
+    return dz < 0 ? 0 : (dy < 0 ? 1 : (dx < 0 ? 2 : (dx > 0 ? 3 : (dy > 0 ? 4 : 5))));
+}
+
+// Edge from local vertex a along the unit offset (dz, dy, dx): its id and key.
+__device__ __forceinline__ uint32_t edge_id_at(const Item& it, int64_t a, int dz, int dy, int dx) {
+    const int64_t lo = a + (dz < 0 ? -int64_t(it.H) * it.W : 0) + (dy < 0 ? -int64_t(it.W) : 0) + (dx < 0 ? -1 : 0);
+    return uint32_t(3 * (it.voff + lo) + (dx ? 0 : (dy ? 1 : 2)));
+}
+__device__ __forceinline__ uint64_t edge_key_at(const Item& it, int64_t a, int dz, int dy, int dx) {
+    const int64_t lo = a + (dz < 0 ? -int64_t(it.H) * it.W : 0) + (dy < 0 ? -int64_t(it.W) : 0) + (dx < 0 ? -1 : 0);
+    return edge_key(it, lo, dx ? 0 : (dy ? 1 : 2));
+}
+__device__ __forceinline__ int64_t step_of(const Item& it, int dz, int dy, int dx) {
+    return dz * int64_t(it.H) * it.W + dy * int64_t(it.W) + dx;
+}
+
+// The two unit offsets of square k and its far edge j: (start vertex offset, direction).
+__device__ __forceinline__ void far_edge(int k, int j, int& sz, int& sy, int& sx, int& dz, int& dy, int& dx) {
+    const int o[3] = {kSqA[k][0], kSqA[k][1], kSqA[k][2]};
+    const int i1 = o[0] ? 0 : 1, i2 = o[2] ? 2 : 1;  // the two nonzero components
+    int u1[3] = {0, 0, 0}, u2[3] = {0, 0, 0};
+    u1[i1] = o[i1];
+    u2[i2] = o[i2];
+    const int* st = j == 0 ? u1 : u2;
+    const int* dr = j == 0 ? u2 : u1;
+    sz = st[0];
+    sy = st[1];
+    sx = st[2];
+    dz = dr[0];
+    dy = dr[1];
+    dx = dr[2];
+}
+
+// Keys of the edges of a star column (mask over the slots of L(m)), descending.
+__device__ uint32_t decode(const Item& it, int64_t m, uint32_t mask, uint64_t* keys) {
+    uint32_t n = 0;
+    for (int f = 5; f >= 0; --f)
+        if ((mask >> (24 + f)) & 1u) keys[n++] = edge_key_at(it, m, kFace[f][0], kFace[f][1], kFace[f][2]);
+    const uint32_t n0 = n;
+    for (int sl = 0; sl < 24; ++sl) {
+        if (!((mask >> sl) & 1u)) continue;
+        int sz, sy, sx, dz, dy, dx;
+        far_edge(sl >> 1, sl & 1, sz, sy, sx, dz, dy, dx);
+        const uint64_t k = edge_key_at(it, m + step_of(it, sz, sy, sx), dz, dy, dx);
+        uint32_t j = n++;
+        while (j > n0 && keys[j - 1] < k) {
+            keys[j] = keys[j - 1];
+            --j;
+        }
+        keys[j] = k;
+    }
+    return n;
+}
+
+// The column of square id q: its key, the item, and its star vertex m (local).
+__device__ __forceinline__ uint64_t column_key(const ItemTable& tab, uint32_t q, const Item*& itp, int64_t& m) {
+    const Item& it = tab.it[item_of_vertex(tab, q / 3u)];
+    itp = &it;
+    const uint64_t k = square_key(it, int64_t(q / 3u) - it.voff, int(q % 3u));
+    m = int64_t(key_vertex(k)) - it.voff;
+    return k;
+}
+
+// Pool offset of column q's entries (its current region), or ~0 while the
+// column is still its star mask.
+__device__ __forceinline__ uint64_t column_at(const H1Bufs& b, uint32_t q) {
+    const uint64_t o = __ldcg(b.coff + q);
+    if (o == ~0ull) return o;
+    const uint32_t c = __ldcg(b.ccap + q);
+    return o + ((c >> 31) ? uint64_t(c & 0x7FFFFFFFu) : 0ull);
+}
+
+__device__ __forceinline__ uint64_t column_low(const H1Bufs& b, const Item& it, int64_t m, uint32_t q) {
+    const uint64_t o = column_at(b, q);
+    if (o != ~0ull) return __ldcg(b.pool + o);
+    uint64_t keys[30];
+    decode(it, m, __ldcg(b.cmask + q), keys);
+    return keys[0];
+}
+
+// ---- every lower star: its columns (squares not paired in H2) reduced
+// among themselves, and the check counts
+__global__ void __launch_bounds__(kHT) k_h1_local(const __grid_constant__ ItemTable tab, H1Bufs b, int64_t v0,
+                                                  int64_t v1) {
+    uint32_t ne = 0, pe = 0, pq = 0, nm = 0;
+    const unsigned lane = lane_id();
     for (int64_t base = v0 + int64_t(blockIdx.x) * kHT; base < v1; base += int64_t(gridDim.x) * kHT) {
         const int64_t g = base + threadIdx.x;
         const bool live = g < v1;
-        const Item& it = tab.it[item_of_vertex(tab, uint32_t(live ? g : v0))];
-        const int64_t v = g - it.voff;
-        const int x = int(v % it.W), y = int((v / it.W) % it.H), z = int(v / (int64_t(it.W) * it.H));
-        const bool room[3] = {x < it.W - 1, y < it.H - 1, z < it.D - 1};
-        for (int a = 0; a < 3; ++a) {
-            const uint32_t id = uint32_t(3 * g + a);
-            if (live && room[a]) {
-                if (get_bit(b.neg_e, id)) ++ne;
-                else ++pe;
-            }
-            bool want = false;
-            uint64_t key = 0;
-            if (live && room[a == 0 ? 1 : 0] && room[a == 2 ? 1 : 2]) {
-                if (get_bit(b.pos_q, id)) {
-                    ++pq;
-                } else {
-                    want = true;
-                    key = square_key(it, v, a);
+        uint32_t nonlocal[12];
+        uint32_t nn = 0;
+        if (live) {
+            const Item& it = tab.it[item_of_vertex(tab, uint32_t(g))];
+            const int64_t W = it.W, HW = int64_t(it.H) * it.W;
+            const int64_t m = g - it.voff;
+            const int x = int(m % W), y = int((m / W) % it.H), z = int(m / HW);
+            const bool room[3] = {x < it.W - 1, y < it.H - 1, z < it.D - 1};
+            for (int a = 0; a < 3; ++a) {  // cells whose lowest corner is m
+                const uint32_t id = uint32_t(3 * g + a);
+                if (room[a]) {
+                    if (get_bit(b.neg_e, id)) ++ne;
+                    else ++pe;
                 }
+                if (room[a == 0 ? 1 : 0] && room[a == 2 ? 1 : 2] && get_bit(b.pos_q, id)) ++pq;
             }
-            const uint32_t pos = warp_append(&b.ctl->m, want);
-            if (want && pos < b.mcap) b.ckeys[pos] = key;
+            const uint64_t km = vkey(it.img, m);
+            uint32_t low = 0;
+            for (int n = 0; n < 27; ++n) {
+                const int dz = n / 9 - 1, dy = (n / 3) % 3 - 1, dx = n % 3 - 1;
+                const int nz = z + dz, ny = y + dy, nx = x + dx;
+                if (n == 13 || nz < 0 || nz >= it.D || ny < 0 || ny >= it.H || nx < 0 || nx >= it.W) continue;
+                if (vkey(it.img, m + dz * HW + dy * W + dx) < km) low |= 1u << n;
+            }
+            // the edges through m that are rows: lower neighbour, not merging in H0
+            uint32_t rows = 0;
+            for (int f = 0; f < 6; ++f)
+                if (((low >> n3(kFace[f][0], kFace[f][1], kFace[f][2])) & 1u) &&
+                    !get_bit(b.neg_e, edge_id_at(it, m, kFace[f][0], kFace[f][1], kFace[f][2])))
+                    rows |= 1u << (24 + f);
+            uint32_t colmask[12];
+            int8_t owner[6] = {-1, -1, -1, -1, -1, -1};
+            const uint32_t ordm = uint32_t(km >> 32);
+            for (int k = 0; k < 12; ++k) {
+                colmask[k] = 0;
+                const int oz = kSqA[k][0], oy = kSqA[k][1], ox = kSqA[k][2];
+                const bool in_star = ((low >> n3(oz, oy, ox)) & 1u) && (oz == 0 || ((low >> n3(oz, 0, 0)) & 1u)) &&
+                                     (oy == 0 || ((low >> n3(0, oy, 0)) & 1u)) && (ox == 0 || ((low >> n3(0, 0, ox)) & 1u));
+                if (!in_star) continue;
+                const int a = oz == 0 ? 2 : (oy == 0 ? 1 : 0);
+                const int64_t lo = m + (oz < 0 ? -HW : 0) + (oy < 0 ? -W : 0) + (ox < 0 ? -1 : 0);
+                const uint32_t q = uint32_t(3 * (it.voff + lo) + a);
+                if (get_bit(b.pos_q, q)) continue;  // paired in H2: its column reduces to zero
+                ++nm;
+                // its four edges, the rows among them
+                uint32_t mask = 0;
+                for (int j = 0; j < 2; ++j) {
+                    int sz, sy, sx, dz, dy, dx;
+                    far_edge(k, j, sz, sy, sx, dz, dy, dx);
+                    mask |= (1u << (24 + face_of(sz, sy, sx))) & rows;  // the edge from m to the start
+                    if (!get_bit(b.neg_e, edge_id_at(it, m + step_of(it, sz, sy, sx), dz, dy, dx))) mask |= 1u << (2 * k + j);
+                }
+                // the sequential reduction inside the star: the owner of a row
+                // through m is a column of this star, already final
+                while (mask & kThrough) {
+                    const int f = 31 - __clz(mask) - 24;
+                    if (owner[f] < 0) {
+                        owner[f] = int8_t(k);
+                        b.pivot[edge_id_at(it, m, kFace[f][0], kFace[f][1], kFace[f][2])] =
+                            make_key(ordm, uint64_t(it.voff + m), uint32_t(n3(oz, oy, ox)));
+                        break;
+                    }
+                    mask ^= colmask[owner[f]];
+                }
+                colmask[k] = mask;
+                b.cmask[q] = mask;
+                b.coff[q] = ~0ull;
+                if (!(mask & kThrough)) nonlocal[nn++] = q;  // (mask 0 only with inconsistent marks: flagged by the counts)
+            }
         }
+        // the columns that leave their star, appended warp by warp
+        uint32_t incl = nn;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+            if (lane >= unsigned(o)) incl += t;
+        }
+        uint32_t at = 0;
+        if (lane == 31 && incl) at = atomicAdd(&b.ctl->nl, incl);
+        at = __shfl_sync(0xFFFFFFFFu, at, 31) + incl - nn;
+        for (uint32_t i = 0; i < nn; ++i)
+            if (at + i < b.mcap) b.list0[at + i] = nonlocal[i];
     }
     ne = __reduce_add_sync(0xFFFFFFFFu, ne);
     pe = __reduce_add_sync(0xFFFFFFFFu, pe);
     pq = __reduce_add_sync(0xFFFFFFFFu, pq);
-    if (lane_id() == 0) {
+    nm = __reduce_add_sync(0xFFFFFFFFu, nm);
+    if (lane == 0) {
         if (ne) atomicAdd(&b.ctl->neg_e, ne);
         if (pe) atomicAdd(&b.ctl->pos_e, pe);
         if (pq) atomicAdd(&b.ctl->pos_q, pq);
-    }
-}
-
-// ---- column c (rank c of the sorted keys): the square's unmarked edges,
-// descending; 4 pool entries per column
-__global__ void __launch_bounds__(kHT) k_h1_build(const __grid_constant__ ItemTable tab, H1Bufs b, Counters* ctr) {
-    const H1Ctl* ctl = b.ctl;
-    if (ld_acquire_u32(&ctr->status) & kStSkip) return;
-    if (blockIdx.x == 0 && threadIdx.x == 0 &&
-        (ctl->m != b.mcap || ctl->pos_e != b.mcap || ctl->neg_e != b.exp_neg_e || ctl->pos_q != b.exp_pos_q))
-        set_status(ctr, kStInternal);
-    const uint32_t M = min(ctl->m, b.mcap);
-    for (uint32_t c = blockIdx.x * kHT + threadIdx.x; c < M; c += gridDim.x * kHT) {
-        const uint64_t key = b.ckeys[c];
-        const Item& it = tab.it[item_of_vertex(tab, key_vertex(key))];
-        const uint32_t sid = cell_id3(it, key, true);
-        const int a = int(sid % 3u);
-        const int64_t L = int64_t(sid / 3u) - it.voff;  // lowest corner (local)
-        const int p = a == 0 ? 1 : 0, q = a == 2 ? 1 : 2;
-        const int64_t cu[4] = {L, L, L + axis_step(it, q), L + axis_step(it, p)};
-        const int ax[4] = {p, q, p, q};
-        uint64_t e[4];
-        uint32_t n = 0;
-        for (int k = 0; k < 4; ++k) {
-            if (get_bit(b.neg_e, uint32_t(3 * (it.voff + cu[k]) + ax[k]))) continue;
-            uint64_t ek = edge_key(it, cu[k], ax[k]);
-            uint32_t j = n++;
-            while (j > 0 && e[j - 1] < ek) {  // insertion, descending
-                e[j] = e[j - 1];
-                --j;
-            }
-            e[j] = ek;
-        }
-        for (uint32_t k = 0; k < n; ++k) b.pool[4ull * c + k] = e[k];
-        b.off[c] = 4ull * c;
-        b.len[c] = n;
-        if (n == 0) set_status(ctr, kStInternal);  // a column of a square not paired in H2 cannot vanish
+        if (nm) atomicAdd(&b.ctl->m, nm);
     }
 }
 
@@ -284,53 +407,83 @@ struct ReduceArgs {
     Counters* ctr;
 };
 
-// Column c lost its row to an older column: add that column (F2: the
-// symmetric difference; the common lowest entry cancels).
-__device__ void add_winner(const ReduceArgs& a, uint32_t c, uint32_t r) {
+// Column q lost its row to an older column: add that column (F2: the
+// symmetric difference; the common lowest entry cancels).  Columns that no
+// addition has reached yet are read from their star masks.  A column that
+// has been added to owns two pool regions and is rewritten into the one it
+// does not occupy; when the result does not fit, it moves to a fresh pair of
+// twice the size, so the pool holds a few times each column's largest size
+// rather than every intermediate result.
+__device__ void add_winner(const ReduceArgs& a, uint32_t q, uint32_t r) {
     const H1Bufs& b = a.b;
-    const uint64_t oc = __ldcg(b.off + c);
-    const uint32_t lc = __ldcg(b.len + c);
-    const uint64_t low = __ldcg(b.pool + oc);
-    const uint32_t p = __ldcg(b.pivot + edge_id(a.tab, low));
-    if (p >= c) {  // only after an earlier error
+    const Item* itc;
+    int64_t mc;
+    const uint64_t kc = column_key(a.tab, q, itc, mc);
+    uint64_t lc_keys[30], lp_keys[30];
+    const uint64_t oc = column_at(b, q);
+    uint32_t lc;
+    if (oc != ~0ull) lc = __ldcg(b.clen + q);
+    else lc = decode(*itc, mc, __ldcg(b.cmask + q), lc_keys);
+    const uint64_t low = oc != ~0ull ? __ldcg(b.pool + oc) : lc_keys[0];
+    const uint64_t kp = __ldcg(b.pivot + edge_id(a.tab, low));
+    if (lc == 0u || kp >= kc) {  // only after an earlier error
         set_status(a.ctr, kStInternal);
         atomicOr(&b.ctl->stop[r & 1u], 1u);
         return;
     }
-    const uint64_t op = __ldcg(b.off + p);
-    const uint32_t lp = __ldcg(b.len + p);
+    const Item& itp = a.tab.it[item_of_vertex(a.tab, key_vertex(kp))];
+    const uint32_t p = cell_id3(itp, kp, true);
+    const uint64_t op = column_at(b, p);
+    uint32_t lp;
+    if (op != ~0ull) lp = __ldcg(b.clen + p);
+    else lp = decode(itp, int64_t(key_vertex(kp)) - itp.voff, __ldcg(b.cmask + p), lp_keys);
     const uint64_t need = uint64_t(lc) + lp - 2u;
-    const uint64_t base = 4ull * b.mcap;
-    uint64_t at = 0;
-    if (need) {
-        at = atomicAdd(&b.ctl->grown, (unsigned long long)need);
-        if (base + at + need > b.pool_cap) {
+    if (need == 0u || need > 0x1FFFFFFFull) {  // empty: only after an earlier error; 2^29 entries: beyond
+        set_status(a.ctr, need ? kStCapacity : kStInternal);  // any volume this library takes
+        atomicOr(&b.ctl->stop[r & 1u], 1u);
+        return;
+    }
+    uint64_t base = __ldcg(b.coff + q);
+    uint32_t cap = base != ~0ull ? (__ldcg(b.ccap + q) & 0x7FFFFFFFu) : 0u;
+    const uint32_t side = base != ~0ull ? ((__ldcg(b.ccap + q) >> 31) ^ 1u) : 0u;  // the free region
+    uint32_t into = side;
+    if (need > cap) {  // a fresh pair of regions, twice the size needed
+        cap = 4u;
+        while (cap < need) cap <<= 1;
+        cap <<= 1;
+        base = atomicAdd(&b.ctl->grown, (unsigned long long)(2ull * cap));
+        if (base + 2ull * cap > b.pool_cap) {
             set_status(a.ctr, kStCapacity);
             atomicOr(&b.ctl->stop[r & 1u], 1u);
             return;
         }
+        into = 0u;
     }
-    uint64_t* out = b.pool + base + at;
+    const uint64_t at = base + (into ? uint64_t(cap) : 0ull);
+    auto gc = [&](uint32_t i) { return oc != ~0ull ? __ldcg(b.pool + oc + i) : lc_keys[i]; };
+    auto gp = [&](uint32_t i) { return op != ~0ull ? __ldcg(b.pool + op + i) : lp_keys[i]; };
+    uint64_t* out = b.pool + at;
     uint32_t i = 1, j = 1, k = 0;
-    uint64_t x = i < lc ? __ldcg(b.pool + oc + i) : 0, y = j < lp ? __ldcg(b.pool + op + j) : 0;
+    uint64_t x = i < lc ? gc(i) : 0, y = j < lp ? gp(j) : 0;
     while (i < lc || j < lp) {
         if (j >= lp || (i < lc && x > y)) {
             out[k++] = x;
             ++i;
-            x = i < lc ? __ldcg(b.pool + oc + i) : 0;
+            x = i < lc ? gc(i) : 0;
         } else if (i >= lc || y > x) {
             out[k++] = y;
             ++j;
-            y = j < lp ? __ldcg(b.pool + op + j) : 0;
+            y = j < lp ? gp(j) : 0;
         } else {
             ++i;
             ++j;
-            x = i < lc ? __ldcg(b.pool + oc + i) : 0;
-            y = j < lp ? __ldcg(b.pool + op + j) : 0;
+            x = i < lc ? gc(i) : 0;
+            y = j < lp ? gp(j) : 0;
         }
     }
-    __stcg(b.off + c, base + at);
-    __stcg(b.len + c, k);
+    __stcg(b.coff + q, base);
+    __stcg(b.ccap + q, cap | (into << 31));
+    __stcg(b.clen + q, k);
     if (k == 0) {
         set_status(a.ctr, kStInternal);
         atomicOr(&b.ctl->stop[r & 1u], 1u);
@@ -343,24 +496,32 @@ __global__ void __launch_bounds__(kRT) k_h1_reduce(const __grid_constant__ Reduc
     H1Ctl* ctl = b.ctl;
     if (ld_acquire_u32(&ctr->status) & kStSkip) return;  // set before the launch: every CTA returns
     const uint32_t nblocks = gridDim.x, gstride = nblocks * kRT, gtid = blockIdx.x * kRT + threadIdx.x;
+    if (gtid == 0 && (ctl->m != b.mcap || ctl->pos_e != b.mcap || ctl->neg_e != b.exp_neg_e ||
+                      ctl->pos_q != b.exp_pos_q || ctl->nl > b.mcap))
+        set_status(ctr, kStInternal);
     __shared__ uint32_t sh_n, sh_stop;
     uint32_t epoch = 0;
-    uint32_t nchg = min(ctl->m, b.mcap);  // round 0: every column, by rank
+    uint32_t nchg = min(ctl->nl, b.mcap);  // round 0: every column that left its star
     for (uint32_t r = 0;; ++r) {
         uint32_t* work = b.list[r & 1u];
-        const uint32_t* chg = b.list[(r & 1u) ^ 1u];
+        const uint32_t* chg = r == 0 ? b.list0 : b.list[(r & 1u) ^ 1u];
         uint32_t* wcnt = &ctl->cnt[r % 3u];
         // ---- bids: the oldest column of each row keeps it
         for (uint32_t i0 = blockIdx.x * kRT; i0 < nchg; i0 += gstride) {
             const uint32_t i = i0 + threadIdx.x;
             uint32_t lose = kNone;
             if (i < nchg) {
-                const uint32_t c = r == 0 ? i : __ldcg(chg + i);
-                if (__ldcg(b.len + c) != 0u) {
-                    const uint64_t low = __ldcg(b.pool + __ldcg(b.off + c));
-                    const uint32_t old = atomicMin(b.pivot + edge_id(a.tab, low), c);
-                    if (old < c) lose = c;            // an older column holds the row
-                    else if (old != kNone) lose = old;  // c displaces a younger holder
+                const uint32_t q = __ldcg(chg + i);
+                const Item* it;
+                int64_t m;
+                const uint64_t kq = column_key(a.tab, q, it, m);
+                const uint64_t low = column_low(b, *it, m, q);
+                const unsigned long long old =
+                    atomicMin(reinterpret_cast<unsigned long long*>(b.pivot + edge_id(a.tab, low)), kq);
+                if (old < kq) {
+                    lose = q;  // an older column holds the row
+                } else if (old != ~0ull) {  // q displaces a younger holder
+                    lose = cell_id3(a.tab.it[item_of_vertex(a.tab, key_vertex(old))], old, true);
                 }
             }
             const uint32_t pos = warp_append(wcnt, lose != kNone);
@@ -394,28 +555,32 @@ __global__ void __launch_bounds__(kRT) k_h1_reduce(const __grid_constant__ Reduc
     }
 }
 
-// ---- the pairs (lowest entry, square) with nonzero persistence
+// ---- the pairs (lowest entry, square) with nonzero persistence: only the
+// columns that left their star (inside a star both cells enter with m)
 __global__ void __launch_bounds__(kHT) k_h1_emit(const __grid_constant__ ItemTable tab, H1Bufs b, Counters* ctr,
                                                  cp_pair* pairs, uint32_t cap) {
     if (ld_acquire_u32(&ctr->status) & kStSkip) return;
-    const uint32_t M = min(b.ctl->m, b.mcap);
+    const uint32_t M = min(b.ctl->nl, b.mcap);
     for (uint32_t i0 = blockIdx.x * kHT; i0 < M; i0 += gridDim.x * kHT) {
-        const uint32_t c = i0 + threadIdx.x;
+        const uint32_t i = i0 + threadIdx.x;
         bool emit = false;
         cp_pair pr;
-        if (c < M && b.len[c] != 0u) {
-            const uint64_t ek = b.pool[b.off[c]], sk = b.ckeys[c];
+        if (i < M) {
+            const uint32_t q = b.list0[i];
+            const Item* it;
+            int64_t m;
+            const uint64_t sk = column_key(tab, q, it, m);
+            const uint64_t ek = column_low(b, *it, m, q);
             const float fb = ord_float(uint32_t(ek >> 32)), fd = ord_float(uint32_t(sk >> 32));
             if (fb != fd) {  // zero persistence: omitted (Sec. 2.3)
-                const Item& it = tab.it[item_of_vertex(tab, key_vertex(sk))];
                 pr.birth = fb;
                 pr.death = fd;
-                pr.birth_cell = cell_index(it, ek);
-                pr.death_cell = cell_index(it, sk);
-                pr.birth_pixel = int32_t(int64_t(key_vertex(ek)) - it.voff);
-                pr.death_pixel = int32_t(int64_t(key_vertex(sk)) - it.voff);
+                pr.birth_cell = cell_index(*it, ek);
+                pr.death_cell = cell_index(*it, sk);
+                pr.birth_pixel = int32_t(int64_t(key_vertex(ek)) - it->voff);
+                pr.death_pixel = int32_t(m);
                 pr.dim = 1;
-                pr.item = it.user;
+                pr.item = it->user;
                 emit = true;
             }
         }
@@ -448,26 +613,11 @@ cudaError_t launch_h1(const ItemTable& tab, const H1Bufs& b, Counters* ctr, cp_p
     });
     if (reduce_blocks <= 0) return cudaErrorLaunchOutOfResources;
     cudaError_t e = cudaMemsetAsync(b.ctl, 0, sizeof(H1Ctl), s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(b.pivot, 0xFF, sizeof(uint32_t) * size_t(3 * v1), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b.pivot, 0xFF, sizeof(uint64_t) * size_t(3 * v1), s);
     if (e != cudaSuccess) return e;
     k_h1_direct<<<grid_of(v1 - v0), kHT, 0, s>>>(tab, b, v0, v1);
-    k_h1_cols<<<grid_of(v1 - v0), kHT, 0, s>>>(tab, b, v0, v1);
+    k_h1_local<<<grid_of(v1 - v0), kHT, 0, s>>>(tab, b, v0, v1);
     note_launches(2);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    SortBufs sb;
-    sb.keys = b.ckeys;
-    sb.keys_alt = b.ckeys_alt;
-    sb.vals = nullptr;
-    sb.vals_alt = nullptr;
-    sb.d_count = &b.ctl->m;
-    sb.cap = b.mcap;
-    sb.hist = b.hist;
-    sb.status = b.status;
-    sb.tile_ctr = ctr->sort_tile + 24;
-    sb.ctr = ctr;
-    if ((e = sort_keys(sb, 0, 8, 25, s)) != cudaSuccess) return e;
-    k_h1_build<<<grid_of(b.mcap), kHT, 0, s>>>(tab, b, ctr);
-    note_launches(1);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     ReduceArgs ra;
     ra.tab = tab;

@@ -123,39 +123,42 @@ cudaError_t launch_uf(const ItemTable& tab, const UfParams* p, int nprob, cudaSt
 
 // ---- H1 of volumes (cp_h1.cu): column reduction of the square-edge boundary
 // matrix restricted to the squares that do not create 2-cycles and the edges
-// that do not merge components.
+// that do not merge components; first inside each lower star, then across
+// stars.
 struct H1Ctl {
-    uint32_t m;                   // columns (squares) appended
+    uint32_t m;                   // columns (squares not paired in H2)
+    uint32_t nl;                  // columns whose lowest entry leaves their lower star
     uint32_t cnt[3];              // work-list counters of the reduction rounds (rotating)
     uint32_t neg_e, pos_q, pos_e; // checks: marked edges, marked squares, unmarked edges
     uint32_t rounds;              // reduction rounds run
     uint32_t stop[2];             // a round's merges hit an error (read one round later, by parity)
+    uint32_t pad;
     unsigned long long grown;     // pool entries taken by merged columns
-    unsigned long long pad[3];
+    unsigned long long pad2[2];
 };
 struct H1Bufs {
     uint32_t* neg_e;         // bitmap over edge ids (cell_id3): edge kills an H0 class
     uint32_t* pos_q;         // bitmap over square ids: square creates a 2-cycle
     size_t map_words;        // words per bitmap
     H1Ctl* ctl;
-    uint64_t* ckeys;         // column keys (unmarked squares), sorted ascending
-    uint64_t* ckeys_alt;
-    uint32_t* hist;
-    uint64_t* status;
-    uint64_t* off;           // per column: offset of its entries in pool
-    uint32_t* len;           // per column: entry count
+    uint32_t* cmask;         // per square id: its column inside its lower star (30 edge slots), 0: no column
+    uint64_t* coff;          // per square id: pool offset of its column once it has been added to, or ~0
+    uint32_t* clen;          // per square id: entries of that pool column
+    uint32_t* ccap;          // per square id: capacity of the two pool regions at coff (each), and in
+                             // bit 31 which of the two holds the column
+    uint32_t* list0;         // the columns whose lowest entry leaves their star (square ids)
     uint32_t* list[2];       // columns changed in a round (ping-pong)
-    uint32_t* pivot;         // per edge id: the oldest column whose lowest entry it is
-    uint64_t* pool;          // column entries (edge keys, descending); columns 4 apart, then merged ones
+    uint64_t* pivot;         // per edge id: key of the oldest column whose lowest entry it is, or ~0
+    uint64_t* pool;          // explicit columns (edge keys, descending)
     uint64_t pool_cap;
     uint32_t mcap;           // columns expected: sum over 3D items of E - N + 1
     uint32_t exp_neg_e;      // sum over 3D items of N - 1
     uint32_t exp_pos_q;      // sum over 3D items of (D-1)(H-1)(W-1)
 };
 // After the union-finds have marked their committed survivors in the two
-// bitmaps (zeroed before them): marks the direct pairs' cells, lists and
-// sorts the columns, builds and reduces them, and appends the H1 pairs (zero
-// persistence omitted) to pairs.
+// bitmaps (zeroed before them): marks what the lower stars settle, reduces
+// every lower star's columns, reduces the columns that leave their star in
+// rounds, and appends the H1 pairs (zero persistence omitted) to pairs.
 cudaError_t launch_h1(const ItemTable& tab, const H1Bufs& b, Counters* ctr, cp_pair* pairs, uint32_t pair_cap,
                       cudaStream_t s);
 

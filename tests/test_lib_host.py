@@ -184,8 +184,9 @@ def test_full_workspace_sizes(lib):
         D, H, W = dims
         cols = D * H * (W - 1) + D * (H - 1) * W + (D - 1) * H * W - D * H * W + 1
         f, p = full(dims), plain(dims)
-        # at least: two pool regions of 4 entries per column, keys, offsets, pivots
-        assert f >= p + 8 * 8 * cols + 16 * cols + 12 * D * H * W, (dims, f, p)
+        # at least: per edge or square id a mask, an offset, a length and a
+        # pivot; three column lists; the default pool
+        assert f >= p + 3 * D * H * W * 24 + 12 * cols + 8 * (4 * cols + 2**20), (dims, f, p)
         assert full(dims, 10**6) - full(dims, 1) >= 8 * (10**6 - 1) - 256
     assert full((17, 19)) == plain((17, 19))
     assert full((1, 5, 5)) == 0 and full((4, 0, 5)) == 0
