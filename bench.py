@@ -751,9 +751,10 @@ def run_tfilt(args):
 
 
 def run_full(args):
-    """The whole diagram of the benchmark volume (512^3 blurred, sigma 3): H0,
-    H1 and H2 pairs, forward + total-persistence loss backward, device-resident
-    input; the oracle's full diagram on a crop as the CPU line."""
+    """The whole diagram of a volume (128^3 blurred, sigma 2, unless --side is
+    given): H0, H1 and H2 pairs, forward + total-persistence loss backward,
+    device-resident input; the oracle's full diagram on a crop as the CPU
+    line."""
     import torch
 
     ws, rank, local = _dist()
@@ -765,8 +766,11 @@ def run_full(args):
     from paper_2606_04801_gb300 import _lib
 
     lib = _lib.load()
-    side = SIDE
-    vol = _volume(rank)
+    # 128^3 blurred (sigma 2) by default: the cross-star reduction of a smooth
+    # field's long-lived loops runs thousands of rounds, seconds at 128^3
+    side = SIDE if "--side" in sys.argv else 128
+    sigma = 2.0 if side == 128 else SIGMA
+    vol = workloads.blurred((side,) * 3, sigma, 1) if side == 128 else _volume(rank)
     N = vol.size
     x = torch.from_numpy(vol).to(dev)
     from paper_2606_04801_gb300 import autotune
@@ -881,7 +885,7 @@ def run_full(args):
             "value": value, "unit": "Mvoxels/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"3D {side}^3 float32 blurred noise (sigma 3 vox), whole diagram (H0, H1, H2), "
+            "config": {"workload": f"3D {side}^3 float32 blurred noise (sigma {sigma:g} vox), whole diagram (H0, H1, H2), "
                                    "fwd + total-persistence loss bwd", "status": st["rc"], "pairs": st["pairs"],
                        "h1_columns": info[0], "h1_columns_leaving_their_star": info[9], "h1_rounds": info[1],
                        "h1_pool_entries_used": info[2], "h1_pool_entries": info[3],
