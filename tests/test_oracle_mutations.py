@@ -85,3 +85,60 @@ def test_pins_catch_mutant(name, tmp_path):
         timeout=600,
     )
     assert r.returncode != 0, f"mutant {name} survived the pins:\n{r.stdout[-2000:]}"
+
+
+# mistakes in the H1 reduction of volumes, caught by test_oracle_h1_pins.py
+H1_MUTANTS = {
+    # the pair takes the column's first row instead of its lowest (the youngest)
+    "h1_birth_not_lowest": (
+        "const rkey *e = &edges[c[nc - 1]];",
+        "const rkey *e = &edges[c[0]];",
+    ),
+    # no column additions: every square keeps its boundary
+    "h1_not_reduced": (
+        "while (nc > 0 && owner[c[nc - 1]] >= 0) {",
+        "while (0 && nc > 0 && owner[c[nc - 1]] >= 0) {",
+    ),
+    # squares processed from the youngest down
+    "h1_columns_reversed": (
+        "for (int64_t j = 0; j < nsq; ++j) {",
+        "for (int64_t j = nsq - 1; j >= 0; --j) {",
+    ),
+    # a square's boundary with only the edges on its +1 sides
+    "h1_half_boundary": (
+        "c[nc++] = erank[(q[0] * g->GH + q[1]) * g->GW + q[2]];",
+        "if (s > 0) c[nc++] = erank[(q[0] * g->GH + q[1]) * g->GW + q[2]];",
+    ),
+    # birth and death values exchanged
+    "h1_values_swapped": (
+        "emit(out, cap, n, keep_zero, e->fm, sq[j].fm, e->idx, sq[j].idx, e->m, sq[j].m, 1);",
+        "emit(out, cap, n, keep_zero, sq[j].fm, e->fm, e->idx, sq[j].idx, e->m, sq[j].m, 1);",
+    ),
+    # the death pixel taken from the birth edge
+    "h1_death_pixel": (
+        "emit(out, cap, n, keep_zero, e->fm, sq[j].fm, e->idx, sq[j].idx, e->m, sq[j].m, 1);",
+        "emit(out, cap, n, keep_zero, e->fm, sq[j].fm, e->idx, sq[j].idx, e->m, e->m, 1);",
+    ),
+}
+
+
+@pytest.mark.parametrize("name", sorted(H1_MUTANTS))
+def test_h1_pins_catch_mutant(name, tmp_path):
+    old, new = H1_MUTANTS[name]
+    src = open(os.path.join(ROOT, "oracle", "cp_oracle.c")).read()
+    assert src.count(old) == 1, f"mutant {name} no longer applies to the oracle source"
+    d = tmp_path / "repo"
+    (d / "oracle").mkdir(parents=True)
+    (d / "oracle" / "cp_oracle.c").write_text(src.replace(old, new))
+    shutil.copy(os.path.join(ROOT, "oracle", "__init__.py"), d / "oracle" / "__init__.py")
+    shutil.copytree(os.path.join(ROOT, "tests"), d / "tests", ignore=shutil.ignore_patterns("__pycache__"))
+    shutil.copy(os.path.join(ROOT, "workloads.py"), d / "workloads.py")
+    r = subprocess.run(
+        [sys.executable, "-m", "pytest", str(d / "tests" / "test_oracle_h1_pins.py"), "-x", "-q", "-p",
+         "no:cacheprovider"],
+        capture_output=True,
+        text=True,
+        cwd=str(d),
+        timeout=600,
+    )
+    assert r.returncode != 0, f"mutant {name} survived the H1 pins:\n{r.stdout[-2000:]}"
