@@ -33,8 +33,9 @@
 // thread per vertex does it on 32-bit masks over the 30 edges of the star
 // (6 through m, 24 that miss it).  A column that ends holding an edge
 // through m is final: its pair has zero persistence, and the column is the
-// pivot of that edge.  The others (their lowest entry left the star: exactly
-// the pairs of nonzero persistence) are reduced across stars in rounds
+// pivot of that edge.  The others (their lowest entry left the star: every
+// pair of nonzero persistence, and with distinct values only those) are
+// reduced across stars in rounds
 // inside one cooperative kernel: every column whose lowest entry changed
 // bids for that row with an atomic minimum of its key (the filtration order)
 // in a per-edge pivot word; every column that loses a bid, or is displaced
