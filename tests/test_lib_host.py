@@ -196,6 +196,35 @@ def test_full_workspace_sizes(lib):
     assert lib.cubical_persistence_full_batched_workspace_size(2, n, d, 0, 0) > lib.cubical_persistence_batched_workspace_size(2, n, d, 0)
 
 
+def test_full_entry_argument_errors(lib):
+    """The full-diagram entries reject bad arguments before touching a device."""
+    import ctypes
+
+    dims3 = (ctypes.c_int64 * 3)(3, 4, 5)
+    flat = (ctypes.c_int64 * 3)(1, 4, 5)
+    fake = ctypes.c_void_p(0x1000)  # never dereferenced: every call below fails its checks first
+    full = lib.cubical_persistence_full_3d
+    assert full(None, dims3, fake, 10, None, None, fake, 1 << 30, 0, 0, None) == -1  # no image
+    assert full(fake, dims3, fake, 10, None, None, None, 1 << 30, 0, 0, None) == -1  # no workspace
+    assert full(fake, flat, fake, 10, None, None, fake, 1 << 30, 0, 0, None) == -1  # an extent of 1
+    assert full(fake, dims3, fake, 10, None, None, fake, 1 << 30, 0, -5, None) == -1  # a negative pool
+    need = lib.cubical_persistence_full_workspace_size(3, dims3, 0, 0)
+    assert full(fake, dims3, fake, 10, None, None, fake, need - 1, 0, 0, None) == -1  # workspace too small
+    assert full(fake, dims3, None, 10, None, None, fake, need, 0, 0, None) == -1  # no output with capacity
+    nd = (ctypes.c_int32 * 1)(3)
+    ptrs = (ctypes.c_void_p * 1)(0x1000)
+    fb = lib.cubical_persistence_full_batched
+    assert fb(0, ptrs, nd, dims3, fake, 10, None, None, fake, 1 << 30, 0, 0, None) == -1
+    assert fb(1, None, nd, dims3, fake, 10, None, None, fake, 1 << 30, 0, 0, None) == -1
+    # the info entry: bad arguments, and a call without volumes has no H1 stage (nothing read)
+    info = (ctypes.c_int64 * 4)()
+    assert lib.cubical_persistence_full_info(None, 1, nd, dims3, 0, 0, info, 4, None) == -1
+    assert lib.cubical_persistence_full_info(fake, 1, nd, dims3, 0, 0, info, 3, None) == -1
+    nd2 = (ctypes.c_int32 * 1)(2)
+    assert lib.cubical_persistence_full_info(fake, 1, nd2, flat, 0, 0, info, 4, None) == 0
+    assert list(info) == [0, 0, 0, 0]
+
+
 def test_t_entry_argument_errors(lib):
     """The T-filtration entries reject bad arguments before touching a device."""
     import ctypes
