@@ -7,7 +7,9 @@ against things other than itself.
 - Betti numbers at every threshold: b1(t) = b0(t) + b2(t) - chi(t), with b0
   by face-connected labelling of {f <= t}, b2 by the components of the
   complement (Alexander duality) and chi counted from the cells of K_t;
-- pair-count identities and a hand-computed solid torus;
+- pair-count identities, a hand-computed solid torus, and the hand-derived
+  whole diagrams of tests/golden/h1_hand_cases.txt (rings, a notched ring, a
+  capped ring, a hollow cube);
 - metamorphic checks (an increasing map keeps the cells, a flip keeps the
   values).
 """
@@ -18,7 +20,7 @@ import pytest
 
 import oracle
 from brute_force import reduce_pairs
-from test_oracle_pins import _alive, _betti0, _betti_top
+from test_oracle_pins import _alive, _betti0, _betti_top, _build_case, _parse_cases
 
 
 def _cells_full(img):
@@ -142,3 +144,18 @@ def test_h1_metamorphic():
     for ax in range(3):
         assert _h1_values(oracle.persistence_full(np.flip(img, ax).copy())) == _h1_values(base)
     assert _h1_values(oracle.persistence_full(np.transpose(img, (2, 0, 1)).copy())) == _h1_values(base)
+
+
+H1_CASES = _parse_cases("h1_hand_cases.txt")
+
+
+@pytest.mark.parametrize("case", H1_CASES, ids=[c["name"] for c in H1_CASES])
+def test_h1_hand_case(case):
+    img = _build_case(case)
+    got = {}
+    for r in oracle.persistence_full(img):
+        k = (int(r["dim"]), float(r["birth"]), float(r["death"]))
+        got[k] = got.get(k, 0) + 1
+    assert got == {(d, b, e): n for d, b, e, n in case["expect"]}
+    if img.size <= 125:
+        _check_brute(img)

@@ -127,9 +127,9 @@ def test_pixels_and_values_follow_cells(shape):
 
 
 # ---------------------------------------------------------------- hand cases
-def _parse_cases():
+def _parse_cases(name="hand_cases.txt"):
     cases, cur = [], None
-    with open(os.path.join(GOLDEN, "hand_cases.txt")) as fh:
+    with open(os.path.join(GOLDEN, name)) as fh:
         for line in fh:
             line = line.split("#", 1)[0].strip()
             if not line:
