@@ -1,7 +1,7 @@
-// H1 of volumes: the middle dimension of a 3D image, by matrix reduction over
-// the cells that the H0 and H2 computations leave unpaired (Sec. 4.2 computes
-// H0 and the top dimension by union-find and names the dimension between
-// them as the one left to a reduction of the boundary matrix).
+// H1 of volumes: the middle dimension of a 3D image, by an F2 matrix
+// reduction whose rows are the edges not paired in H0 and whose columns are
+// the squares not paired in H2, with the zero-persistence pairs that one
+// lower star settles taken out first (Sec. 4.2, 3D steps 4-5).
 //
 // Over F2 the 1-dimensional pairs come from the column reduction (Sec. 2.1)
 // of the boundary matrix of the squares (columns) over the edges (rows), both
