@@ -227,10 +227,11 @@ int cubical_persistence_batched(int n_items, const float *const *h_images, const
  * The whole diagram of volumes: the pairs of cubical_persistence_3d /
  * _batched plus the H1 pairs of every 3D item (dim 1; zero persistence
  * omitted; birth cell an edge, death cell a square, pixels their largest
- * vertices).  Sec. 4.2 leaves the middle dimension of a volume to a matrix
- * reduction over the cells that H0 and H2 leave unpaired; here it is the F2
- * column reduction (Sec. 2.1) of the boundary matrix of the squares not
- * paired in H2 over the edges not paired in H0, in the refined order of
+ * vertices).  Sec. 4.2 (3D steps 4-5) computes the middle dimension of a
+ * volume by an F2 matrix reduction over the cells that H0 and H2 leave
+ * unpaired; here it is the column reduction (Sec. 2.1) of the boundary
+ * matrix of the squares not paired in H2 over the edges not paired in H0,
+ * in the refined order of
  * Sec. 2.3, on the device: first inside each lower star (a star's cells are
  * consecutive in that order), then, for the columns whose lowest entry
  * leaves their star, in parallel rounds.  2D items get their plain diagram.
