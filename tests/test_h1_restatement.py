@@ -16,6 +16,10 @@ small volumes, with the oracle's zero-persistence pairs as the truth:
    stays an edge through m pairs with that edge, as in the oracle; the
    columns whose lowest entry leaves the star include every pair of nonzero
    persistence, and are exactly those when the values are distinct.
+3. The rounds across stars (bids with the oldest key winning, every loser or
+   displaced holder adding its row's winner at once), in shuffled orders:
+   the final lowest entries are the oracle's pairs, zero persistence
+   included.
 """
 import numpy as np
 import pytest
@@ -189,3 +193,89 @@ def test_star_local_reduction(lib):
         assert nonzero <= left, (img.shape, sorted(nonzero - left))
         if len(np.unique(img)) == img.size:
             assert left == nonzero, (img.shape, len(left), len(nonzero))
+
+
+def _refined(v, cell):
+    """(f(m), m, doubled index) of a cell: the order inside one dimension."""
+    Z, Y, X = cell // (v.GH * v.GW), (cell // v.GW) % v.GH, cell % v.GW
+    best = None
+    for z in {Z // 2, (Z + 1) // 2}:
+        for y in {Y // 2, (Y + 1) // 2}:
+            for x in {X // 2, (X + 1) // 2}:
+                m = v.vid(z, y, x)
+                if best is None or v.key(m) > best:
+                    best = v.key(m)
+    return (best[0], best[1], cell)
+
+
+def test_cross_star_rounds_match_oracle(lib):
+    """The rounds of the device path, restated: columns that left their star
+    bid for their lowest row (the oldest key wins; star pivots hold theirs
+    from the start), every loser or displaced holder adds the winner of its
+    row, all at once, and bids again; processed in shuffled orders, the final
+    lowest entries are the oracle's pairs, zero persistence included."""
+    rng = np.random.default_rng(960)
+    for img in _volumes():
+        v = Vol(img)
+        _, neg_e, pos_q, death_to_birth, _ = _truth(img)
+        cols, pivot, left = {}, {}, []
+        for m in range(v.D * v.H * v.W):
+            rows = [v.lower(m, fc) and v.cell(m, fc) not in neg_e for fc in FACES]
+            owner = [None] * 6
+            for o in reversed(SQ_DESC):
+                sq = v.cell(m, o)
+                if not v.square_in_star(m, o) or sq in pos_q:
+                    continue
+                nz = [i for i in range(3) if o[i]]
+                u1, u2 = [0, 0, 0], [0, 0, 0]
+                u1[nz[0]] = o[nz[0]]
+                u2[nz[1]] = o[nz[1]]
+                col = set()
+                for st, dr in ((u1, u2), (u2, u1)):
+                    if rows[FACES.index(tuple(st))]:
+                        col.add(v.cell(m, tuple(st)))
+                    far = v.cell(m, tuple(2 * st[i] + dr[i] for i in range(3)))
+                    if far not in neg_e:
+                        col.add(far)
+                through = {v.cell(m, fc) for fc in FACES}
+                while col & through:
+                    low = max(col & through, key=lambda e: _refined(v, e))
+                    f = [v.cell(m, fc) for fc in FACES].index(low)
+                    if owner[f] is None:
+                        owner[f] = sq
+                        pivot[low] = sq  # a star pivot: final
+                        break
+                    col ^= cols[owner[f]]
+                cols[sq] = col
+                if not (col & through):
+                    left.append(sq)
+        key = {q: _refined(v, q) for q in cols}
+
+        def low(q):
+            return max(cols[q], key=lambda e: _refined(v, e))
+
+        chg = list(left)
+        for _ in range(100000):
+            rng.shuffle(chg)
+            work = []
+            for q in chg:
+                e = low(q)
+                old = pivot.get(e)
+                if old is None or key[q] < key[old]:
+                    pivot[e] = q
+                    if old is not None:
+                        work.append(old)
+                else:
+                    work.append(q)
+            if not work:
+                break
+            rng.shuffle(work)
+            snapshot = {q: set(cols[q]) for q in work}
+            for q in work:
+                p = pivot[low(q)]
+                assert key[p] < key[q] and p not in snapshot
+                cols[q] = snapshot[q] ^ cols[p]
+                assert cols[q], "a column of a square not paired in H2 cannot vanish"
+            chg = work
+        got = {q: low(q) for q in cols}
+        assert got == death_to_birth, img.shape
