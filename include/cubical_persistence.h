@@ -331,9 +331,10 @@ int cubical_persistence_loss_backward(const cp_pair *d_pairs, int64_t n_pairs, c
 /*
  * Backward scatter that allocates nothing (the paper has no counterpart: it
  * is a convenience of this library).  For callers that cannot allocate
- * device memory, such as code running while a stream is captured into a
- * CUDA graph, or code inside another framework's hooks without access to
- * its allocator, this computes exactly what cubical_persistence_backward
+ * device memory, such as code inside another framework's hooks without
+ * access to its allocator, or deployments whose device memory is reserved
+ * up front by another component, this computes exactly what
+ * cubical_persistence_backward
  * computes, but keeps its double-precision accumulators in a fixed array
  * inside the library's device image instead of a caller-provided workspace.
  *  - The array holds cubical_persistence_backward_noalloc_max_pixels()
@@ -342,7 +343,9 @@ int cubical_persistence_loss_backward(const cp_pair *d_pairs, int64_t n_pairs, c
  *    CP_ERR_CAPACITY without touching the GPU.
  *  - The first call on a device looks the array's device address up
  *    (cudaGetSymbolAddress, with that device current); make that first call
- *    before any stream capture on that device.
+ *    before any stream capture on that device.  The address is cached per
+ *    device ordinal: a cudaDeviceReset of that device after its first call
+ *    here is not supported.
  *  - Every call shares the one array: each call clears the part it uses
  *    before accumulating, so consecutive calls are independent, but calls
  *    whose work overlaps on the GPU (unordered streams) race on it.
@@ -409,12 +412,20 @@ int cubical_persistence_debug_wait_timeout(void *d_workspace, size_t ws_bytes, i
  *   CP_TUNE_ZCHUNK_3D    planes per 3D pruning task (4..4096, default 64)
  *   CP_TUNE_CTAS_PER_SM  3D pruning CTAs per SM (0 = as many as fit, default)
  *   CP_TUNE_ROWS_2D      rows per 2D pruning task (4 .. 4096; default 64)
+ *   CP_TUNE_H1_BUDGET_MS wall-clock budget in milliseconds of the cross-star
+ *                        reduction rounds of the _full calls (0 .. 3,600,000;
+ *                        default 30,000).  Those rounds run in one
+ *                        non-preemptible cooperative launch; once the budget
+ *                        is spent, every block leaves at the next round
+ *                        boundary and the call returns CP_ERR_TIMEOUT (no
+ *                        H1 pairs).  0 stops after the first round.
  * cp_set_tuning returns CP_OK or CP_ERR_ARG; cp_get_tuning the value or -1.
  * The autotuner in the Python package picks these per GPU and shape.
  */
 #define CP_TUNE_ZCHUNK_3D 1
 #define CP_TUNE_CTAS_PER_SM 2
 #define CP_TUNE_ROWS_2D 3
+#define CP_TUNE_H1_BUDGET_MS 4
 int cp_set_tuning(int key, int value);
 int cp_get_tuning(int key);
 

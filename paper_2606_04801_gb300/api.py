@@ -201,11 +201,24 @@ def persistence_batched(imgs: Sequence[torch.Tensor], max_survivors: int = 0, wi
     raise CpError(CP_ERR_CAPACITY, "cubical_persistence_batched (after growing the workspace)")
 
 
+# Volumes beyond this many voxels (in all) need allow_large=True for H1: the
+# cross-star rounds grow with the area of the longest-lived loops, not with
+# the voxel count, and measured 4.6 s at 128^3 and 24 s at 256^3 on smooth
+# fields.  The device stops the rounds once cp_get_tuning(CP_TUNE_H1_BUDGET_MS)
+# is spent, whatever the size.
+H1_PRACTICAL_VOXELS = 128 ** 3
+
+
 def _full_call(imgs: Sequence[torch.Tensor], single: bool, max_survivors: int, pool_entries: int,
-               with_stats: bool) -> Diagram:
+               with_stats: bool, allow_large: bool = False) -> Diagram:
     """The whole diagram (H0, H1 of the volumes, top dimension) of one volume
     (single) or of a batch; grows the survivor bound, the column pool and the
     output until they fit."""
+    nvol = sum(im.numel() for im in imgs if im.dim() == 3)
+    if nvol > H1_PRACTICAL_VOXELS and not allow_large:
+        raise ValueError(
+            f"H1 of {nvol} voxels: above the practical bound of {H1_PRACTICAL_VOXELS} voxels "
+            "(pass allow_large=True; the rounds stop with CP_ERR_TIMEOUT once the H1 time budget is spent)")
     lib = _lib.load()
     dev = imgs[0].device
     k = len(imgs)
@@ -271,20 +284,21 @@ def _full_call(imgs: Sequence[torch.Tensor], single: bool, max_survivors: int, p
 
 
 def persistence_full(img: torch.Tensor, max_survivors: int = 0, pool_entries: int = 0,
-                     with_stats: bool = False) -> Diagram:
+                     with_stats: bool = False, allow_large: bool = False) -> Diagram:
     """Every dimension of one volume: H0, H1 and H2 pairs (V-filtration,
     sorted by (dim, birth cell)); a 2D image gets its plain diagram.  H1 comes
     from the F2 reduction of the squares not paired in H2 over the edges not
     paired in H0, on the device; pool_entries sizes its column pool (0: the
-    default, grown on demand)."""
+    default, grown on demand).  Volumes above H1_PRACTICAL_VOXELS need
+    allow_large=True."""
     _check_image(img)
     if img.dim() == 2:
         return persistence(img, max_survivors, with_stats)
-    return _full_call([img.contiguous()], True, max_survivors, pool_entries, with_stats)
+    return _full_call([img.contiguous()], True, max_survivors, pool_entries, with_stats, allow_large)
 
 
 def persistence_full_batched(imgs: Sequence[torch.Tensor], max_survivors: int = 0, pool_entries: int = 0,
-                             with_stats: bool = False) -> Diagram:
+                             with_stats: bool = False, allow_large: bool = False) -> Diagram:
     """persistence_full over many images and volumes in one pass (pairs carry their item index)."""
     if not imgs:
         raise ValueError("empty batch")
@@ -293,7 +307,7 @@ def persistence_full_batched(imgs: Sequence[torch.Tensor], max_survivors: int = 
     imgs = [im.contiguous() for im in imgs]
     for im in imgs:
         _check_image(im)
-    return _full_call(imgs, False, max_survivors, pool_entries, with_stats)
+    return _full_call(imgs, False, max_survivors, pool_entries, with_stats, allow_large)
 
 
 def pairs_backward(raw: torch.Tensor, grad_birth: torch.Tensor, grad_death: torch.Tensor, n_pixels: int,

@@ -46,6 +46,8 @@
 // those of the sequential reduction, whatever the order of additions.
 // Rounds end when no bid is lost.  Every wait is bounded; pool overflow and
 // failed checks set a status bit and stop the rounds.
+#include <atomic>
+
 #include "cp_common.cuh"
 #include "cp_grid.cuh"
 #include "cp_kernels.h"
@@ -406,6 +408,7 @@ struct ReduceArgs {
     ItemTable tab;
     H1Bufs b;
     Counters* ctr;
+    uint64_t budget_ns;  // wall-clock budget of the rounds
 };
 
 // Column q lost its row to an older column: add that column (F2: the
@@ -502,6 +505,7 @@ __global__ void __launch_bounds__(kRT) k_h1_reduce(const __grid_constant__ Reduc
         set_status(ctr, kStInternal);
     __shared__ uint32_t sh_n, sh_stop;
     uint32_t epoch = 0;
+    const uint64_t t_start = global_timer_ns();  // read by thread 0 of the grid only
     uint32_t nchg = min(ctl->nl, b.mcap);  // round 0: every column that left its star
     for (uint32_t r = 0;; ++r) {
         uint32_t* work = b.list[r & 1u];
@@ -551,6 +555,12 @@ __global__ void __launch_bounds__(kRT) k_h1_reduce(const __grid_constant__ Reduc
         if (gtid == 0) ctl->cnt[(r + 1u) % 3u] = 0u;  // the next round's bids (last read two rounds ago)
         // ---- every losing column adds the winner of its row
         for (uint32_t i = gtid; i < nw; i += gstride) add_winner(a, __ldcg(work + i), r);
+        // the budget: one thread decides, every CTA reads the decision (this
+        // round's stop word) after the next barrier, so all leave together
+        if (gtid == 0 && global_timer_ns() - t_start > a.budget_ns) {
+            set_status(ctr, kStTimeout);
+            atomicOr(&ctl->stop[r & 1u], 2u);
+        }
         grid_barrier(ctr, nblocks, epoch);
         nchg = nw;
     }
@@ -593,6 +603,8 @@ __global__ void __launch_bounds__(kHT) k_h1_emit(const __grid_constant__ ItemTab
     }
 }
 
+std::atomic<int> g_h1_budget_ms{30000};
+
 int grid_of(int64_t n) {
     const int64_t blocks = (n + kHT - 1) / kHT;
     const int64_t cap = int64_t(device_sm_count()) * 8;
@@ -600,6 +612,9 @@ int grid_of(int64_t n) {
 }
 
 }  // namespace
+
+void set_h1_budget_ms(int ms) { g_h1_budget_ms.store(ms); }
+int get_h1_budget_ms() { return g_h1_budget_ms.load(); }
 
 cudaError_t launch_h1(const ItemTable& tab, const H1Bufs& b, Counters* ctr, cp_pair* pairs, uint32_t pair_cap,
                       cudaStream_t s) {
@@ -624,6 +639,7 @@ cudaError_t launch_h1(const ItemTable& tab, const H1Bufs& b, Counters* ctr, cp_p
     ra.tab = tab;
     ra.b = b;
     ra.ctr = ctr;
+    ra.budget_ns = uint64_t(get_h1_budget_ms()) * 1000000ull;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(reduce_blocks);
     cfg.blockDim = dim3(kRT);

@@ -161,6 +161,11 @@ struct H1Bufs {
 // rounds, and appends the H1 pairs (zero persistence omitted) to pairs.
 cudaError_t launch_h1(const ItemTable& tab, const H1Bufs& b, Counters* ctr, cp_pair* pairs, uint32_t pair_cap,
                       cudaStream_t s);
+// Wall-clock budget of the cross-star rounds (one non-preemptible launch):
+// once it is spent, the rounds stop at the next round boundary and the call
+// returns CP_ERR_TIMEOUT.
+void set_h1_budget_ms(int ms);
+int get_h1_budget_ms();
 
 // ---- K4 emission, K5 backward
 cudaError_t launch_init(const ItemTable& tab, Counters* ctr, uint32_t* uft, uint64_t* aget, uint64_t* rest,

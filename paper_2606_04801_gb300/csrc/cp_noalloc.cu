@@ -1,9 +1,8 @@
 // Backward scatter that allocates nothing: cubical_persistence_backward_noalloc.
 //
-// Some callers cannot allocate device memory at all: code that runs while a
-// stream is being captured into a CUDA graph (where cudaMalloc is not
-// allowed), code inside another framework's callbacks that has no handle on
-// its allocator, or deployments whose memory is fully reserved up front.
+// Some callers cannot allocate device memory at all: code inside another
+// framework's callbacks that has no handle on its allocator, or deployments
+// whose device memory is fully reserved up front by another component.
 // Those callers can still pass their own inputs and output, but not a
 // workspace.  This entry point computes the same gradient as
 // cubical_persistence_backward with its double-precision accumulators in a
@@ -56,7 +55,9 @@ __global__ void k_noalloc_round(const double* __restrict__ acc, float* __restric
 
 // Device address of g_noalloc_acc per device, looked up once per device with
 // that device current.  In host code the array's name only stands for the
-// host-side shadow of the symbol, never for device memory.
+// host-side shadow of the symbol, never for device memory.  The cache is
+// keyed by device ordinal, so a cudaDeviceReset of a device after its first
+// call here is not supported (the module would reload at another address).
 std::mutex g_noalloc_mu;
 double* g_noalloc_ptr[64] = {nullptr};
 

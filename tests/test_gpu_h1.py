@@ -196,3 +196,29 @@ def test_full_nonfinite(cp):
     with pytest.raises(cp.CpError):
         cp.persistence_full(bad)
     _check(cp, np.random.default_rng(813).random((5, 6, 7), dtype=np.float32), "after an error")
+
+
+def test_full_time_budget(cp):
+    """The cross-star rounds run in one non-preemptible launch; their
+    wall-clock budget (CP_TUNE_H1_BUDGET_MS) stops them at a round boundary
+    with CP_ERR_TIMEOUT, and the context stays usable.  Budget 0 stops after
+    the first round; this blurred volume needs many more."""
+    from paper_2606_04801_gb300._lib import CP_ERR_TIMEOUT, CpError
+
+    lib = cp.load()
+    img = workloads.blurred((40, 36, 44), 2.0, 17)
+    x = torch.from_numpy(img).cuda()
+    old = lib.cp_get_tuning(4)
+    assert old == 30000
+    assert lib.cp_set_tuning(4, -1) != 0 and lib.cp_set_tuning(4, 3600001) != 0
+    assert lib.cp_set_tuning(4, 0) == 0
+    try:
+        with pytest.raises(CpError) as e:
+            cp.persistence_full(x)
+        assert e.value.code == CP_ERR_TIMEOUT
+    finally:
+        assert lib.cp_set_tuning(4, old) == 0
+    _check(cp, img, "after a spent budget")
+    # volumes above the practical bound need an explicit opt-in
+    with pytest.raises(ValueError):
+        cp.persistence_full(torch.zeros((129, 128, 128), device="cuda"))

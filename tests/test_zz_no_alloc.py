@@ -1,8 +1,8 @@
 """The backward entry point that allocates nothing.
 
-Callers that cannot allocate device memory (for example code running while a
-stream is being captured into a CUDA graph, or inside another framework's
-hooks without access to its allocator) use
+Callers that cannot allocate device memory (for example code inside another
+framework's hooks without access to its allocator, or deployments whose
+device memory is reserved up front by another component) use
 cubical_persistence_backward_noalloc, which keeps its accumulators in a fixed
 array inside the library instead of a workspace.  These tests call it through
 the C-ABI and check it against cubical_persistence_backward on the same pairs
