@@ -1110,6 +1110,7 @@ def main():
     alg = 4 * N + 4 * N + 4 * (T + 1) + 8 * (s0 + stp) + 16 * (r0 + rt)
     achieved = alg / k1 / 1e9 if k1 else None
     traffic = None
+    limiter = None
     tpath = os.path.join(ROOT, "profiles", "k1_prune3d_traffic.json")
     if os.path.exists(tpath):
         try:
@@ -1117,8 +1118,14 @@ def main():
                 tj = json.load(fh)
             if tj.get("source_hash") == _k1_hash():
                 traffic = tj.get("bytes_per_launch_full")
+                lm = tj.get("limiter_metrics") or {}
+                if lm:
+                    limiter = (f"issue/ALU (ncu, {tj['capture']['side']}^3 capture of this source: issue slots "
+                               f"{lm['issue_slots_busy_pct']}% busy, ALU pipe {lm['alu_pipe_pct']}%, DRAM "
+                               f"{lm['dram_throughput_pct']}%, {lm['warp_instructions'] / lm['vertices'] * 32:.0f} warp "
+                               f"instructions per 32 vertices)")
         except Exception:
-            traffic = None
+            traffic = limiter = None
     roofline = {
         "bound": "hbm",
         "achieved": achieved,
@@ -1127,9 +1134,9 @@ def main():
         "frac": (achieved / peak) if achieved else None,
         "traffic": traffic,
         "kernel": "k_prune3d",
-        # what actually limits the kernel (ncu, profiles/k_prune3d_384_blurred.md):
-        # instruction issue, not DRAM
-        "limiter": "issue/ALU (ncu: issue slots 66% busy, ALU pipe 61%, DRAM 8%)",
+        # what limits the kernel, from the ncu capture recorded with the traffic
+        # (null once the kernel source differs from the captured one)
+        "limiter": limiter,
         "peak_source": peak_kind,
         "algorithmic_bytes": alg,
         "read_lower_bound_bytes": 4 * N,  # the image read once, nothing written

@@ -888,11 +888,17 @@ int cubical_persistence_debug_wait_timeout(void* d_workspace, size_t ws_bytes, i
 
 int cp_set_tuning(int key, int value) {
     std::lock_guard<std::mutex> lk(g_mu);
+    if (key == CP_TUNE_H1_BUDGET_MS) {
+        if (value < 0 || value > 3600000) return CP_ERR_ARG;
+        set_h1_budget_ms(value);
+        return CP_OK;
+    }
     return set_tuning(key, value) == 0 ? CP_OK : CP_ERR_ARG;
 }
 
 int cp_get_tuning(int key) {
     std::lock_guard<std::mutex> lk(g_mu);
+    if (key == CP_TUNE_H1_BUDGET_MS) return get_h1_budget_ms();
     return get_tuning(key);
 }
 

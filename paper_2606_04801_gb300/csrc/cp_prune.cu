@@ -1014,17 +1014,13 @@ int set_tuning(int key, int value) {
             if (value < 4 || value > 4096) return -1;
             g_rows2d = value;
             return 0;
-        case 4:  // wall-clock budget of the H1 cross-star rounds, ms
-            if (value < 0 || value > 3600000) return -1;
-            set_h1_budget_ms(value);
-            return 0;
         default:
             return -1;
     }
 }
 
 int get_tuning(int key) {
-    return key == 1 ? g_zchunk3d : key == 2 ? g_ctas3d : key == 3 ? g_rows2d : key == 4 ? get_h1_budget_ms() : -1;
+    return key == 1 ? g_zchunk3d : key == 2 ? g_ctas3d : key == 3 ? g_rows2d : -1;
 }
 
 // Table entry as two 32-bit words:
