@@ -412,6 +412,14 @@ int cubical_persistence_debug_wait_timeout(void *d_workspace, size_t ws_bytes, i
  *   CP_TUNE_ZCHUNK_3D    planes per 3D pruning task (4..4096, default 64)
  *   CP_TUNE_CTAS_PER_SM  3D pruning CTAs per SM (0 = as many as fit, default)
  *   CP_TUNE_ROWS_2D      rows per 2D pruning task (4 .. 4096; default 64)
+ *   CP_TUNE_CROSS_PRUNE_2D  1: the top dimension of 2D images waits for H0
+ *                        and takes only the edges H0 leaves positive (the
+ *                        cross-pruning of Sec. 3.2, Sec. 4.1 step 4: two sorts
+ *                        and two union-find launches in sequence); 0 (default):
+ *                        both dimensions run at once (one sort and one
+ *                        union-find launch), the dual list keeping the edges
+ *                        the table cannot settle, which the dual union-find
+ *                        then finds closing dual cycles.  Same pairs.
  *   CP_TUNE_H1_BUDGET_MS wall-clock budget in milliseconds of the cross-star
  *                        reduction rounds of the _full calls (0 .. 3,600,000;
  *                        default 30,000).  Those rounds run in one
@@ -426,6 +434,7 @@ int cubical_persistence_debug_wait_timeout(void *d_workspace, size_t ws_bytes, i
 #define CP_TUNE_CTAS_PER_SM 2
 #define CP_TUNE_ROWS_2D 3
 #define CP_TUNE_H1_BUDGET_MS 4
+#define CP_TUNE_CROSS_PRUNE_2D 5
 int cp_set_tuning(int key, int value);
 int cp_get_tuning(int key);
 

@@ -153,6 +153,7 @@ int make_plan(int n_items, const int32_t* ndims, const int64_t* dims, const floa
     }
     P.tab.rows2d = prune_tile_y2d();
     P.tab.zchunk3d = prune_tile_z3d();
+    P.tab.cross2d = prune_cross2d();
     P.ntot = voff;
     P.ttot = toff;
     int64_t ms = max_survivors > 0 ? max_survivors : voff / 2 + 65536;
@@ -379,7 +380,9 @@ int run(const Plan& P, cp_pair* d_out, int64_t capacity, int64_t* h_out_count, i
         if (e != cudaSuccess) return e;
         return launch_place_roots(ra, s);
     };
-    const bool joint = P.tab.n2d == 0;  // volumes only: the two lists are independent
+    // The two lists are independent unless 2D items use cross-pruning (their
+    // dual list then waits for the H0 union-find).
+    const bool joint = P.tab.n2d == 0 || !P.tab.cross2d;
     if (joint) {
         // both lists walked, then sorted together (one launch per pass), then
         // placed side by side; the dual list's scratch sits in the pairs buffer
@@ -441,7 +444,7 @@ int run(const Plan& P, cp_pair* d_out, int64_t capacity, int64_t* h_out_count, i
     up[0].log = salt;  // the sort's spare buffer is free from here to the pair sort
     up[0].pairs = pairs;
     up[0].pair_cap = P.cap_p;
-    up[0].dual_keys = P.tab.n2d > 0 ? st : nullptr;  // cross-pruning feeds the dual list of 2D items only
+    up[0].dual_keys = joint ? nullptr : st;  // cross-pruning feeds the dual list of 2D items
     up[0].d_ndual = &ctr->n_st;
     up[0].dual_cap = P.cap_s;
     up[0].ctr = ctr;
@@ -470,8 +473,8 @@ int run(const Plan& P, cp_pair* d_out, int64_t capacity, int64_t* h_out_count, i
         CP_TRY(launch_uf(P.tab, &up[1], 1, s));
         mark(5, s);
     } else {
-        // volumes only: both union-finds share one launch and its rounds (the
-        // dual list after the H0 list)
+        // both union-finds share one launch and its rounds (the dual list after
+        // the H0 list)
         mark(3, s);
         g_ev_joint = true;
         CP_TRY(launch_uf(P.tab, up, 2, s));

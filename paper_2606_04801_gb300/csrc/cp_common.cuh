@@ -40,7 +40,7 @@ struct ItemTable {
     int32_t tiles2d, tiles3d; // total pruning tiles of each kind
     int32_t rows2d;           // vertex rows per 2D pruning task (4 .. 4096)
     int32_t zchunk3d;         // planes per 3D pruning task
-    int32_t pad;
+    int32_t cross2d;          // 2D items: 1 = the dual list waits for H0 (cross-pruning), 0 = both at once
     Item it[kMaxItems];
 };
 
@@ -99,7 +99,8 @@ __host__ __device__ __forceinline__ float ord_float(uint32_t u) {
 
 // Survivor / age key: ord(f(v)) << 32 | v << 5 | low.  `low` orders the cells
 // of one lower star (second-order tie-break): the stencil bit n in 3D, n << 1
-// (| flag) in 2D.
+// in 2D (| 1 on an H0 survivor whose dual status waits for the H0 union-find,
+// under cross-pruning).
 __host__ __device__ __forceinline__ uint64_t make_key(uint32_t ord, uint64_t v, uint32_t low) {
     return (uint64_t(ord) << 32) | (v << 5) | low;
 }

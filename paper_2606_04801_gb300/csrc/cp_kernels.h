@@ -28,6 +28,7 @@ int prune_tile_x3d();
 int prune_tile_y2d();
 int prune_tile_y3d();
 int prune_tile_z3d();
+int prune_cross2d();
 int set_tuning(int key, int value);
 int get_tuning(int key);
 cudaError_t upload_luts(const uint64_t* lut2d, const uint16_t* disp3d, const uint64_t* entries3d,

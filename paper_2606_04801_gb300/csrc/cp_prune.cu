@@ -861,7 +861,12 @@ __global__ void __launch_bounds__(kW2 * 32) k_prune2d(ItemTable tab, Outs o) {
             }
             const uint32_t h0s = owned ? (e.x >> 3) & 0xFu : 0u;
             const uint32_t ds = owned ? (e.x >> 9) & 0xFu : 0u;
-            const uint32_t dn = ds & ~h0s;  // dual survivors that are not also H0 survivors
+            // cross-pruning: dual survivors that are also H0 survivors wait for the
+            // H0 union-find (flag bit of the H0 key); otherwise every dual survivor
+            // goes to the dual list now (one that kills an H0 class closes a dual
+            // cycle there: a no-op)
+            const uint32_t flg = tab.cross2d ? ds : 0u;
+            const uint32_t dn = tab.cross2d ? ds & ~h0s : ds;
             // ---- the top cell with smallest corner (y-1, x)
             const uint32_t cprev_r = __shfl_down_sync(0xFFFFFFFFu, cprev, 1);
             const uint32_t ccur_r = __shfl_down_sync(0xFFFFFFFFu, e.y, 1);
@@ -939,8 +944,8 @@ __global__ void __launch_bounds__(kW2 * 32) k_prune2d(ItemTable tab, Outs o) {
                     bits &= bits - 1;
                     const bool mine = (h0s >> s) & 1u;
                     const unsigned m = __ballot_sync(0xFFFFFFFFu, mine);
-                    if (mine)  // face slot s is stencil offset 2s+1; low bit: also a dual survivor
-                        ws.s0[cnt.s0 + __popc(m & lt)] = make_key(ord, vg, (uint32_t(2 * s + 1) << 1) | ((ds >> s) & 1u));
+                    if (mine)  // face slot s is stencil offset 2s+1; low bit: the dual waits for it
+                        ws.s0[cnt.s0 + __popc(m & lt)] = make_key(ord, vg, (uint32_t(2 * s + 1) << 1) | ((flg >> s) & 1u));
                     cnt.s0 += __popc(m);
                 }
                 bits = ort;
@@ -995,10 +1000,11 @@ bool encode_plane_map(CUtensorMap* map, const float* img, int64_t D, int64_t H, 
 }
 int prune_tile_x() { return kOX2; }
 int prune_tile_x3d() { return kOX; }
-int g_rows2d = 64, g_zchunk3d = kZC, g_ctas3d = 0;  // tuning (cp_set_tuning)
+int g_rows2d = 64, g_zchunk3d = kZC, g_ctas3d = 0, g_cross2d = 0;  // tuning (cp_set_tuning)
 int prune_tile_y2d() { return g_rows2d; }
 int prune_tile_y3d() { return kOY; }
 int prune_tile_z3d() { return g_zchunk3d; }
+int prune_cross2d() { return g_cross2d; }
 
 int set_tuning(int key, int value) {
     switch (key) {
@@ -1014,13 +1020,17 @@ int set_tuning(int key, int value) {
             if (value < 4 || value > 4096) return -1;
             g_rows2d = value;
             return 0;
+        case 5:  // 2D items: sequential cross-pruning (1) or H0 and the dual at once (0)
+            if (value != 0 && value != 1) return -1;
+            g_cross2d = value;
+            return 0;
         default:
             return -1;
     }
 }
 
 int get_tuning(int key) {
-    return key == 1 ? g_zchunk3d : key == 2 ? g_ctas3d : key == 3 ? g_rows2d : -1;
+    return key == 1 ? g_zchunk3d : key == 2 ? g_ctas3d : key == 3 ? g_rows2d : key == 5 ? g_cross2d : -1;
 }
 
 // Table entry as two 32-bit words:

@@ -28,11 +28,17 @@ def ord_bits(x):
 
 
 class Pruned:
-    """K1's outputs for one image, computed one vertex at a time."""
+    """K1's outputs for one image, computed one vertex at a time.
 
-    def __init__(self, lib, img):
+    cross: 2D cross-pruning (the dual list takes an H0 survivor only once the
+    H0 union-find finds it positive); otherwise every dual survivor of the
+    table goes to the dual list at once, where one that kills an H0 class
+    closes a dual cycle (a no-op)."""
+
+    def __init__(self, lib, img, cross=False):
         nd = img.ndim
         self.nd = nd
+        self.cross = bool(cross) and nd == 2
         f = np.where(img == 0, 0.0, img).astype(np.float64)
         shape = img.shape if nd == 3 else (1,) + img.shape
         D, H, W = shape
@@ -96,9 +102,9 @@ class Pruned:
         h0s, ds = (e >> 3) & 0x3F, (e >> 41) & 0xFFF
         for s, b in enumerate(self.faces):
             if (h0s >> s) & 1:
-                self.s0.append((kv, b, v, bool((ds >> s) & 1) if nd == 2 else False))
+                self.s0.append((kv, b, v, bool((ds >> s) & 1) if self.cross else False))
         for s, b in enumerate(self.facets):
-            if (ds >> s) & 1 and not (nd == 2 and (h0s >> s) & 1):
+            if (ds >> s) & 1 and not (self.cross and (h0s >> s) & 1):
                 self.st.append((kv, b, v))
         for t, b in enumerate(self.tops):
             code = (e >> (9 + 4 * t)) & 15
@@ -122,7 +128,8 @@ class Pruned:
         return sorted(self.key(kv, n, v) for kv, n, v in self.st)
 
     def pairs(self):
-        """Sequential elder-rule union-finds over the survivors (with 2D cross-pruning)."""
+        """Sequential elder-rule union-finds over the survivors (with 2D
+        cross-pruning when chosen)."""
         nd, offs = self.nd, self.offs
         D, H, W = self.shape
         GH, GW = 2 * H - 1, 2 * W - 1

@@ -103,6 +103,26 @@ def test_config_2d_2048(cp):
         _check(cp, img, f"2048^2 {name}")
 
 
+def test_config_2d_cross_pruning(cp):
+    """The paper's sequential 2D order (CP_TUNE_CROSS_PRUNE_2D = 1: the dual
+    list takes the H0-positive edges after the H0 union-find) gives the same
+    pairs as the default, where both dimensions run at once."""
+    lib = cp.load()
+    assert lib.cp_set_tuning(5, 1) == 0
+    try:
+        for img, name in zip(workloads.config("2d_2048_grf"), ("grf", "quantised")):
+            _check(cp, img, f"2048^2 {name}, cross-pruned")
+        _check(cp, workloads.uniform((64, 64), 0), "64x64 uniform, cross-pruned")
+        rng = np.random.default_rng(19)
+        for _ in range(20):
+            shape = tuple(int(v) for v in rng.integers(2, 60, 2))
+            img = rng.integers(0, 3, shape).astype(np.float32) if rng.random() < 0.5 else rng.random(shape, dtype=np.float32)
+            _check(cp, img, f"{shape}, cross-pruned")
+        _batch_check(cp, workloads.batch(0, n2d=8, n3d=2, scale=0.2))
+    finally:
+        assert lib.cp_set_tuning(5, 0) == 0
+
+
 def test_config_3d_128(cp):
     for img, name in zip(workloads.config("3d_128"), ("uniform", "blurred")):
         _check(cp, img, f"128^3 {name}")

@@ -68,8 +68,8 @@ def _kernel_stage(cp, img):
     return uf0, uft, s0, st, n_r0, n_rt
 
 
-def _check(cp, lib, img):
-    ref = Pruned(lib, img)
+def _check(cp, lib, img, cross=False):
+    ref = Pruned(lib, img, cross=cross)
     uf0, uft, s0, st, n_r0, n_rt = _kernel_stage(cp, img)
     assert s0.tolist() == ref.s0_keys()
     assert st.tolist() == ref.st_keys()
@@ -95,6 +95,21 @@ def test_prune_stage_2d(cp, seed):
         shape = tuple(int(v) for v in rng.integers(2, 40, 2))
         img = rng.integers(0, 3, shape).astype(np.float32) if rng.random() < 0.5 else rng.random(shape, dtype=np.float32)
         _check(cp, lib, img)
+
+
+def test_prune_stage_2d_cross_pruning(cp):
+    """Under cross-pruning (CP_TUNE_CROSS_PRUNE_2D = 1) the H0 survivors that
+    the dual needs carry the flag bit and stay out of the dual list."""
+    lib = cp.load()
+    rng = np.random.default_rng(430)
+    assert lib.cp_set_tuning(5, 1) == 0
+    try:
+        for _ in range(8):
+            shape = tuple(int(v) for v in rng.integers(2, 40, 2))
+            img = rng.integers(0, 3, shape).astype(np.float32) if rng.random() < 0.5 else rng.random(shape, dtype=np.float32)
+            _check(cp, lib, img, cross=True)
+    finally:
+        assert lib.cp_set_tuning(5, 0) == 0
 
 
 @pytest.mark.parametrize("seed", range(3))

@@ -100,8 +100,8 @@ def test_collapse_matches_independent_enumeration(lib):
 from prune_restatement import Pruned
 
 
-def _pruned_pipeline(lib, img):
-    return Pruned(lib, img).pairs()
+def _pruned_pipeline(lib, img, cross=False):
+    return Pruned(lib, img, cross=cross).pairs()
 
 
 def _oracle_rows(img):
@@ -113,13 +113,16 @@ def _oracle_rows(img):
     )
 
 
+@pytest.mark.parametrize("cross", [False, True])
 @pytest.mark.parametrize("seed", range(4))
-def test_pruned_restatement_matches_oracle_2d(lib, seed):
+def test_pruned_restatement_matches_oracle_2d(lib, seed, cross):
+    """Both forms of the 2D top dimension (cross-pruned after H0, or at once
+    with every dual survivor of the table) give the oracle's pairs."""
     rng = np.random.default_rng(200 + seed)
     for _ in range(25):
         shape = tuple(int(v) for v in rng.integers(2, 10, 2))
         img = rng.integers(0, 3, shape).astype(np.float32) if rng.random() < 0.5 else rng.random(shape, dtype=np.float32)
-        assert _pruned_pipeline(lib, img) == _oracle_rows(img)
+        assert _pruned_pipeline(lib, img, cross) == _oracle_rows(img)
 
 
 @pytest.mark.parametrize("seed", range(3))
@@ -132,7 +135,8 @@ def test_pruned_restatement_matches_oracle_3d(lib, seed):
 
 
 def test_tuning_arguments(lib):
-    keys = {1: (64, [4, 16, 256], [0, 3, 5000]), 2: (0, [0, 2, 4], [-1, 9]), 3: (64, [4, 37, 4096], [0, 3, 4097])}
+    keys = {1: (64, [4, 16, 256], [0, 3, 5000]), 2: (0, [0, 2, 4], [-1, 9]), 3: (64, [4, 37, 4096], [0, 3, 4097]),
+            4: (30000, [0, 1, 3600000], [-1, 3600001]), 5: (0, [0, 1], [-1, 2])}
     for key, (default, good, bad) in keys.items():
         old = lib.cp_get_tuning(key)
         try:
