@@ -11,7 +11,7 @@ import os
 
 import numpy as np
 
-from .build import LIB
+from .build import LIB, LIB_CHECKED
 
 CP_OK = 0
 CP_ERR_ARG = -1
@@ -113,15 +113,17 @@ _lib = None
 
 
 def load():
-    """Load the library (it must have been built: see paper_2606_04801_gb300.build)."""
+    """Load the library (it must have been built: see paper_2606_04801_gb300.build).
+    CP_LIB_VARIANT=checked in the environment loads the bounds-checked build."""
     global _lib
     if _lib is None:
-        if not os.path.exists(LIB):
+        path = LIB_CHECKED if os.environ.get("CP_LIB_VARIANT") == "checked" else LIB
+        if not os.path.exists(path):
             raise RuntimeError(
-                f"libcp_gb300.so is missing ({LIB}); build it first with "
+                f"{os.path.basename(path)} is missing ({path}); build it first with "
                 "`python -c 'import __graft_entry__ as g; g.build()'` or `python -m paper_2606_04801_gb300.build`"
             )
-        lib = ctypes.CDLL(LIB)
+        lib = ctypes.CDLL(path)
         for name, (res, args) in _SIGS.items():
             fn = getattr(lib, name)
             fn.restype = res

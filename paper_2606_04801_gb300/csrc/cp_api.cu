@@ -11,6 +11,8 @@
 #include <mutex>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "cp_common.cuh"
 #include "cp_kernels.h"
 #include "cp_lut.h"
@@ -38,6 +40,25 @@ bool g_ev_joint = false;  // the last profiled call ran both union-finds in one 
 void mark(int i, cudaStream_t s) {
     if (g_profile && g_ev_made) cudaEventRecord(g_ev[i], s);
 }
+
+// NVTX ranges on the host timeline of a forward call: one enclosing range and
+// one per stage, marking when each stage is enqueued (a profiler that records
+// NVTX, such as ncu with --nvtx, can filter or group the kernels by them).
+struct StageRanges {
+    int depth = 0;
+    StageRanges() {
+        nvtxRangePushA("cp.forward");
+        depth = 1;
+    }
+    void next(const char* name) {
+        if (depth == 2) nvtxRangePop();
+        nvtxRangePushA(name);
+        depth = 2;
+    }
+    ~StageRanges() {
+        while (depth-- > 0) nvtxRangePop();
+    }
+};
 
 bool build_host_luts() {
     if (g_lut_built) return true;
@@ -236,7 +257,7 @@ int status_to_code(uint32_t st) {
     if (st & kStNonfinite) return CP_ERR_NONFINITE;
     if (st & kStTimeout) return CP_ERR_TIMEOUT;
     if (st & kStCapacity) return CP_ERR_CAPACITY;
-    if (st & kStInternal) return CP_ERR_INTERNAL;
+    if (st & (kStInternal | kStBounds)) return CP_ERR_INTERNAL;
     return CP_OK;
 }
 
@@ -273,6 +294,8 @@ int run(const Plan& P, cp_pair* d_out, int64_t capacity, int64_t* h_out_count, i
     do {                                           \
         if ((x) != cudaSuccess) return CP_ERR_CUDA; \
     } while (0)
+    StageRanges nv;
+    nv.next("cp.prune");
     CP_TRY(cudaMemsetAsync(ctr, 0, sizeof(Counters), s));
     CP_TRY(launch_init(P.tab, ctr, uft, aget, rest, s));
     mark(0, s);
@@ -290,6 +313,8 @@ int run(const Plan& P, cp_pair* d_out, int64_t capacity, int64_t* h_out_count, i
         po.cap_r0 = P.cap_r0;
         po.cap_rt = P.cap_rt;
         po.ctr = ctr;
+        po.n_uf0 = uint32_t(P.ntot);
+        po.n_uft = uint32_t(P.ttot);
         CP_TRY(launch_prune(P.tab, po, P.tma, s));
         mark(1, s);
         return CP_OK;
@@ -314,6 +339,7 @@ int run(const Plan& P, cp_pair* d_out, int64_t capacity, int64_t* h_out_count, i
         hb.mcap = P.h1_mcap;
         hb.exp_neg_e = P.h1_neg;
         hb.exp_pos_q = P.h1_posq;
+        hb.n_ids = uint32_t(3 * P.ntot);
         // the union-finds mark their committed survivors in these
         CP_TRY(cudaMemsetAsync(hb.neg_e, 0, sizeof(uint32_t) * P.h1_words, s));
         CP_TRY(cudaMemsetAsync(hb.pos_q, 0, sizeof(uint32_t) * P.h1_words, s));
@@ -332,9 +358,12 @@ int run(const Plan& P, cp_pair* d_out, int64_t capacity, int64_t* h_out_count, i
     po.cap_r0 = P.cap_r0;
     po.cap_rt = P.cap_rt;
     po.ctr = ctr;
+    po.n_uf0 = uint32_t(P.ntot);
+    po.n_uft = uint32_t(P.ttot);
     CP_TRY(launch_prune(P.tab, po, P.tma, s));
     if (tm) CP_TRY(launch_t_flatten(uf0, tm->items, s));
     mark(1, s);
+    nv.next("cp.roots+sort");
 
     // First-round root walks over the unsorted survivors (tile order), then the
     // sort carrying each survivor's position, then the first active list.
@@ -357,6 +386,7 @@ int run(const Plan& P, cp_pair* d_out, int64_t capacity, int64_t* h_out_count, i
     ra.na = na0;
     ra.nb = nb0;
     ra.ctr = ctr;
+    ra.n_nodes = uint32_t(P.ntot);
     SortBufs sb;
     sb.keys_alt = salt;
     sb.vals = act1;
@@ -369,6 +399,7 @@ int run(const Plan& P, cp_pair* d_out, int64_t capacity, int64_t* h_out_count, i
         ra.keys = dual ? st : s0;
         ra.d_n = dual ? &ctr->n_st : &ctr->n_s0;
         ra.uf = dual ? uft : uf0;
+        ra.n_nodes = uint32_t(dual ? P.ttot : P.ntot);
         ra.dual = dual;
         ra.d_n_before = d_n_before;
         cudaError_t e = launch_roots(ra, s);
@@ -394,6 +425,7 @@ int run(const Plan& P, cp_pair* d_out, int64_t capacity, int64_t* h_out_count, i
         rt.keys = st;
         rt.d_n = &ctr->n_st;
         rt.uf = uft;
+        rt.n_nodes = uint32_t(P.ttot);
         rt.dual = 1;
         rt.ra = raT;
         rt.rb = rbT;
@@ -403,6 +435,7 @@ int run(const Plan& P, cp_pair* d_out, int64_t capacity, int64_t* h_out_count, i
         ra.keys = s0;
         ra.d_n = &ctr->n_s0;
         ra.uf = uf0;
+        ra.n_nodes = uint32_t(P.ntot);
         ra.dual = 0;
         ra.d_n_before = nullptr;
         CP_TRY(launch_roots2(ra, rt, s));
@@ -424,6 +457,7 @@ int run(const Plan& P, cp_pair* d_out, int64_t capacity, int64_t* h_out_count, i
         CP_TRY(prepare(0, nullptr));
     }
     mark(2, s);
+    nv.next("cp.union-find");
 
     UfParams up[2];
     up[0].keys = s0;
@@ -461,6 +495,10 @@ int run(const Plan& P, cp_pair* d_out, int64_t capacity, int64_t* h_out_count, i
     up[1].dual = 1;
     up[0].h1flags = P.h1 ? hb.neg_e : nullptr;
     up[1].h1flags = P.h1 ? hb.pos_q : nullptr;
+    up[0].n_nodes = uint32_t(P.ntot);
+    up[0].n_rids = P.cap_r0;
+    up[1].n_nodes = uint32_t(P.ttot);
+    up[1].n_rids = P.cap_rt;
 
     if (!joint) {
         // the H0 union-find appends positive edges of 2D items to the dual list
@@ -482,8 +520,13 @@ int run(const Plan& P, cp_pair* d_out, int64_t capacity, int64_t* h_out_count, i
         mark(5, s);
     }
 
+    nv.next("cp.emit");
     CP_TRY(launch_essential(P.tab, ctr, pairs, P.cap_p, s));
-    if (P.h1) CP_TRY(launch_h1(P.tab, hb, ctr, pairs, P.cap_p, s));
+    if (P.h1) {
+        nv.next("cp.h1");
+        CP_TRY(launch_h1(P.tab, hb, ctr, pairs, P.cap_p, s));
+        nv.next("cp.emit");
+    }
     uint32_t* pvals = at<uint32_t>(ws, P.o_pvals);
     uint32_t* pvalt = at<uint32_t>(ws, P.o_pvalt);
     // output order (item, dim, birth cell): only as many key bytes as this call's
@@ -968,9 +1011,11 @@ int cubical_persistence_loss_backward(const cp_pair* d_pairs, int64_t n_pairs, c
     if (ws_bytes < cubical_persistence_loss_backward_workspace_size(n_pixels)) return CP_ERR_ARG;
     double* acc = static_cast<double*>(d_workspace);
     double* parts = reinterpret_cast<double*>(static_cast<char*>(d_workspace) + align_up(sizeof(double) * size_t(n_pixels)));
+    nvtxRangePushA("cp.loss_backward");
     cudaError_t e = launch_loss_backward(d_pairs, n_pairs, d_n_pairs, min_persistence, d_item_offsets, acc, parts,
                                          loss_partials(), d_loss, d_grad_image, n_pixels,
                                          static_cast<cudaStream_t>(stream));
+    nvtxRangePop();
     return e == cudaSuccess ? CP_OK : CP_ERR_CUDA;
 }
 
@@ -985,9 +1030,11 @@ int cubical_persistence_backward(const cp_pair* d_pairs, int64_t n_pairs, const 
     if (n_pairs < 0 || n_pixels <= 0 || !d_grad_image || !d_workspace) return CP_ERR_ARG;
     if (n_pairs > 0 && (!d_pairs || !d_grad_birth || !d_grad_death)) return CP_ERR_ARG;
     if (ws_bytes < cubical_persistence_backward_workspace_size(n_pixels)) return CP_ERR_ARG;
+    nvtxRangePushA("cp.backward");
     cudaError_t e = launch_backward(d_pairs, n_pairs, d_grad_birth, d_grad_death, d_item_offsets,
                                     static_cast<double*>(d_workspace), d_grad_image, n_pixels,
                                     static_cast<cudaStream_t>(stream));
+    nvtxRangePop();
     return e == cudaSuccess ? CP_OK : CP_ERR_CUDA;
 }
 

@@ -18,6 +18,7 @@ constexpr uint32_t kStNonfinite = 1u << 0;
 constexpr uint32_t kStCapacity = 1u << 1;
 constexpr uint32_t kStTimeout = 1u << 2;
 constexpr uint32_t kStInternal = 1u << 3;
+constexpr uint32_t kStBounds = 1u << 4;   // bounds-checked build: a data-dependent index was out of range
 
 // ---------------------------------------------------------------- items
 // One image or volume of a call.  2D items have D = 1.  Vertices of item i
@@ -157,6 +158,20 @@ __host__ __device__ __forceinline__ uint32_t top_of_octant(const Item& it, int z
 // ---------------------------------------------------------------- device utils
 #ifdef __CUDACC__
 __device__ __forceinline__ void set_status(Counters* c, uint32_t bit) { atomicOr(&c->status, bit); }
+
+// CP_IN(i, n, ctr): in the bounds-checked build (-DCP_CHECKED), true when the
+// data-dependent index i lies in [0, n), else the call is flagged
+// (kStBounds) and the caller skips the access; in the normal build, true.
+#ifdef CP_CHECKED
+__device__ __forceinline__ bool cp_in_checked(uint64_t i, uint64_t n, Counters* c) {
+    if (i < n) return true;
+    set_status(c, kStBounds);
+    return false;
+}
+#define CP_IN(i, n, ctr) ::cp::cp_in_checked(uint64_t(i), uint64_t(n), (ctr))
+#else
+#define CP_IN(i, n, ctr) true
+#endif
 
 __device__ __forceinline__ uint64_t global_timer_ns() {
     uint64_t t;

@@ -420,6 +420,10 @@ struct ReduceArgs {
 // rather than every intermediate result.
 __device__ void add_winner(const ReduceArgs& a, uint32_t q, uint32_t r) {
     const H1Bufs& b = a.b;
+    if (!CP_IN(q, b.n_ids, a.ctr)) {
+        atomicOr(&b.ctl->stop[r & 1u], 1u);
+        return;
+    }
     const Item* itc;
     int64_t mc;
     const uint64_t kc = column_key(a.tab, q, itc, mc);
@@ -428,8 +432,17 @@ __device__ void add_winner(const ReduceArgs& a, uint32_t q, uint32_t r) {
     uint32_t lc;
     if (oc != ~0ull) lc = __ldcg(b.clen + q);
     else lc = decode(*itc, mc, __ldcg(b.cmask + q), lc_keys);
+    if (oc != ~0ull && !CP_IN(oc + lc, b.pool_cap + 1, a.ctr)) {
+        atomicOr(&b.ctl->stop[r & 1u], 1u);
+        return;
+    }
     const uint64_t low = oc != ~0ull ? __ldcg(b.pool + oc) : lc_keys[0];
-    const uint64_t kp = __ldcg(b.pivot + edge_id(a.tab, low));
+    const uint32_t eid = edge_id(a.tab, low);
+    if (!CP_IN(eid, b.n_ids, a.ctr)) {
+        atomicOr(&b.ctl->stop[r & 1u], 1u);
+        return;
+    }
+    const uint64_t kp = __ldcg(b.pivot + eid);
     if (lc == 0u || kp >= kc) {  // only after an earlier error
         set_status(a.ctr, kStInternal);
         atomicOr(&b.ctl->stop[r & 1u], 1u);
@@ -437,10 +450,18 @@ __device__ void add_winner(const ReduceArgs& a, uint32_t q, uint32_t r) {
     }
     const Item& itp = a.tab.it[item_of_vertex(a.tab, key_vertex(kp))];
     const uint32_t p = cell_id3(itp, kp, true);
+    if (!CP_IN(p, b.n_ids, a.ctr)) {
+        atomicOr(&b.ctl->stop[r & 1u], 1u);
+        return;
+    }
     const uint64_t op = column_at(b, p);
     uint32_t lp;
     if (op != ~0ull) lp = __ldcg(b.clen + p);
     else lp = decode(itp, int64_t(key_vertex(kp)) - itp.voff, __ldcg(b.cmask + p), lp_keys);
+    if (op != ~0ull && !CP_IN(op + lp, b.pool_cap + 1, a.ctr)) {
+        atomicOr(&b.ctl->stop[r & 1u], 1u);
+        return;
+    }
     const uint64_t need = uint64_t(lc) + lp - 2u;
     if (need == 0u || need > 0x1FFFFFFFull) {  // empty: only after an earlier error; 2^29 entries: beyond
         set_status(a.ctr, need ? kStCapacity : kStInternal);  // any volume this library takes
@@ -516,13 +537,16 @@ __global__ void __launch_bounds__(kRT) k_h1_reduce(const __grid_constant__ Reduc
             const uint32_t i = i0 + threadIdx.x;
             uint32_t lose = kNone;
             if (i < nchg) {
-                const uint32_t q = __ldcg(chg + i);
+                uint32_t q = __ldcg(chg + i);
+                if (!CP_IN(q, b.n_ids, ctr)) q = 0;
                 const Item* it;
                 int64_t m;
                 const uint64_t kq = column_key(a.tab, q, it, m);
                 const uint64_t low = column_low(b, *it, m, q);
+                uint32_t eid = edge_id(a.tab, low);
+                if (!CP_IN(eid, b.n_ids, ctr)) eid = 0;
                 const unsigned long long old =
-                    atomicMin(reinterpret_cast<unsigned long long*>(b.pivot + edge_id(a.tab, low)), kq);
+                    atomicMin(reinterpret_cast<unsigned long long*>(b.pivot + eid), kq);
                 if (old < kq) {
                     lose = q;  // an older column holds the row
                 } else if (old != ~0ull) {  // q displaces a younger holder

@@ -20,6 +20,7 @@ struct PruneOuts {
     uint64_t* rest;  // reservation word of each dual root id
     uint32_t cap_s, cap_r0, cap_rt;
     Counters* ctr;
+    uint32_t n_uf0, n_uft;  // forest sizes (for the bounds-checked build)
 };
 size_t prune_smem2d();
 size_t prune_smem3d();
@@ -90,6 +91,8 @@ struct UfParams {
     // H1 of volumes: bit cell_id3 of every committed survivor of a 3D item
     // (H0: a negative edge; dual: a square that creates a 2-cycle), or nullptr
     uint32_t* h1flags = nullptr;
+    uint32_t n_nodes = 0;     // forest entries, and root ids (age / res entries):
+    uint32_t n_rids = 0;      // bounds of the bounds-checked build
 };
 // First-round root walks, before the sort (k_roots: ra / rb / pos per unsorted
 // survivor), and the first active list from the sorted positions
@@ -111,6 +114,7 @@ struct RootArgs {
     uint32_t* na;
     uint32_t* nb;
     Counters* ctr;
+    uint32_t n_nodes;            // forest entries (bounds-checked build)
 };
 cudaError_t launch_roots(const RootArgs& r, cudaStream_t s);
 // Both lists' first-round walks in one launch (one work counter over both).
@@ -155,6 +159,7 @@ struct H1Bufs {
     uint32_t mcap;           // columns expected: sum over 3D items of E - N + 1
     uint32_t exp_neg_e;      // sum over 3D items of N - 1
     uint32_t exp_pos_q;      // sum over 3D items of (D-1)(H-1)(W-1)
+    uint32_t n_ids = 0;      // edge / square ids (entries of the per-id arrays; bounds-checked build)
 };
 // After the union-finds have marked their committed survivors in the two
 // bitmaps (zeroed before them): marks what the lower stars settle, reduces

@@ -53,6 +53,7 @@ struct Outs {
     uint64_t* rest;
     uint32_t cap_s, cap_r0, cap_rt;
     Counters* ctr;
+    uint32_t n_uf0, n_uft;  // forest sizes (bounds-checked build)
 };
 
 __device__ __forceinline__ unsigned long long warp_min_u64(unsigned long long v) {
@@ -211,8 +212,8 @@ __device__ __forceinline__ void warp_flush(WS& ws, WarpCounts& c, const Outs& o)
         if (g < o.cap_r0) {
             o.age0[g] = ws.r0age[i];
             o.res0[g] = 0;
-            o.uf0[ws.r0node[i]] = kTag | g;
-        } else {
+            if (CP_IN(ws.r0node[i], o.n_uf0, o.ctr)) o.uf0[ws.r0node[i]] = kTag | g;
+        } else if (CP_IN(ws.r0node[i], o.n_uf0, o.ctr)) {
             o.uf0[ws.r0node[i]] = kTag;  // out of capacity: keep the forest well formed (result flagged invalid)
         }
     }
@@ -221,8 +222,8 @@ __device__ __forceinline__ void warp_flush(WS& ws, WarpCounts& c, const Outs& o)
         if (g < o.cap_rt) {
             o.aget[g] = ws.rtage[i];
             o.rest[g] = 0;
-            o.uft[ws.rtnode[i]] = kTag | g;
-        } else {
+            if (CP_IN(ws.rtnode[i], o.n_uft, o.ctr)) o.uft[ws.rtnode[i]] = kTag | g;
+        } else if (CP_IN(ws.rtnode[i], o.n_uft, o.ctr)) {
             o.uft[ws.rtnode[i]] = kTag;
         }
     }
@@ -553,7 +554,7 @@ __device__ __forceinline__ void prune_task3d(Smem3& sm, const ItemTable& tab, co
                 // that the z-1 neighbour (same thread, previous step) started
                 const uint32_t u = vg + uint32_t(sm.h0link[__ffs(f0) - 1]);
                 far = ((f0 & 16u) && z > sm.t_z0) ? far : u;
-                o.uf0[vg] = far;
+                if (CP_IN(vg, o.n_uf0, o.ctr)) o.uf0[vg] = far;
             }
         }
         // survivor fields (owned survivor vertices only; rare)
@@ -588,7 +589,7 @@ __device__ __forceinline__ void prune_task3d(Smem3& sm, const ItemTable& tab, co
                 // that top cell in the previous step
                 const bool chain = (bits & kMvChain) && z - 1 > sm.t_z0;
                 far_t = chain ? far_t : ((bits & bnd) ? sm.t_OUT : self + uint32_t(lk.x));
-                o.uft[self] = far_t;
+                if (CP_IN(self, o.n_uft, o.ctr)) o.uft[self] = far_t;
             } else if (bits & kMvRoot) {
                 rootT = true;
                 rt_node = self;
@@ -601,7 +602,7 @@ __device__ __forceinline__ void prune_task3d(Smem3& sm, const ItemTable& tab, co
                 rt_age = make_key(ord_bits(mv), mg, age_slot(t));
             } else {
                 far_t = kTag;
-                o.uft[self] = kTag;  // only reachable with non-finite input (flagged): keep the forest well formed
+                if (CP_IN(self, o.n_uft, o.ctr)) o.uft[self] = kTag;  // only reachable with non-finite input (flagged): keep the forest well formed
             }
         }
         // ---- stage survivors and roots (rare in smooth fields)
@@ -856,7 +857,7 @@ __global__ void __launch_bounds__(kW2 * 32) k_prune2d(ItemTable tab, Outs o) {
                     const uint32_t mag = (direct == 0u || direct == 3u) ? W : 1u;
                     const uint32_t u = direct < 2u ? vg - mag : vg + mag;
                     far = (direct == 0u && y > y0) ? far : u;
-                    o.uf0[vg] = far;
+                    if (CP_IN(vg, o.n_uf0, o.ctr)) o.uf0[vg] = far;
                 }
             }
             const uint32_t h0s = owned ? (e.x >> 3) & 0xFu : 0u;
@@ -904,10 +905,10 @@ __global__ void __launch_bounds__(kW2 * 32) k_prune2d(ItemTable tab, Outs o) {
                     // cell in the previous step
                     const bool chain = ty == y - 2 && tx == x && y - 1 > y0;
                     far_t = chain ? far_t : (out ? OUT : toff + uint32_t(ty) * W1 + uint32_t(tx));
-                    o.uft[self] = far_t;
+                    if (CP_IN(self, o.n_uft, o.ctr)) o.uft[self] = far_t;
                 } else {
                     far_t = kTag;
-                    o.uft[self] = kTag;  // only reachable with non-finite input (flagged): keep the forest well formed
+                    if (CP_IN(self, o.n_uft, o.ctr)) o.uft[self] = kTag;  // only reachable with non-finite input (flagged): keep the forest well formed
                 }
             }
             cprev = e.y;
@@ -1103,6 +1104,8 @@ cudaError_t launch_prune(const ItemTable& tab, const PruneOuts& po, const TmaMap
     o.cap_r0 = po.cap_r0;
     o.cap_rt = po.cap_rt;
     o.ctr = po.ctr;
+    o.n_uf0 = po.n_uf0;
+    o.n_uft = po.n_uft;
     const int blocks3d = device_cached(kCachePrune3d, [] {
         cudaFuncSetAttribute(k_prune3d, cudaFuncAttributeMaxDynamicSharedMemorySize, int(prune_smem3d()));
         int per_sm = 0;

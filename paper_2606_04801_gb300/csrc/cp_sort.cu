@@ -240,8 +240,10 @@ __global__ void __launch_bounds__(kT) k_onesweep(const __grid_constant__ SweepAr
             if (idx < n) {
                 uint32_t dd = uint32_t(key[r] >> shift) & 255u;
                 uint32_t pos = sm.excl[dd] + sm.whist[warp][dd] + rank[r];
-                sm.stage[pos] = key[r];
-                if (has_vals) sm.vstage[pos] = val[r];
+                if (CP_IN(pos, kSortTile, ctr)) {
+                    sm.stage[pos] = key[r];
+                    if (has_vals) sm.vstage[pos] = val[r];
+                }
             }
         }
         __syncthreads();

@@ -50,18 +50,21 @@ struct UfKernelArgs {
 // writes into the large forest array would cost read-modify-write traffic.
 // Paths end at roots (the forests are acyclic); the wall-clock bound only
 // guards against a corrupted forest (the walk then stops and reports false).
-__device__ __forceinline__ bool walk(const uint32_t* uf, uint32_t& a, uint32_t& pa, uint32_t& b, uint32_t& pb,
-                                     uint32_t& hops) {
+// (Bounds-checked build: a parent outside the forest ends the walk, flagged.)
+__device__ __forceinline__ bool walk(const uint32_t* uf, uint32_t n_nodes, Counters* ctr, uint32_t& a, uint32_t& pa,
+                                     uint32_t& b, uint32_t& pb, uint32_t& hops) {
     uint64_t t0 = 0;
+    (void)n_nodes;
+    (void)ctr;
     while (!(pa & kTag) || !(pb & kTag)) {
         ++hops;
         if (!(pa & kTag)) {
             a = pa;
-            pa = __ldcg(uf + a);
+            pa = CP_IN(a, n_nodes, ctr) ? __ldcg(uf + a) : kTag;
         }
         if (!(pb & kTag)) {
             b = pb;
-            pb = __ldcg(uf + b);
+            pb = CP_IN(b, n_nodes, ctr) ? __ldcg(uf + b) : kTag;
         }
         if ((hops & 1023u) == 0) {
             const uint64_t now = global_timer_ns();
@@ -72,10 +75,10 @@ __device__ __forceinline__ bool walk(const uint32_t* uf, uint32_t& a, uint32_t& 
     return true;
 }
 
-__device__ __forceinline__ bool find_two(const uint32_t* uf, uint32_t a, uint32_t b, uint32_t& rida, uint32_t& ridb,
-                                         uint32_t& ra, uint32_t& rb, uint32_t& hops) {
-    uint32_t pa = __ldcg(uf + a), pb = __ldcg(uf + b);
-    const bool ok = walk(uf, a, pa, b, pb, hops);
+__device__ __forceinline__ bool find_two(const uint32_t* uf, uint32_t n_nodes, Counters* ctr, uint32_t a, uint32_t b,
+                                         uint32_t& rida, uint32_t& ridb, uint32_t& ra, uint32_t& rb, uint32_t& hops) {
+    uint32_t pa = CP_IN(a, n_nodes, ctr) ? __ldcg(uf + a) : kTag, pb = CP_IN(b, n_nodes, ctr) ? __ldcg(uf + b) : kTag;
+    const bool ok = walk(uf, n_nodes, ctr, a, pa, b, pb, hops);
     ra = a;
     rb = b;
     rida = pa & ~kTag;
@@ -88,11 +91,20 @@ __device__ __forceinline__ bool find_two(const uint32_t* uf, uint32_t a, uint32_
 constexpr uint64_t kDead = 0xFFFFFFFF00000000ull;
 
 // Current root id of a class given a root id it once had.
-__device__ __forceinline__ bool find_rid(const uint64_t* res, uint32_t& rid, uint32_t& hops) {
+// (Bounds-checked build: an id outside the root ids becomes 0, flagged.)
+__device__ __forceinline__ bool find_rid(const uint64_t* res, uint32_t n_rids, Counters* ctr, uint32_t& rid,
+                                         uint32_t& hops) {
+    (void)n_rids;
+    (void)ctr;
+    if (!CP_IN(rid, n_rids, ctr)) rid = 0;
     uint64_t w = __ldcg(res + rid);
     uint64_t t0 = 0;
     while ((w & kDead) == kDead) {
         rid = uint32_t(w);
+        if (!CP_IN(rid, n_rids, ctr)) {
+            rid = 0;
+            return true;
+        }
         w = __ldcg(res + rid);
         if ((++hops & 1023u) == 0) {
             const uint64_t now = global_timer_ns();
@@ -246,7 +258,7 @@ __global__ void __launch_bounds__(kFT) k_roots(const __grid_constant__ RootArgs 
         }
 #pragma unroll
         for (int k = 0; k < 2 * kRootsPerLane; ++k)
-            par[k] = base + 32u * (k >> 1) + lane < n ? __ldcg(r.uf + node[k]) : kTag;
+            par[k] = base + 32u * (k >> 1) + lane < n && CP_IN(node[k], r.n_nodes, ctr) ? __ldcg(r.uf + node[k]) : kTag;
         // walk all paths one hop per step until every one has reached its root
         uint64_t t0 = 0;
         uint32_t steps = 0;
@@ -256,7 +268,7 @@ __global__ void __launch_bounds__(kFT) k_roots(const __grid_constant__ RootArgs 
             for (int k = 0; k < 2 * kRootsPerLane; ++k) {
                 if (!(par[k] & kTag)) {
                     node[k] = par[k];
-                    par[k] = __ldcg(r.uf + node[k]);
+                    par[k] = CP_IN(node[k], r.n_nodes, ctr) ? __ldcg(r.uf + node[k]) : kTag;
                     more = true;
                 }
             }
@@ -315,8 +327,8 @@ __global__ void __launch_bounds__(kFT) k_roots2(const __grid_constant__ RootArgs
             if (r.dual) key = ~key;
             int item;
             endpoints(r0.tab, key, r.dual, node[0], node[1], item);
-            par[0] = __ldcg(r.uf + node[0]);
-            par[1] = __ldcg(r.uf + node[1]);
+            par[0] = CP_IN(node[0], r.n_nodes, ctr) ? __ldcg(r.uf + node[0]) : kTag;
+            par[1] = CP_IN(node[1], r.n_nodes, ctr) ? __ldcg(r.uf + node[1]) : kTag;
         }
         uint64_t t0 = 0;
         uint32_t steps = 0;
@@ -326,7 +338,7 @@ __global__ void __launch_bounds__(kFT) k_roots2(const __grid_constant__ RootArgs
             for (int k = 0; k < 2; ++k) {
                 if (!(par[k] & kTag)) {
                     node[k] = par[k];
-                    par[k] = __ldcg(r.uf + node[k]);
+                    par[k] = CP_IN(node[k], r.n_nodes, ctr) ? __ldcg(r.uf + node[k]) : kTag;
                     more = true;
                 }
             }
@@ -391,7 +403,7 @@ __device__ __forceinline__ void fresh_roots(const UfKernelArgs& args, const UfPa
     uint32_t a, b, va, vb;
     int item;
     endpoints(args.tab, key, p.dual, a, b, item);
-    if (!find_two(p.uf, a, b, ra, rb, va, vb, hops)) {
+    if (!find_two(p.uf, p.n_nodes, p.ctr, a, b, ra, rb, va, vb, hops)) {
         set_status(p.ctr, kStTimeout);
         rb = ra;
     }
@@ -412,7 +424,7 @@ __device__ __forceinline__ void phase_a_mem(const UfKernelArgs& args, int q, uin
         a = __ldcg(p.na[cur] + slot);
         b = __ldcg(p.nb[cur] + slot);
     }
-    if (!find_rid(p.res, a, hops) || !find_rid(p.res, b, hops)) {
+    if (!find_rid(p.res, p.n_rids, p.ctr, a, hops) || !find_rid(p.res, p.n_rids, p.ctr, b, hops)) {
         set_status(p.ctr, kStTimeout);
         b = a;
     }
@@ -502,8 +514,11 @@ __device__ void uf_rounds(const UfKernelArgs& args, uint32_t n0, uint32_t n1, ui
             // reservation words of the carried roots (loads of the kR items in flight together)
 #pragma unroll
             for (int k = 0; k < kR; ++k) {
-                const uint64_t* res = ((isq1 >> k) & 1u) ? args.p[1].res : args.p[0].res;
+                const UfParams& pk = args.p[(isq1 >> k) & 1u];
+                const uint64_t* res = pk.res;
                 const bool h = (has >> k) & 1u;
+                if (h && !CP_IN(a[k], pk.n_rids, ctr)) a[k] = 0;
+                if (h && !CP_IN(b[k], pk.n_rids, ctr)) b[k] = 0;
                 wa[k] = h ? __ldcg(res + a[k]) : 0ull;
                 wb[k] = h ? __ldcg(res + b[k]) : 0ull;
             }
@@ -516,12 +531,12 @@ __device__ void uf_rounds(const UfKernelArgs& args, uint32_t n0, uint32_t n1, ui
                 uint32_t h = 0;
                 if ((wa[k] & kDead) == kDead) {
                     a[k] = uint32_t(wa[k]);
-                    if (!find_rid(res, a[k], h)) set_status(ctr, kStTimeout);
+                    if (!find_rid(res, args.p[q].n_rids, ctr, a[k], h)) set_status(ctr, kStTimeout);
                     ++h;
                 }
                 if ((wb[k] & kDead) == kDead) {
                     b[k] = uint32_t(wb[k]);
-                    if (!find_rid(res, b[k], h)) set_status(ctr, kStTimeout);
+                    if (!find_rid(res, args.p[q].n_rids, ctr, b[k], h)) set_status(ctr, kStTimeout);
                     ++h;
                 }
                 if (q) hops1 += h;
