@@ -411,6 +411,80 @@ struct ReduceArgs {
     uint64_t budget_ns;  // wall-clock budget of the rounds
 };
 
+// A column's entries: in the pool (off != ~0) or decoded into shared memory.
+struct ColSrc {
+    uint64_t off;
+    const uint64_t* sm;
+    uint32_t len;
+};
+
+// The warp merges the entries of c and p after their common lowest one into
+// out (symmetric difference over F2) and returns how many it wrote.  Each
+// lane takes an equal share of the merged sequence, its start found by a
+// binary search on the merge path; an entry in both columns lands next to
+// its twin (ties put c's first) and both are dropped.  A first pass counts
+// each lane's survivors, a warp prefix sum places them, a second pass writes.
+__device__ uint32_t warp_merge(const H1Bufs& b, const ColSrc& c, const ColSrc& p, uint64_t* out) {
+    const unsigned lane = lane_id();
+    const uint32_t nc = c.len - 1u, np = p.len - 1u, total = nc + np;
+    auto gc = [&](uint32_t i) { return c.off != ~0ull ? __ldcg(b.pool + c.off + 1 + i) : c.sm[1 + i]; };
+    auto gp = [&](uint32_t i) { return p.off != ~0ull ? __ldcg(b.pool + p.off + 1 + i) : p.sm[1 + i]; };
+    const uint32_t chunk = (total + 31u) / 32u;
+    const uint32_t d0 = min(total, lane * chunk), d1 = min(total, d0 + chunk);
+    // split at d0: the smallest i such that c's entry i would not precede p's
+    // entry d0-i-1 (keys descending)
+    uint32_t lo = d0 > np ? d0 - np : 0u, hi = min(d0, nc);
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (gc(mid) >= gp(d0 - mid - 1)) lo = mid + 1;
+        else hi = mid;
+    }
+    const uint32_t i0 = lo, j0 = d0 - lo;
+    uint32_t kept = 0;  // pass 1
+    {
+        uint32_t i = i0, j = j0;
+        uint64_t x = i < nc ? gc(i) : 0, y = j < np ? gp(j) : 0;
+        uint64_t prevc = i > 0 ? gc(i - 1) : ~0ull;  // the last entry of c taken
+        for (uint32_t d = d0; d < d1; ++d) {
+            if (j >= np || (i < nc && x >= y)) {
+                kept += (j < np && y == x) ? 0u : 1u;
+                prevc = x;
+                ++i;
+                x = i < nc ? gc(i) : 0;
+            } else {
+                kept += (i > 0 && prevc == y) ? 0u : 1u;
+                ++j;
+                y = j < np ? gp(j) : 0;
+            }
+        }
+    }
+    uint32_t incl = kept;
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= unsigned(o)) incl += t;
+    }
+    {  // pass 2
+        uint64_t* w = out + (incl - kept);
+        uint32_t i = i0, j = j0;
+        uint64_t x = i < nc ? gc(i) : 0, y = j < np ? gp(j) : 0;
+        uint64_t prevc = i > 0 ? gc(i - 1) : ~0ull;
+        for (uint32_t d = d0; d < d1; ++d) {
+            if (j >= np || (i < nc && x >= y)) {
+                if (!(j < np && y == x)) *w++ = x;
+                prevc = x;
+                ++i;
+                x = i < nc ? gc(i) : 0;
+            } else {
+                if (!(i > 0 && prevc == y)) *w++ = y;
+                ++j;
+                y = j < np ? gp(j) : 0;
+            }
+        }
+    }
+    __syncwarp();
+    return __shfl_sync(0xFFFFFFFFu, incl, 31);
+}
+
 // Column q lost its row to an older column: add that column (F2: the
 // symmetric difference; the common lowest entry cancels).  Columns that no
 // addition has reached yet are read from their star masks.  A column that
@@ -418,101 +492,79 @@ struct ReduceArgs {
 // does not occupy; when the result does not fit, it moves to a fresh pair of
 // twice the size, so the pool holds a few times each column's largest size
 // rather than every intermediate result.
-__device__ void add_winner(const ReduceArgs& a, uint32_t q, uint32_t r) {
+//
+// The addition is done by a whole warp, one warp per losing column
+// (warp_merge).  Columns still in their star masks are decoded once, by lane
+// 0, into shared memory (sc, sp: 30 keys each).
+__device__ void add_winner_warp(const ReduceArgs& a, uint32_t q, uint32_t r, uint64_t* sc, uint64_t* sp) {
     const H1Bufs& b = a.b;
-    if (!CP_IN(q, b.n_ids, a.ctr)) {
-        atomicOr(&b.ctl->stop[r & 1u], 1u);
-        return;
-    }
+    const unsigned lane = lane_id();
+    auto stop = [&](uint32_t status) {
+        if (lane == 0) {
+            if (status) set_status(a.ctr, status);
+            atomicOr(&b.ctl->stop[r & 1u], 1u);
+        }
+    };
+    if (!CP_IN(q, b.n_ids, a.ctr)) return stop(0);
     const Item* itc;
     int64_t mc;
     const uint64_t kc = column_key(a.tab, q, itc, mc);
-    uint64_t lc_keys[30], lp_keys[30];
-    const uint64_t oc = column_at(b, q);
-    uint32_t lc;
-    if (oc != ~0ull) lc = __ldcg(b.clen + q);
-    else lc = decode(*itc, mc, __ldcg(b.cmask + q), lc_keys);
-    if (oc != ~0ull && !CP_IN(oc + lc, b.pool_cap + 1, a.ctr)) {
-        atomicOr(&b.ctl->stop[r & 1u], 1u);
-        return;
+    ColSrc c;
+    c.off = column_at(b, q);
+    c.sm = sc;
+    if (c.off != ~0ull) {
+        c.len = __ldcg(b.clen + q);
+    } else {
+        uint32_t n = 0;
+        if (lane == 0) n = decode(*itc, mc, __ldcg(b.cmask + q), sc);
+        c.len = __shfl_sync(0xFFFFFFFFu, n, 0);
+        __syncwarp();
     }
-    const uint64_t low = oc != ~0ull ? __ldcg(b.pool + oc) : lc_keys[0];
+    if (c.off != ~0ull && !CP_IN(c.off + c.len, b.pool_cap + 1, a.ctr)) return stop(0);
+    const uint64_t low = c.off != ~0ull ? __ldcg(b.pool + c.off) : sc[0];
     const uint32_t eid = edge_id(a.tab, low);
-    if (!CP_IN(eid, b.n_ids, a.ctr)) {
-        atomicOr(&b.ctl->stop[r & 1u], 1u);
-        return;
-    }
+    if (!CP_IN(eid, b.n_ids, a.ctr)) return stop(0);
     const uint64_t kp = __ldcg(b.pivot + eid);
-    if (lc == 0u || kp >= kc) {  // only after an earlier error
-        set_status(a.ctr, kStInternal);
-        atomicOr(&b.ctl->stop[r & 1u], 1u);
-        return;
-    }
+    if (c.len == 0u || kp >= kc) return stop(kStInternal);  // only after an earlier error
     const Item& itp = a.tab.it[item_of_vertex(a.tab, key_vertex(kp))];
     const uint32_t p = cell_id3(itp, kp, true);
-    if (!CP_IN(p, b.n_ids, a.ctr)) {
-        atomicOr(&b.ctl->stop[r & 1u], 1u);
-        return;
+    if (!CP_IN(p, b.n_ids, a.ctr)) return stop(0);
+    ColSrc pc;
+    pc.off = column_at(b, p);
+    pc.sm = sp;
+    if (pc.off != ~0ull) {
+        pc.len = __ldcg(b.clen + p);
+    } else {
+        uint32_t n = 0;
+        if (lane == 0) n = decode(itp, int64_t(key_vertex(kp)) - itp.voff, __ldcg(b.cmask + p), sp);
+        pc.len = __shfl_sync(0xFFFFFFFFu, n, 0);
+        __syncwarp();
     }
-    const uint64_t op = column_at(b, p);
-    uint32_t lp;
-    if (op != ~0ull) lp = __ldcg(b.clen + p);
-    else lp = decode(itp, int64_t(key_vertex(kp)) - itp.voff, __ldcg(b.cmask + p), lp_keys);
-    if (op != ~0ull && !CP_IN(op + lp, b.pool_cap + 1, a.ctr)) {
-        atomicOr(&b.ctl->stop[r & 1u], 1u);
-        return;
-    }
-    const uint64_t need = uint64_t(lc) + lp - 2u;
-    if (need == 0u || need > 0x1FFFFFFFull) {  // empty: only after an earlier error; 2^29 entries: beyond
-        set_status(a.ctr, need ? kStCapacity : kStInternal);  // any volume this library takes
-        atomicOr(&b.ctl->stop[r & 1u], 1u);
-        return;
-    }
+    if (pc.off != ~0ull && !CP_IN(pc.off + pc.len, b.pool_cap + 1, a.ctr)) return stop(0);
+    const uint64_t need = uint64_t(c.len) + pc.len - 2u;
+    if (need == 0u || need > 0x1FFFFFFFull)  // empty: only after an earlier error; 2^29 entries: beyond
+        return stop(need ? kStCapacity : kStInternal);  // any volume this library takes
+    // the free region of q's pair, or a fresh pair twice the size needed
     uint64_t base = __ldcg(b.coff + q);
     uint32_t cap = base != ~0ull ? (__ldcg(b.ccap + q) & 0x7FFFFFFFu) : 0u;
-    const uint32_t side = base != ~0ull ? ((__ldcg(b.ccap + q) >> 31) ^ 1u) : 0u;  // the free region
-    uint32_t into = side;
-    if (need > cap) {  // a fresh pair of regions, twice the size needed
+    uint32_t into = base != ~0ull ? ((__ldcg(b.ccap + q) >> 31) ^ 1u) : 0u;
+    if (need > cap) {
         cap = 4u;
         while (cap < need) cap <<= 1;
         cap <<= 1;
-        base = atomicAdd(&b.ctl->grown, (unsigned long long)(2ull * cap));
-        if (base + 2ull * cap > b.pool_cap) {
-            set_status(a.ctr, kStCapacity);
-            atomicOr(&b.ctl->stop[r & 1u], 1u);
-            return;
-        }
+        uint64_t got = 0;
+        if (lane == 0) got = atomicAdd(&b.ctl->grown, (unsigned long long)(2ull * cap));
+        base = __shfl_sync(0xFFFFFFFFu, got, 0);
+        if (base + 2ull * cap > b.pool_cap) return stop(kStCapacity);
         into = 0u;
     }
-    const uint64_t at = base + (into ? uint64_t(cap) : 0ull);
-    auto gc = [&](uint32_t i) { return oc != ~0ull ? __ldcg(b.pool + oc + i) : lc_keys[i]; };
-    auto gp = [&](uint32_t i) { return op != ~0ull ? __ldcg(b.pool + op + i) : lp_keys[i]; };
-    uint64_t* out = b.pool + at;
-    uint32_t i = 1, j = 1, k = 0;
-    uint64_t x = i < lc ? gc(i) : 0, y = j < lp ? gp(j) : 0;
-    while (i < lc || j < lp) {
-        if (j >= lp || (i < lc && x > y)) {
-            out[k++] = x;
-            ++i;
-            x = i < lc ? gc(i) : 0;
-        } else if (i >= lc || y > x) {
-            out[k++] = y;
-            ++j;
-            y = j < lp ? gp(j) : 0;
-        } else {
-            ++i;
-            ++j;
-            x = i < lc ? gc(i) : 0;
-            y = j < lp ? gp(j) : 0;
-        }
+    const uint32_t k = warp_merge(b, c, pc, b.pool + base + (into ? uint64_t(cap) : 0ull));
+    if (lane == 0) {
+        __stcg(b.coff + q, base);
+        __stcg(b.ccap + q, cap | (into << 31));
+        __stcg(b.clen + q, k);
     }
-    __stcg(b.coff + q, base);
-    __stcg(b.ccap + q, cap | (into << 31));
-    __stcg(b.clen + q, k);
-    if (k == 0) {
-        set_status(a.ctr, kStInternal);
-        atomicOr(&b.ctl->stop[r & 1u], 1u);
-    }
+    if (k == 0) stop(kStInternal);
 }
 
 __global__ void __launch_bounds__(kRT) k_h1_reduce(const __grid_constant__ ReduceArgs a) {
@@ -525,6 +577,7 @@ __global__ void __launch_bounds__(kRT) k_h1_reduce(const __grid_constant__ Reduc
                       ctl->pos_q != b.exp_pos_q || ctl->nl > b.mcap))
         set_status(ctr, kStInternal);
     __shared__ uint32_t sh_n, sh_stop;
+    __shared__ uint64_t sh_col[kRT / 32][2][32];  // per warp: two star columns decoded
     uint32_t epoch = 0;
     const uint64_t t_start = global_timer_ns();  // read by thread 0 of the grid only
     uint32_t nchg = min(ctl->nl, b.mcap);  // round 0: every column that left its star
@@ -578,7 +631,9 @@ __global__ void __launch_bounds__(kRT) k_h1_reduce(const __grid_constant__ Reduc
         }
         if (gtid == 0) ctl->cnt[(r + 1u) % 3u] = 0u;  // the next round's bids (last read two rounds ago)
         // ---- every losing column adds the winner of its row
-        for (uint32_t i = gtid; i < nw; i += gstride) add_winner(a, __ldcg(work + i), r);
+        // (one warp per losing column: long columns are merged 32 lanes wide)
+        for (uint32_t i = gtid >> 5; i < nw; i += gstride >> 5)
+            add_winner_warp(a, __ldcg(work + i), r, sh_col[threadIdx.x >> 5][0], sh_col[threadIdx.x >> 5][1]);
         // the budget: one thread decides, every CTA reads the decision (this
         // round's stop word) after the next barrier, so all leave together
         if (gtid == 0 && global_timer_ns() - t_start > a.budget_ns) {
