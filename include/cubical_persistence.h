@@ -158,6 +158,47 @@ int cubical_persistence_3d(const float *d_image, const int64_t dims[3], cp_pair 
                            int64_t max_survivors, void *stream);
 
 /*
+ * Slab split of the two union-finds (the parallelisation across devices that
+ * Sec. 6 leaves to future work), run on one GPU.  The image is cut into
+ * n_slabs slabs along its slowest axis (z for a volume, y for an image;
+ * element c of that axis lies in slab c * n_slabs / extent).  After the
+ * pruning pass, each root class of the pruned forests belongs to the slab of
+ * the vertex its age key names (the outside vertex to slab 0), and a surviving
+ * edge (facet) is internal when both endpoint classes lie in one slab.
+ * Stage 1: the elder-rule union-find of every slab over its internal
+ * survivors (one launch; the slabs share no class).  Stage 2: one union-find
+ * over the survivors that stage 1 committed and those between slabs, in
+ * filtration order; it writes the pairs.  The result equals
+ * cubical_persistence_2d / _3d on the same image, pair for pair: a survivor
+ * that its slab does not commit closes a cycle of earlier survivors, so the
+ * whole image's union-find does not commit it either (Kruskal's minimum
+ * spanning forest; the keys are distinct).
+ *  n_slabs  : 1 .. 65536 (more slabs than planes leaves some empty).
+ *  h_stats  : host, optional: the split's counts (makes the call
+ *             synchronous).
+ *  d_workspace : ws_bytes >= cubical_persistence_slabs_workspace_size()
+ *             with the same n_slabs.
+ * Other arguments, ownership and errors as for cubical_persistence_2d /
+ * _3d.  CP_ERR_ARG also when cross-pruning of images is switched on
+ * (CP_TUNE_CROSS_PRUNE_2D = 1): both survivor lists must be ready before the
+ * union-finds.  CP_ERR_CAPACITY when the two survivor lists together exceed
+ * max_survivors.
+ */
+typedef struct cp_slab_stats {
+    int64_t survivors[2];    /* [0] H0 edges, [1] dual facets, after pruning */
+    int64_t internal[2];     /* survivors whose endpoint classes lie in one slab */
+    int64_t crossing[2];     /* survivors whose endpoint classes lie in two slabs */
+    int64_t committed[2];    /* internal survivors that their slab's union-find committed */
+    int64_t merged[2];       /* survivors of stage 2: committed + crossing */
+    int64_t rounds_slab[2];  /* rounds of stage 1 (its slowest slab) */
+    int64_t rounds_merge[2]; /* rounds of stage 2 */
+} cp_slab_stats;
+size_t cubical_persistence_slabs_workspace_size(int ndim, const int64_t *dims, int n_slabs, int64_t max_survivors);
+int cubical_persistence_slabs(int ndim, const float *d_image, const int64_t *dims, int n_slabs, cp_pair *d_out_pairs,
+                              int64_t capacity, int64_t *h_out_count, int64_t *d_out_count, void *d_workspace,
+                              size_t ws_bytes, int64_t max_survivors, void *stream, cp_slab_stats *h_stats);
+
+/*
  * T-filtration (the T-construction of Sec. 2.2; the paper leaves it to future
  * work in Sec. 6): the pixel values sit on the top cells of the lattice
  * complex [0,H]x[0,W] (x[0,D]), and every other cell takes the smallest value

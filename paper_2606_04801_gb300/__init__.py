@@ -12,5 +12,6 @@ from .api import (  # noqa: F401
     persistence_batched,
     persistence_full,
     persistence_full_batched,
+    persistence_slabs,
 )
 from .batched import BatchedPersistence  # noqa: F401

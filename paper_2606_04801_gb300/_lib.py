@@ -52,6 +52,13 @@ class CpStats(ctypes.Structure):
     ]
 
 
+class CpSlabStats(ctypes.Structure):
+    _fields_ = [
+        (name, ctypes.c_int64 * 2)
+        for name in ("survivors", "internal", "crossing", "committed", "merged", "rounds_slab", "rounds_merge")
+    ]
+
+
 # name -> (restype, argtypes); must match include/cubical_persistence.h
 _P = ctypes.c_void_p
 _I64 = ctypes.c_int64
@@ -63,6 +70,12 @@ _SIGS = {
     "cubical_persistence_workspace_size": (ctypes.c_size_t, [ctypes.c_int, _P, _I64]),
     "cubical_persistence_2d": (ctypes.c_int, [_P, _P, _P, _I64, _P, _P, _P, ctypes.c_size_t, _I64, _P]),
     "cubical_persistence_3d": (ctypes.c_int, [_P, _P, _P, _I64, _P, _P, _P, ctypes.c_size_t, _I64, _P]),
+    "cubical_persistence_slabs_workspace_size": (ctypes.c_size_t, [ctypes.c_int, _P, ctypes.c_int, _I64]),
+    "cubical_persistence_slabs": (
+        ctypes.c_int,
+        [ctypes.c_int, _P, _P, ctypes.c_int, _P, _I64, _P, _P, _P, ctypes.c_size_t, _I64, _P,
+         ctypes.POINTER(CpSlabStats)],
+    ),
     "cubical_persistence_t_workspace_size": (ctypes.c_size_t, [ctypes.c_int, _P, _I64]),
     "cubical_persistence_t_2d": (ctypes.c_int, [_P, _P, _P, _I64, _P, _P, _P, ctypes.c_size_t, _I64, _P]),
     "cubical_persistence_t_3d": (ctypes.c_int, [_P, _P, _P, _I64, _P, _P, _P, ctypes.c_size_t, _I64, _P]),

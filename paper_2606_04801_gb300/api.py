@@ -147,6 +147,49 @@ def persistence(img: torch.Tensor, max_survivors: int = 0, with_stats: bool = Fa
     raise CpError(CP_ERR_CAPACITY, "cubical_persistence (after growing the workspace)")
 
 
+def persistence_slabs(img: torch.Tensor, n_slabs: int, max_survivors: int = 0) -> Diagram:
+    """The pairs of ``persistence(img)``, with the union-finds split into
+    ``n_slabs`` slabs along the slowest axis: each slab's union-find over the
+    survivors inside it, then one union-find over what the slabs committed and
+    the survivors between slabs.  ``stats`` holds the split's counts
+    (per list: [H0, top dimension])."""
+    _check_image(img)
+    if int(n_slabs) < 1:
+        raise ValueError("n_slabs must be at least 1")
+    lib = _lib.load()
+    img = img.contiguous()
+    nd = img.dim()
+    dims = (ctypes.c_int64 * nd)(*img.shape)
+    n = img.numel()
+    n_all = n + int(np.prod([s - 1 for s in img.shape])) + 1
+    ms = int(max_survivors)
+    for _ in range(4):
+        ws_bytes = lib.cubical_persistence_slabs_workspace_size(nd, dims, int(n_slabs), ms)
+        if ws_bytes == 0:
+            raise CpError(_lib.CP_ERR_ARG, "slabs workspace size")
+        ws = torch.empty(ws_bytes, dtype=torch.uint8, device=img.device)
+        eff = ms if ms > 0 else n // 2 + 65536
+        cap = min(n_all, eff + 4096)
+        out = torch.empty((cap, 8), dtype=torch.int32, device=img.device)
+        cnt = ctypes.c_int64(0)
+        sst = _lib.CpSlabStats()
+        rc = lib.cubical_persistence_slabs(
+            nd, ctypes.c_void_p(img.data_ptr()), dims, int(n_slabs), ctypes.c_void_p(out.data_ptr()), cap,
+            ctypes.byref(cnt), None, ctypes.c_void_p(ws.data_ptr()), ws_bytes, ms,
+            ctypes.c_void_p(_stream_ptr(img.device)), ctypes.byref(sst),
+        )
+        if rc == CP_ERR_CAPACITY:
+            st = _stats(ws)
+            # the two survivor lists sit side by side in the scratch lists
+            ms = max(_grow(st, eff, n), int(1.25 * (st["h0_survivors"] + st["top_survivors"])) + 65536)
+            continue
+        if rc != CP_OK:
+            raise CpError(rc, "cubical_persistence_slabs")
+        stats = {k: [int(v) for v in getattr(sst, k)] for k, _ in _lib.CpSlabStats._fields_}
+        return Diagram(out[: cnt.value], stats)
+    raise CpError(CP_ERR_CAPACITY, "cubical_persistence_slabs (after growing the workspace)")
+
+
 def persistence_batched(imgs: Sequence[torch.Tensor], max_survivors: int = 0, with_stats: bool = False,
                         filtration: str = "V") -> Diagram:
     """Pairs of many images and volumes in one pass; each pair carries its item index.

@@ -97,6 +97,10 @@ struct Plan {
     size_t h1_words = 0;
     size_t o_h1_neg, o_h1_pos, o_h1_ctl, o_h1_cmask, o_h1_coff, o_h1_clen, o_h1_ccap, o_h1_list0, o_h1_l0, o_h1_l1,
         o_h1_piv, o_h1_pool;
+    // slab split of the union-finds (calls that ask for it): slabs per item
+    // and the buffers of cp_slab.cu
+    int slabs = 0;
+    size_t o_sl_ctr, o_sl_flag, o_sl_vcnt, o_sl_k0, o_sl_k1, o_sl_act, o_sl_a, o_sl_b, o_sl_map;
     size_t bytes = 0;
 };
 
@@ -244,6 +248,33 @@ int make_plan(int n_items, const int32_t* ndims, const int64_t* dims, const floa
         P.o_h1_piv = take(sizeof(uint64_t) * ids);
         P.o_h1_pool = take(sizeof(uint64_t) * P.h1_pool);
     }
+    P.bytes = o;
+    return CP_OK;
+}
+
+// Appends the slab split's buffers to a plan: S slabs per item (each item
+// cut along its slowest axis).  Both survivor lists must sit side by side in
+// the scratch lists, so 2D items with cross-pruning are refused.
+int plan_slabs(Plan& P, int S) {
+    if (S < 1 || S > (1 << 16)) return CP_ERR_ARG;
+    if (P.tab.n2d > 0 && P.tab.cross2d) return CP_ERR_ARG;
+    if (P.h1) return CP_ERR_ARG;
+    size_t o = P.bytes;
+    auto take = [&](size_t bytes) {
+        size_t at = o;
+        o = align_up(o + bytes);
+        return at;
+    };
+    P.slabs = S;
+    P.o_sl_ctr = take(sizeof(SlabCtr));
+    P.o_sl_flag = take(size_t(P.cap_s));
+    P.o_sl_vcnt = take(sizeof(uint32_t) * slab_vblocks_cap(P.cap_s));
+    P.o_sl_k0 = take(sizeof(uint64_t) * P.cap_s);
+    P.o_sl_k1 = take(sizeof(uint64_t) * P.cap_s);
+    P.o_sl_act = take(sizeof(uint32_t) * P.cap_s);
+    P.o_sl_a = take(sizeof(uint32_t) * P.cap_s);
+    P.o_sl_b = take(sizeof(uint32_t) * P.cap_s);
+    P.o_sl_map = take(sizeof(uint32_t) * P.cap_s);
     P.bytes = o;
     return CP_OK;
 }
@@ -510,6 +541,68 @@ int run(const Plan& P, cp_pair* d_out, int64_t capacity, int64_t* h_out_count, i
         mark(4, s);
         CP_TRY(launch_uf(P.tab, &up[1], 1, s));
         mark(5, s);
+    } else if (P.slabs > 0) {
+        // slab split: each slab's union-find over the survivors inside it (one
+        // launch for all slabs), then one union-find over what they committed
+        // and the survivors between slabs
+        mark(3, s);
+        g_ev_joint = true;
+        SlabCtr* sc = at<SlabCtr>(ws, P.o_sl_ctr);
+        CP_TRY(cudaMemsetAsync(sc, 0, sizeof(SlabCtr), s));
+        SlabArgs sa;
+        sa.tab = P.tab;
+        sa.S = P.slabs;
+        sa.d_n[0] = &ctr->n_s0;
+        sa.d_n[1] = &ctr->n_st;
+        sa.cap = P.cap_s;
+        sa.keys[0] = s0;
+        sa.keys[1] = st;
+        sa.age[0] = age0;
+        sa.age[1] = aget;
+        sa.n_rids[0] = P.cap_r0;
+        sa.n_rids[1] = P.cap_rt;
+        sa.res[0] = res0;
+        sa.res[1] = rest;
+        sa.na = na0;
+        sa.nb = nb0;
+        sa.flag = at<uint8_t>(ws, P.o_sl_flag);
+        sa.vcnt = at<uint32_t>(ws, P.o_sl_vcnt);
+        sa.sc = sc;
+        sa.ctr = ctr;
+        sa.ko[0] = at<uint64_t>(ws, P.o_sl_k0);
+        sa.ko[1] = at<uint64_t>(ws, P.o_sl_k1);
+        sa.act = at<uint32_t>(ws, P.o_sl_act);
+        sa.oa = at<uint32_t>(ws, P.o_sl_a);
+        sa.ob = at<uint32_t>(ws, P.o_sl_b);
+        sa.map = at<uint32_t>(ws, P.o_sl_map);
+        sa.log = salt;
+        CP_TRY(launch_slab_classify(sa, s));
+        CP_TRY(launch_slab_compact(sa, 0, sc->n_in, s));
+        // stage 1 works on its own active lists: the full lists' root ids in
+        // na0 / nb0 stay for stage 2
+        UfParams u[2] = {up[0], up[1]};
+        for (int q = 0; q < 2; ++q) {
+            u[q].keys = sa.ko[q];
+            u[q].d_nkeys = &sc->n_in[q];
+            u[q].act[0] = sa.act;
+            u[q].na[0] = sa.oa;
+            u[q].nb[0] = sa.ob;
+            u[q].pairs = nullptr;
+            u[q].h1flags = nullptr;
+            u[q].dual_keys = nullptr;
+            u[q].d_ndual = nullptr;
+        }
+        CP_TRY(launch_uf(P.tab, u, 2, s));
+        CP_TRY(launch_slab_mark(sa, s));
+        sa.map = nullptr;
+        CP_TRY(launch_slab_compact(sa, 1, sc->n_merge, s));
+        for (int q = 0; q < 2; ++q) {
+            u[q].d_nkeys = &sc->n_merge[q];
+            u[q].pairs = up[q].pairs;
+        }
+        CP_TRY(launch_uf(P.tab, u, 2, s));
+        mark(4, s);
+        mark(5, s);
     } else {
         // both union-finds share one launch and its rounds (the dual list after
         // the H0 list)
@@ -756,6 +849,53 @@ int cubical_persistence_3d(const float* d_image, const int64_t dims[3], cp_pair*
                            int64_t max_survivors, void* stream) {
     return single(3, d_image, dims, d_out_pairs, capacity, h_out_count, d_out_count, d_workspace, ws_bytes,
                   max_survivors, stream);
+}
+
+size_t cubical_persistence_slabs_workspace_size(int ndim, const int64_t* dims, int n_slabs, int64_t max_survivors) {
+    if ((ndim != 2 && ndim != 3) || !dims) return 0;
+    int32_t nd = ndim;
+    int64_t d3[3] = {ndim == 3 ? dims[0] : 1, dims[ndim - 2], dims[ndim - 1]};
+    Plan P;
+    if (make_plan(1, &nd, d3, nullptr, max_survivors, P) != CP_OK) return 0;
+    if (plan_slabs(P, n_slabs) != CP_OK) return 0;
+    return P.bytes;
+}
+
+int cubical_persistence_slabs(int ndim, const float* d_image, const int64_t* dims, int n_slabs, cp_pair* d_out_pairs,
+                              int64_t capacity, int64_t* h_out_count, int64_t* d_out_count, void* d_workspace,
+                              size_t ws_bytes, int64_t max_survivors, void* stream, cp_slab_stats* h_stats) {
+    if ((ndim != 2 && ndim != 3) || !d_image || !dims) return CP_ERR_ARG;
+    int32_t nd = ndim;
+    int64_t d3[3] = {ndim == 3 ? dims[0] : 1, dims[ndim - 2], dims[ndim - 1]};
+    Plan P;
+    int rc = make_plan(1, &nd, d3, &d_image, max_survivors, P);
+    if (rc != CP_OK) return rc;
+    rc = plan_slabs(P, n_slabs);
+    if (rc != CP_OK) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    rc = run(P, d_out_pairs, capacity, h_out_count, d_out_count, d_workspace, ws_bytes, s);
+    if (!h_stats || rc == CP_ERR_ARG || rc == CP_ERR_CUDA) return rc;
+    Counters h;
+    SlabCtr hs;
+    if (cudaMemcpyAsync(&h, at<Counters>(d_workspace, P.o_ctr), sizeof(Counters), cudaMemcpyDeviceToHost, s) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(&hs, at<SlabCtr>(d_workspace, P.o_sl_ctr), sizeof(SlabCtr), cudaMemcpyDeviceToHost, s) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return CP_ERR_CUDA;
+    std::memset(h_stats, 0, sizeof(*h_stats));
+    h_stats->survivors[0] = h.n_s0;
+    h_stats->survivors[1] = h.n_st;
+    h_stats->rounds_merge[0] = h.rounds0;
+    h_stats->rounds_merge[1] = h.roundst;
+    for (int q = 0; q < 2; ++q) {
+        h_stats->internal[q] = hs.n_in[q];
+        h_stats->crossing[q] = hs.n_cross[q];
+        h_stats->committed[q] = hs.n_event[q];
+        h_stats->merged[q] = hs.n_merge[q];
+        h_stats->rounds_slab[q] = hs.rounds_slab[q];
+    }
+    return rc != CP_OK ? rc : status_to_code(h.status);
 }
 
 size_t cubical_persistence_t_workspace_size(int ndim, const int64_t* dims, int64_t max_survivors) {

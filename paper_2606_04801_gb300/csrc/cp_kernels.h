@@ -81,7 +81,7 @@ struct UfParams {
     uint32_t* onode;
     uint32_t scratch_cap;     // entries of act / na / nb / ynode / onode and of log
     uint64_t* log;            // per survivor: young root << 32 | its age id, or ~0 (no commit)
-    cp_pair* pairs;
+    cp_pair* pairs;           // nullptr: commits are logged, no pairs written
     uint32_t pair_cap;
     uint64_t* dual_keys;      // H0 of 2D items: positive edges that the dual needs (cross-pruning)
     uint32_t* d_ndual;
@@ -125,6 +125,47 @@ cudaError_t launch_place_roots(const RootArgs& r, cudaStream_t s);
 // the same rounds.  Two problems share the scratch lists (the pointers of p[0])
 // side by side when both fit, else they run one after the other.
 cudaError_t launch_uf(const ItemTable& tab, const UfParams* p, int nprob, cudaStream_t s);
+
+// ---- slab decomposition of the union-finds (cp_slab.cu)
+struct SlabCtr {
+    uint32_t n_in[2];        // stage 1 survivors (both endpoint classes in one slab), per list
+    uint32_t n_cross[2];     // survivors whose endpoint classes lie in two slabs
+    uint32_t n_event[2];     // stage 1 survivors that committed
+    uint32_t n_merge[2];     // stage 2 survivors (committed + crossing)
+    uint32_t rounds_slab[2]; // rounds of stage 1
+    uint32_t pad[2];
+};
+struct SlabArgs {
+    ItemTable tab;
+    int S;                       // slabs per item
+    const uint32_t* d_n[2];      // survivors of the H0 and dual lists (device counts)
+    uint32_t cap;                // scratch capacity (the two lists side by side)
+    const uint64_t* keys[2];     // the sorted lists
+    const uint64_t* age[2];      // age of each root id, per list
+    uint32_t n_rids[2];          // root ids per list
+    uint64_t* res[2];            // reservation word of each root id, per list
+    const uint32_t* na;          // root ids of both endpoints of every slot (list 1 after list 0)
+    const uint32_t* nb;
+    uint8_t* flag;               // per slot: 1 internal, 2 crossing, 3 committed in stage 1
+    uint32_t* vcnt;              // per virtual block of the compaction: count, then offset
+    SlabCtr* sc;
+    Counters* ctr;
+    uint64_t* ko[2];             // compaction output: the selected keys of each list
+    uint32_t* act;               // and the active lists (survivor index, root ids), side by side
+    uint32_t* oa;
+    uint32_t* ob;
+    uint32_t* map;               // stage 1 only: the slot each selected survivor came from
+    const uint64_t* log;         // stage 1's commit log (read by the marking pass)
+};
+// Entries of SlabArgs::vcnt for a scratch capacity.
+uint32_t slab_vblocks_cap(uint32_t cap);
+// Flags each slot internal or crossing (kStCapacity if the lists are not side by side).
+cudaError_t launch_slab_classify(const SlabArgs& a, cudaStream_t s);
+// Stable compaction of the slots selected by sel (0: internal, 1: crossing or
+// committed) to ko / act / oa / ob (/ map); n_out[q] receives list q's count.
+cudaError_t launch_slab_compact(const SlabArgs& a, int sel, uint32_t* n_out, cudaStream_t s);
+// After stage 1: flags its committed survivors, then clears the reservation words.
+cudaError_t launch_slab_mark(const SlabArgs& a, cudaStream_t s);
 
 // ---- H1 of volumes (cp_h1.cu): column reduction of the square-edge boundary
 // matrix restricted to the squares that do not create 2-cycles and the edges

@@ -707,6 +707,7 @@ __device__ void uf_rounds(const UfKernelArgs& args, uint32_t n0, uint32_t n1, ui
     for (int q = 0; q < 2; ++q) {
         if (!((live >> q) & 1u)) continue;
         const UfParams& p = args.p[q];
+        if (!p.pairs) continue;  // the commit log is the result (the first stage of a slab split)
         const uint64_t* log = p.log + (q ? base1 : 0u);
         for (uint32_t i0 = blockIdx.x * kT; i0 < ninit[q]; i0 += gstride) {
             const uint32_t i = i0 + threadIdx.x;
