@@ -899,6 +899,121 @@ def run_full(args):
         torch.distributed.destroy_process_group()
 
 
+def run_slabs(args):
+    """The slab split of the union-finds on the 512^3 volume (forward, H0 + H2
+    pairs): per slab count, the time per call, the stage times and what stage
+    1 hands to stage 2 (the records a multi-device run would exchange, 24
+    bytes each); the unsplit forward timed the same way beside it."""
+    import torch
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        torch.distributed.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import paper_2606_04801_gb300 as cp
+    from paper_2606_04801_gb300 import _lib, autotune
+
+    lib = _lib.load()
+    vol = _volume(rank)
+    N = vol.size
+    x = torch.from_numpy(vol).to(dev)
+    autotune.autotune([x])
+    stream = torch.cuda.current_stream(dev)
+    sp = ctypes.c_void_p(int(stream.cuda_stream))
+    dims = (ctypes.c_int64 * 3)(SIDE, SIDE, SIDE)
+    cap = N // 2 + 65536 + 4096
+    out = torch.empty((cap, 8), dtype=torch.int32, device=dev)
+    dcount = torch.zeros(1, dtype=torch.int64, device=dev)
+    slab_counts = [int(v) for v in args.slabs.split(",")]
+    gpu_index = int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[local]) if os.environ.get("CUDA_VISIBLE_DEVICES") else local
+
+    def timed(call, wsp):
+        for _ in range(args.warmup):
+            call()
+        torch.cuda.synchronize(dev)
+        st = cp.api._stats(wsp)
+        if st["rc"] != 0:
+            raise cp.CpError(st["rc"], "slabs warm-up")
+        stage = (ctypes.c_float * 6)()
+        stage_sum = [0.0] * 6
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        lib.cp_profile(1)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            call()
+            if lib.cp_stage_times(stage, 6) == 6:
+                for i in range(6):
+                    stage_sum[i] += stage[i]
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        lib.cp_profile(0)
+        st = cp.api._stats(wsp)
+        if st["rc"] != 0:
+            raise cp.CpError(st["rc"], "slabs timed steps")
+        return ev0.elapsed_time(ev1) / args.steps, [v / args.steps for v in stage_sum], st
+
+    # the unsplit forward
+    pws = lib.cubical_persistence_workspace_size(3, dims, 0)
+    pwsp = torch.empty(pws, dtype=torch.uint8, device=dev)
+
+    def plain():
+        rc = lib.cubical_persistence_3d(ctypes.c_void_p(x.data_ptr()), dims, ctypes.c_void_p(out.data_ptr()), cap, None,
+                                        ctypes.c_void_p(dcount.data_ptr()), ctypes.c_void_p(pwsp.data_ptr()), pws, 0, sp)
+        if rc != 0:
+            raise cp.CpError(rc, "forward")
+
+    sweep = []
+    with Clocks(gpu_index) as clk:
+        plain_ms, plain_stages, pst = timed(plain, pwsp)
+        ref = out[: int(dcount.item())].clone()
+        del pwsp
+        for S in slab_counts:
+            wsb = lib.cubical_persistence_slabs_workspace_size(3, dims, S, 0)
+            wsp = torch.empty(wsb, dtype=torch.uint8, device=dev)
+            sst = _lib.CpSlabStats()
+
+            def split(S=S, wsp=wsp, wsb=wsb):
+                rc = lib.cubical_persistence_slabs(3, ctypes.c_void_p(x.data_ptr()), dims, S, ctypes.c_void_p(out.data_ptr()),
+                                                   cap, None, ctypes.c_void_p(dcount.data_ptr()),
+                                                   ctypes.c_void_p(wsp.data_ptr()), wsb, 0, sp, None)
+                if rc != 0:
+                    raise cp.CpError(rc, "slabs")
+
+            ms, stages, st = timed(split, wsp)
+            rc = lib.cubical_persistence_slabs(3, ctypes.c_void_p(x.data_ptr()), dims, S, ctypes.c_void_p(out.data_ptr()),
+                                               cap, None, ctypes.c_void_p(dcount.data_ptr()), ctypes.c_void_p(wsp.data_ptr()),
+                                               wsb, 0, sp, ctypes.byref(sst))
+            if rc != 0:
+                raise cp.CpError(rc, "slabs stats")
+            same = bool(torch.equal(out[: int(dcount.item())], ref))
+            sd = {k: [int(v) for v in getattr(sst, k)] for k, _ in _lib.CpSlabStats._fields_}
+            sweep.append({"slabs": S, "ms": ms, "same_as_unsplit": same,
+                          "stages_ms": {"prune": stages[0], "roots+sort": stages[1], "stage1": stages[2],
+                                        "stage2": stages[4], "emit": stages[5]},
+                          "exchange_bytes": 24 * (sd["merged"][0] + sd["merged"][1]), **sd})
+            del wsp
+    if rank == 0:
+        first = sweep[0]
+        print(json.dumps({
+            "metric": f"Mvoxels/s, H0 + H2 pairs ({SIDE}^3 fp32), union-finds split into slabs, forward",
+            "value": N / (first["ms"] / 1e3) / 1e6, "unit": "Mvoxels/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": first["ms"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"3D {SIDE}^3 float32 blurred noise (sigma 3 vox), slab split into {first['slabs']} "
+                                   "slabs along z (first entry of the sweep)",
+                       "l2": "input larger than L2; no flush", "parallelism": "single"},
+            "unsplit": {"ms": plain_ms, "stages_ms": {"prune": plain_stages[0], "roots+sort": plain_stages[1],
+                                                      "uf": plain_stages[2], "emit": plain_stages[5]},
+                        "survivors": [pst["h0_survivors"], pst["top_survivors"]],
+                        "rounds": [pst["h0_rounds"], pst["top_rounds"]]},
+            "sweep": sweep,
+            "clocks": clk.summary(),
+        }), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -909,11 +1024,13 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--side", type=int, default=512, help="cube side (512 is the benchmark; smaller for profiling)")
     ap.add_argument("--no-batched", action="store_true")
-    ap.add_argument("--workload", default="volume", choices=["volume", "batched", "survivors", "tfilt", "2d", "full"],
+    ap.add_argument("--workload", default="volume",
+                    choices=["volume", "batched", "survivors", "tfilt", "2d", "full", "slabs"],
                     help="volume: the 512^3 plain path (the headline line); batched: the batched fwd + bwd workload "
                     "alone; survivors: survivor fractions S/N of every config; tfilt: the T-filtration on 510^3; "
                     "2d: the 2048x2048 random field and its 256-level form; full: the whole diagram (H0, H1, H2) "
-                    "of the 512^3 volume")
+                    "of the 512^3 volume; slabs: the slab split of the union-finds on the 512^3 volume")
+    ap.add_argument("--slabs", default="2,4,8,16,64,152", help="slab counts of the slabs workload (comma-separated)")
     ap.add_argument("--eager", action="store_true", help="batched workload without the CUDA graph (per-kernel profiling)")
     args = ap.parse_args()
     global SIDE
@@ -937,6 +1054,9 @@ def main():
         return
     if args.workload == "full":
         run_full(args)
+        return
+    if args.workload == "slabs":
+        run_slabs(args)
         return
 
     import torch

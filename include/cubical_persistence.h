@@ -164,15 +164,20 @@ int cubical_persistence_3d(const float *d_image, const int64_t dims[3], cp_pair 
  * element c of that axis lies in slab c * n_slabs / extent).  After the
  * pruning pass, each root class of the pruned forests belongs to the slab of
  * the vertex its age key names (the outside vertex to slab 0), and a surviving
- * edge (facet) is internal when both endpoint classes lie in one slab.
- * Stage 1: the elder-rule union-find of every slab over its internal
- * survivors (one launch; the slabs share no class).  Stage 2: one union-find
- * over the survivors that stage 1 committed and those between slabs, in
- * filtration order; it writes the pairs.  The result equals
- * cubical_persistence_2d / _3d on the same image, pair for pair: a survivor
- * that its slab does not commit closes a cycle of earlier survivors, so the
- * whole image's union-find does not commit it either (Kruskal's minimum
- * spanning forest; the keys are distinct).
+ * edge (facet) is internal when both endpoint classes lie in one slab,
+ * crossing otherwise.
+ *  Stage 1: the elder-rule union-find of every slab over its internal
+ *  survivors (one launch; the slabs share no class).  A commit whose dying
+ *  class has met no crossing survivor (no root of that class is an endpoint
+ *  of one) writes its pair here: the whole image's union-find kills the same
+ *  class then.  Every other commit is handed to stage 2 with its endpoints
+ *  replaced by the two classes' roots at its time.
+ *  Stage 2: one union-find over the handed-on commits and the crossing
+ *  survivors, in filtration order; it writes the other pairs.
+ * The result equals cubical_persistence_2d / _3d on the same image, pair for
+ * pair.  Across devices, stage 2's input is what the slabs would exchange
+ * (the boundary part of each slab's merge forest plus the crossing
+ * survivors); h_stats reports its size.
  *  n_slabs  : 1 .. 65536 (more slabs than planes leaves some empty).
  *  h_stats  : host, optional: the split's counts (makes the call
  *             synchronous).
@@ -189,7 +194,8 @@ typedef struct cp_slab_stats {
     int64_t internal[2];     /* survivors whose endpoint classes lie in one slab */
     int64_t crossing[2];     /* survivors whose endpoint classes lie in two slabs */
     int64_t committed[2];    /* internal survivors that their slab's union-find committed */
-    int64_t merged[2];       /* survivors of stage 2: committed + crossing */
+    int64_t final_pairs[2];  /* of those, the ones whose pairs stage 1 wrote (zero persistence included) */
+    int64_t merged[2];       /* survivors of stage 2: committed - final_pairs + crossing */
     int64_t rounds_slab[2];  /* rounds of stage 1 (its slowest slab) */
     int64_t rounds_merge[2]; /* rounds of stage 2 */
 } cp_slab_stats;
@@ -491,7 +497,9 @@ long long cp_launch_count(void);
  * includes the first-round root walks of its list.  In a call with volumes
  * only, both lists are walked and sorted together and both union-finds run in
  * one launch: ms[1] and ms[2] hold those joint times and ms[3], ms[4] are 0.
- * cp_profile(0) stops recording.  Not thread-safe across concurrent calls.
+ * In a cubical_persistence_slabs call, ms[2] holds stage 1 (the split and the
+ * slabs' union-finds) and ms[4] stage 2 (marking, compaction and the merge
+ * union-find).  cp_profile(0) stops recording.  Not thread-safe across concurrent calls.
  */
 int cp_profile(int enable);
 int cp_stage_times(float *ms, int cap);

@@ -55,7 +55,8 @@ class CpStats(ctypes.Structure):
 class CpSlabStats(ctypes.Structure):
     _fields_ = [
         (name, ctypes.c_int64 * 2)
-        for name in ("survivors", "internal", "crossing", "committed", "merged", "rounds_slab", "rounds_merge")
+        for name in ("survivors", "internal", "crossing", "committed", "final_pairs", "merged", "rounds_slab",
+                     "rounds_merge")
     ]
 
 

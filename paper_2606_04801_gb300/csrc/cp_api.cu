@@ -100,7 +100,8 @@ struct Plan {
     // slab split of the union-finds (calls that ask for it): slabs per item
     // and the buffers of cp_slab.cu
     int slabs = 0;
-    size_t o_sl_ctr, o_sl_flag, o_sl_vcnt, o_sl_k0, o_sl_k1, o_sl_act, o_sl_a, o_sl_b, o_sl_map;
+    size_t o_sl_ctr, o_sl_flag, o_sl_vcnt, o_sl_k0, o_sl_k1, o_sl_act, o_sl_a, o_sl_b, o_sl_map, o_sl_sub0,
+        o_sl_sub1, o_sl_died0, o_sl_died1;
     size_t bytes = 0;
 };
 
@@ -275,6 +276,10 @@ int plan_slabs(Plan& P, int S) {
     P.o_sl_a = take(sizeof(uint32_t) * P.cap_s);
     P.o_sl_b = take(sizeof(uint32_t) * P.cap_s);
     P.o_sl_map = take(sizeof(uint32_t) * P.cap_s);
+    P.o_sl_sub0 = take(sizeof(uint32_t) * P.cap_r0);
+    P.o_sl_sub1 = take(sizeof(uint32_t) * P.cap_rt);
+    P.o_sl_died0 = take(sizeof(uint32_t) * P.cap_r0);
+    P.o_sl_died1 = take(sizeof(uint32_t) * P.cap_rt);
     P.bytes = o;
     return CP_OK;
 }
@@ -565,6 +570,12 @@ int run(const Plan& P, cp_pair* d_out, int64_t capacity, int64_t* h_out_count, i
         sa.res[1] = rest;
         sa.na = na0;
         sa.nb = nb0;
+        sa.sub[0] = at<uint32_t>(ws, P.o_sl_sub0);
+        sa.sub[1] = at<uint32_t>(ws, P.o_sl_sub1);
+        sa.died[0] = at<uint32_t>(ws, P.o_sl_died0);
+        sa.died[1] = at<uint32_t>(ws, P.o_sl_died1);
+        sa.pairs = pairs;
+        sa.pair_cap = P.cap_p;
         sa.flag = at<uint8_t>(ws, P.o_sl_flag);
         sa.vcnt = at<uint32_t>(ws, P.o_sl_vcnt);
         sa.sc = sc;
@@ -579,7 +590,8 @@ int run(const Plan& P, cp_pair* d_out, int64_t capacity, int64_t* h_out_count, i
         CP_TRY(launch_slab_classify(sa, s));
         CP_TRY(launch_slab_compact(sa, 0, sc->n_in, s));
         // stage 1 works on its own active lists: the full lists' root ids in
-        // na0 / nb0 stay for stage 2
+        // na0 / nb0 stay for stage 2 (the marking pass rewrites the slots of
+        // the commits it hands on)
         UfParams u[2] = {up[0], up[1]};
         for (int q = 0; q < 2; ++q) {
             u[q].keys = sa.ko[q];
@@ -593,6 +605,7 @@ int run(const Plan& P, cp_pair* d_out, int64_t capacity, int64_t* h_out_count, i
             u[q].d_ndual = nullptr;
         }
         CP_TRY(launch_uf(P.tab, u, 2, s));
+        mark(4, s);  // stage times: stage 1 in the union-find slot, stage 2 in the dual one
         CP_TRY(launch_slab_mark(sa, s));
         sa.map = nullptr;
         CP_TRY(launch_slab_compact(sa, 1, sc->n_merge, s));
@@ -601,7 +614,6 @@ int run(const Plan& P, cp_pair* d_out, int64_t capacity, int64_t* h_out_count, i
             u[q].pairs = up[q].pairs;
         }
         CP_TRY(launch_uf(P.tab, u, 2, s));
-        mark(4, s);
         mark(5, s);
     } else {
         // both union-finds share one launch and its rounds (the dual list after
@@ -891,7 +903,8 @@ int cubical_persistence_slabs(int ndim, const float* d_image, const int64_t* dim
     for (int q = 0; q < 2; ++q) {
         h_stats->internal[q] = hs.n_in[q];
         h_stats->crossing[q] = hs.n_cross[q];
-        h_stats->committed[q] = hs.n_event[q];
+        h_stats->committed[q] = int64_t(hs.n_sent[q]) + hs.n_final[q];
+        h_stats->final_pairs[q] = hs.n_final[q];
         h_stats->merged[q] = hs.n_merge[q];
         h_stats->rounds_slab[q] = hs.rounds_slab[q];
     }

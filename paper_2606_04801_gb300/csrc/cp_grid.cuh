@@ -18,6 +18,11 @@ __host__ __device__ __forceinline__ uint32_t cell_id3(const Item& it, uint64_t k
     return uint32_t(3 * corner + axis);
 }
 
+// Union-find reservation word of a root that has died: this mark in the
+// high half (above every reservation stamp, whose high half is the round)
+// and the root id it was linked under in the low half.
+constexpr uint64_t kDead = 0xFFFFFFFF00000000ull;
+
 #ifdef __CUDACC__
 // Grid-wide barrier for a cooperative launch (all CTAs co-resident): a
 // monotonic arrival counter (zeroed before the launch).  Barrier number e of

@@ -130,10 +130,10 @@ cudaError_t launch_uf(const ItemTable& tab, const UfParams* p, int nprob, cudaSt
 struct SlabCtr {
     uint32_t n_in[2];        // stage 1 survivors (both endpoint classes in one slab), per list
     uint32_t n_cross[2];     // survivors whose endpoint classes lie in two slabs
-    uint32_t n_event[2];     // stage 1 survivors that committed
-    uint32_t n_merge[2];     // stage 2 survivors (committed + crossing)
+    uint32_t n_sent[2];      // stage 1 commits handed to stage 2
+    uint32_t n_merge[2];     // stage 2 survivors (sent + crossing)
     uint32_t rounds_slab[2]; // rounds of stage 1
-    uint32_t pad[2];
+    uint32_t n_final[2];     // stage 1 commits whose pairs stage 1 wrote (their dying class met no crossing survivor)
 };
 struct SlabArgs {
     ItemTable tab;
@@ -144,9 +144,12 @@ struct SlabArgs {
     const uint64_t* age[2];      // age of each root id, per list
     uint32_t n_rids[2];          // root ids per list
     uint64_t* res[2];            // reservation word of each root id, per list
-    const uint32_t* na;          // root ids of both endpoints of every slot (list 1 after list 0)
-    const uint32_t* nb;
-    uint8_t* flag;               // per slot: 1 internal, 2 crossing, 3 committed in stage 1
+    uint32_t* na;                // root ids of both endpoints of every slot (list 1 after list 0); a commit
+    uint32_t* nb;                // that stage 1 sends on gets the two classes' roots at its time instead
+    uint32_t* sub[2];            // per root id: bit 0 an endpoint of a crossing survivor, bit 1 its
+                                 // subtree of stage 1's links holds such a root
+    uint32_t* died[2];           // per root id that stage 1 killed: the index of the commit
+    uint8_t* flag;               // per slot: 1 internal, 2 crossing, 3 committed in stage 1 and sent on
     uint32_t* vcnt;              // per virtual block of the compaction: count, then offset
     SlabCtr* sc;
     Counters* ctr;
@@ -156,15 +159,20 @@ struct SlabArgs {
     uint32_t* ob;
     uint32_t* map;               // stage 1 only: the slot each selected survivor came from
     const uint64_t* log;         // stage 1's commit log (read by the marking pass)
+    cp_pair* pairs;              // the final commits' pairs are appended here
+    uint32_t pair_cap;
 };
 // Entries of SlabArgs::vcnt for a scratch capacity.
 uint32_t slab_vblocks_cap(uint32_t cap);
-// Flags each slot internal or crossing (kStCapacity if the lists are not side by side).
+// Flags each slot internal or crossing (kStCapacity if the lists are not
+// side by side) and marks the crossing survivors' endpoint classes.
 cudaError_t launch_slab_classify(const SlabArgs& a, cudaStream_t s);
 // Stable compaction of the slots selected by sel (0: internal, 1: crossing or
 // committed) to ko / act / oa / ob (/ map); n_out[q] receives list q's count.
 cudaError_t launch_slab_compact(const SlabArgs& a, int sel, uint32_t* n_out, cudaStream_t s);
-// After stage 1: flags its committed survivors, then clears the reservation words.
+// After stage 1: marks the classes that met a crossing survivor, writes the
+// pairs of the commits whose dying class did not and flags the others (with
+// their classes' roots) for stage 2, then clears the reservation words.
 cudaError_t launch_slab_mark(const SlabArgs& a, cudaStream_t s);
 
 // ---- H1 of volumes (cp_h1.cu): column reduction of the square-edge boundary

@@ -8,26 +8,43 @@
 // otherwise.  Stage 1 runs the elder-rule union-find over the internal
 // survivors only: their root classes are disjoint between slabs, so this one
 // launch is S independent union-finds (no reservation word is shared by two
-// slabs, and each slab's rounds go exactly as they would alone).  Its commits
-// are each slab's merge forest.  Stage 2 runs the union-find over the
-// committed internal survivors and the crossing survivors, in filtration
-// order, and writes the pairs.
+// slabs, and each slab's rounds go exactly as they would alone).  Stage 2 runs
+// the union-find over what stage 1 hands on and the crossing survivors, in
+// filtration order, and writes the remaining pairs.
 //
-// Why the pairs are exact: with distinct keys the survivors that the
-// sequential union-find commits form the minimum spanning forest of the
-// survivor graph (Kruskal's algorithm), and a survivor that does not commit
-// changes nothing.  An internal survivor that its slab's union-find does not
-// commit closes a cycle of earlier internal survivors, so the whole graph's
-// union-find does not commit it either.  Dropping it leaves the sequence of
-// commits, hence of elder-rule pairs, unchanged.  Only the committed internal
-// survivors and the crossing ones (what each slab would send to the merge on
-// several devices) reach stage 2.
+// What stage 1 hands on.  A class of a slab is a boundary class once one of
+// its roots is an endpoint of a crossing survivor.  A stage 1 commit whose
+// dying class is not a boundary class at that time is final: no survivor
+// leads out of that class, so the whole image's union-find sees exactly it
+// then, and sees the surviving class inside a class at least as old; the
+// same class dies with the same pair.  Stage 1 writes that pair, and nothing
+// of the dead class is needed again.  Every other commit goes to stage 2 with
+// its endpoints replaced by the two classes' roots at its time (their oldest
+// members), since stage 2 does not see the final commits that built those
+// classes.  Stage 2 then sees, for every class of the whole image that spans
+// slabs, its slab classes' roots joined through the commits and crossing
+// survivors in filtration order: its commits and pairs are the whole image's.
+// (Without the reduction, stage 1 hands on every commit: a survivor that its
+// slab does not commit closes a cycle of earlier survivors, so the whole
+// image's union-find, Kruskal's minimum spanning forest with distinct keys,
+// does not commit it either.)
+//
+// A dying class's members at its death all lie in its root's subtree of
+// stage 1's links, so "met a crossing survivor" is tested by an upward
+// propagation of the endpoint marks through those links.  The subtree can be
+// larger: a commit of a later survivor in the same round may link a class
+// under a root that an earlier survivor of that round has just killed.  The
+// test then errs towards handing a commit on, which is always exact.  For the
+// same reason the root a commit records as its surviving side may have died
+// earlier in the filtration; the surviving class's root at the commit's time
+// is found by following the links whose commits came before it.
 //
 // The lists are compacted stably (filtration order kept) by a count pass, one
 // scan over the per-block counts and a scatter pass.
 #include "cp_common.cuh"
 #include "cp_grid.cuh"
 #include "cp_kernels.h"
+#include "cp_pairs.cuh"
 
 namespace cp {
 namespace {
@@ -109,7 +126,22 @@ __device__ __forceinline__ uint32_t cta_rank(bool p, uint32_t* sh, uint32_t& tot
     return r;
 }
 
-// Flags every slot of both lists internal or crossing.
+// Root counts of the two lists (registered by the pruning pass).
+__device__ __forceinline__ void root_counts(const SlabArgs& a, uint32_t& r0, uint32_t& r1) {
+    r0 = min(a.ctr->n_r0, a.n_rids[0]);
+    r1 = min(a.ctr->n_rt, a.n_rids[1]);
+}
+
+__global__ void __launch_bounds__(kST) k_slab_clear(const __grid_constant__ SlabArgs a) {
+    uint32_t r0, r1;
+    root_counts(a, r0, r1);
+    const uint32_t stride = gridDim.x * kST;
+    for (uint32_t i = blockIdx.x * kST + threadIdx.x; i < r0; i += stride) a.sub[0][i] = 0;
+    for (uint32_t i = blockIdx.x * kST + threadIdx.x; i < r1; i += stride) a.sub[1][i] = 0;
+}
+
+// Flags every slot of both lists internal or crossing; marks the endpoint
+// classes of the crossing survivors.
 __global__ void __launch_bounds__(kST) k_slab_classify(const __grid_constant__ SlabArgs a) {
     Counters* ctr = a.ctr;
     if (ld_acquire_u32(&ctr->status) & (kStTimeout | kStNonfinite)) return;
@@ -126,10 +158,15 @@ __global__ void __launch_bounds__(kST) k_slab_classify(const __grid_constant__ S
         int q = 0;
         if (j < n) {
             q = j >= n0 ? 1 : 0;
-            const uint32_t sa = slab_of_root(a.tab, a.age[q], __ldcg(a.na + j), a.n_rids[q], ctr, a.S);
-            const uint32_t sb = slab_of_root(a.tab, a.age[q], __ldcg(a.nb + j), a.n_rids[q], ctr, a.S);
+            const uint32_t ra = __ldcg(a.na + j), rb = __ldcg(a.nb + j);
+            const uint32_t sa = slab_of_root(a.tab, a.age[q], ra, a.n_rids[q], ctr, a.S);
+            const uint32_t sb = slab_of_root(a.tab, a.age[q], rb, a.n_rids[q], ctr, a.S);
             cross = sa != sb;
             a.flag[j] = cross ? kFlagCrossing : kFlagInternal;
+            if (cross && CP_IN(ra, a.n_rids[q], ctr) && CP_IN(rb, a.n_rids[q], ctr)) {
+                atomicOr(a.sub[q] + ra, 1u);
+                atomicOr(a.sub[q] + rb, 1u);
+            }
         }
         warp_append(&a.sc->n_cross[0], cross && q == 0);
         warp_append(&a.sc->n_cross[1], cross && q == 1);
@@ -238,7 +275,47 @@ __global__ void __launch_bounds__(kST) k_compact_scatter(const __grid_constant__
     }
 }
 
-// After stage 1: the committed internal survivors are flagged for stage 2.
+// After stage 1: bit 1 on every root whose subtree of stage 1's links holds
+// an endpoint of a crossing survivor (walks up from each marked root; a walk
+// stops where another has passed).
+__global__ void __launch_bounds__(kST) k_slab_up(const __grid_constant__ SlabArgs a) {
+    Counters* ctr = a.ctr;
+    if (ld_acquire_u32(&ctr->status) & (kStTimeout | kStNonfinite | kStCapacity)) return;
+    uint32_t r0, r1;
+    root_counts(a, r0, r1);
+    for (uint32_t g = blockIdx.x * kST + threadIdx.x; g < r0 + r1; g += gridDim.x * kST) {
+        const int q = g >= r0 ? 1 : 0;
+        uint32_t x = q ? g - r0 : g;
+        if (!(__ldcg(a.sub[q] + x) & 1u)) continue;
+        const uint64_t t0 = global_timer_ns();
+        for (uint32_t hops = 1;; ++hops) {
+            if (atomicOr(a.sub[q] + x, 2u) & 2u) break;
+            const uint64_t w = __ldcg(a.res[q] + x);
+            if ((w & kDead) != kDead) break;  // a root of stage 1's result
+            x = uint32_t(w);
+            if (!CP_IN(x, a.n_rids[q], ctr)) break;
+            if ((hops & 1023u) == 0 && global_timer_ns() - t0 > kWaitLimitNs) {  // only corrupted links get here
+                set_status(ctr, kStTimeout);
+                break;
+            }
+        }
+    }
+}
+
+// After stage 1: the commit index of every root that stage 1 killed.
+__global__ void __launch_bounds__(kST) k_slab_died(const __grid_constant__ SlabArgs a) {
+    Counters* ctr = a.ctr;
+    if (ld_acquire_u32(&ctr->status) & (kStTimeout | kStNonfinite | kStCapacity)) return;
+    const uint32_t ni0 = a.sc->n_in[0], n = ni0 + a.sc->n_in[1];
+    for (uint32_t k = blockIdx.x * kST + threadIdx.x; k < n; k += gridDim.x * kST) {
+        const uint64_t e = __ldcg(a.log + k);
+        const int q = k >= ni0 ? 1 : 0;
+        if (e != ~0ull && CP_IN(uint32_t(e), a.n_rids[q], ctr)) a.died[q][uint32_t(e)] = q ? k - ni0 : k;
+    }
+}
+
+// After stage 1: each commit either writes its pair (its dying class met no
+// crossing survivor) or is flagged for stage 2 with its classes' roots.
 __global__ void __launch_bounds__(kST) k_slab_mark(const __grid_constant__ SlabArgs a) {
     Counters* ctr = a.ctr;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -249,16 +326,48 @@ __global__ void __launch_bounds__(kST) k_slab_mark(const __grid_constant__ SlabA
     const uint32_t ni0 = a.sc->n_in[0], n = ni0 + a.sc->n_in[1];
     for (uint32_t k0 = blockIdx.x * kST; k0 < n; k0 += gridDim.x * kST) {
         const uint32_t k = k0 + threadIdx.x;
-        bool c = false;
-        if (k < n && __ldcg(a.log + k) != ~0ull) {
-            const uint32_t j = __ldcg(a.map + k);
-            if (CP_IN(j, a.cap, ctr)) {
-                a.flag[j] = kFlagCommitted;
-                c = true;
+        const int q = k >= ni0 ? 1 : 0;
+        bool sent = false, emit = false, fin = false;
+        cp_pair pr;
+        if (k < n) {
+            const uint64_t e = __ldcg(a.log + k);
+            if (e != ~0ull) {
+                const uint32_t y = uint32_t(e), j = __ldcg(a.map + k);
+                if (CP_IN(y, a.n_rids[q], ctr) && CP_IN(j, a.cap, ctr)) {
+                    const uint32_t kl = q ? k - ni0 : k;
+                    if (__ldcg(a.sub[q] + y) & 2u) {
+                        // the surviving class's root at this commit: past the
+                        // links whose commits came earlier
+                        uint32_t o = uint32_t(__ldcg(a.res[q] + y));
+                        for (uint32_t hops = 0; hops < a.n_rids[q]; ++hops) {
+                            if (!CP_IN(o, a.n_rids[q], ctr)) break;
+                            const uint64_t w = __ldcg(a.res[q] + o);
+                            if ((w & kDead) != kDead || __ldcg(a.died[q] + o) >= kl) break;
+                            o = uint32_t(w);
+                        }
+                        a.flag[j] = kFlagCommitted;
+                        a.na[j] = y;
+                        a.nb[j] = o;
+                        sent = true;
+                    } else {
+                        uint64_t key = __ldcg(a.ko[q] + kl);
+                        if (q) key = ~key;
+                        const int item = item_of_vertex(a.tab, key_vertex(key));
+                        emit = commit_pair(a.tab, a.age[q], q, key, item, y, pr);
+                        fin = true;
+                    }
+                }
             }
         }
-        warp_append(&a.sc->n_event[0], c && k < ni0);
-        warp_append(&a.sc->n_event[1], c && k >= ni0);
+        warp_append(&a.sc->n_sent[0], sent && q == 0);
+        warp_append(&a.sc->n_sent[1], sent && q == 1);
+        warp_append(&a.sc->n_final[0], fin && q == 0);
+        warp_append(&a.sc->n_final[1], fin && q == 1);
+        const uint32_t pp = warp_append(&ctr->n_pairs, emit);
+        if (emit) {
+            if (pp < a.pair_cap) a.pairs[pp] = pr;
+            else set_status(ctr, kStCapacity);
+        }
     }
 }
 
@@ -278,8 +387,9 @@ int slab_blocks() { return device_sm_count() * 2; }
 uint32_t slab_vblocks_cap(uint32_t cap) { return 2 * ((cap + kVB - 1) / kVB) + 2; }
 
 cudaError_t launch_slab_classify(const SlabArgs& a, cudaStream_t s) {
+    k_slab_clear<<<slab_blocks(), kST, 0, s>>>(a);
     k_slab_classify<<<slab_blocks(), kST, 0, s>>>(a);
-    note_launches(1);
+    note_launches(2);
     return cudaGetLastError();
 }
 
@@ -292,9 +402,11 @@ cudaError_t launch_slab_compact(const SlabArgs& a, int sel, uint32_t* n_out, cud
 }
 
 cudaError_t launch_slab_mark(const SlabArgs& a, cudaStream_t s) {
+    k_slab_up<<<slab_blocks(), kST, 0, s>>>(a);
+    k_slab_died<<<slab_blocks(), kST, 0, s>>>(a);
     k_slab_mark<<<slab_blocks(), kST, 0, s>>>(a);
     k_slab_reset<<<slab_blocks(), kST, 0, s>>>(a);
-    note_launches(2);
+    note_launches(4);
     return cudaGetLastError();
 }
 

@@ -31,6 +31,7 @@
 #include "cp_common.cuh"
 #include "cp_grid.cuh"
 #include "cp_kernels.h"
+#include "cp_pairs.cuh"
 
 namespace cp {
 namespace {
@@ -86,9 +87,6 @@ __device__ __forceinline__ bool find_two(const uint32_t* uf, uint32_t n_nodes, C
     return ok;
 }
 
-// Reservation word of a root that has died: the dead mark in the high half
-// (above every stamp, whose high half is the round) and the parent root id.
-constexpr uint64_t kDead = 0xFFFFFFFF00000000ull;
 
 // Current root id of a class given a root id it once had.
 // (Bounds-checked build: an id outside the root ids becomes 0, flagged.)
@@ -155,51 +153,10 @@ __device__ __forceinline__ void endpoints(const ItemTable& tab, uint64_t k, int 
     b = top_of_octant(it, z, y, x, sz1, sy1, sx1);
 }
 
-// The pair of a committed survivor with key `key`, whose dying class has root
-// id yrid (the root's age key names the root vertex, or for the dual the
-// vertex whose lower star holds the dying top cell).
+// The pair of a committed survivor (see commit_pair).
 __device__ __forceinline__ void emit_pair(const UfParams& p, const ItemTable& tab, uint64_t key, int item,
                                           uint32_t yrid, bool* emitted, cp_pair& out) {
-    const Item& it = tab.it[item];
-    uint64_t age = p.age[yrid];
-    const uint32_t young = key_vertex(age);
-    uint32_t vg = key_vertex(key);
-    int n = int(key_n(key, it.ndim));
-    int dz, dy, dx;
-    stencil_off(it.ndim, n, dz, dy, dx);
-    int64_t lv = int64_t(vg) - it.voff;
-    int x = int(lv % it.W), y = int((lv / it.W) % it.H), z = int(lv / (int64_t(it.W) * it.H));
-    float fv = ord_float(uint32_t(key >> 32));
-    float fy = ord_float(uint32_t(age >> 32));
-    if (!p.dual) {
-        // H0: birth at the dying root vertex, death at the edge (value of its higher endpoint v)
-        out.birth = fy;
-        out.death = fv;
-        int64_t ly = int64_t(young) - it.voff;
-        int yx = int(ly % it.W), yy = int((ly / it.W) % it.H), yz = int(ly / (int64_t(it.W) * it.H));
-        out.birth_cell = int32_t(doubled_index(it, yz, yy, yx, 0, 0, 0));
-        out.death_cell = int32_t(doubled_index(it, z, y, x, dz, dy, dx));
-        out.birth_pixel = int32_t(ly);
-        out.death_pixel = int32_t(lv);
-        out.dim = 0;
-    } else {
-        // top dimension: birth at the facet, death at the dying top cell
-        uint32_t mg = key_vertex(age);
-        int nt = int(key_n(age, it.ndim));
-        int tz, ty, tx;
-        stencil_off(it.ndim, nt, tz, ty, tx);
-        int64_t lm = int64_t(mg) - it.voff;
-        int mx = int(lm % it.W), my = int((lm / it.W) % it.H), mz = int(lm / (int64_t(it.W) * it.H));
-        out.birth = fv;
-        out.death = fy;
-        out.birth_cell = int32_t(doubled_index(it, z, y, x, dz, dy, dx));
-        out.death_cell = int32_t(doubled_index(it, mz, my, mx, tz, ty, tx));
-        out.birth_pixel = int32_t(lv);
-        out.death_pixel = int32_t(lm);
-        out.dim = it.ndim - 1;
-    }
-    out.item = it.user;
-    *emitted = out.birth != out.death;  // zero persistence: omitted (Sec. 2.3)
+    *emitted = commit_pair(tab, p.age, p.dual, key, item, yrid, out);
 }
 
 __device__ __forceinline__ bool side_by_side(const UfKernelArgs& args, uint32_t n0, uint32_t n1) {

@@ -168,8 +168,8 @@ def class_slab(cx: Complex, age: int, S: int) -> int:
 def union_find(records, dual: bool):
     """Elder-rule union-find over records (key, age a, age b, ...) taken in
     ascending processing-key order.  H0: the class with the larger age dies;
-    dual: the smaller.  Returns the committed records, each with the age of
-    the class it killed."""
+    dual: the smaller.  Returns the committed records, each with the ages of
+    the class it killed and of the class that absorbed it (both roots)."""
     parent = {}
 
     def find(x):
@@ -187,22 +187,48 @@ def union_find(records, dual: bool):
             continue
         young, old = (max(ra, rb), min(ra, rb)) if not dual else (min(ra, rb), max(ra, rb))
         parent[young] = old
-        commits.append((rec, young))
+        commits.append((rec, young, old))
     return commits
 
 
-def slab_records(cx: Complex, S: int, slabs, dual: bool):
+def slab_records(cx: Complex, S: int, slabs, dual: bool, reduce: bool = False):
     """Stage 1 for the slabs in `slabs`: each slab's union-find over its
-    internal records; returns what those slabs send to the merge (their
-    commits and the crossing records whose key vertex lies in them)."""
+    internal records.  Returns (sent, final): what those slabs send to the
+    merge, and the commits whose pairs they write themselves.
+
+    reduce=False: every commit is sent as it is, with the crossing records
+    whose key vertex lies in the slab.
+    reduce=True: a class is a boundary class when one of its vertices (top
+    cells) is an endpoint of a crossing record.  A commit whose dying class is
+    not a boundary class at its time is final: the whole image's union-find
+    sees exactly that class then (no record leads out of it), and the other
+    class there contains the slab's surviving class, so it is at least as old;
+    the same class dies with the same pair, and the slab writes it.  Nothing
+    of the dead class reaches the merge again.  The other commits are sent
+    with their endpoints replaced by the two classes' roots at that time (the
+    age keys of their oldest members): the merge does not see the final
+    commits, so a record's own endpoints may lie in classes it never joined."""
     recs = cx.dual_records() if dual else cx.h0_records()
-    send = []
+    crossing = [r for r in recs if class_slab(cx, r[1], S) != class_slab(cx, r[2], S)]
+    touched = {r[1] for r in crossing} | {r[2] for r in crossing}
+    sent, final = [], []
     for s in slabs:
         internal = [r for r in recs if class_slab(cx, r[1], S) == s and class_slab(cx, r[2], S) == s]
-        send += [rec for rec, _ in union_find(internal, dual)]
-        send += [r for r in recs if class_slab(cx, r[1], S) != class_slab(cx, r[2], S)
-                 and cx.slab_of_vertex(r[3], S) == s]
-    return send
+        commits = union_find(internal, dual)
+        if not reduce:
+            sent += [rec for rec, _, _ in commits]
+        else:
+            boundary = {}  # root -> its class touches a crossing record
+            for rec, young, old in commits:
+                by = boundary.get(young, young in touched)
+                bo = boundary.get(old, old in touched)
+                if not by:
+                    final.append((rec, young, old))
+                else:
+                    sent.append((rec[0], young, old, rec[3]))
+                boundary[old] = by or bo
+        sent += [r for r in crossing if cx.slab_of_vertex(r[3], S) == s]
+    return sent, final
 
 
 def pairs_from_commits(cx: Complex, commits, dual: bool):
@@ -215,7 +241,7 @@ def pairs_from_commits(cx: Complex, commits, dual: bool):
     for lst in (cx.edges, cx.facets):
         for rec in lst:
             cells[int(rec[0])] = rec
-    for rec, young in commits:
+    for rec, young, *_ in commits:
         key = int(~np.uint64(rec[0])) if dual else rec[0]
         cell = cells[key]
         fcell = float(cx.fflat[cell[3]])
@@ -235,14 +261,15 @@ def pairs_from_commits(cx: Complex, commits, dual: bool):
     return out
 
 
-def split_pairs(img, S: int):
-    """The pairs of the slab split (stage 1 per slab, stage 2 over the
-    union of what the slabs send), without the essential class."""
+def split_pairs(img, S: int, reduce: bool = False):
+    """The pairs of the slab split (stage 1 per slab, stage 2 over the union
+    of what the slabs send), without the essential class."""
     cx = Complex(img)
     out = []
     for dual in (False, True):
-        merged = slab_records(cx, S, range(S), dual)
-        out += pairs_from_commits(cx, union_find(merged, dual), dual)
+        sent, final = slab_records(cx, S, range(S), dual, reduce)
+        out += pairs_from_commits(cx, final, dual)
+        out += pairs_from_commits(cx, union_find(sent, dual), dual)
     return sorted(out)
 
 

@@ -36,8 +36,8 @@ def _same(got, want, what):
 def _stats_ok(st, S):
     for q in range(2):
         assert st["internal"][q] + st["crossing"][q] == st["survivors"][q]
-        assert st["merged"][q] == st["committed"][q] + st["crossing"][q]
-        assert st["committed"][q] <= st["internal"][q]
+        assert st["merged"][q] == st["committed"][q] - st["final_pairs"][q] + st["crossing"][q]
+        assert st["final_pairs"][q] <= st["committed"][q] <= st["internal"][q]
         if S == 1:
             assert st["crossing"][q] == 0
 

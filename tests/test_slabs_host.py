@@ -26,10 +26,21 @@ def _images():
     yield rng.integers(0, 3, size=(9, 12)).astype(np.float32)
 
 
+@pytest.mark.parametrize("reduce", [False, True])
 @pytest.mark.parametrize("S", [1, 2, 3, 4, 7, 20])
-def test_split_equals_oracle(S):
+def test_split_equals_oracle(S, reduce):
     for img in _images():
-        assert sr.split_pairs(img, S) == sr.oracle_pairs(oracle.persistence(img))
+        assert sr.split_pairs(img, S, reduce) == sr.oracle_pairs(oracle.persistence(img))
+
+
+def test_boundary_reduction_sends_less():
+    img = np.random.default_rng(3).random((12, 7, 6)).astype(np.float32)
+    cx = sr.Complex(img)
+    for dual in (False, True):
+        full, none = sr.slab_records(cx, 2, range(2), dual, reduce=False)
+        part, final = sr.slab_records(cx, 2, range(2), dual, reduce=True)
+        assert not none and final
+        assert len(part) + len(final) == len(full)
 
 
 def test_whole_union_find_equals_oracle():
@@ -37,27 +48,54 @@ def test_whole_union_find_equals_oracle():
         assert sr.whole_pairs(img) == sr.oracle_pairs(oracle.persistence(img))
 
 
-def test_split_needs_both_record_kinds():
-    """Dropping the crossing records, or a slab's commits, changes the pairs:
-    the parity tests above would see either mistake."""
-    img = np.random.default_rng(5).random((8, 7, 6)).astype(np.float32)
-    cx = sr.Complex(img)
-    want = sr.oracle_pairs(oracle.persistence(img))
-    S = 3
-    for drop in ("crossing", "commits"):
-        out = []
-        for dual in (False, True):
-            recs = cx.dual_records() if dual else cx.h0_records()
-            send = []
-            for s in range(S):
-                internal = [r for r in recs if sr.class_slab(cx, r[1], S) == s and sr.class_slab(cx, r[2], S) == s]
-                if drop != "commits":
-                    send += [rec for rec, _ in sr.union_find(internal, dual)]
-                if drop != "crossing":
-                    send += [r for r in recs if sr.class_slab(cx, r[1], S) != sr.class_slab(cx, r[2], S)
-                             and cx.slab_of_vertex(r[3], S) == s]
-            out += sr.pairs_from_commits(cx, sr.union_find(send, dual), dual)
-        assert sorted(out) != want, drop
+def _mutant_pairs(cx, S, drop):
+    """The split with one planted mistake."""
+    out = []
+    for dual in (False, True):
+        recs = cx.dual_records() if dual else cx.h0_records()
+        crossing = [r for r in recs if sr.class_slab(cx, r[1], S) != sr.class_slab(cx, r[2], S)]
+        touched = {r[1] for r in crossing} | {r[2] for r in crossing}
+        send, final = [], []
+        for s in range(S):
+            internal = [r for r in recs if sr.class_slab(cx, r[1], S) == s and sr.class_slab(cx, r[2], S) == s]
+            commits = sr.union_find(internal, dual)
+            if drop == "commits":
+                pass
+            elif drop in ("own endpoints", "surviving side"):
+                boundary = {}
+                for rec, young, old in commits:
+                    by = boundary.get(young, young in touched)
+                    bo = boundary.get(old, old in touched)
+                    if not (bo if drop == "surviving side" else by):
+                        final.append((rec, young, old))
+                    else:  # "own endpoints": the record's own endpoints instead of the classes' roots
+                        send.append(rec if drop == "own endpoints" else (rec[0], young, old, rec[3]))
+                    boundary[old] = by or bo
+            else:
+                send += [rec for rec, _, _ in commits]
+            if drop != "crossing":
+                send += [r for r in crossing if cx.slab_of_vertex(r[3], S) == s]
+        out += sr.pairs_from_commits(cx, final, dual)
+        out += sr.pairs_from_commits(cx, sr.union_find(send, dual), dual)
+    return sorted(out)
+
+
+@pytest.mark.parametrize("drop", ["crossing", "commits", "own endpoints", "surviving side"])
+def test_split_mistakes_fail(drop):
+    """Planted mistakes in the split change the pairs, so the parity tests
+    above would see them: dropping the crossing records or a slab's commits;
+    under the boundary reduction, sending a commit with its own endpoints
+    instead of the two classes' roots, or deciding finality on the surviving
+    class instead of the dying one."""
+    want = [sr.oracle_pairs(oracle.persistence(img)) for img in _mutant_images()]
+    got = [_mutant_pairs(sr.Complex(img), 3, drop) for img in _mutant_images()]
+    assert got != want, drop
+
+
+def _mutant_images():
+    rng = np.random.default_rng(5)
+    return [rng.random((8, 7, 6)).astype(np.float32), rng.random((9, 5, 7)).astype(np.float32),
+            rng.random((15, 12)).astype(np.float32)]
 
 
 def test_slab_of():
@@ -88,17 +126,22 @@ def _rank_main(rank, world, port, S, img, out):
         mine = [s for s in range(S) if s % world == rank]  # this rank's slabs
         result = []
         for dual in (False, True):
-            sent = sr.slab_records(cx, S, mine, dual)
+            sent, final = sr.slab_records(cx, S, mine, dual, reduce=True)
+            local = sr.pairs_from_commits(cx, final, dual)  # written by the slab's own rank
+            gathered = [None] * world if rank == 0 else None
+            dist.gather_object(local, gathered, dst=0)
             merged = slabs.exchange(_to_records(sent))
             if rank != 0:
                 assert merged is None
                 continue
-            assert np.all(np.diff(merged["key"].astype(np.float64)) >= 0)
+            assert np.all(merged["key"][1:] > merged["key"][:-1])
             recs = [(int(k), int(a), int(b)) for k, a, b in merged]
             result += sr.pairs_from_commits(cx, sr.union_find(recs, dual), dual)
+            for g in gathered:
+                result += g
             result.append(("records", dual, len(recs)))
         # a record sent twice is refused
-        dup = _to_records(sr.slab_records(cx, S, [0], False)[:1])
+        dup = _to_records(sr.slab_records(cx, S, [0], False)[0][:1])
         try:
             slabs.exchange(dup)
             refused = False
