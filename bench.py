@@ -807,8 +807,8 @@ def run_full(args):
             raise cp.CpError(rc, "loss backward")
 
     def h1_info():
-        info = (ctypes.c_int64 * 10)()
-        rc = lib.cubical_persistence_full_info(ctypes.c_void_p(wsp.data_ptr()), 1, one, dims, 0, pool, info, 10, sp)
+        info = (ctypes.c_int64 * 36)()
+        rc = lib.cubical_persistence_full_info(ctypes.c_void_p(wsp.data_ptr()), 1, one, dims, 0, pool, info, 36, sp)
         if rc != 0:
             raise cp.CpError(rc, "full info")
         return [int(v) for v in info]
@@ -889,6 +889,12 @@ def run_full(args):
                                    "fwd + total-persistence loss bwd", "status": st["rc"], "pairs": st["pairs"],
                        "h1_columns": info[0], "h1_columns_leaving_their_star": info[9], "h1_rounds": info[1],
                        "h1_pool_entries_used": info[2], "h1_pool_entries": info[3],
+                       "h1_solo_from_round": info[10], "h1_grid_rounds_ms": info[11] / 1e6,
+                       "h1_solo_rounds_ms": info[12] / 1e6,
+                       "h1_rounds_by_log2_additions": info[13:29],
+                       "h1_round_phases_ms": {k: v / 1e6 for k, v in zip(("bids", "wait", "additions", "wait2"),
+                                                                          info[29:33])},
+                       "h1_additions": info[33], "h1_entries_merged": info[34], "h1_solo_entries": info[35],
                        "plain_h0_h2_forward_ms": plain_ms,
                        "l2": "input larger than L2; no flush", "parallelism": "replicas" if ws > 1 else "single"},
             "gpu_launches": launches,

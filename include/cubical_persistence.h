@@ -315,7 +315,15 @@ int cubical_persistence_full_batched(int n_items, const float *const *h_images, 
  * with cap >= 10 also [4] edges paired in H0, [5] squares paired in H2,
  * [6] edges not paired in H0, [7] and [8] the byte offsets of the two
  * bitmaps of those edges and squares (bit 3 * lowest corner + axis) in the
- * workspace, [9] columns whose lowest entry left their lower star.
+ * workspace, [9] columns whose lowest entry left their lower star; with
+ * cap >= 13 also [10] the first round that the first CTA ran alone while
+ * the others waited (0: never), [11] and [12] the wall time in ns of the
+ * rounds on the whole grid and in that CTA alone; [13 + k] (k < 16, as far as cap allows) the
+ * rounds in which 2^k .. 2^(k+1) - 1 columns added (k = 15: 2^15 or more);
+ * [29 .. 32] thread 0 of the first CTA's time in ns, summed over the
+ * rounds: its bids, the wait after them, its additions, the wait after them;
+ * [33] column additions, [34] the entries those additions read, [35] times
+ * the first CTA went on alone (cap >= 36 for [33 .. 35]).
  * cap >= 4.
  */
 int cubical_persistence_full_info(const void *d_workspace, int n_items, const int32_t *ndims, const int64_t *dims,
@@ -474,6 +482,11 @@ int cubical_persistence_debug_wait_timeout(void *d_workspace, size_t ws_bytes, i
  *                        is spent, every block leaves at the next round
  *                        boundary and the call returns CP_ERR_TIMEOUT (no
  *                        H1 pairs).  0 stops after the first round.
+ *   CP_TUNE_H1_SOLO      the cross-star rounds: once at most this many
+ *                        columns enter a round, the first CTA runs the rounds
+ *                        alone while the others wait, until more than twice
+ *                        as many enter one (0 .. 1024; 0: every round on the
+ *                        whole grid; default 16).  Same pairs.
  * cp_set_tuning returns CP_OK or CP_ERR_ARG; cp_get_tuning the value or -1.
  * The autotuner in the Python package picks these per GPU and shape.
  */
@@ -482,6 +495,7 @@ int cubical_persistence_debug_wait_timeout(void *d_workspace, size_t ws_bytes, i
 #define CP_TUNE_ROWS_2D 3
 #define CP_TUNE_H1_BUDGET_MS 4
 #define CP_TUNE_CROSS_PRUNE_2D 5
+#define CP_TUNE_H1_SOLO 6
 int cp_set_tuning(int key, int value);
 int cp_get_tuning(int key);
 

@@ -1049,6 +1049,18 @@ int cubical_persistence_full_info(const void* d_workspace, int n_items, const in
         h_info[8] = int64_t(P.o_h1_pos);
         h_info[9] = c.nl;
     }
+    if (cap >= 13) {
+        h_info[10] = c.solo_round;
+        h_info[11] = int64_t(c.t_grid_ns);
+        h_info[12] = int64_t(c.t_solo_ns);
+    }
+    for (int k = 0; k < 16 && 13 + k < cap; ++k) h_info[13 + k] = c.nw_hist[k];
+    for (int k = 0; k < 4 && 29 + k < cap; ++k) h_info[29 + k] = int64_t(c.t_phase_ns[k]);
+    if (cap >= 36) {
+        h_info[33] = int64_t(c.additions);
+        h_info[34] = int64_t(c.merged);
+        h_info[35] = c.solo_entries;
+    }
     return CP_OK;
 }
 
@@ -1092,12 +1104,18 @@ int cp_set_tuning(int key, int value) {
         set_h1_budget_ms(value);
         return CP_OK;
     }
+    if (key == CP_TUNE_H1_SOLO) {
+        if (value < 0 || value > 1024) return CP_ERR_ARG;
+        set_h1_solo_cols(value);
+        return CP_OK;
+    }
     return set_tuning(key, value) == 0 ? CP_OK : CP_ERR_ARG;
 }
 
 int cp_get_tuning(int key) {
     std::lock_guard<std::mutex> lk(g_mu);
     if (key == CP_TUNE_H1_BUDGET_MS) return get_h1_budget_ms();
+    if (key == CP_TUNE_H1_SOLO) return get_h1_solo_cols();
     return get_tuning(key);
 }
 

@@ -36,7 +36,8 @@
 // pivot of that edge.  The others (their lowest entry left the star: every
 // pair of nonzero persistence, and with distinct values only those) are
 // reduced across stars in rounds
-// inside one cooperative kernel: every column whose lowest entry changed
+// inside one cooperative kernel (the last rounds, once few columns change,
+// in its first CTA alone, with CTA barriers): every column whose lowest entry changed
 // bids for that row with an atomic minimum of its key (the filtration order)
 // in a per-edge pivot word; every column that loses a bid, or is displaced
 // by an older one, then adds the winner of its row (all such additions at
@@ -59,6 +60,12 @@ constexpr int kHT = 256;  // threads per CTA of the element-wise kernels
 constexpr int kRT = 512;  // threads per CTA of the reduction
 constexpr uint32_t kNone = 0xFFFFFFFFu;
 constexpr uint32_t kMaxRounds = 1u << 20;
+// Once at most solo_cols columns enter a round, CTA 0 runs the rounds alone
+// while the other CTAs wait parked (a grid barrier costs microseconds, a CTA
+// barrier a fraction of one, and the long tails of rounds carry few
+// columns); when more than twice as many enter a round again, CTA 0 wakes
+// the grid.
+constexpr int kSoloDefault = kRT / 32;
 // A bounded wait that gave up earlier leaves the sorted columns unreliable;
 // non-finite input leaves the order unreliable: the call fails anyway.
 constexpr uint32_t kStSkip = kStTimeout | kStNonfinite;
@@ -254,25 +261,44 @@ __device__ __forceinline__ void far_edge(int k, int j, int& sz, int& sy, int& sx
     dx = dr[2];
 }
 
-// Keys of the edges of a star column (mask over the slots of L(m)), descending.
-__device__ uint32_t decode(const Item& it, int64_t m, uint32_t mask, uint64_t* keys) {
-    uint32_t n = 0;
-    for (int f = 5; f >= 0; --f)
-        if ((mask >> (24 + f)) & 1u) keys[n++] = edge_key_at(it, m, kFace[f][0], kFace[f][1], kFace[f][2]);
-    const uint32_t n0 = n;
-    for (int sl = 0; sl < 24; ++sl) {
-        if (!((mask >> sl) & 1u)) continue;
-        int sz, sy, sx, dz, dy, dx;
-        far_edge(sl >> 1, sl & 1, sz, sy, sx, dz, dy, dx);
-        const uint64_t k = edge_key_at(it, m + step_of(it, sz, sy, sx), dz, dy, dx);
-        uint32_t j = n++;
-        while (j > n0 && keys[j - 1] < k) {
-            keys[j] = keys[j - 1];
-            --j;
-        }
-        keys[j] = k;
+// Key of slot sl of L(m).
+__device__ __forceinline__ uint64_t slot_key(const Item& it, int64_t m, int sl) {
+    if (sl >= 24) return edge_key_at(it, m, kFace[sl - 24][0], kFace[sl - 24][1], kFace[sl - 24][2]);
+    int sz, sy, sx, dz, dy, dx;
+    far_edge(sl >> 1, sl & 1, sz, sy, sx, dz, dy, dx);
+    return edge_key_at(it, m + step_of(it, sz, sy, sx), dz, dy, dx);
+}
+
+// Keys of the edges of a star column (mask over the slots of L(m)),
+// descending, decoded by a whole warp: lane l computes slot l's key (the
+// image loads of all slots in flight together), and each key goes to its
+// rank among the column's keys (all distinct).  Returns the count.
+__device__ uint32_t warp_decode(const Item& it, int64_t m, uint32_t mask, uint64_t* keys) {
+    const unsigned lane = lane_id();
+    const bool has = lane < 30u && ((mask >> lane) & 1u);
+    const uint64_t k = has ? slot_key(it, m, int(lane)) : 0ull;
+    uint32_t rank = 0;
+#pragma unroll
+    for (int j = 0; j < 30; ++j) {
+        const uint64_t kj = __shfl_sync(0xFFFFFFFFu, k, j);
+        rank += (((mask >> j) & 1u) && kj > k) ? 1u : 0u;
     }
-    return n;
+    if (has) keys[rank] = k;
+    __syncwarp();
+    return uint32_t(__popc(mask & 0x3FFFFFFFu));
+}
+
+// The lowest entry (largest key) of a star column: its last edge through m
+// if it holds one (those come after every edge that misses m, in slot
+// order), else the largest of its other edges' keys.
+__device__ __forceinline__ uint64_t star_low(const Item& it, int64_t m, uint32_t mask) {
+    mask &= 0x3FFFFFFFu;
+    if (mask & kThrough) return slot_key(it, m, 31 - __clz(mask));
+    uint64_t best = 0;
+#pragma unroll
+    for (int sl = 0; sl < 24; ++sl)
+        if ((mask >> sl) & 1u) best = max(best, slot_key(it, m, sl));
+    return best;
 }
 
 // The column of square id q: its key, the item, and its star vertex m (local).
@@ -288,17 +314,15 @@ __device__ __forceinline__ uint64_t column_key(const ItemTable& tab, uint32_t q,
 // column is still its star mask.
 __device__ __forceinline__ uint64_t column_at(const H1Bufs& b, uint32_t q) {
     const uint64_t o = __ldcg(b.coff + q);
+    const uint32_t c = __ldcg(b.ccap + q);  // both loads in flight together
     if (o == ~0ull) return o;
-    const uint32_t c = __ldcg(b.ccap + q);
     return o + ((c >> 31) ? uint64_t(c & 0x7FFFFFFFu) : 0ull);
 }
 
 __device__ __forceinline__ uint64_t column_low(const H1Bufs& b, const Item& it, int64_t m, uint32_t q) {
     const uint64_t o = column_at(b, q);
     if (o != ~0ull) return __ldcg(b.pool + o);
-    uint64_t keys[30];
-    decode(it, m, __ldcg(b.cmask + q), keys);
-    return keys[0];
+    return star_low(it, m, __ldcg(b.cmask + q));
 }
 
 // ---- every lower star: its columns (squares not paired in H2) reduced
@@ -409,6 +433,7 @@ struct ReduceArgs {
     H1Bufs b;
     Counters* ctr;
     uint64_t budget_ns;  // wall-clock budget of the rounds
+    uint32_t solo_cols;  // see kSoloDefault (0: never alone)
 };
 
 // A column's entries: in the pool (off != ~0) or decoded into shared memory.
@@ -419,70 +444,102 @@ struct ColSrc {
 };
 
 // The warp merges the entries of c and p after their common lowest one into
-// out (symmetric difference over F2) and returns how many it wrote.  Each
-// lane takes an equal share of the merged sequence, its start found by a
-// binary search on the merge path; an entry in both columns lands next to
-// its twin (ties put c's first) and both are dropped.  A first pass counts
-// each lane's survivors, a warp prefix sum places them, a second pass writes.
-__device__ uint32_t warp_merge(const H1Bufs& b, const ColSrc& c, const ColSrc& p, uint64_t* out) {
+// out (symmetric difference over F2) and returns how many it wrote.  The
+// merged sequence is taken in tiles of kMT positions: the warp stages the
+// tile's slices of both columns in shared memory, every lane issuing all of
+// its loads before its first store (one round trip per tile instead of one
+// per entry), then each lane takes kME positions of the tile, its start found
+// by a binary search on the merge path in shared memory.  An entry in both
+// columns lands next to its twin (ties put c's first) and both are dropped: a
+// lane keeps a c entry unless the next p entry equals it, and a p entry unless
+// the last c entry taken equals it.  A first pass counts each lane's
+// survivors, a warp prefix sum places them, a second pass writes.
+constexpr uint32_t kME = 4;          // merged positions per lane and tile
+constexpr uint32_t kMT = 32 * kME;   // merged positions per tile
+struct MergeTile {
+    uint64_t c[kMT + 1];  // c[it - 1 .. it + kMT) (~0 before c's first entry)
+    uint64_t p[kMT];      // p[jt .. jt + kMT)
+};
+
+__device__ uint32_t warp_merge(const H1Bufs& b, const ColSrc& c, const ColSrc& p, uint64_t* out, MergeTile& t) {
     const unsigned lane = lane_id();
     const uint32_t nc = c.len - 1u, np = p.len - 1u, total = nc + np;
     auto gc = [&](uint32_t i) { return c.off != ~0ull ? __ldcg(b.pool + c.off + 1 + i) : c.sm[1 + i]; };
     auto gp = [&](uint32_t i) { return p.off != ~0ull ? __ldcg(b.pool + p.off + 1 + i) : p.sm[1 + i]; };
-    const uint32_t chunk = (total + 31u) / 32u;
-    const uint32_t d0 = min(total, lane * chunk), d1 = min(total, d0 + chunk);
-    // split at d0: the smallest i such that c's entry i would not precede p's
-    // entry d0-i-1 (keys descending)
-    uint32_t lo = d0 > np ? d0 - np : 0u, hi = min(d0, nc);
-    while (lo < hi) {
-        const uint32_t mid = (lo + hi) >> 1;
-        if (gc(mid) >= gp(d0 - mid - 1)) lo = mid + 1;
-        else hi = mid;
-    }
-    const uint32_t i0 = lo, j0 = d0 - lo;
-    uint32_t kept = 0;  // pass 1
-    {
-        uint32_t i = i0, j = j0;
-        uint64_t x = i < nc ? gc(i) : 0, y = j < np ? gp(j) : 0;
-        uint64_t prevc = i > 0 ? gc(i - 1) : ~0ull;  // the last entry of c taken
-        for (uint32_t d = d0; d < d1; ++d) {
-            if (j >= np || (i < nc && x >= y)) {
-                kept += (j < np && y == x) ? 0u : 1u;
-                prevc = x;
-                ++i;
-                x = i < nc ? gc(i) : 0;
-            } else {
-                kept += (i > 0 && prevc == y) ? 0u : 1u;
-                ++j;
-                y = j < np ? gp(j) : 0;
+    uint32_t it = 0, jt = 0, written = 0;  // entries of c and p before this tile, entries written
+    for (uint32_t dt = 0; dt < total; dt += kMT) {
+        const uint32_t tn = min(kMT, total - dt);
+        const uint32_t cn = min(tn, nc - it), pn = min(tn, np - jt);  // staged entries of each
+        {
+            uint64_t vc[kME + 1], vp[kME];
+#pragma unroll
+            for (uint32_t s = 0; s <= kME; ++s) {
+                const uint32_t k = lane + 32u * s;
+                vc[s] = k <= cn ? ((it + k == 0u) ? ~0ull : gc(it + k - 1u)) : 0ull;
             }
-        }
-    }
-    uint32_t incl = kept;
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-        if (lane >= unsigned(o)) incl += t;
-    }
-    {  // pass 2
-        uint64_t* w = out + (incl - kept);
-        uint32_t i = i0, j = j0;
-        uint64_t x = i < nc ? gc(i) : 0, y = j < np ? gp(j) : 0;
-        uint64_t prevc = i > 0 ? gc(i - 1) : ~0ull;
-        for (uint32_t d = d0; d < d1; ++d) {
-            if (j >= np || (i < nc && x >= y)) {
-                if (!(j < np && y == x)) *w++ = x;
-                prevc = x;
-                ++i;
-                x = i < nc ? gc(i) : 0;
-            } else {
-                if (!(i > 0 && prevc == y)) *w++ = y;
-                ++j;
-                y = j < np ? gp(j) : 0;
+#pragma unroll
+            for (uint32_t s = 0; s < kME; ++s) {
+                const uint32_t k = lane + 32u * s;
+                vp[s] = k < pn ? gp(jt + k) : 0ull;
             }
+#pragma unroll
+            for (uint32_t s = 0; s <= kME; ++s)
+                if (lane + 32u * s <= cn) t.c[lane + 32u * s] = vc[s];
+#pragma unroll
+            for (uint32_t s = 0; s < kME; ++s)
+                if (lane + 32u * s < pn) t.p[lane + 32u * s] = vp[s];
         }
+        __syncwarp();
+        const uint32_t d0 = min(tn, lane * kME), d1 = min(tn, d0 + kME);
+        // split at d0: the smallest i such that C(i) would not precede P(d0-i-1) (keys descending)
+        uint32_t lo = d0 > pn ? d0 - pn : 0u, hi = min(d0, cn);
+        while (lo < hi) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (t.c[mid + 1u] >= t.p[d0 - mid - 1u]) lo = mid + 1u;
+            else hi = mid;
+        }
+        const uint32_t i0 = lo, j0 = d0 - lo;
+        uint32_t kept = 0, ie = i0, je = j0;
+        for (int pass = 0; pass < 2; ++pass) {
+            uint64_t* w = nullptr;
+            if (pass == 1) {
+                uint32_t incl = kept;
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+                    if (lane >= unsigned(o)) incl += v;
+                }
+                w = out + written + (incl - kept);
+                written += __shfl_sync(0xFFFFFFFFu, incl, 31);
+            }
+            uint32_t i = i0, j = j0;
+            uint64_t x = i < cn ? t.c[i + 1u] : 0, y = j < pn ? t.p[j] : 0;
+            uint64_t prevc = t.c[i];  // the last entry of c taken (~0: none)
+            for (uint32_t d = d0; d < d1; ++d) {
+                if (j >= pn || (i < cn && x >= y)) {
+                    const bool keep = !(j < pn && y == x);
+                    if (pass == 0) kept += keep ? 1u : 0u;
+                    else if (keep) *w++ = x;
+                    prevc = x;
+                    ++i;
+                    x = i < cn ? t.c[i + 1u] : 0;
+                } else {
+                    const bool keep = prevc != y;
+                    if (pass == 0) kept += keep ? 1u : 0u;
+                    else if (keep) *w++ = y;
+                    ++j;
+                    y = j < pn ? t.p[j] : 0;
+                }
+            }
+            ie = i;
+            je = j;
+        }
+        // the next tile starts where the last lane's range ended (lane 31's
+        // range ends at tn: its start is min(tn, kMT - kME))
+        it += __shfl_sync(0xFFFFFFFFu, ie, 31);
+        jt += __shfl_sync(0xFFFFFFFFu, je, 31);
+        __syncwarp();  // the tile is read by every lane before the next one is staged
     }
-    __syncwarp();
-    return __shfl_sync(0xFFFFFFFFu, incl, 31);
+    return written;
 }
 
 // Column q lost its row to an older column: add that column (F2: the
@@ -494,9 +551,10 @@ __device__ uint32_t warp_merge(const H1Bufs& b, const ColSrc& c, const ColSrc& p
 // rather than every intermediate result.
 //
 // The addition is done by a whole warp, one warp per losing column
-// (warp_merge).  Columns still in their star masks are decoded once, by lane
-// 0, into shared memory (sc, sp: 30 keys each).
-__device__ void add_winner_warp(const ReduceArgs& a, uint32_t q, uint32_t r, uint64_t* sc, uint64_t* sp) {
+// (warp_merge).  Columns still in their star masks are decoded by the warp
+// into shared memory (sc, sp: 30 keys each).
+__device__ void add_winner_warp(const ReduceArgs& a, uint32_t q, uint32_t r, uint64_t* sc, uint64_t* sp,
+                                MergeTile& tile) {
     const H1Bufs& b = a.b;
     const unsigned lane = lane_id();
     auto stop = [&](uint32_t status) {
@@ -515,10 +573,7 @@ __device__ void add_winner_warp(const ReduceArgs& a, uint32_t q, uint32_t r, uin
     if (c.off != ~0ull) {
         c.len = __ldcg(b.clen + q);
     } else {
-        uint32_t n = 0;
-        if (lane == 0) n = decode(*itc, mc, __ldcg(b.cmask + q), sc);
-        c.len = __shfl_sync(0xFFFFFFFFu, n, 0);
-        __syncwarp();
+        c.len = warp_decode(*itc, mc, __ldcg(b.cmask + q), sc);
     }
     if (c.off != ~0ull && !CP_IN(c.off + c.len, b.pool_cap + 1, a.ctr)) return stop(0);
     const uint64_t low = c.off != ~0ull ? __ldcg(b.pool + c.off) : sc[0];
@@ -535,10 +590,7 @@ __device__ void add_winner_warp(const ReduceArgs& a, uint32_t q, uint32_t r, uin
     if (pc.off != ~0ull) {
         pc.len = __ldcg(b.clen + p);
     } else {
-        uint32_t n = 0;
-        if (lane == 0) n = decode(itp, int64_t(key_vertex(kp)) - itp.voff, __ldcg(b.cmask + p), sp);
-        pc.len = __shfl_sync(0xFFFFFFFFu, n, 0);
-        __syncwarp();
+        pc.len = warp_decode(itp, int64_t(key_vertex(kp)) - itp.voff, __ldcg(b.cmask + p), sp);
     }
     if (pc.off != ~0ull && !CP_IN(pc.off + pc.len, b.pool_cap + 1, a.ctr)) return stop(0);
     const uint64_t need = uint64_t(c.len) + pc.len - 2u;
@@ -558,8 +610,10 @@ __device__ void add_winner_warp(const ReduceArgs& a, uint32_t q, uint32_t r, uin
         if (base + 2ull * cap > b.pool_cap) return stop(kStCapacity);
         into = 0u;
     }
-    const uint32_t k = warp_merge(b, c, pc, b.pool + base + (into ? uint64_t(cap) : 0ull));
+    const uint32_t k = warp_merge(b, c, pc, b.pool + base + (into ? uint64_t(cap) : 0ull), tile);
     if (lane == 0) {
+        atomicAdd(&b.ctl->additions, 1ull);
+        atomicAdd(&b.ctl->merged, (unsigned long long)(c.len + pc.len));
         __stcg(b.coff + q, base);
         __stcg(b.ccap + q, cap | (into << 31));
         __stcg(b.clen + q, k);
@@ -572,19 +626,34 @@ __global__ void __launch_bounds__(kRT) k_h1_reduce(const __grid_constant__ Reduc
     Counters* ctr = a.ctr;
     H1Ctl* ctl = b.ctl;
     if (ld_acquire_u32(&ctr->status) & kStSkip) return;  // set before the launch: every CTA returns
-    const uint32_t nblocks = gridDim.x, gstride = nblocks * kRT, gtid = blockIdx.x * kRT + threadIdx.x;
-    if (gtid == 0 && (ctl->m != b.mcap || ctl->pos_e != b.mcap || ctl->neg_e != b.exp_neg_e ||
-                      ctl->pos_q != b.exp_pos_q || ctl->nl > b.mcap))
+    if (blockIdx.x == 0 && threadIdx.x == 0 &&
+        (ctl->m != b.mcap || ctl->pos_e != b.mcap || ctl->neg_e != b.exp_neg_e || ctl->pos_q != b.exp_pos_q ||
+         ctl->nl > b.mcap))
         set_status(ctr, kStInternal);
     __shared__ uint32_t sh_n, sh_stop;
     __shared__ uint64_t sh_col[kRT / 32][2][32];  // per warp: two star columns decoded
+    __shared__ MergeTile sh_tile[kRT / 32];       // per warp: the staged tile of a merge
     uint32_t epoch = 0;
-    const uint64_t t_start = global_timer_ns();  // read by thread 0 of the grid only
+    const uint64_t t_start = global_timer_ns();  // read by thread 0 of CTA 0 only
+    uint64_t t_mode = t_start;   // start of the current mode (thread 0 of CTA 0)
+    uint32_t pgen = 0;           // wake-ups of the parked CTAs so far
+    __shared__ uint32_t sh_wake[3];
     uint32_t nchg = min(ctl->nl, b.mcap);  // round 0: every column that left its star
+    // the whole grid while many columns change; CTA 0 alone while few do (the
+    // switches are decided on counts every CTA reads after the same barrier)
+    bool solo = false;
+    auto barrier = [&]() {
+        if (solo) __syncthreads();  // orders the CTA's global writes and atomics too
+        else grid_barrier(ctr, gridDim.x, epoch);
+    };
     for (uint32_t r = 0;; ++r) {
+        const uint32_t nblocks = solo ? 1u : gridDim.x, gstride = nblocks * kRT;
+        const uint32_t gtid = blockIdx.x * kRT + threadIdx.x;  // CTA 0 is the one that stays
         uint32_t* work = b.list[r & 1u];
         const uint32_t* chg = r == 0 ? b.list0 : b.list[(r & 1u) ^ 1u];
         uint32_t* wcnt = &ctl->cnt[r % 3u];
+        uint64_t tp0 = 0, tp1 = 0, tp2 = 0;
+        if (gtid == 0) tp0 = global_timer_ns();
         // ---- bids: the oldest column of each row keeps it
         for (uint32_t i0 = blockIdx.x * kRT; i0 < nchg; i0 += gstride) {
             const uint32_t i = i0 + threadIdx.x;
@@ -609,7 +678,8 @@ __global__ void __launch_bounds__(kRT) k_h1_reduce(const __grid_constant__ Reduc
             const uint32_t pos = warp_append(wcnt, lose != kNone);
             if (lose != kNone && pos < b.mcap) work[pos] = lose;
         }
-        grid_barrier(ctr, nblocks, epoch);
+        if (gtid == 0) tp1 = global_timer_ns();
+        barrier();
         // one thread reads the round's outcome for the CTA, so that every CTA
         // takes the same path (the stop word of the previous round is
         // complete; this round's merges write the other one)
@@ -626,22 +696,96 @@ __global__ void __launch_bounds__(kRT) k_h1_reduce(const __grid_constant__ Reduc
             if (gtid == 0) {
                 ctl->rounds = r + 1u;
                 if (nw != 0u && !stop) set_status(ctr, kStInternal);
+                const uint64_t now = global_timer_ns();
+                if (solo) ctl->t_solo_ns += now - t_mode;
+                else ctl->t_grid_ns += now - t_mode;
+                if (solo) {  // the parked CTAs leave too
+                    ctl->park_exit = 1u;
+                    st_release_u32(&ctl->park_gen, pgen + 1u);
+                }
             }
             break;
         }
-        if (gtid == 0) ctl->cnt[(r + 1u) % 3u] = 0u;  // the next round's bids (last read two rounds ago)
+        if (gtid == 0) {
+            ctl->cnt[(r + 1u) % 3u] = 0u;  // the next round's bids (last read two rounds ago)
+            ctl->nw_hist[min(31u - __clz(nw), 15u)] += 1u;
+            tp2 = global_timer_ns();
+            ctl->t_phase_ns[0] += tp1 - tp0;
+            ctl->t_phase_ns[1] += tp2 - tp1;
+        }
         // ---- every losing column adds the winner of its row
         // (one warp per losing column: long columns are merged 32 lanes wide)
         for (uint32_t i = gtid >> 5; i < nw; i += gstride >> 5)
-            add_winner_warp(a, __ldcg(work + i), r, sh_col[threadIdx.x >> 5][0], sh_col[threadIdx.x >> 5][1]);
+            add_winner_warp(a, __ldcg(work + i), r, sh_col[threadIdx.x >> 5][0], sh_col[threadIdx.x >> 5][1],
+                            sh_tile[threadIdx.x >> 5]);
         // the budget: one thread decides, every CTA reads the decision (this
         // round's stop word) after the next barrier, so all leave together
-        if (gtid == 0 && global_timer_ns() - t_start > a.budget_ns) {
-            set_status(ctr, kStTimeout);
-            atomicOr(&ctl->stop[r & 1u], 2u);
+        uint64_t tp3 = 0;
+        if (gtid == 0) {
+            tp3 = global_timer_ns();
+            if (tp3 - t_start > a.budget_ns) {
+                set_status(ctr, kStTimeout);
+                atomicOr(&ctl->stop[r & 1u], 2u);
+            }
         }
-        grid_barrier(ctr, nblocks, epoch);
+        barrier();
+        if (gtid == 0) {
+            ctl->t_phase_ns[2] += tp3 - tp2;
+            ctl->t_phase_ns[3] += global_timer_ns() - tp3;
+        }
         nchg = nw;
+        if (!solo && nchg <= a.solo_cols) {
+            if (gtid == 0) {
+                const uint64_t now = global_timer_ns();
+                ctl->t_grid_ns += now - t_mode;
+                t_mode = now;
+                if (ctl->solo_round == 0u) ctl->solo_round = r + 1u;
+                ctl->solo_entries += 1u;
+            }
+            if (blockIdx.x != 0) {
+                // parked (nothing of this CTA is in flight) until CTA 0 wakes
+                // the grid or ends the rounds; bounded by the rounds' budget
+                if (threadIdx.x == 0) {
+                    const uint64_t t0 = global_timer_ns();
+                    uint32_t g;
+                    while ((g = ld_acquire_u32(&ctl->park_gen)) == pgen) {
+                        if (global_timer_ns() - t0 > a.budget_ns + kWaitLimitNs) {
+                            set_status(ctr, kStTimeout);
+                            break;
+                        }
+                        __nanosleep(1000);
+                    }
+                    sh_wake[0] = g == pgen ? 1u : ld_acquire_u32(&ctl->park_exit);
+                    sh_wake[1] = ctl->park_round;
+                    sh_wake[2] = ctl->park_nchg;
+                }
+                __syncthreads();
+                const bool leave = sh_wake[0] != 0u;
+                const uint32_t rr = sh_wake[1], nn = sh_wake[2];
+                __syncthreads();
+                if (leave) return;
+                ++pgen;
+                r = rr - 1u;  // the loop's increment makes it rr
+                nchg = nn;
+                continue;
+            }
+            solo = true;
+        } else if (solo && nchg > 2u * a.solo_cols) {
+            // wake the grid for round r + 1 (every global write of this CTA
+            // is ordered before the release)
+            __threadfence();
+            __syncthreads();
+            if (gtid == 0) {
+                const uint64_t now = global_timer_ns();
+                ctl->t_solo_ns += now - t_mode;
+                t_mode = now;
+                ctl->park_round = r + 1u;
+                ctl->park_nchg = nchg;
+                st_release_u32(&ctl->park_gen, pgen + 1u);
+            }
+            ++pgen;
+            solo = false;
+        }
     }
 }
 
@@ -683,6 +827,7 @@ __global__ void __launch_bounds__(kHT) k_h1_emit(const __grid_constant__ ItemTab
 }
 
 std::atomic<int> g_h1_budget_ms{30000};
+std::atomic<int> g_h1_solo_cols{kSoloDefault};
 
 int grid_of(int64_t n) {
     const int64_t blocks = (n + kHT - 1) / kHT;
@@ -694,6 +839,8 @@ int grid_of(int64_t n) {
 
 void set_h1_budget_ms(int ms) { g_h1_budget_ms.store(ms); }
 int get_h1_budget_ms() { return g_h1_budget_ms.load(); }
+void set_h1_solo_cols(int n) { g_h1_solo_cols.store(n); }
+int get_h1_solo_cols() { return g_h1_solo_cols.load(); }
 
 cudaError_t launch_h1(const ItemTable& tab, const H1Bufs& b, Counters* ctr, cp_pair* pairs, uint32_t pair_cap,
                       cudaStream_t s) {
@@ -719,6 +866,7 @@ cudaError_t launch_h1(const ItemTable& tab, const H1Bufs& b, Counters* ctr, cp_p
     ra.b = b;
     ra.ctr = ctr;
     ra.budget_ns = uint64_t(get_h1_budget_ms()) * 1000000ull;
+    ra.solo_cols = uint32_t(get_h1_solo_cols());
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(reduce_blocks);
     cfg.blockDim = dim3(kRT);

@@ -186,9 +186,15 @@ struct H1Ctl {
     uint32_t neg_e, pos_q, pos_e; // checks: marked edges, marked squares, unmarked edges
     uint32_t rounds;              // reduction rounds run
     uint32_t stop[2];             // a round's merges hit an error (read one round later, by parity)
-    uint32_t pad;
+    uint32_t solo_round;          // the round from which the first CTA ran the rounds alone (0: never)
     unsigned long long grown;     // pool entries taken by merged columns
-    unsigned long long pad2[2];
+    unsigned long long t_grid_ns, t_solo_ns;  // wall time of the rounds on the whole grid / in one CTA
+    unsigned long long t_phase_ns[4];  // thread 0 of CTA 0, summed over rounds: its bids, the wait after
+                                       // them, its merges, the wait after them
+    unsigned long long additions, merged;  // column additions, and the entries they read
+    uint32_t park_gen, park_exit, park_round, park_nchg;  // the first CTA wakes the parked ones
+    uint32_t solo_entries;        // times the first CTA went on alone
+    uint32_t nw_hist[16];         // rounds by losing columns: bucket floor(log2(count)), capped at 15
 };
 struct H1Bufs {
     uint32_t* neg_e;         // bitmap over edge ids (cell_id3): edge kills an H0 class
@@ -221,6 +227,10 @@ cudaError_t launch_h1(const ItemTable& tab, const H1Bufs& b, Counters* ctr, cp_p
 // returns CP_ERR_TIMEOUT.
 void set_h1_budget_ms(int ms);
 int get_h1_budget_ms();
+// Columns entering a round at or below which the first CTA runs the
+// cross-star rounds alone (0: never).
+void set_h1_solo_cols(int n);
+int get_h1_solo_cols();
 
 // ---- K4 emission, K5 backward
 cudaError_t launch_init(const ItemTable& tab, Counters* ctr, uint32_t* uft, uint64_t* aget, uint64_t* rest,

@@ -222,3 +222,22 @@ def test_full_time_budget(cp):
     # volumes above the practical bound need an explicit opt-in
     with pytest.raises(ValueError):
         cp.persistence_full(torch.zeros((129, 128, 128), device="cuda"))
+
+
+@pytest.mark.parametrize("solo", [0, 1, 8, 1024])
+def test_full_solo_rounds(cp, solo):
+    """The cross-star rounds give the same pairs whether the grid runs every
+    round (0), or the first CTA runs the rounds with few columns alone and
+    wakes the grid again (1, 8), or runs nearly all of them alone (1024)."""
+    from paper_2606_04801_gb300 import _lib
+
+    lib = _lib.load()
+    old = lib.cp_get_tuning(6)
+    try:
+        assert lib.cp_set_tuning(6, solo) == 0
+        for seed, (shape, sigma) in enumerate([((24, 20, 22), 1.5), ((33, 17, 19), 2.0)]):
+            _check(cp, workloads.blurred(shape, sigma, seed), f"blurred {shape} solo={solo}")
+        rng = np.random.default_rng(900 + solo)
+        _check(cp, rng.random((14, 15, 16), dtype=np.float32), f"uniform solo={solo}")
+    finally:
+        lib.cp_set_tuning(6, old)
