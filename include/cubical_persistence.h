@@ -88,7 +88,7 @@ typedef struct cp_stats {
     int64_t top_rounds;       /* rounds of the dual union-find */
     int64_t pairs;            /* reported pairs (nonzero persistence + essential) */
     uint32_t status;          /* raw device status bits */
-    uint32_t pad;
+    uint32_t mst_rounds;      /* Borůvka rounds (CP_TUNE_UF_VARIANT = 1), else 0 */
 } cp_stats;
 
 /* ---------------------------------------------------------------- info */
@@ -487,6 +487,14 @@ int cubical_persistence_debug_wait_timeout(void *d_workspace, size_t ws_bytes, i
  *                        alone while the others wait, until more than twice
  *                        as many enter one (0 .. 1024; 0: every round on the
  *                        whole grid; default 16).  Same pairs.
+ *   CP_TUNE_UF_VARIANT   0 (default): the elder-rule union-find runs in
+ *                        reservation rounds over every survivor; 1: Borůvka's
+ *                        minimum spanning forest of the survivor graph first
+ *                        (the survivors the union-find commits), then the
+ *                        rounds over the forest's edges alone.  Same pairs.
+ *                        Calls with H1 or with cross-pruning of images keep
+ *                        0.  Read when the workspace is sized: set it before
+ *                        the _workspace_size call.
  * cp_set_tuning returns CP_OK or CP_ERR_ARG; cp_get_tuning the value or -1.
  * The autotuner in the Python package picks these per GPU and shape.
  */
@@ -496,6 +504,7 @@ int cubical_persistence_debug_wait_timeout(void *d_workspace, size_t ws_bytes, i
 #define CP_TUNE_H1_BUDGET_MS 4
 #define CP_TUNE_CROSS_PRUNE_2D 5
 #define CP_TUNE_H1_SOLO 6
+#define CP_TUNE_UF_VARIANT 7
 int cp_set_tuning(int key, int value);
 int cp_get_tuning(int key);
 

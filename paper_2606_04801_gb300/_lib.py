@@ -48,7 +48,7 @@ class CpStats(ctypes.Structure):
         ("top_rounds", ctypes.c_int64),
         ("pairs", ctypes.c_int64),
         ("status", ctypes.c_uint32),
-        ("pad", ctypes.c_uint32),
+        ("mst_rounds", ctypes.c_uint32),
     ]
 
 

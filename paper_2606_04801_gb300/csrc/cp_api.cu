@@ -100,12 +100,17 @@ struct Plan {
     // slab split of the union-finds (calls that ask for it): slabs per item
     // and the buffers of cp_slab.cu
     int slabs = 0;
+    bool split_bufs = false;  // the compaction buffers below are laid out
     size_t o_sl_ctr, o_sl_flag, o_sl_vcnt, o_sl_k0, o_sl_k1, o_sl_act, o_sl_a, o_sl_b, o_sl_map, o_sl_sub0,
         o_sl_sub1, o_sl_died0, o_sl_died1;
+    // the Borůvka variant of the union-finds (CP_TUNE_UF_VARIANT = 1)
+    bool boruvka = false;
+    size_t o_bv_comp0, o_bv_comp1, o_bv_best0, o_bv_best1, o_bv_hook0, o_bv_hook1, o_bv_act0, o_bv_act1;
     size_t bytes = 0;
 };
 
 size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
+void plan_boruvka(Plan& P);
 
 // h1: also lay out the H1 stage of the 3D items, with h1_pool pool entries
 // for the columns that additions create (0: 4 per column + 2^20).
@@ -250,23 +255,24 @@ int make_plan(int n_items, const int32_t* ndims, const int64_t* dims, const floa
         P.o_h1_pool = take(sizeof(uint64_t) * P.h1_pool);
     }
     P.bytes = o;
+    if (uf_variant() == 1) plan_boruvka(P);
     return CP_OK;
 }
 
 // Appends the slab split's buffers to a plan: S slabs per item (each item
 // cut along its slowest axis).  Both survivor lists must sit side by side in
 // the scratch lists, so 2D items with cross-pruning are refused.
-int plan_slabs(Plan& P, int S) {
-    if (S < 1 || S > (1 << 16)) return CP_ERR_ARG;
-    if (P.tab.n2d > 0 && P.tab.cross2d) return CP_ERR_ARG;
-    if (P.h1) return CP_ERR_ARG;
+// The stable compactions' buffers (shared by the slab split and the
+// Borůvka variant).
+void plan_split_buffers(Plan& P) {
+    if (P.split_bufs) return;
     size_t o = P.bytes;
     auto take = [&](size_t bytes) {
         size_t at = o;
         o = align_up(o + bytes);
         return at;
     };
-    P.slabs = S;
+    P.split_bufs = true;
     P.o_sl_ctr = take(sizeof(SlabCtr));
     P.o_sl_flag = take(size_t(P.cap_s));
     P.o_sl_vcnt = take(sizeof(uint32_t) * slab_vblocks_cap(P.cap_s));
@@ -281,7 +287,38 @@ int plan_slabs(Plan& P, int S) {
     P.o_sl_died0 = take(sizeof(uint32_t) * P.cap_r0);
     P.o_sl_died1 = take(sizeof(uint32_t) * P.cap_rt);
     P.bytes = o;
+}
+
+int plan_slabs(Plan& P, int S) {
+    if (S < 1 || S > (1 << 16)) return CP_ERR_ARG;
+    if (P.tab.n2d > 0 && P.tab.cross2d) return CP_ERR_ARG;
+    if (P.h1) return CP_ERR_ARG;
+    P.slabs = S;
+    plan_split_buffers(P);
     return CP_OK;
+}
+
+// The Borůvka variant's arrays (calls whose two lists run side by side and
+// without H1).
+void plan_boruvka(Plan& P) {
+    if (P.h1 || (P.tab.n2d > 0 && P.tab.cross2d)) return;
+    plan_split_buffers(P);
+    size_t o = P.bytes;
+    auto take = [&](size_t bytes) {
+        size_t at = o;
+        o = align_up(o + bytes);
+        return at;
+    };
+    P.boruvka = true;
+    P.o_bv_comp0 = take(sizeof(uint32_t) * P.cap_r0);
+    P.o_bv_comp1 = take(sizeof(uint32_t) * P.cap_rt);
+    P.o_bv_best0 = take(sizeof(uint32_t) * P.cap_r0);
+    P.o_bv_best1 = take(sizeof(uint32_t) * P.cap_rt);
+    P.o_bv_hook0 = take(sizeof(uint32_t) * P.cap_r0);
+    P.o_bv_hook1 = take(sizeof(uint32_t) * P.cap_rt);
+    P.o_bv_act0 = take(sizeof(uint32_t) * P.cap_s);
+    P.o_bv_act1 = take(sizeof(uint32_t) * P.cap_s);
+    P.bytes = o;
 }
 
 template <class T>
@@ -612,6 +649,68 @@ int run(const Plan& P, cp_pair* d_out, int64_t capacity, int64_t* h_out_count, i
         for (int q = 0; q < 2; ++q) {
             u[q].d_nkeys = &sc->n_merge[q];
             u[q].pairs = up[q].pairs;
+        }
+        CP_TRY(launch_uf(P.tab, u, 2, s));
+        mark(5, s);
+    } else if (P.boruvka) {
+        // Borůvka's forest of both lists, then the union-find rounds over its
+        // edges alone (compacted in order); stage times: the forest in the
+        // union-find slot, compaction and pairing in the dual one
+        mark(3, s);
+        g_ev_joint = true;
+        SlabCtr* sc = at<SlabCtr>(ws, P.o_sl_ctr);
+        CP_TRY(cudaMemsetAsync(sc, 0, sizeof(SlabCtr), s));
+        BoruvkaArgs ba;
+        ba.d_n[0] = &ctr->n_s0;
+        ba.d_n[1] = &ctr->n_st;
+        ba.cap = P.cap_s;
+        ba.n_rids[0] = P.cap_r0;
+        ba.n_rids[1] = P.cap_rt;
+        ba.na = na0;
+        ba.nb = nb0;
+        ba.comp[0] = at<uint32_t>(ws, P.o_bv_comp0);
+        ba.comp[1] = at<uint32_t>(ws, P.o_bv_comp1);
+        ba.best[0] = at<uint32_t>(ws, P.o_bv_best0);
+        ba.best[1] = at<uint32_t>(ws, P.o_bv_best1);
+        ba.hook[0] = at<uint32_t>(ws, P.o_bv_hook0);
+        ba.hook[1] = at<uint32_t>(ws, P.o_bv_hook1);
+        ba.act[0] = at<uint32_t>(ws, P.o_bv_act0);
+        ba.act[1] = at<uint32_t>(ws, P.o_bv_act1);
+        ba.flag = at<uint8_t>(ws, P.o_sl_flag);
+        ba.d_rounds = &ctr->mst_rounds;
+        ba.ctr = ctr;
+        CP_TRY(launch_boruvka(ba, s));
+        mark(4, s);
+        SlabArgs sa = {};
+        sa.tab = P.tab;
+        sa.S = 1;
+        sa.d_n[0] = &ctr->n_s0;
+        sa.d_n[1] = &ctr->n_st;
+        sa.cap = P.cap_s;
+        sa.keys[0] = s0;
+        sa.keys[1] = st;
+        sa.n_rids[0] = P.cap_r0;
+        sa.n_rids[1] = P.cap_rt;
+        sa.na = na0;
+        sa.nb = nb0;
+        sa.flag = ba.flag;
+        sa.vcnt = at<uint32_t>(ws, P.o_sl_vcnt);
+        sa.sc = sc;
+        sa.ctr = ctr;
+        sa.ko[0] = at<uint64_t>(ws, P.o_sl_k0);
+        sa.ko[1] = at<uint64_t>(ws, P.o_sl_k1);
+        sa.act = at<uint32_t>(ws, P.o_sl_act);
+        sa.oa = at<uint32_t>(ws, P.o_sl_a);
+        sa.ob = at<uint32_t>(ws, P.o_sl_b);
+        sa.map = nullptr;
+        CP_TRY(launch_slab_compact(sa, 0, sc->n_in, s));
+        UfParams u[2] = {up[0], up[1]};
+        for (int q = 0; q < 2; ++q) {
+            u[q].keys = sa.ko[q];
+            u[q].d_nkeys = &sc->n_in[q];
+            u[q].act[0] = sa.act;
+            u[q].na[0] = sa.oa;
+            u[q].nb[0] = sa.ob;
         }
         CP_TRY(launch_uf(P.tab, u, 2, s));
         mark(5, s);
@@ -1079,6 +1178,7 @@ int cubical_persistence_stats(const void* d_workspace, cp_stats* h_stats, void* 
     h_stats->top_rounds = h.roundst;
     h_stats->pairs = h.out_count;
     h_stats->status = h.status;
+    h_stats->mst_rounds = h.mst_rounds;
     return status_to_code(h.status);
 }
 

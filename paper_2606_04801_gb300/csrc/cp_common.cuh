@@ -61,7 +61,7 @@ struct Counters {
     uint32_t find_ctr;        // work counter of the first union-find round's root walks
     uint32_t tma_tasks;       // 3D pruning tasks whose planes came by TMA (a check that the path runs)
     uint32_t t_keep;          // T-filtration calls: pairs kept after the mapping (the output count)
-    uint32_t pad;
+    uint32_t mst_rounds;      // Borůvka rounds (the spanning-forest union-find variant), else 0
     unsigned long long gmin[kMaxItems];  // (ord bits << 32 | local vertex) of each item's minimum
     int64_t out_count;
     // union-find trace: active survivors and device time at the start of each

@@ -135,6 +135,7 @@ struct SlabCtr {
     uint32_t rounds_slab[2]; // rounds of stage 1
     uint32_t n_final[2];     // stage 1 commits whose pairs stage 1 wrote (their dying class met no crossing survivor)
 };
+// The Borůvka variant's counts share this block: n_in = forest edges per list.
 struct SlabArgs {
     ItemTable tab;
     int S;                       // slabs per item
@@ -162,6 +163,24 @@ struct SlabArgs {
     cp_pair* pairs;              // the final commits' pairs are appended here
     uint32_t pair_cap;
 };
+// ---- Borůvka's minimum spanning forest of both survivor lists (cp_boruvka.cu)
+struct BoruvkaArgs {
+    const uint32_t* d_n[2];      // survivors of the H0 and dual lists (device counts)
+    uint32_t cap;                // scratch capacity (the two lists side by side)
+    uint32_t n_rids[2];          // root ids per list
+    const uint32_t* na;          // root ids of both endpoints of every slot (list 1 after list 0)
+    const uint32_t* nb;
+    uint32_t* comp[2];           // per root id: its component's representative
+    uint32_t* best[2];           // per representative: the smallest sorted index leaving it
+    uint32_t* hook[2];           // per representative: the component it hooks to this round
+    uint32_t* act[2];            // active slots (ping-pong, cap entries each)
+    uint8_t* flag;               // per slot: 1 a forest edge, 2 not
+    uint32_t* d_rounds;          // rounds run
+    Counters* ctr;
+};
+cudaError_t launch_boruvka(const BoruvkaArgs& a, cudaStream_t s);
+int uf_variant();  // 0: reservation rounds over every survivor; 1: Borůvka, then rounds over its forest
+
 // Entries of SlabArgs::vcnt for a scratch capacity.
 uint32_t slab_vblocks_cap(uint32_t cap);
 // Flags each slot internal or crossing (kStCapacity if the lists are not
@@ -270,7 +289,7 @@ cudaError_t launch_backward(const cp_pair* pairs, int64_t n, const float* gb, co
 int device_sm_count();
 // init() run once per device and slot (thread-safe), its result cached: the
 // launch set-up of a kernel (attributes, occupancy-derived grid size).
-enum { kCachePrune3d, kCachePrune2d, kCacheSort, kCacheUf, kCacheRoots, kCacheH1, kCacheSlots };
+enum { kCachePrune3d, kCachePrune2d, kCacheSort, kCacheUf, kCacheRoots, kCacheH1, kCacheBoruvka, kCacheSlots };
 int device_cached(int slot, int (*init)());
 
 // Kernel launches made by the library (for the benchmark's launch count).

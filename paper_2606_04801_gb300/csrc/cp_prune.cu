@@ -1001,11 +1001,12 @@ bool encode_plane_map(CUtensorMap* map, const float* img, int64_t D, int64_t H, 
 }
 int prune_tile_x() { return kOX2; }
 int prune_tile_x3d() { return kOX; }
-int g_rows2d = 64, g_zchunk3d = kZC, g_ctas3d = 0, g_cross2d = 0;  // tuning (cp_set_tuning)
+int g_rows2d = 64, g_zchunk3d = kZC, g_ctas3d = 0, g_cross2d = 0, g_uf_variant = 0;  // tuning (cp_set_tuning)
 int prune_tile_y2d() { return g_rows2d; }
 int prune_tile_y3d() { return kOY; }
 int prune_tile_z3d() { return g_zchunk3d; }
 int prune_cross2d() { return g_cross2d; }
+int uf_variant() { return g_uf_variant; }
 
 int set_tuning(int key, int value) {
     switch (key) {
@@ -1025,13 +1026,22 @@ int set_tuning(int key, int value) {
             if (value != 0 && value != 1) return -1;
             g_cross2d = value;
             return 0;
+        case 7:  // union-find design: reservation rounds (0) or Borůvka's forest first (1)
+            if (value != 0 && value != 1) return -1;
+            g_uf_variant = value;
+            return 0;
         default:
             return -1;
     }
 }
 
 int get_tuning(int key) {
-    return key == 1 ? g_zchunk3d : key == 2 ? g_ctas3d : key == 3 ? g_rows2d : key == 5 ? g_cross2d : -1;
+    return key == 1 ? g_zchunk3d
+           : key == 2 ? g_ctas3d
+           : key == 3 ? g_rows2d
+           : key == 5 ? g_cross2d
+           : key == 7 ? g_uf_variant
+                      : -1;
 }
 
 // Table entry as two 32-bit words:

@@ -47,7 +47,29 @@ def test_autotune_picks_and_caches(cp, tmp_path):
         cfg = autotune.autotune([vol], cache=str(tmp_path / "t.json"))
         assert cfg["trials"] >= 15 and cfg["ms"] > 0
         assert autotune.current()["zchunk3d"] == cfg["zchunk3d"]
+        # the union-find design is measured too, and the faster one kept
+        assert set(cfg["forward_ms"]) == {"0", "1"}
+        assert cfg["uf_variant"] == min((0, 1), key=lambda v: cfg["forward_ms"][str(v)])
+        assert autotune.current()["uf_variant"] == cfg["uf_variant"]
+        assert "|surv:" in cfg["key"]
         again = autotune.autotune([vol], cache=str(tmp_path / "t.json"))
         assert again["ms"] == cfg["ms"]  # served from the cache
+    finally:
+        autotune.apply(saved)
+
+
+def test_autotune_key_follows_the_data(cp, tmp_path):
+    """Smooth fields and i.i.d. noise of one shape leave very different
+    survivor fractions, so they get separate cache entries."""
+    from paper_2606_04801_gb300 import autotune
+
+    saved = autotune.current()
+    try:
+        smooth = torch.from_numpy(workloads.blurred((64, 64, 64), 3.0, 44)).cuda()
+        noise = torch.from_numpy(workloads.uniform((64, 64, 64), 45)).cuda()
+        assert autotune.survivor_fraction([noise]) > 8 * autotune.survivor_fraction([smooth])
+        a = autotune.autotune([smooth], cache=str(tmp_path / "k.json"))
+        b = autotune.autotune([noise], cache=str(tmp_path / "k.json"))
+        assert a["key"] != b["key"]
     finally:
         autotune.apply(saved)

@@ -136,7 +136,8 @@ def test_pruned_restatement_matches_oracle_3d(lib, seed):
 
 def test_tuning_arguments(lib):
     keys = {1: (64, [4, 16, 256], [0, 3, 5000]), 2: (0, [0, 2, 4], [-1, 9]), 3: (64, [4, 37, 4096], [0, 3, 4097]),
-            4: (30000, [0, 1, 3600000], [-1, 3600001]), 5: (0, [0, 1], [-1, 2]), 6: (16, [0, 1, 1024], [-1, 1025])}
+            4: (30000, [0, 1, 3600000], [-1, 3600001]), 5: (0, [0, 1], [-1, 2]), 6: (16, [0, 1, 1024], [-1, 1025]),
+            7: (0, [0, 1], [-1, 2])}
     for key, (default, good, bad) in keys.items():
         old = lib.cp_get_tuning(key)
         try:
