@@ -1037,6 +1037,9 @@ def main():
                     "2d: the 2048x2048 random field and its 256-level form; full: the whole diagram (H0, H1, H2) "
                     "of the 512^3 volume; slabs: the slab split of the union-finds on the 512^3 volume")
     ap.add_argument("--slabs", default="2,4,8,16,64,152", help="slab counts of the slabs workload (comma-separated)")
+    ap.add_argument("--uf-variant", default="auto", choices=["auto", "0", "1"],
+                    help="union-find design of the volume workload: the autotuner's pick (auto), reservation rounds "
+                    "(0) or Borůvka's forest first (1)")
     ap.add_argument("--eager", action="store_true", help="batched workload without the CUDA graph (per-kernel profiling)")
     args = ap.parse_args()
     global SIDE
@@ -1083,6 +1086,9 @@ def main():
     from paper_2606_04801_gb300 import autotune
 
     tuned = autotune.autotune([torch.from_numpy(vol).to(dev)])
+    if args.uf_variant != "auto":  # profiling one union-find design regardless of the tuner's pick
+        lib.cp_set_tuning(7, int(args.uf_variant))
+        tuned["uf_variant"] = int(args.uf_variant)
     T = (SIDE - 1) ** 3
     x = torch.from_numpy(vol).to(dev)
     stream = torch.cuda.current_stream(dev)
@@ -1300,7 +1306,7 @@ def main():
             "loss_min_persistence": TAU,
             "l2": "input (512 MiB) larger than L2; no flush",
             "parallelism": "replicas" if ws > 1 else "single",
-            "tuning": {k: tuned[k] for k in ("zchunk3d", "ctas3d", "rows2d")},
+            "tuning": {k: tuned[k] for k in ("zchunk3d", "ctas3d", "rows2d", "uf_variant")},
         },
         "roofline": roofline,
         "cpu_baseline": cpu,
@@ -1315,7 +1321,8 @@ def main():
         "uf_trace": trace,
         "counts": {"pairs": st["pairs"], "h0_survivors": s0, "top_survivors": stp, "h0_roots": r0, "top_roots": rt,
                    "survivor_fraction": (s0 + stp) / N,
-                   "h0_rounds": st["h0_rounds"], "top_rounds": st["top_rounds"]},
+                   "h0_rounds": st["h0_rounds"], "top_rounds": st["top_rounds"],
+                   "mst_rounds": st.get("mst_rounds", 0)},
     }
     print(json.dumps(line), flush=True)
 
