@@ -454,7 +454,7 @@ struct ColSrc {
 // lane keeps a c entry unless the next p entry equals it, and a p entry unless
 // the last c entry taken equals it.  A first pass counts each lane's
 // survivors, a warp prefix sum places them, a second pass writes.
-constexpr uint32_t kME = 4;          // merged positions per lane and tile
+constexpr uint32_t kME = 12;         // merged positions per lane and tile
 constexpr uint32_t kMT = 32 * kME;   // merged positions per tile
 struct MergeTile {
     uint64_t c[kMT + 1];  // c[it - 1 .. it + kMT) (~0 before c's first entry)
@@ -632,7 +632,7 @@ __global__ void __launch_bounds__(kRT) k_h1_reduce(const __grid_constant__ Reduc
         set_status(ctr, kStInternal);
     __shared__ uint32_t sh_n, sh_stop;
     __shared__ uint64_t sh_col[kRT / 32][2][32];  // per warp: two star columns decoded
-    __shared__ MergeTile sh_tile[kRT / 32];       // per warp: the staged tile of a merge
+    extern __shared__ MergeTile sh_tile[];        // per warp: the staged tile of a merge (kRT / 32)
     uint32_t epoch = 0;
     const uint64_t t_start = global_timer_ns();  // read by thread 0 of CTA 0 only
     uint64_t t_mode = t_start;   // start of the current mode (thread 0 of CTA 0)
@@ -848,9 +848,13 @@ cudaError_t launch_h1(const ItemTable& tab, const H1Bufs& b, Counters* ctr, cp_p
     const int64_t v0 = tab.it[tab.n2d].voff;
     const Item& last = tab.it[tab.n - 1];
     const int64_t v1 = last.voff + int64_t(last.D) * last.H * last.W;
+    constexpr size_t kTileBytes = sizeof(MergeTile) * (kRT / 32);
     const int reduce_blocks = device_cached(kCacheH1, [] {
+        if (cudaFuncSetAttribute(k_h1_reduce, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kTileBytes)) !=
+            cudaSuccess)
+            return -1;
         int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_h1_reduce, kRT, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_h1_reduce, kRT, kTileBytes);
         return per_sm > 0 ? device_sm_count() * per_sm : -1;
     });
     if (reduce_blocks <= 0) return cudaErrorLaunchOutOfResources;
@@ -870,7 +874,7 @@ cudaError_t launch_h1(const ItemTable& tab, const H1Bufs& b, Counters* ctr, cp_p
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(reduce_blocks);
     cfg.blockDim = dim3(kRT);
-    cfg.dynamicSmemBytes = 0;
+    cfg.dynamicSmemBytes = kTileBytes;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;
