@@ -57,6 +57,19 @@ def main():
     for img in (workloads.uniform((9, 10, 11), 6), workloads.blurred((24, 20, 22), 1.5, 7)):
         got = cp.persistence_full(torch.from_numpy(img).to(dev)).numpy()
         same(got, oracle.persistence_full(img), f"full {img.shape}")
+    # the slab split of the union-finds (with the boundary reduction) and the
+    # Borůvka design of the union-finds
+    for img, S in ((workloads.blurred((40, 24, 28), 1.5, 8), 3), (workloads.uniform((33, 29), 9), 4),
+                   (workloads.uniform((20, 12, 14), 10), 20)):
+        d = cp.persistence_slabs(torch.from_numpy(img).to(dev), S)
+        same(d.numpy(), oracle.persistence(img), f"slabs {img.shape} S={S}")
+    assert lib.cp_set_tuning(7, 1) == 0
+    try:
+        for img in (workloads.blurred((36, 30, 26), 1.5, 11), workloads.uniform((45, 51), 12)):
+            d = cp.persistence(torch.from_numpy(img).to(dev))
+            same(d.numpy(), oracle.persistence(img), f"boruvka {img.shape}")
+    finally:
+        lib.cp_set_tuning(7, 0)
     # the fused loss backward through the batched graph
     items = workloads.batch(0, n2d=3, n3d=1, scale=0.12)
     bp = cp.BatchedPersistence([a.shape for a in items], tau=0.05, graph=True)
