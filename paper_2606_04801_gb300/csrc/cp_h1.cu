@@ -542,6 +542,127 @@ __device__ uint32_t warp_merge(const H1Bufs& b, const ColSrc& c, const ColSrc& p
     return written;
 }
 
+// A merge that the first CTA, running the rounds alone, does with all its
+// threads (a long one): the same merge path as warp_merge, in tiles of kCT
+// positions, kCE per thread, with a CTA-wide prefix sum placing the kept
+// entries.  The tile reuses the warps' shared tile space (no warp merge runs
+// meanwhile).
+constexpr uint32_t kCE = 4;
+constexpr uint32_t kCT = kRT * kCE;
+constexpr uint32_t kCtaMergeMin = 1024;  // entries from which a lone CTA merges together
+struct CtaTile {
+    uint64_t c[kCT + 1];
+    uint64_t p[kCT];
+};
+static_assert(sizeof(CtaTile) <= sizeof(MergeTile) * (kRT / 32), "the CTA tile reuses the warps' tiles");
+struct MergeJob {
+    ColSrc c, p;
+    uint64_t base;
+    uint32_t q, cap, into;
+    uint64_t sc[32], sp[32];  // a source still in its star mask, decoded (its ColSrc points here)
+};
+constexpr uint32_t kJobs = 16;  // long merges queued per round; beyond, warps merge them
+
+__device__ uint32_t cta_merge(const H1Bufs& b, const ColSrc& c, const ColSrc& p, uint64_t* out, CtaTile& t,
+                              uint32_t* sh) {
+    const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+    const uint32_t nc = c.len - 1u, np = p.len - 1u, total = nc + np;
+    auto gc = [&](uint32_t i) { return c.off != ~0ull ? __ldcg(b.pool + c.off + 1 + i) : c.sm[1 + i]; };
+    auto gp = [&](uint32_t i) { return p.off != ~0ull ? __ldcg(b.pool + p.off + 1 + i) : p.sm[1 + i]; };
+    uint32_t it = 0, jt = 0, written = 0;
+    for (uint32_t dt = 0; dt < total; dt += kCT) {
+        const uint32_t tn = min(kCT, total - dt);
+        const uint32_t cn = min(tn, nc - it), pn = min(tn, np - jt);
+        {
+            uint64_t vc[kCE + 1], vp[kCE];
+#pragma unroll
+            for (uint32_t s = 0; s <= kCE; ++s) {
+                const uint32_t k = tid + kRT * s;
+                vc[s] = k <= cn ? ((it + k == 0u) ? ~0ull : gc(it + k - 1u)) : 0ull;
+            }
+#pragma unroll
+            for (uint32_t s = 0; s < kCE; ++s) {
+                const uint32_t k = tid + kRT * s;
+                vp[s] = k < pn ? gp(jt + k) : 0ull;
+            }
+#pragma unroll
+            for (uint32_t s = 0; s <= kCE; ++s)
+                if (tid + kRT * s <= cn) t.c[tid + kRT * s] = vc[s];
+#pragma unroll
+            for (uint32_t s = 0; s < kCE; ++s)
+                if (tid + kRT * s < pn) t.p[tid + kRT * s] = vp[s];
+        }
+        __syncthreads();
+        const uint32_t d0 = min(tn, tid * kCE), d1 = min(tn, d0 + kCE);
+        uint32_t lo = d0 > pn ? d0 - pn : 0u, hi = min(d0, cn);
+        while (lo < hi) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (t.c[mid + 1u] >= t.p[d0 - mid - 1u]) lo = mid + 1u;
+            else hi = mid;
+        }
+        const uint32_t i0 = lo, j0 = d0 - lo;
+        uint32_t kept = 0, ie = i0, je = j0, tile_total = 0;
+        for (int pass = 0; pass < 2; ++pass) {
+            uint64_t* w = nullptr;
+            if (pass == 1) {
+                // CTA-wide exclusive scan of kept (warp scans, then the warp totals)
+                uint32_t incl = kept;
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+                    if (lane >= unsigned(o)) incl += v;
+                }
+                if (lane == 31) sh[warp] = incl;
+                __syncthreads();
+                if (warp == 0) {
+                    const uint32_t v = lane < kRT / 32 ? sh[lane] : 0u;
+                    uint32_t x = v;
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const uint32_t u = __shfl_up_sync(0xFFFFFFFFu, x, o);
+                        if (lane >= unsigned(o)) x += u;
+                    }
+                    if (lane < kRT / 32) sh[lane] = x - v;
+                    if (lane == 31) sh[32] = x;
+                }
+                __syncthreads();
+                w = out + written + sh[warp] + (incl - kept);
+                tile_total = sh[32];
+            }
+            uint32_t i = i0, j = j0;
+            uint64_t x = i < cn ? t.c[i + 1u] : 0, y = j < pn ? t.p[j] : 0;
+            uint64_t prevc = t.c[i];
+            for (uint32_t d = d0; d < d1; ++d) {
+                if (j >= pn || (i < cn && x >= y)) {
+                    const bool keep = !(j < pn && y == x);
+                    if (pass == 0) kept += keep ? 1u : 0u;
+                    else if (keep) *w++ = x;
+                    prevc = x;
+                    ++i;
+                    x = i < cn ? t.c[i + 1u] : 0;
+                } else {
+                    const bool keep = prevc != y;
+                    if (pass == 0) kept += keep ? 1u : 0u;
+                    else if (keep) *w++ = y;
+                    ++j;
+                    y = j < pn ? t.p[j] : 0;
+                }
+            }
+            ie = i;
+            je = j;
+        }
+        __syncthreads();  // sh[0 .. 32] is read by every thread before it is rewritten
+        if (tid == kRT - 1u) {  // its range ends at tn
+            sh[33] = ie;
+            sh[34] = je;
+        }
+        __syncthreads();
+        it += sh[33];
+        jt += sh[34];
+        written += tile_total;
+        __syncthreads();  // the tile and sh are read by every thread before the next tile
+    }
+    return written;
+}
+
 // Column q lost its row to an older column: add that column (F2: the
 // symmetric difference; the common lowest entry cancels).  Columns that no
 // addition has reached yet are read from their star masks.  A column that
@@ -553,8 +674,12 @@ __device__ uint32_t warp_merge(const H1Bufs& b, const ColSrc& c, const ColSrc& p
 // The addition is done by a whole warp, one warp per losing column
 // (warp_merge).  Columns still in their star masks are decoded by the warp
 // into shared memory (sc, sp: 30 keys each).
+// With jobs set (the first CTA running the rounds alone), a long merge is
+// not done here while the queue has room: the warp queues it for the whole
+// CTA (cta_merge), with the keys of a source still in its star mask copied
+// into the job, and the column's region words are written after it.
 __device__ void add_winner_warp(const ReduceArgs& a, uint32_t q, uint32_t r, uint64_t* sc, uint64_t* sp,
-                                MergeTile& tile) {
+                                MergeTile& tile, MergeJob* jobs = nullptr, uint32_t* njobs = nullptr) {
     const H1Bufs& b = a.b;
     const unsigned lane = lane_id();
     auto stop = [&](uint32_t status) {
@@ -610,6 +735,28 @@ __device__ void add_winner_warp(const ReduceArgs& a, uint32_t q, uint32_t r, uin
         if (base + 2ull * cap > b.pool_cap) return stop(kStCapacity);
         into = 0u;
     }
+    if (jobs && need >= kCtaMergeMin) {
+        uint32_t slot = 0;
+        if (lane == 0) slot = atomicAdd(njobs, 1u);
+        slot = __shfl_sync(0xFFFFFFFFu, slot, 0);
+        if (slot < kJobs) {
+            MergeJob& j = jobs[slot];
+            if (c.off == ~0ull) j.sc[lane] = sc[lane];
+            if (pc.off == ~0ull) j.sp[lane] = sp[lane];
+            if (lane == 0) {
+                j.c = c;
+                j.p = pc;
+                j.c.sm = j.sc;
+                j.p.sm = j.sp;
+                j.base = base;
+                j.q = q;
+                j.cap = cap;
+                j.into = into;
+            }
+            __syncwarp();
+            return;
+        }
+    }
     const uint32_t k = warp_merge(b, c, pc, b.pool + base + (into ? uint64_t(cap) : 0ull), tile);
     if (lane == 0) {
         atomicAdd(&b.ctl->additions, 1ull);
@@ -633,6 +780,8 @@ __global__ void __launch_bounds__(kRT) k_h1_reduce(const __grid_constant__ Reduc
     __shared__ uint32_t sh_n, sh_stop;
     __shared__ uint64_t sh_col[kRT / 32][2][32];  // per warp: two star columns decoded
     extern __shared__ MergeTile sh_tile[];        // per warp: the staged tile of a merge (kRT / 32)
+    __shared__ MergeJob sh_jobs[kJobs];           // the first CTA alone: the round's long merges
+    __shared__ uint32_t sh_njobs, sh_scan[35];
     uint32_t epoch = 0;
     const uint64_t t_start = global_timer_ns();  // read by thread 0 of CTA 0 only
     uint64_t t_mode = t_start;   // start of the current mode (thread 0 of CTA 0)
@@ -715,9 +864,37 @@ __global__ void __launch_bounds__(kRT) k_h1_reduce(const __grid_constant__ Reduc
         }
         // ---- every losing column adds the winner of its row
         // (one warp per losing column: long columns are merged 32 lanes wide)
-        for (uint32_t i = gtid >> 5; i < nw; i += gstride >> 5)
-            add_winner_warp(a, __ldcg(work + i), r, sh_col[threadIdx.x >> 5][0], sh_col[threadIdx.x >> 5][1],
-                            sh_tile[threadIdx.x >> 5]);
+        if (!solo) {
+            for (uint32_t i = gtid >> 5; i < nw; i += gstride >> 5)
+                add_winner_warp(a, __ldcg(work + i), r, sh_col[threadIdx.x >> 5][0], sh_col[threadIdx.x >> 5][1],
+                                sh_tile[threadIdx.x >> 5]);
+        } else {
+            // the warps take the additions as on the grid, queueing the long
+            // merges; then the whole CTA does the queued merges one by one
+            if (threadIdx.x == 0) sh_njobs = 0;
+            __syncthreads();
+            for (uint32_t i = threadIdx.x >> 5; i < nw; i += kRT / 32)
+                add_winner_warp(a, __ldcg(work + i), r, sh_col[threadIdx.x >> 5][0], sh_col[threadIdx.x >> 5][1],
+                                sh_tile[threadIdx.x >> 5], sh_jobs, &sh_njobs);
+            __syncthreads();
+            const uint32_t nj = min(sh_njobs, kJobs);
+            for (uint32_t jb = 0; jb < nj; ++jb) {
+                const MergeJob& j = sh_jobs[jb];
+                const uint32_t k = cta_merge(b, j.c, j.p, b.pool + j.base + (j.into ? uint64_t(j.cap) : 0ull),
+                                             *reinterpret_cast<CtaTile*>(sh_tile), sh_scan);
+                if (threadIdx.x == 0) {
+                    atomicAdd(&ctl->additions, 1ull);
+                    atomicAdd(&ctl->merged, (unsigned long long)(j.c.len + j.p.len));
+                    __stcg(b.coff + j.q, j.base);
+                    __stcg(b.ccap + j.q, j.cap | (j.into << 31));
+                    __stcg(b.clen + j.q, k);
+                    if (k == 0) {
+                        set_status(ctr, kStInternal);
+                        atomicOr(&ctl->stop[r & 1u], 1u);
+                    }
+                }
+            }
+        }
         // the budget: one thread decides, every CTA reads the decision (this
         // round's stop word) after the next barrier, so all leave together
         uint64_t tp3 = 0;
