@@ -864,16 +864,12 @@ __global__ void __launch_bounds__(kRT) k_h1_reduce(const __grid_constant__ Reduc
         }
         // ---- every losing column adds the winner of its row
         // (one warp per losing column: long columns are merged 32 lanes wide)
-        if (!solo) {
-            for (uint32_t i = gtid >> 5; i < nw; i += gstride >> 5)
-                add_winner_warp(a, __ldcg(work + i), r, sh_col[threadIdx.x >> 5][0], sh_col[threadIdx.x >> 5][1],
-                                sh_tile[threadIdx.x >> 5]);
-        } else {
-            // the warps take the additions as on the grid, queueing the long
-            // merges; then the whole CTA does the queued merges one by one
+        {
+            // the warps take the additions, queueing the long merges of their
+            // CTA; then the whole CTA does its queued merges one by one
             if (threadIdx.x == 0) sh_njobs = 0;
             __syncthreads();
-            for (uint32_t i = threadIdx.x >> 5; i < nw; i += kRT / 32)
+            for (uint32_t i = gtid >> 5; i < nw; i += gstride >> 5)
                 add_winner_warp(a, __ldcg(work + i), r, sh_col[threadIdx.x >> 5][0], sh_col[threadIdx.x >> 5][1],
                                 sh_tile[threadIdx.x >> 5], sh_jobs, &sh_njobs);
             __syncthreads();
