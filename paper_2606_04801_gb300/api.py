@@ -246,10 +246,11 @@ def persistence_batched(imgs: Sequence[torch.Tensor], max_survivors: int = 0, wi
 
 # Volumes beyond this many voxels (in all) need allow_large=True for H1: the
 # cross-star rounds grow with the area of the longest-lived loops, not with
-# the voxel count, and measured 4.6 s at 128^3 and 24 s at 256^3 on smooth
-# fields.  The device stops the rounds once cp_get_tuning(CP_TUNE_H1_BUDGET_MS)
-# is spent, whatever the size.
-H1_PRACTICAL_VOXELS = 128 ** 3
+# the voxel count (smooth fields, one GB300: 0.11 s at 128^3, 0.84 s at
+# 256^3; at 512^3 the growing columns outran a 45 GB workspace).  The device
+# stops the rounds once cp_get_tuning(CP_TUNE_H1_BUDGET_MS) is spent, whatever
+# the size.
+H1_PRACTICAL_VOXELS = 256 ** 3
 
 
 def _full_call(imgs: Sequence[torch.Tensor], single: bool, max_survivors: int, pool_entries: int,
