@@ -1,7 +1,7 @@
-"""The bounds-checked build (SURVEY's stand-in for a memory checker, which is
-closed on this pool): the parity suite's small cases run through
-libcp_gb300_checked.so in a fresh process and must equal the oracle with no
-call flagged for an out-of-range index (CP_ERR_INTERNAL would fail them)."""
+"""The bounds-checked build (a stand-in for a device memory checker): the
+parity suite's small cases run through libcp_gb300_checked.so in a fresh
+process and must equal the oracle with no call flagged for an out-of-range
+index (CP_ERR_INTERNAL would fail them)."""
 import os
 import subprocess
 import sys
