@@ -13,7 +13,7 @@
 // hooks are flattened, until no survivor leaves a component.  The dual list
 // runs in descending filtration order, which its sorted index already is.
 //
-// One cooperative launch carries both lists through the rounds (three grid
+// One cooperative launch carries both lists through the rounds (four grid
 // barriers per round), in root-id space (the first round's root walks ran
 // before the sort).  The forest's edges are then compacted in order and
 // paired by the union-find (cp_uf.cu).
