@@ -77,3 +77,14 @@ def test_equals_reservation_rounds(cp, boruvka):
         assert a.stats["mst_rounds"] >= 1 and b.stats["mst_rounds"] == 0
         del x
     torch.cuda.empty_cache()
+
+
+def test_with_h1_and_slabs(cp, boruvka):
+    """Calls with H1 keep the reservation rounds, and the slab split keeps its
+    own stages, whatever the setting: both still give the oracle's pairs."""
+    rng = np.random.default_rng(72)
+    img = rng.random((11, 12, 13), dtype=np.float32)
+    _same(cp.persistence_full(torch.from_numpy(img).cuda()).numpy(), oracle.persistence_full(img), "full")
+    d = cp.persistence_slabs(torch.from_numpy(img).cuda(), 3)
+    _same(d.numpy(), oracle.persistence(img), "slabs")
+    assert d.stats["crossing"][0] > 0
