@@ -220,8 +220,10 @@ def test_full_time_budget(cp):
         assert lib.cp_set_tuning(4, old) == 0
     _check(cp, img, "after a spent budget")
     # volumes above the practical bound need an explicit opt-in
+    side = round(cp.api.H1_PRACTICAL_VOXELS ** (1 / 3))
+    assert side ** 3 == cp.api.H1_PRACTICAL_VOXELS
     with pytest.raises(ValueError):
-        cp.persistence_full(torch.zeros((129, 128, 128), device="cuda"))
+        cp.persistence_full(torch.zeros((side + 1, side, side), device="cuda"))
 
 
 @pytest.mark.parametrize("solo", [0, 1, 8, 1024])
