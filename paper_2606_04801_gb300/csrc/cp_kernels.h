@@ -186,8 +186,10 @@ uint32_t slab_vblocks_cap(uint32_t cap);
 // Flags each slot internal or crossing (kStCapacity if the lists are not
 // side by side) and marks the crossing survivors' endpoint classes.
 cudaError_t launch_slab_classify(const SlabArgs& a, cudaStream_t s);
-// Stable compaction of the slots selected by sel (0: internal, 1: crossing or
-// committed) to ko / act / oa / ob (/ map); n_out[q] receives list q's count.
+// Stable compaction of the slots selected by sel (0: flag 1, the slab
+// split's internal survivors or the Borůvka forest's edges; 1: flag 2 or 3,
+// the slab split's crossing and handed-on survivors) to ko / act / oa / ob
+// (/ map); n_out[q] receives list q's count.
 cudaError_t launch_slab_compact(const SlabArgs& a, int sel, uint32_t* n_out, cudaStream_t s);
 // After stage 1: marks the classes that met a crossing survivor, writes the
 // pairs of the commits whose dying class did not and flags the others (with
