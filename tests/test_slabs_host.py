@@ -152,6 +152,37 @@ def _rank_main(rank, world, port, S, img, out):
         dist.destroy_process_group()
 
 
+def _empty_rank_main(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world)
+    try:
+        recs = np.zeros(0 if rank == 1 else 3, dtype=slabs.RECORD_DTYPE)
+        if rank == 0:
+            recs["key"] = [30, 10, 20]
+            recs["age_a"] = [1, 2, 3]
+        merged = slabs.exchange(recs)  # rank 1 sends nothing
+        none = slabs.exchange(np.zeros(0, dtype=slabs.RECORD_DTYPE), dst=1)  # nobody sends anything
+        out.put((rank, None if merged is None else merged.tolist(), None if none is None else len(none)))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_exchange_empty_ranks():
+    world = 2
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_empty_rank_main, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(120)
+        assert p.exitcode == 0
+    res = sorted((q.get(timeout=10) for _ in range(world)), key=lambda r: r[0])
+    assert res[0][1] == [(10, 2, 0), (20, 3, 0), (30, 1, 0)] and res[0][2] is None
+    assert res[1][1] is None and res[1][2] == 0
+
+
 @pytest.mark.parametrize("S", [2, 4])
 def test_exchange_two_gloo_ranks(S):
     world = 2
