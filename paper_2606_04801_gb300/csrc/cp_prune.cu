@@ -231,16 +231,18 @@ __device__ __forceinline__ void warp_flush(WS& ws, WarpCounts& c, const Outs& o)
     __syncwarp();
 }
 
-// lower-than bit: all ones when the neighbour precedes the centre
-__device__ __forceinline__ uint32_t set_le(float a, float b) {
-    uint32_t r;
-    asm("set.le.u32.f32 %0, %1, %2;" : "=r"(r) : "f"(a), "f"(b));
-    return r;
-}
-__device__ __forceinline__ uint32_t set_lt(float a, float b) {
-    uint32_t r;
-    asm("set.lt.u32.f32 %0, %1, %2;" : "=r"(r) : "f"(a), "f"(b));
-    return r;
+// raw |= kBit when the neighbour value u precedes the centre value c (kLe:
+// the neighbour comes earlier in linear order, so it also precedes on a tie;
+// NaN, the out-of-image fill, never precedes): a compare into a predicate and
+// a predicated OR, two instructions per bit
+template <uint32_t kBit, bool kLe>
+__device__ __forceinline__ void or_if_precedes(uint32_t& raw, float u, float c) {
+    if constexpr (kLe)
+        asm("{\n\t.reg .pred p;\n\tsetp.le.f32 p, %1, %2;\n\t@p or.b32 %0, %0, %3;\n\t}"
+            : "+r"(raw) : "f"(u), "f"(c), "n"(kBit));
+    else
+        asm("{\n\t.reg .pred p;\n\tsetp.lt.f32 p, %1, %2;\n\t@p or.b32 %0, %0, %3;\n\t}"
+            : "+r"(raw) : "f"(u), "f"(c), "n"(kBit));
 }
 
 struct Nbr {
@@ -254,20 +256,44 @@ __device__ __forceinline__ void read_nbr(const float* plane, int ly, int lx, Nbr
         for (int c = 0; c < 3; ++c) P.v[r][c] = plane[(ly + r) * kRS + (lx + c)];
 }
 
+template <int n>
+__device__ __forceinline__ void mask_bit(uint32_t& raw, const Nbr& A, const Nbr& B, const Nbr& C, float cv) {
+    constexpr int a = n / 9, b = (n / 3) % 3, c = n % 3;
+    const Nbr& P = a == 0 ? A : (a == 1 ? B : C);
+    or_if_precedes<(1u << n), (n < 13)>(raw, P.v[b][c], cv);
+}
+
 // raw mask: bit n = 9a + 3b + c set when the neighbour at plane a, row b,
 // column c precedes the centre (ties: earlier linear index first)
 __device__ __forceinline__ uint32_t mask26(const Nbr& A, const Nbr& B, const Nbr& C) {
     const float cv = B.v[1][1];
     uint32_t raw = 0;
-#pragma unroll
-    for (int n = 26; n >= 0; --n) {
-        if (n == 13) continue;
-        const int a = n / 9, b = (n / 3) % 3, c = n % 3;
-        const Nbr& P = a == 0 ? A : (a == 1 ? B : C);
-        const uint32_t t = n < 13 ? set_le(P.v[b][c], cv) : set_lt(P.v[b][c], cv);
-        raw = (raw << 1) - t;  // append one bit (t is 0 or all ones)
-        if (n == 14) raw <<= 1;  // leave bit 13 (the centre) clear
-    }
+    mask_bit<0>(raw, A, B, C, cv);
+    mask_bit<1>(raw, A, B, C, cv);
+    mask_bit<2>(raw, A, B, C, cv);
+    mask_bit<3>(raw, A, B, C, cv);
+    mask_bit<4>(raw, A, B, C, cv);
+    mask_bit<5>(raw, A, B, C, cv);
+    mask_bit<6>(raw, A, B, C, cv);
+    mask_bit<7>(raw, A, B, C, cv);
+    mask_bit<8>(raw, A, B, C, cv);
+    mask_bit<9>(raw, A, B, C, cv);
+    mask_bit<10>(raw, A, B, C, cv);
+    mask_bit<11>(raw, A, B, C, cv);
+    mask_bit<12>(raw, A, B, C, cv);
+    mask_bit<14>(raw, A, B, C, cv);
+    mask_bit<15>(raw, A, B, C, cv);
+    mask_bit<16>(raw, A, B, C, cv);
+    mask_bit<17>(raw, A, B, C, cv);
+    mask_bit<18>(raw, A, B, C, cv);
+    mask_bit<19>(raw, A, B, C, cv);
+    mask_bit<20>(raw, A, B, C, cv);
+    mask_bit<21>(raw, A, B, C, cv);
+    mask_bit<22>(raw, A, B, C, cv);
+    mask_bit<23>(raw, A, B, C, cv);
+    mask_bit<24>(raw, A, B, C, cv);
+    mask_bit<25>(raw, A, B, C, cv);
+    mask_bit<26>(raw, A, B, C, cv);
     return raw;
 }
 
@@ -830,14 +856,14 @@ __global__ void __launch_bounds__(kW2 * 32) k_prune2d(ItemTable tab, Outs o) {
             // i + 1 (i >= 4); offsets before the centre in linear order precede on ties
             const float cv = B.c;
             uint32_t raw = 0;
-            raw = (raw << 1) - set_lt(C.r, cv);
-            raw = (raw << 1) - set_lt(C.c, cv);
-            raw = (raw << 1) - set_lt(C.l, cv);
-            raw = (raw << 1) - set_lt(B.r, cv);
-            raw = (raw << 1) - set_le(B.l, cv);
-            raw = (raw << 1) - set_le(A.r, cv);
-            raw = (raw << 1) - set_le(A.c, cv);
-            raw = (raw << 1) - set_le(A.l, cv);
+            or_if_precedes<1u << 0, true>(raw, A.l, cv);
+            or_if_precedes<1u << 1, true>(raw, A.c, cv);
+            or_if_precedes<1u << 2, true>(raw, A.r, cv);
+            or_if_precedes<1u << 3, true>(raw, B.l, cv);
+            or_if_precedes<1u << 4, false>(raw, B.r, cv);
+            or_if_precedes<1u << 5, false>(raw, C.l, cv);
+            or_if_precedes<1u << 6, false>(raw, C.c, cv);
+            or_if_precedes<1u << 7, false>(raw, C.r, cv);
             const uint2 e = sm.lut[raw];
             const bool owned = owned_x && y < y1;
             const uint32_t ord = ord_bits(cv);
