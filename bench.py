@@ -319,7 +319,7 @@ def batched_vs_plain(dev, steps: int, warmup: int):
     nvox = int(sum(a.size for a in items))
     from paper_2606_04801_gb300 import autotune
 
-    autotune.autotune([torch.from_numpy(a).to(dev) for a in items])
+    tuned = autotune.autotune([torch.from_numpy(a).to(dev) for a in items])
     bp = cp.BatchedPersistence(shapes, tau=TAU, device=dev, graph=True)
     bp.load([torch.from_numpy(a) for a in items])
     for _ in range(warmup):
@@ -387,6 +387,7 @@ def batched_vs_plain(dev, steps: int, warmup: int):
         "speedup": t_plain / t_batched,
         "same_loss": same,
         "status": st["rc"],
+        "tuning": {k: tuned[k] for k in ("zchunk3d", "ctas3d", "rows2d", "uf_variant")},
     }
 
 
