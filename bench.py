@@ -1350,7 +1350,7 @@ def _k1_hash():
     import hashlib
 
     h = hashlib.sha256()
-    for f in ("cp_prune.cu", "cp_common.cuh"):
+    for f in ("cp_prune.cu", "cp_common.cuh", "cp_mask3.cuh"):
         with open(os.path.join(ROOT, "paper_2606_04801_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

@@ -116,6 +116,18 @@ int cp_lut_num_classes(int ndim);
  */
 int cp_lut_lookup(int ndim, uint32_t raw, uint32_t *relevant, uint64_t *entry);
 
+/*
+ * Self-check of the 3D pruning kernel's mask form (host only, for tests):
+ * the kernel builds the 26 neighbour comparisons into its own bit layout
+ * and collapses them there with a few multiplications and masks (Sec. 3.3's
+ * rule that an offset matters only when every nonzero sub-offset precedes).
+ * This runs that collapse on the host for all 2^26 raw masks and compares it
+ * with the definition; *n_mismatch receives the number of masks that
+ * differ (0 when the layout is right).  Takes a few seconds.  Returns CP_OK,
+ * or CP_ERR_ARG for a null pointer.
+ */
+int cp_lut_check_layout(uint64_t *n_mismatch);
+
 /* ---------------------------------------------------------------- forward */
 
 /*

@@ -68,6 +68,7 @@ _SIGS = {
     "cp_error_string": (ctypes.c_char_p, [ctypes.c_int]),
     "cp_lut_num_classes": (ctypes.c_int, [ctypes.c_int]),
     "cp_lut_lookup": (ctypes.c_int, [ctypes.c_int, ctypes.c_uint32, _P, _P]),
+    "cp_lut_check_layout": (ctypes.c_int, [_P]),
     "cubical_persistence_workspace_size": (ctypes.c_size_t, [ctypes.c_int, _P, _I64]),
     "cubical_persistence_2d": (ctypes.c_int, [_P, _P, _P, _I64, _P, _P, _P, ctypes.c_size_t, _I64, _P]),
     "cubical_persistence_3d": (ctypes.c_int, [_P, _P, _P, _I64, _P, _P, _P, ctypes.c_size_t, _I64, _P]),

@@ -26,7 +26,8 @@ OUT_CHECKED = os.path.join(HERE, "_build_checked")
 LIB_CHECKED = os.path.join(OUT_CHECKED, "libcp_gb300_checked.so")
 CU = ["cp_prune.cu", "cp_sort.cu", "cp_uf.cu", "cp_emit.cu", "cp_api.cu", "cp_noalloc.cu", "cp_tfilt.cu", "cp_h1.cu", "cp_slab.cu", "cp_boruvka.cu"]
 CPP = ["cp_lut.cpp"]
-HEADERS = ["cp_common.cuh", "cp_grid.cuh", "cp_kernels.h", "cp_lut.h", os.path.join("..", "..", "include", "cubical_persistence.h")]
+HEADERS = ["cp_common.cuh", "cp_grid.cuh", "cp_kernels.h", "cp_lut.h", "cp_mask3.cuh", "cp_pairs.cuh",
+           os.path.join("..", "..", "include", "cubical_persistence.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

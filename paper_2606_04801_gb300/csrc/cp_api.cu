@@ -939,6 +939,12 @@ int cp_lut_lookup(int ndim, uint32_t raw, uint32_t* relevant, uint64_t* entry) {
     return CP_OK;
 }
 
+int cp_lut_check_layout(uint64_t* n_mismatch) {
+    if (!n_mismatch) return CP_ERR_ARG;
+    *n_mismatch = check_mask3_layout();
+    return CP_OK;
+}
+
 size_t cubical_persistence_workspace_size(int ndim, const int64_t* dims, int64_t max_survivors) {
     if ((ndim != 2 && ndim != 3) || !dims) return 0;
     int32_t nd = ndim;

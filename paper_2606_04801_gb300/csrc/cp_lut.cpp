@@ -25,6 +25,7 @@
 //    - a facet joining two classes that each hold an older top cell is left
 //      for the global dual union-find.
 #include "cp_lut.h"
+#include "cp_mask3.cuh"
 
 #include <algorithm>
 #include <cstring>
@@ -232,8 +233,11 @@ std::vector<uint32_t> relevant_masks(const Stencil& st) {
     return out;
 }
 
-static inline uint32_t hash_bucket(uint32_t m) { return (m * kH1) >> (32 - kLog2Buckets); }
-static inline uint32_t hash_slot(uint32_t m, uint32_t d) { return ((m ^ (d * kD)) * kH2) >> (32 - kLog2Slots); }
+// the hash takes a mask in the pruning kernel's bit layout (cp_mask3.cuh)
+static inline uint32_t hash_bucket(uint32_t m) { return (mask3_from_canonical(m) * kH1) >> (32 - kLog2Buckets); }
+static inline uint32_t hash_slot(uint32_t m, uint32_t d) {
+    return ((mask3_from_canonical(m) ^ (d * kD)) * kH2) >> (32 - kLog2Slots);
+}
 
 bool build_lut3d(Lut3D& out) {
     const Stencil& st = stencil(3);
@@ -276,6 +280,23 @@ bool build_lut3d(Lut3D& out) {
     }
     out.nclasses = int(masks.size());
     return true;
+}
+
+uint64_t check_mask3_layout() {
+    const Stencil& st = stencil(3);
+    // the layout one byte of the canonical mask at a time
+    uint32_t perm[4][256];
+    for (int b = 0; b < 4; ++b)
+        for (uint32_t v = 0; v < 256; ++v) perm[b][v] = mask3_from_canonical((v << (8 * b)) & 0x7FFDFFFu);
+    auto dev = [&](uint32_t raw) {
+        return perm[0][raw & 255u] | perm[1][(raw >> 8) & 255u] | perm[2][(raw >> 16) & 255u] | perm[3][raw >> 24];
+    };
+    uint64_t bad = 0;
+    for (uint32_t raw = 0; raw < (1u << 27); ++raw) {
+        if (raw & (1u << 13)) continue;
+        if (collapse3_lattice(dev(raw)) != dev(collapse(st, raw))) ++bad;
+    }
+    return bad;
 }
 
 void build_lut2d(std::vector<uint64_t>& out, int* nclasses) {

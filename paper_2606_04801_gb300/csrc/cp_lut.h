@@ -63,6 +63,11 @@ const Stencil& stencil(int ndim);
 // Relevant (collapsed) mask of a raw lower-neighbour mask.
 uint32_t collapse(const Stencil& st, uint32_t raw);
 
+// Number of raw 3D masks (all 2^26) whose collapse in the pruning kernel's
+// bit layout (cp_mask3.cuh) differs from the definition above, carried into
+// that layout; 0 when the layout is right.
+uint64_t check_mask3_layout();
+
 // Lookup entry of a relevant mask.
 uint64_t classify(const Stencil& st, uint32_t rel);
 
@@ -71,7 +76,8 @@ std::vector<uint32_t> relevant_masks(const Stencil& st);
 
 // Perfect hash of the 15,935 relevant 3D masks into a table of 2^kLog2Slots
 // entries: bucket = (m * kH1) >> (32 - kLog2Buckets), slot =
-// ((m ^ disp[bucket] * kD) * kH2) >> (32 - kLog2Slots).
+// ((m ^ disp[bucket] * kD) * kH2) >> (32 - kLog2Slots), with m the relevant
+// mask in the pruning kernel's bit layout (cp_mask3.cuh).
 constexpr int kLog2Buckets = 12;
 constexpr int kLog2Slots = 14;
 constexpr uint32_t kH1 = 0x9E3779B1u;

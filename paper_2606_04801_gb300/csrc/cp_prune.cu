@@ -20,6 +20,7 @@
 // global arrays with one atomic per buffer per flush.
 #include "cp_common.cuh"
 #include "cp_kernels.h"
+#include "cp_mask3.cuh"
 
 namespace cp {
 
@@ -75,39 +76,14 @@ __device__ __forceinline__ int tile_item(const ItemTable& t, int first, int last
     return lo;
 }
 
-// 3D relevant mask from the raw mask (bit n = 9(dz+1)+3(dy+1)+(dx+1)):
-// an edge diagonal needs its two faces, a corner its three edge diagonals.
-__device__ __forceinline__ uint32_t collapse3(uint32_t raw) {
-    constexpr uint32_t X0 = (1u << 1) | (1u << 4) | (1u << 7) | (1u << 10) | (1u << 13) | (1u << 16) | (1u << 19) |
-                            (1u << 22) | (1u << 25);
-    constexpr uint32_t Y0 = (7u << 3) | (7u << 12) | (7u << 21);
-    constexpr uint32_t Z0 = 0x1FFu << 9;
-    constexpr uint32_t FACES = (1u << 4) | (1u << 10) | (1u << 12) | (1u << 14) | (1u << 16) | (1u << 22);
-    constexpr uint32_t EDXY = (1u << 9) | (1u << 11) | (1u << 15) | (1u << 17);
-    constexpr uint32_t EDXZ = (1u << 3) | (1u << 5) | (1u << 21) | (1u << 23);
-    constexpr uint32_t EDYZ = (1u << 1) | (1u << 7) | (1u << 19) | (1u << 25);
-    constexpr uint32_t CORN = (1u << 0) | (1u << 2) | (1u << 6) | (1u << 8) | (1u << 18) | (1u << 20) | (1u << 24) |
-                              (1u << 26);
-    uint32_t f = raw & FACES;
-    uint32_t ux = ((f & X0) << 1) | ((f & X0) >> 1);
-    uint32_t uy = ((f & Y0) << 3) | ((f & Y0) >> 3);
-    uint32_t uz = ((f & Z0) << 9) | ((f & Z0) >> 9);
-    uint32_t ed = raw & ((EDXY & ux & uy) | (EDXZ & ux & uz) | (EDYZ & uy & uz));
-    uint32_t vx = ((ed & X0) << 1) | ((ed & X0) >> 1);
-    uint32_t vy = ((ed & Y0) << 3) | ((ed & Y0) >> 3);
-    uint32_t vz = ((ed & Z0) << 9) | ((ed & Z0) >> 9);
-    uint32_t co = raw & CORN & vx & vy & vz;
-    return f | ed | co;
-}
-
-// Perfect hash of the 15,935 relevant masks: bucket -> displacement (a copy
-// of the 8 KB displacement table in shared memory) -> slot.
+// Perfect hash of the 15,935 relevant masks (device layout, cp_mask3.cuh):
+// bucket -> displacement (a copy of the 8 KB displacement table in shared
+// memory) -> slot.
 __device__ __forceinline__ uint32_t hash_slot3(uint32_t rel, const uint16_t* disp) {
     const uint32_t b = (rel * 0x9E3779B1u) >> (32 - 12);
     const uint32_t d = disp[b];
     return ((rel ^ (d * 0x27D4EB2Fu)) * 0x85EBCA77u) >> (32 - 14);
 }
-constexpr uint32_t kFaces3 = (1u << 4) | (1u << 10) | (1u << 12) | (1u << 14) | (1u << 16) | (1u << 22);
 
 }  // namespace
 
@@ -171,7 +147,7 @@ struct Smem3 {
     uint32_t t_HW, t_HW1, t_OUT;
     int t_z0, t_z1, t_D, t_zneed;
     int2 tlink[8 * 16];        // dual links by (t, v), for the current item
-    int32_t h0link[24];        // H0 link offset by face bit n, for the current item
+    int32_t h0link[6];         // H0 link offset by face slot (z-, y-, x-, x+, y+, z+), for the current item
     uint16_t disp[1 << 12];    // displacement table of the 3D perfect hash
     uint32_t sbits[1 << 9];    // survivor bit of each slot
     // per column and plane step: the code fields of the top cells on the +z
@@ -260,11 +236,12 @@ template <int n>
 __device__ __forceinline__ void mask_bit(uint32_t& raw, const Nbr& A, const Nbr& B, const Nbr& C, float cv) {
     constexpr int a = n / 9, b = (n / 3) % 3, c = n % 3;
     const Nbr& P = a == 0 ? A : (a == 1 ? B : C);
-    or_if_precedes<(1u << n), (n < 13)>(raw, P.v[b][c], cv);
+    or_if_precedes<(1u << mask3_pos(n)), (n < 13)>(raw, P.v[b][c], cv);
 }
 
-// raw mask: bit n = 9a + 3b + c set when the neighbour at plane a, row b,
-// column c precedes the centre (ties: earlier linear index first)
+// raw mask in the device layout (cp_mask3.cuh): the bit of canonical
+// neighbour n = 9a + 3b + c set when the neighbour at plane a, row b, column
+// c precedes the centre (ties: earlier linear index first)
 __device__ __forceinline__ uint32_t mask26(const Nbr& A, const Nbr& B, const Nbr& C) {
     const float cv = B.v[1][1];
     uint32_t raw = 0;
@@ -532,10 +509,10 @@ __device__ __forceinline__ void prune_task3d(Smem3& sm, const ItemTable& tab, co
             d.y = int(v == 9 ? kMvRoot : kMvInvalid);
         }
         sm.tlink[threadIdx.x] = d;
-    } else if (threadIdx.x < 8 * 16 + 24) {
-        const int n = threadIdx.x - 8 * 16;
+    } else if (threadIdx.x < 8 * 16 + 6) {
+        const int s = threadIdx.x - 8 * 16;
         const int hw = int(cc.HW), w = int(cc.W);
-        sm.h0link[n] = n == 4 ? -hw : (n == 10 ? -w : (n == 12 ? -1 : (n == 14 ? 1 : (n == 16 ? w : (n == 22 ? hw : 0)))));
+        sm.h0link[s] = s == 0 ? -hw : (s == 1 ? -w : (s == 2 ? -1 : (s == 3 ? 1 : (s == 4 ? w : hw))));
     }
 #pragma unroll
     for (int k = -1; k < kAhead; ++k) issue_plane<kTma>(sm, it, z0 + k, rp, cc.HW, src);
@@ -555,7 +532,7 @@ __device__ __forceinline__ void prune_task3d(Smem3& sm, const ItemTable& tab, co
         read_nbr(sm.ring[(z + 1) & (kRing - 1)] + xo, warp, lane, C);
         // ---- lookup of (z, y, x)
         const float cv = B.v[1][1];
-        const uint32_t rel = collapse3(mask26(A, B, C));
+        const uint32_t rel = collapse3_lattice(mask26(A, B, C));
         const uint32_t slot = hash_slot3(rel, sm.disp);
         const uint32_t codes = __ldg(g_codes3d + slot);
         // top cells on the +z side of (z-1, y, x) are slots 4..7 of that vertex,
@@ -566,7 +543,7 @@ __device__ __forceinline__ void prune_task3d(Smem3& sm, const ItemTable& tab, co
         const bool owned = cc.owned_xy && z < sm.t_z1;
         const uint32_t ord = ord_bits(cv);
         const uint32_t vg = colv + uint32_t(z) * sm.t_HW;
-        const uint32_t f0 = rel & kFaces3;  // the first edge of L(v) is its lowest face bit
+        const uint32_t f0 = rel & kM3Faces;  // the first edge of L(v) is its lowest face bit
         bool root0 = false;
         if (owned) {
             if (!(fabsf(cv) <= 3.40282347e38f)) set_status(o.ctr, kStNonfinite);
@@ -576,10 +553,10 @@ __device__ __forceinline__ void prune_task3d(Smem3& sm, const ItemTable& tab, co
                 const unsigned long long k = (unsigned long long)(uint64_t(ord) << 32 | (vg - uint32_t(it.voff)));
                 if (k < sm.tmin[threadIdx.x]) sm.tmin[threadIdx.x] = k;
             } else {
-                // a link to (z-1, y, x) (face bit 4, the lowest) continues the chain
+                // a link to (z-1, y, x) (face bit 0, the lowest) continues the chain
                 // that the z-1 neighbour (same thread, previous step) started
                 const uint32_t u = vg + uint32_t(sm.h0link[__ffs(f0) - 1]);
-                far = ((f0 & 16u) && z > sm.t_z0) ? far : u;
+                far = ((f0 & 1u) && z > sm.t_z0) ? far : u;
                 if (CP_IN(vg, o.n_uf0, o.ctr)) o.uf0[vg] = far;
             }
         }

@@ -50,6 +50,18 @@ def test_lut_class_counts(lib):
     assert lib.cp_lut_num_classes(4) == -1
 
 
+def test_kernel_mask_layout(lib):
+    """The 3D pruning kernel collapses its comparison mask in its own bit
+    layout with multiplications and masks; on all 2^26 raw masks that
+    collapse equals the sub-offset rule of Sec. 3.3 (the library's
+    definition, itself pinned by the class counts above and by the pruned
+    restatement against the oracle below)."""
+    n = ctypes.c_uint64(1)
+    assert lib.cp_lut_check_layout(ctypes.byref(n)) == 0
+    assert n.value == 0
+    assert lib.cp_lut_check_layout(None) == _lib.CP_ERR_ARG
+
+
 def _offsets(ndim):
     n = 27 if ndim == 3 else 9
     if ndim == 3:
