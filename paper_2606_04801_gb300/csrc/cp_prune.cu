@@ -147,7 +147,7 @@ struct Smem3 {
     uint32_t t_HW, t_HW1, t_OUT;
     int t_z0, t_z1, t_D, t_zneed;
     int2 tlink[8 * 16];        // dual links by (t, v), for the current item
-    int32_t h0link[6];         // H0 link offset by face slot (z-, y-, x-, x+, y+, z+), for the current item
+    int32_t h0link[8];         // H0 link offset by face slot (z-, y-, x-, x+, y+, z+; two unused), for the current item
     uint16_t disp[1 << 12];    // displacement table of the 3D perfect hash
     uint32_t sbits[1 << 9];    // survivor bit of each slot
     // per column and plane step: the code fields of the top cells on the +z
@@ -509,10 +509,10 @@ __device__ __forceinline__ void prune_task3d(Smem3& sm, const ItemTable& tab, co
             d.y = int(v == 9 ? kMvRoot : kMvInvalid);
         }
         sm.tlink[threadIdx.x] = d;
-    } else if (threadIdx.x < 8 * 16 + 6) {
+    } else if (threadIdx.x < 8 * 16 + 8) {
         const int s = threadIdx.x - 8 * 16;
         const int hw = int(cc.HW), w = int(cc.W);
-        sm.h0link[s] = s == 0 ? -hw : (s == 1 ? -w : (s == 2 ? -1 : (s == 3 ? 1 : (s == 4 ? w : hw))));
+        sm.h0link[s] = s == 0 ? -hw : (s == 1 ? -w : (s == 2 ? -1 : (s == 3 ? 1 : (s == 4 ? w : (s == 5 ? hw : 0)))));
     }
 #pragma unroll
     for (int k = -1; k < kAhead; ++k) issue_plane<kTma>(sm, it, z0 + k, rp, cc.HW, src);
@@ -544,22 +544,15 @@ __device__ __forceinline__ void prune_task3d(Smem3& sm, const ItemTable& tab, co
         const uint32_t ord = ord_bits(cv);
         const uint32_t vg = colv + uint32_t(z) * sm.t_HW;
         const uint32_t f0 = rel & kM3Faces;  // the first edge of L(v) is its lowest face bit
-        bool root0 = false;
-        if (owned) {
-            if (!(fabsf(cv) <= 3.40282347e38f)) set_status(o.ctr, kStNonfinite);
-            if (f0 == 0u) {
-                root0 = true;
-                far = vg;
-                const unsigned long long k = (unsigned long long)(uint64_t(ord) << 32 | (vg - uint32_t(it.voff)));
-                if (k < sm.tmin[threadIdx.x]) sm.tmin[threadIdx.x] = k;
-            } else {
-                // a link to (z-1, y, x) (face bit 0, the lowest) continues the chain
-                // that the z-1 neighbour (same thread, previous step) started
-                const uint32_t u = vg + uint32_t(sm.h0link[__ffs(f0) - 1]);
-                far = ((f0 & 1u) && z > sm.t_z0) ? far : u;
-                if (CP_IN(vg, o.n_uf0, o.ctr)) o.uf0[vg] = far;
-            }
-        }
+        // H0: a local minimum becomes a root (registered in the staging block
+        // below); otherwise the link along the first edge, where a link to
+        // (z-1, y, x) (face bit 0, the lowest) continues the chain that the
+        // z-1 neighbour (same thread, previous step) started
+        const bool root0 = owned && f0 == 0u;
+        if (__any_sync(0xFFFFFFFFu, owned && !(fabsf(cv) <= 3.40282347e38f))) set_status(o.ctr, kStNonfinite);
+        const uint32_t u = vg + uint32_t(sm.h0link[(__ffs(f0) - 1) & 7]);  // (f0 == 0: unused)
+        if (owned) far = root0 ? vg : (((f0 & 1u) && z > sm.t_z0) ? far : u);
+        if (owned && !root0 && CP_IN(vg, o.n_uf0, o.ctr)) o.uf0[vg] = far;
         // survivor fields (owned survivor vertices only; rare)
         const bool sbit = owned && ((sm.sbits[slot >> 5] >> (slot & 31u)) & 1u);
         const uint32_t sv = sbit ? __ldg(g_surv3d + slot) : 0u;
@@ -573,40 +566,24 @@ __device__ __forceinline__ void prune_task3d(Smem3& sm, const ItemTable& tab, co
         __syncthreads();              // column words of plane step z and image plane z+2 visible
         const uint32_t q10 = sm.q[qs][warp + 1][lane];
         const uint32_t q11 = __shfl_down_sync(0xFFFFFFFFu, q10, 1);
-        bool rootT = false;
-        uint32_t rt_node = 0;
-        uint64_t rt_age = 0;
-        if (cc.cube_xy && z > z0) {
-            const uint32_t acc = acc_row | (q10 & kM51) | (q11 & kM40);
-            const uint32_t self = colt + uint32_t(z - 1) * sm.t_HW1;
-            uint32_t fs = 0;
-            int2 lk = make_int2(0, int(kMvInvalid));
-            if (acc != 0u) {
-                fs = uint32_t(31 - __clz(acc)) & 28u;  // 4 t: the field that is set
-                lk = sm.tlink[(fs << 2) | ((acc >> fs) & 15u)];
-            }
-            const uint32_t bits = uint32_t(lk.y);
-            if (!(bits & (kMvRoot | kMvInvalid))) {
-                const uint32_t bnd = cc.bmv | (z == 1 ? 1u : 0u) | (uint32_t(z) == cc.D - 1u ? 32u : 0u);
-                // a link to (z-2, y, x) continues the chain that this thread wrote for
-                // that top cell in the previous step
-                const bool chain = (bits & kMvChain) && z - 1 > sm.t_z0;
-                far_t = chain ? far_t : ((bits & bnd) ? sm.t_OUT : self + uint32_t(lk.x));
-                if (CP_IN(self, o.n_uft, o.ctr)) o.uft[self] = far_t;
-            } else if (bits & kMvRoot) {
-                rootT = true;
-                rt_node = self;
-                far_t = self;
-                const uint32_t t = fs >> 2, k = 7u - t;  // m = corner k
-                const uint32_t dz = k >> 2, dy = (k >> 1) & 1u, dx = k & 1u;
-                const Nbr& P = dz ? B : A;
-                const float mv = dy ? (dx ? P.v[2][2] : P.v[2][1]) : (dx ? P.v[1][2] : P.v[1][1]);
-                const uint32_t mg = colv + (uint32_t(z - 1) + dz) * cc.HW + dy * uint32_t(it.W) + dx;
-                rt_age = make_key(ord_bits(mv), mg, age_slot(t));
-            } else {
-                far_t = kTag;
-                if (CP_IN(self, o.n_uft, o.ctr)) o.uft[self] = kTag;  // only reachable with non-finite input (flagged): keep the forest well formed
-            }
+        // the field that is set is the one of the largest corner m; with
+        // non-finite input none may be, and any field then reads "invalid"
+        const bool cube = cc.cube_xy && z > z0;
+        const uint32_t acc = acc_row | (q10 & kM51) | (q11 & kM40);
+        const uint32_t fs = uint32_t(31 - __clz(acc)) & 28u;  // 4 t: the field that is set
+        const int2 lk = sm.tlink[(fs << 2) | ((acc >> fs) & 15u)];
+        const uint32_t bits = uint32_t(lk.y);
+        const uint32_t self = colt + uint32_t(z - 1) * sm.t_HW1;
+        const bool rootT = cube && (bits & kMvRoot);  // registered in the staging block below
+        {
+            const uint32_t bnd = cc.bmv | (z == 1 ? 1u : 0u) | (uint32_t(z) == cc.D - 1u ? 32u : 0u);
+            // a link to (z-2, y, x) continues the chain that this thread wrote for
+            // that top cell in the previous step; an invalid entry (non-finite
+            // input only, flagged) writes a root tag to keep the forest well formed
+            const bool chain = (bits & kMvChain) && z - 1 > sm.t_z0;
+            const uint32_t tgt = (bits & kMvInvalid) ? kTag : ((bits & bnd) ? sm.t_OUT : self + uint32_t(lk.x));
+            if (cube) far_t = rootT ? self : (chain ? far_t : tgt);
+            if (cube && !rootT && CP_IN(self, o.n_uft, o.ctr)) o.uft[self] = far_t;
         }
         // ---- stage survivors and roots (rare in smooth fields)
         if (__any_sync(0xFFFFFFFFu, root0 || rootT || sv != 0u)) {
@@ -622,14 +599,23 @@ __device__ __forceinline__ void prune_task3d(Smem3& sm, const ItemTable& tab, co
                     const uint32_t p = cnt.r0 + __popc(m_r0 & lt);
                     ws.r0node[p] = vg;
                     ws.r0age[p] = make_key(ord, vg, 0);
+                    const unsigned long long k = (unsigned long long)(uint64_t(ord) << 32 | (vg - uint32_t(it.voff)));
+                    if (k < sm.tmin[threadIdx.x]) sm.tmin[threadIdx.x] = k;
                 }
                 cnt.r0 += __popc(m_r0);
             }
             if (m_rt) {
                 if (rootT) {
+                    // the age of a dual root: the key of the top cell, whose
+                    // largest corner m is corner k = 7 - t of the cube
+                    const uint32_t t = fs >> 2, k = 7u - t;
+                    const uint32_t dz = k >> 2, dy = (k >> 1) & 1u, dx = k & 1u;
+                    const Nbr& P = dz ? B : A;
+                    const float mv = dy ? (dx ? P.v[2][2] : P.v[2][1]) : (dx ? P.v[1][2] : P.v[1][1]);
+                    const uint32_t mg = colv + (uint32_t(z - 1) + dz) * cc.HW + dy * uint32_t(it.W) + dx;
                     const uint32_t p = cnt.rt + __popc(m_rt & lt);
-                    ws.rtnode[p] = rt_node;
-                    ws.rtage[p] = rt_age;
+                    ws.rtnode[p] = self;
+                    ws.rtage[p] = make_key(ord_bits(mv), mg, age_slot(t));
                 }
                 cnt.rt += __popc(m_rt);
             }
