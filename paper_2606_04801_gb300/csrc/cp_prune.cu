@@ -22,6 +22,8 @@
 #include "cp_kernels.h"
 #include "cp_mask3.cuh"
 
+#include <type_traits>
+
 namespace cp {
 
 // Lookup tables in global memory, read through the read-only cache (lanes of
@@ -373,15 +375,17 @@ struct PlaneSrc {
     int zneed;               // last plane the task reads (TMA path loads no plane beyond it)
 };
 
-template <bool kTma>
+// kCheck false: the caller knows that plane z lies inside the volume and
+// within the task's reads (an interior plane step)
+template <bool kTma, bool kCheck>
 __device__ __forceinline__ void issue_plane(Smem3& sm, const Item& it, int z, const RingPos& rp, uint32_t HW,
                                             const PlaneSrc& ps) {
     const int slot = (z + kRing) & (kRing - 1);
     float* plane = sm.ring[slot];
     const float inf = __int_as_float(0x7F800000);
     if constexpr (kTma) {
-        if (z > ps.zneed) return;
-        if (unsigned(z) < unsigned(it.D)) {
+        if (kCheck && z > ps.zneed) return;
+        if (!kCheck || unsigned(z) < unsigned(it.D)) {
             if (threadIdx.x == 0) {
                 // earlier generic-proxy accesses of the slot come before the copy
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -393,7 +397,7 @@ __device__ __forceinline__ void issue_plane(Smem3& sm, const Item& it, int z, co
         }
         return;
     }
-    if (unsigned(z) < unsigned(it.D)) {
+    if (!kCheck || unsigned(z) < unsigned(it.D)) {
         const float* base = it.img + uint32_t(z) * HW;
         if (rp.in0) cp_async4(plane + rp.dst0, base + rp.off0);
         if (rp.in1) cp_async4(plane + rp.dst1, base + rp.off1);
@@ -406,9 +410,9 @@ __device__ __forceinline__ void issue_plane(Smem3& sm, const Item& it, int z, co
 
 // Before reading plane z: wait for its TMA copy (cp.async planes are covered
 // by the wait_group and the barrier of the previous step).
-template <bool kTma>
+template <bool kTma, bool kCheck>
 __device__ __forceinline__ void wait_plane(Smem3& sm, const Item& it, int z, uint32_t& par, Counters* ctr) {
-    if (!kTma || unsigned(z) >= unsigned(it.D)) return;
+    if (!kTma || (kCheck && unsigned(z) >= unsigned(it.D))) return;
     const int slot = z & (kRing - 1);
     mbar_wait(&sm.bar[slot], (par >> slot) & 1u, ctr);
     par ^= 1u << slot;
@@ -515,20 +519,23 @@ __device__ __forceinline__ void prune_task3d(Smem3& sm, const ItemTable& tab, co
         sm.h0link[s] = s == 0 ? -hw : (s == 1 ? -w : (s == 2 ? -1 : (s == 3 ? 1 : (s == 4 ? w : (s == 5 ? hw : 0)))));
     }
 #pragma unroll
-    for (int k = -1; k < kAhead; ++k) issue_plane<kTma>(sm, it, z0 + k, rp, cc.HW, src);
+    for (int k = -1; k < kAhead; ++k) issue_plane<kTma, true>(sm, it, z0 + k, rp, cc.HW, src);
     cp_async_wait<kAhead - 2>();  // planes z0-1 .. z0+1 have landed
     __syncthreads();
     Nbr A, B, C;
-    wait_plane<kTma>(sm, it, z0 - 1, par, o.ctr);
+    wait_plane<kTma, true>(sm, it, z0 - 1, par, o.ctr);
     read_nbr(sm.ring[(z0 - 1 + kRing) & (kRing - 1)] + xo, warp, lane, A);
-    wait_plane<kTma>(sm, it, z0, par, o.ctr);
+    wait_plane<kTma, true>(sm, it, z0, par, o.ctr);
     read_nbr(sm.ring[z0 & (kRing - 1)] + xo, warp, lane, B);
     // One plane step: P (plane z-1) and Q (plane z) in registers, R gets plane
     // z+1.  The loop below rotates the three register planes and the three
     // column-word slots, so nothing is copied.
-    auto step = [&](const Nbr& A, const Nbr& B, Nbr& C, const int z, const int qs) {
-        issue_plane<kTma>(sm, it, z + kAhead, rp, cc.HW, src);
-        wait_plane<kTma>(sm, it, z + 1, par, o.ctr);
+    // interior: a std::integral_constant; true for a step with z >= z0 + 2 and
+    // z + kAhead <= zlast, where no boundary plane or end-of-task case arises
+    auto step = [&](const Nbr& A, const Nbr& B, Nbr& C, const int z, const int qs, auto interior) {
+        constexpr bool kIn = decltype(interior)::value;
+        issue_plane<kTma, !kIn>(sm, it, z + kAhead, rp, cc.HW, src);
+        wait_plane<kTma, !kIn>(sm, it, z + 1, par, o.ctr);
         read_nbr(sm.ring[(z + 1) & (kRing - 1)] + xo, warp, lane, C);
         // ---- lookup of (z, y, x)
         const float cv = B.v[1][1];
@@ -540,7 +547,7 @@ __device__ __forceinline__ void prune_task3d(Smem3& sm, const ItemTable& tab, co
         const uint32_t q = (cprev & 0xFFFF0000u) | (codes & 0x0000FFFFu);
         sm.q[qs][warp][lane] = q;
         cprev = codes;
-        const bool owned = cc.owned_xy && z < sm.t_z1;
+        const bool owned = cc.owned_xy && (kIn || z < sm.t_z1);
         const uint32_t ord = ord_bits(cv);
         const uint32_t vg = colv + uint32_t(z) * sm.t_HW;
         const uint32_t f0 = rel & kM3Faces;  // the first edge of L(v) is its lowest face bit
@@ -551,7 +558,7 @@ __device__ __forceinline__ void prune_task3d(Smem3& sm, const ItemTable& tab, co
         const bool root0 = owned && f0 == 0u;
         if (__any_sync(0xFFFFFFFFu, owned && !(fabsf(cv) <= 3.40282347e38f))) set_status(o.ctr, kStNonfinite);
         const uint32_t u = vg + uint32_t(sm.h0link[(__ffs(f0) - 1) & 7]);  // (f0 == 0: unused)
-        if (owned) far = root0 ? vg : (((f0 & 1u) && z > sm.t_z0) ? far : u);
+        if (owned) far = root0 ? vg : (((f0 & 1u) && (kIn || z > sm.t_z0)) ? far : u);
         if (owned && !root0 && CP_IN(vg, o.n_uf0, o.ctr)) o.uf0[vg] = far;
         // survivor fields (owned survivor vertices only; rare)
         const bool sbit = owned && ((sm.sbits[slot >> 5] >> (slot & 31u)) & 1u);
@@ -568,7 +575,7 @@ __device__ __forceinline__ void prune_task3d(Smem3& sm, const ItemTable& tab, co
         const uint32_t q11 = __shfl_down_sync(0xFFFFFFFFu, q10, 1);
         // the field that is set is the one of the largest corner m; with
         // non-finite input none may be, and any field then reads "invalid"
-        const bool cube = cc.cube_xy && z > z0;
+        const bool cube = cc.cube_xy && (kIn || z > z0);
         const uint32_t acc = acc_row | (q10 & kM51) | (q11 & kM40);
         const uint32_t fs = uint32_t(31 - __clz(acc)) & 28u;  // 4 t: the field that is set
         const int2 lk = sm.tlink[(fs << 2) | ((acc >> fs) & 15u)];
@@ -576,11 +583,11 @@ __device__ __forceinline__ void prune_task3d(Smem3& sm, const ItemTable& tab, co
         const uint32_t self = colt + uint32_t(z - 1) * sm.t_HW1;
         const bool rootT = cube && (bits & kMvRoot);  // registered in the staging block below
         {
-            const uint32_t bnd = cc.bmv | (z == 1 ? 1u : 0u) | (uint32_t(z) == cc.D - 1u ? 32u : 0u);
+            const uint32_t bnd = kIn ? cc.bmv : (cc.bmv | (z == 1 ? 1u : 0u) | (uint32_t(z) == cc.D - 1u ? 32u : 0u));
             // a link to (z-2, y, x) continues the chain that this thread wrote for
             // that top cell in the previous step; an invalid entry (non-finite
             // input only, flagged) writes a root tag to keep the forest well formed
-            const bool chain = (bits & kMvChain) && z - 1 > sm.t_z0;
+            const bool chain = (bits & kMvChain) && (kIn || z - 1 > sm.t_z0);
             const uint32_t tgt = (bits & kMvInvalid) ? kTag : ((bits & bnd) ? sm.t_OUT : self + uint32_t(lk.x));
             if (cube) far_t = rootT ? self : (chain ? far_t : tgt);
             if (cube && !rootT && CP_IN(self, o.n_uft, o.ctr)) o.uft[self] = far_t;
@@ -649,13 +656,28 @@ __device__ __forceinline__ void prune_task3d(Smem3& sm, const ItemTable& tab, co
             __syncwarp();
         }
     };
-    for (int z = z0;;) {
-        step(A, B, C, z, 0);
-        if (++z > zlast) break;
-        step(B, C, A, z, 1);
-        if (++z > zlast) break;
-        step(C, A, B, z, 2);
-        if (++z > zlast) break;
+    // The first three planes and the last few take every check, one at a time
+    // with the register planes copied along; the interior planes go three at
+    // a time with the planes and column-word slots rotated, nothing copied.
+    const std::integral_constant<bool, false> kEdge;
+    const std::integral_constant<bool, true> kInner;
+    int z = z0, qs = 0;
+    for (; z <= zlast && z < z0 + 3; ++z) {
+        step(A, B, C, z, qs, kEdge);
+        A = B;
+        B = C;
+        qs = qs == 2 ? 0 : qs + 1;
+    }
+    for (; z + 2 + kAhead <= zlast; z += 3) {
+        step(A, B, C, z, 0, kInner);
+        step(B, C, A, z + 1, 1, kInner);
+        step(C, A, B, z + 2, 2, kInner);
+    }
+    for (; z <= zlast; ++z) {
+        step(A, B, C, z, qs, kEdge);
+        A = B;
+        B = C;
+        qs = qs == 2 ? 0 : qs + 1;
     }
     cp_async_wait<0>();
     const unsigned long long w = warp_min_u64(sm.tmin[threadIdx.x]);
