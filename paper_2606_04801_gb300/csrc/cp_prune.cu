@@ -149,7 +149,7 @@ struct Smem3 {
     uint32_t t_HW, t_HW1, t_OUT;
     int t_z0, t_z1, t_D, t_zneed;
     int2 tlink[8 * 16];        // dual links by (t, v), for the current item
-    int32_t h0link[8];         // H0 link offset by face slot (z-, y-, x-, x+, y+, z+; two unused), for the current item
+    int32_t h0link[64];        // H0 link offset by the face bits of the mask (their lowest: z-, y-, x-, x+, y+, z+), for the current item
     uint16_t disp[1 << 12];    // displacement table of the 3D perfect hash
     uint32_t sbits[1 << 9];    // survivor bit of each slot
     // per column and plane step: the code fields of the top cells on the +z
@@ -483,6 +483,7 @@ __device__ __forceinline__ void prune_task3d(Smem3& sm, const ItemTable& tab, co
     const uint32_t colt = cc.toff + uint32_t(cc.y) * cc.W1 + uint32_t(cc.x);
     uint32_t far = 0, far_t = 0;  // last H0 link / dual link written by this thread
     uint32_t cprev = 0;           // code fields of this column's vertex one plane behind
+    bool nonfinite = false;       // an owned value is NaN or infinite (checked once per task)
     __syncthreads();  // the rings, link tables and task constants may still be read by the previous task
     if (threadIdx.x == 0) {
         sm.t_HW = cc.HW;
@@ -513,10 +514,10 @@ __device__ __forceinline__ void prune_task3d(Smem3& sm, const ItemTable& tab, co
             d.y = int(v == 9 ? kMvRoot : kMvInvalid);
         }
         sm.tlink[threadIdx.x] = d;
-    } else if (threadIdx.x < 8 * 16 + 8) {
-        const int s = threadIdx.x - 8 * 16;
+    } else if (threadIdx.x < 8 * 16 + 64) {
+        const int f = threadIdx.x - 8 * 16, s = __ffs(f) - 1;  // f == 0 (a root): unused
         const int hw = int(cc.HW), w = int(cc.W);
-        sm.h0link[s] = s == 0 ? -hw : (s == 1 ? -w : (s == 2 ? -1 : (s == 3 ? 1 : (s == 4 ? w : (s == 5 ? hw : 0)))));
+        sm.h0link[f] = s == 0 ? -hw : (s == 1 ? -w : (s == 2 ? -1 : (s == 3 ? 1 : (s == 4 ? w : (s == 5 ? hw : 0)))));
     }
 #pragma unroll
     for (int k = -1; k < kAhead; ++k) issue_plane<kTma, true>(sm, it, z0 + k, rp, cc.HW, src);
@@ -556,8 +557,8 @@ __device__ __forceinline__ void prune_task3d(Smem3& sm, const ItemTable& tab, co
         // (z-1, y, x) (face bit 0, the lowest) continues the chain that the
         // z-1 neighbour (same thread, previous step) started
         const bool root0 = owned && f0 == 0u;
-        if (__any_sync(0xFFFFFFFFu, owned && !(fabsf(cv) <= 3.40282347e38f))) set_status(o.ctr, kStNonfinite);
-        const uint32_t u = vg + uint32_t(sm.h0link[(__ffs(f0) - 1) & 7]);  // (f0 == 0: unused)
+        nonfinite |= owned && !(fabsf(cv) <= 3.40282347e38f);
+        const uint32_t u = vg + uint32_t(sm.h0link[f0]);  // (f0 == 0: unused)
         if (owned) far = root0 ? vg : (((f0 & 1u) && (kIn || z > sm.t_z0)) ? far : u);
         if (owned && !root0 && CP_IN(vg, o.n_uf0, o.ctr)) o.uf0[vg] = far;
         // survivor fields (owned survivor vertices only; rare)
@@ -680,6 +681,7 @@ __device__ __forceinline__ void prune_task3d(Smem3& sm, const ItemTable& tab, co
         qs = qs == 2 ? 0 : qs + 1;
     }
     cp_async_wait<0>();
+    if (__any_sync(0xFFFFFFFFu, nonfinite) && lane == 0) set_status(o.ctr, kStNonfinite);
     const unsigned long long w = warp_min_u64(sm.tmin[threadIdx.x]);
     if (lane == 0 && w != ~0ull) atomicMin(&o.ctr->gmin[ii], w);
 }
