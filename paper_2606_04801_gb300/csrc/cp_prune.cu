@@ -773,9 +773,11 @@ struct RowPos {
     bool in0, in1;    // inside the image
 };
 
+// kCheck false: the caller knows that row y lies inside the image
+template <bool kCheck = true>
 __device__ __forceinline__ void issue_row(float (*ring)[kRW2], const RowPos& p, int lane, int y) {
     float* slot = ring[(y + kRing2) & (kRing2 - 1)];
-    if (unsigned(y) < p.H) {
+    if (!kCheck || unsigned(y) < p.H) {
         const float* base = p.img + uint32_t(y) * p.W;
         if (p.in0) cp_async4(slot + lane + 1, base + p.gx0);
         if (p.in1) cp_async4(slot + p.idx1, base + p.gx1);
@@ -836,8 +838,12 @@ __global__ void __launch_bounds__(kW2 * 32) k_prune2d(ItemTable tab, Outs o) {
         read_row(ring[y0 & (kRing2 - 1)], lane, B);
         unsigned long long my_min = ~0ull;
         uint32_t far = 0, far_t = 0, cprev = 0;  // last H0 link / dual link written by this lane
-        for (int y = y0; y <= ylast; ++y) {
-            issue_row(ring, rp, lane, y + kAhead2);
+        bool nonfinite = false;                   // an owned value is NaN or infinite (checked once per task)
+        // interior: a std::integral_constant; true for a row with y >= y0 + 2 and
+        // y + kAhead2 <= ylast, where no boundary row or end-of-task case arises
+        auto step = [&](const int y, auto interior) {
+            constexpr bool kIn = decltype(interior)::value;
+            issue_row<!kIn>(ring, rp, lane, y + kAhead2);
             read_row(ring[(y + 1) & (kRing2 - 1)], lane, C);
             // ---- lookup of (y, x): bit i of the mask is stencil offset n = i (i < 4) or
             // i + 1 (i >= 4); offsets before the centre in linear order precede on ties
@@ -852,26 +858,22 @@ __global__ void __launch_bounds__(kW2 * 32) k_prune2d(ItemTable tab, Outs o) {
             or_if_precedes<1u << 6, false>(raw, C.c, cv);
             or_if_precedes<1u << 7, false>(raw, C.r, cv);
             const uint2 e = sm.lut[raw];
-            const bool owned = owned_x && y < y1;
+            const bool owned = owned_x && (kIn || y < y1);
             const uint32_t ord = ord_bits(cv);
             const uint32_t vl = uint32_t(y) * W + uint32_t(x);
             const uint32_t vg = voff + vl;
             const uint32_t direct = e.x & 7u;
-            bool root0 = false;
-            if (owned) {
-                if (!(fabsf(cv) <= 3.40282347e38f)) set_status(o.ctr, kStNonfinite);
-                if (direct == 7u) {
-                    root0 = true;
-                    far = vg;
-                    const unsigned long long k = (unsigned long long)(uint64_t(ord) << 32 | vl);
-                    my_min = k < my_min ? k : my_min;
-                } else {
-                    // face slots: up, left, right, down
-                    const uint32_t mag = (direct == 0u || direct == 3u) ? W : 1u;
-                    const uint32_t u = direct < 2u ? vg - mag : vg + mag;
-                    far = (direct == 0u && y > y0) ? far : u;
-                    if (CP_IN(vg, o.n_uf0, o.ctr)) o.uf0[vg] = far;
-                }
+            // H0: a local minimum becomes a root (registered in the staging block
+            // below); otherwise the link along the first edge (face slots: up,
+            // left, right, down), where a link up continues the chain that this
+            // lane started one row before
+            const bool root0 = owned && direct == 7u;
+            nonfinite |= owned && !(fabsf(cv) <= 3.40282347e38f);
+            {
+                const uint32_t mag = (direct == 0u || direct == 3u) ? W : 1u;
+                const uint32_t u = direct < 2u ? vg - mag : vg + mag;
+                if (owned) far = root0 ? vg : ((direct == 0u && (kIn || y > y0)) ? far : u);
+                if (owned && !root0 && CP_IN(vg, o.n_uf0, o.ctr)) o.uf0[vg] = far;
             }
             const uint32_t h0s = owned ? (e.x >> 3) & 0xFu : 0u;
             const uint32_t ds = owned ? (e.x >> 9) & 0xFu : 0u;
@@ -881,48 +883,40 @@ __global__ void __launch_bounds__(kW2 * 32) k_prune2d(ItemTable tab, Outs o) {
             // cycle there: a no-op)
             const uint32_t flg = tab.cross2d ? ds : 0u;
             const uint32_t dn = tab.cross2d ? ds & ~h0s : ds;
-            // ---- the top cell with smallest corner (y-1, x)
+            // ---- the top cell with smallest corner (y-1, x): its largest corner m
+            // (value, then linear index) holds it; m's code field for it says where
+            // it dies locally (8: a dual root, registered in the staging block
+            // below; 15: not held, non-finite input only)
             const uint32_t cprev_r = __shfl_down_sync(0xFFFFFFFFu, cprev, 1);
             const uint32_t ccur_r = __shfl_down_sync(0xFFFFFFFFu, e.y, 1);
-            bool rootT = false;
-            uint32_t rt_node = 0;
-            uint64_t rt_age = 0;
-            if (cube_x && y > y0) {
-                // largest of the 4 corners under (value, linear index), in index order
-                const float cvals[4] = {A.c, A.r, B.c, B.r};
-                int k = 0;
-                float best = cvals[0];
+            const bool cube = cube_x && (kIn || y > y0);
+            const float cvals[4] = {A.c, A.r, B.c, B.r};
+            int k = 0;
+            float best = cvals[0];
 #pragma unroll
-                for (int j = 1; j < 4; ++j) {
-                    const bool ge = cvals[j] >= best;
-                    best = ge ? cvals[j] : best;
-                    k = ge ? j : k;
-                }
-                const uint32_t word = k == 0 ? cprev : (k == 1 ? cprev_r : (k == 2 ? e.y : ccur_r));
-                const uint32_t t = uint32_t(3 - k);  // quadrant of the top cell as seen from m
-                const uint32_t code = (word >> (4u * t)) & 15u;
-                const uint32_t self = toff + uint32_t(y - 1) * W1 + uint32_t(x);
+            for (int j = 1; j < 4; ++j) {
+                const bool ge = cvals[j] >= best;
+                best = ge ? cvals[j] : best;
+                k = ge ? j : k;
+            }
+            const uint32_t word = k == 0 ? cprev : (k == 1 ? cprev_r : (k == 2 ? e.y : ccur_r));
+            const uint32_t t = uint32_t(3 - k);  // quadrant of the top cell as seen from m
+            const uint32_t code = (word >> (4u * t)) & 15u;
+            const uint32_t self = toff + uint32_t(y - 1) * W1 + uint32_t(x);
+            const bool rootT = cube && code == 8u;
+            {
+                // the top cell across: quadrant `code` of m, smallest corner m - (negative axes)
                 const int my = y - 1 + (k >> 1), mx = x + (k & 1);
-                if (code == 8u) {
-                    rootT = true;
-                    rt_node = self;
-                    far_t = self;
-                    const uint32_t mg = voff + uint32_t(my) * W + uint32_t(mx);
-                    rt_age = make_key(ord_bits(best), mg, (6u * (t >> 1) + 2u * (t & 1u)) << 1);
-                } else if (code < 4u) {
-                    // the top cell across: quadrant `code` of m, smallest corner m - (negative axes)
-                    const int ty = my - int(((code >> 1) & 1u) ^ 1u);
-                    const int tx = mx - int((code & 1u) ^ 1u);
-                    const bool out = unsigned(ty) >= H - 1u || unsigned(tx) >= W1;
-                    // a link to (y-2, x) continues the chain that this lane wrote for that top
-                    // cell in the previous step
-                    const bool chain = ty == y - 2 && tx == x && y - 1 > y0;
-                    far_t = chain ? far_t : (out ? OUT : toff + uint32_t(ty) * W1 + uint32_t(tx));
-                    if (CP_IN(self, o.n_uft, o.ctr)) o.uft[self] = far_t;
-                } else {
-                    far_t = kTag;
-                    if (CP_IN(self, o.n_uft, o.ctr)) o.uft[self] = kTag;  // only reachable with non-finite input (flagged): keep the forest well formed
-                }
+                const int ty = my - int(((code >> 1) & 1u) ^ 1u);
+                const int tx = mx - int((code & 1u) ^ 1u);
+                const bool out = unsigned(ty) >= H - 1u || unsigned(tx) >= W1;
+                // a link to (y-2, x) continues the chain that this lane wrote for that top
+                // cell in the previous step; a code of 15 writes a root tag to keep the
+                // forest well formed
+                const bool chain = ty == y - 2 && tx == x && (kIn || y - 1 > y0);
+                const uint32_t tgt = code < 4u ? (out ? OUT : toff + uint32_t(ty) * W1 + uint32_t(tx)) : kTag;
+                if (cube) far_t = rootT ? self : ((code < 4u && chain) ? far_t : tgt);
+                if (cube && !rootT && CP_IN(self, o.n_uft, o.ctr)) o.uft[self] = far_t;
             }
             cprev = e.y;
             // ---- stage survivors and roots
@@ -941,14 +935,18 @@ __global__ void __launch_bounds__(kW2 * 32) k_prune2d(ItemTable tab, Outs o) {
                         const uint32_t p = cnt.r0 + __popc(m_r0 & lt);
                         ws.r0node[p] = vg;
                         ws.r0age[p] = make_key(ord, vg, 0);
+                        const unsigned long long kk = (unsigned long long)(uint64_t(ord) << 32 | vl);
+                        my_min = kk < my_min ? kk : my_min;
                     }
                     cnt.r0 += __popc(m_r0);
                 }
                 if (m_rt) {
                     if (rootT) {
+                        const uint32_t my = uint32_t(y - 1 + (k >> 1)), mx = uint32_t(x + (k & 1));
+                        const uint32_t mg = voff + my * W + mx;
                         const uint32_t p = cnt.rt + __popc(m_rt & lt);
-                        ws.rtnode[p] = rt_node;
-                        ws.rtage[p] = rt_age;
+                        ws.rtnode[p] = self;
+                        ws.rtage[p] = make_key(ord_bits(best), mg, (6u * (t >> 1) + 2u * (t & 1u)) << 1);
                     }
                     cnt.rt += __popc(m_rt);
                 }
@@ -977,7 +975,14 @@ __global__ void __launch_bounds__(kW2 * 32) k_prune2d(ItemTable tab, Outs o) {
             __syncwarp();
             A = B;
             B = C;
-        }
+        };
+        // the first two rows and the last few take every check; the interior rows
+        // are a second instantiation of the step without them
+        int y = y0;
+        for (; y <= ylast && y < y0 + 2; ++y) step(y, std::false_type());
+        for (; y + kAhead2 <= ylast; ++y) step(y, std::true_type());
+        for (; y <= ylast; ++y) step(y, std::false_type());
+        if (__any_sync(0xFFFFFFFFu, nonfinite) && lane == 0) set_status(o.ctr, kStNonfinite);
         cp_async_wait<0>();
         const unsigned long long w = warp_min_u64(my_min);
         if (lane == 0 && w != ~0ull) atomicMin(&o.ctr->gmin[ii], w);
