@@ -96,17 +96,23 @@ __device__ __forceinline__ uint32_t hash_slot3(uint32_t rel, const uint16_t* dis
 // needed, but whose outputs belong to the neighbouring CTA.
 //
 // Per plane step z:
-//  1. cp.async prefetch of image plane z+kAhead (34 x 11 floats: the CTA's
-//     vertices and a one-vertex border) into an 8-slot shared-memory ring;
+//  1. one thread issues the TMA copy of image plane z+kAhead (a 40 x 11 box:
+//     the CTA's vertices and a one-vertex border) into an 8-slot shared ring
+//     (items without a tensor map: every thread's cp.async copies);
 //  2. the 26-neighbour mask of (z, y, x) from registers (planes z-1, z) and
-//     the ring (plane z+1), table lookup, the H0 forest link and the
-//     survivors and H0 root of owned vertices; the entry's dual codes go to
-//     a 3-plane shared ring;
+//     the ring (plane z+1), built in the lattice layout of cp_mask3.cuh and
+//     collapsed there, the perfect-hash lookup, the H0 forest link and the
+//     survivor bits of owned vertices; the entry's code fields for the top
+//     cells above and below the vertex go to a 3-slot column-word ring;
 //  3. one barrier;
-//  4. the top cell whose smallest corner is (z-1, y, x): its largest corner
-//     m among the 8 corner values (in registers) holds, in its lookup entry,
-//     where this top cell dies locally; one coalesced store of its dual
-//     forest link (or it becomes a dual root).
+//  4. the top cell whose smallest corner is (z-1, y, x): of its 8 corners
+//     exactly the largest holds it, so the OR of the 4 columns' words has
+//     one field set, which gives the top cell across the facet where it
+//     dies locally (or marks it a dual root); one coalesced store of its
+//     dual forest link.
+// The first three and the last few steps of a task take every boundary
+// check; the interior steps are a second instantiation of the step without
+// them.
 // Survivors and roots are staged per warp with ballots and flushed with one
 // atomic per buffer when a buffer would overflow and at the end.
 constexpr int kW3 = 9;                     // warps per CTA
@@ -147,7 +153,7 @@ struct Smem3 {
     int tma_xs, tma_ys;
     // the current task's constants, read where used (fewer live registers)
     uint32_t t_HW, t_HW1, t_OUT;
-    int t_z0, t_z1, t_D, t_zneed;
+    int t_z0, t_z1;
     int2 tlink[8 * 16];        // dual links by (t, v), for the current item
     int32_t h0link[64];        // H0 link offset by the face bits of the mask (their lowest: z-, y-, x-, x+, y+, z+), for the current item
     uint16_t disp[1 << 12];    // displacement table of the 3D perfect hash
@@ -491,8 +497,6 @@ __device__ __forceinline__ void prune_task3d(Smem3& sm, const ItemTable& tab, co
         sm.t_OUT = cc.OUT;
         sm.t_z0 = z0;
         sm.t_z1 = z1;
-        sm.t_D = it.D;
-        sm.t_zneed = zlast + 1;
     }
     __syncthreads();  // the task constants are read from here on
     sm.tmin[threadIdx.x] = ~0ull;
@@ -528,9 +532,8 @@ __device__ __forceinline__ void prune_task3d(Smem3& sm, const ItemTable& tab, co
     read_nbr(sm.ring[(z0 - 1 + kRing) & (kRing - 1)] + xo, warp, lane, A);
     wait_plane<kTma, true>(sm, it, z0, par, o.ctr);
     read_nbr(sm.ring[z0 & (kRing - 1)] + xo, warp, lane, B);
-    // One plane step: P (plane z-1) and Q (plane z) in registers, R gets plane
-    // z+1.  The loop below rotates the three register planes and the three
-    // column-word slots, so nothing is copied.
+    // One plane step: A (plane z-1) and B (plane z) in registers, C receives
+    // plane z+1.
     // interior: a std::integral_constant; true for a step with z >= z0 + 2 and
     // z + kAhead <= zlast, where no boundary plane or end-of-task case arises
     auto step = [&](const Nbr& A, const Nbr& B, Nbr& C, const int z, const int qs, auto interior) {
